@@ -1,0 +1,389 @@
+/*
+ * FP64 CPU oracle for the flat-window voting sparse FFT.  TEST INFRASTRUCTURE
+ * ONLY: see sfft_oracle.h.  Plain C99, single-threaded, no blocking or fusion
+ * beyond what each step's definition states.
+ */
+#include "sfft_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ---------------------------------------------------------------- Philox */
+/* Philox4x64 round function and key schedule as published by Salmon, Moraes,
+   Dror and Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
+   two 64x64->128 multiplies per round, outputs permuted and xored with the
+   round key, key bumped by the Weyl constants between rounds. */
+static void philox_mulhilo(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void oracle_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t hi0, lo0, hi1, lo1;
+        philox_mulhilo(M0, x0, &hi0, &lo0);
+        philox_mulhilo(M1, x2, &hi1, &lo1);
+        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------ arithmetic */
+static int is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int64_t mod_pos(int64_t a, int64_t n)
+{
+    int64_t r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+int64_t oracle_modinv(int64_t a, int64_t N)
+{
+    /* extended Euclid on (a, N) */
+    int64_t r0 = N, r1 = mod_pos(a, N), s0 = 0, s1 = 1;
+    while (r1 != 0) {
+        int64_t q = r0 / r1, t;
+        t = r0 - q * r1; r0 = r1; r1 = t;
+        t = s0 - q * s1; s0 = s1; s1 = t;
+    }
+    if (r0 != 1) return -1; /* not invertible */
+    return mod_pos(s0, N);
+}
+
+/* ------------------------------------------------------- a0: parameters */
+/* Random odd scaling sigma ("Scaling method") and shift tau (Eq. 6-7). */
+int oracle_loop_params(int64_t N, int L, uint64_t seed, int64_t *sigma, int64_t *tau,
+                       int64_t *sigma_inv)
+{
+    if (!is_pow2(N) || N < 2) return -1;
+    for (int l = 0; l < L; ++l) {
+        uint64_t ctr[4] = {(uint64_t)l, 0, 0, 0}, key[2] = {seed, 0}, out[4];
+        oracle_philox4x64_10(ctr, key, out);
+        int64_t s = 2 * (int64_t)(out[0] % (uint64_t)(N / 2)) + 1;
+        sigma[l] = s;
+        tau[l] = (int64_t)(out[1] % (uint64_t)N);
+        if (sigma_inv) sigma_inv[l] = oracle_modinv(s, N);
+    }
+    return 0;
+}
+
+/* --------------------------------------------------- a0': flat window */
+/* Eq. 12 (sinc of width B, centre value 1/B) times Eq. 13 (Gaussian with
+   sigma_g = B sqrt(log2 N)), both centred at Omega/2 = w/2. */
+void oracle_window_taps(int64_t N, int64_t B, int64_t w, double *g)
+{
+    double sg = (double)B * sqrt(log2((double)N));
+    for (int64_t q = 0; q < w; ++q) {
+        int64_t m = q - w / 2;
+        double sinc = (m == 0) ? 1.0 / (double)B
+                               : sin(M_PI * (double)m / (double)B) / (M_PI * (double)m);
+        double t = (double)m / sg;
+        g[q] = sinc * exp(-0.5 * t * t);
+    }
+}
+
+/* exp(+2 pi i r / N) with the integer r reduced first (exact argument) */
+static double complex unit_root(int64_t r, int64_t N)
+{
+    double a = 2.0 * M_PI * (double)mod_pos(r, N) / (double)N;
+    return cos(a) + I * sin(a);
+}
+
+void oracle_filter_gain_at(int64_t N, int64_t w, const double *g, int64_t o, double out[2])
+{
+    double complex s = 0;
+    for (int64_t q = 0; q < w; ++q) {
+        int64_t m = q - w / 2;
+        s += g[q] * unit_root(mod_pos(m * o, N), N);
+    }
+    out[0] = creal(s);
+    out[1] = cimag(s);
+}
+
+void oracle_filter_gain(int64_t N, int64_t B, int64_t w, const double *g, double *Gt)
+{
+    int64_t NB = N / B, half = NB / 2;
+    for (int64_t i = 0; i < NB; ++i) oracle_filter_gain_at(N, w, g, i - half, Gt + 2 * i);
+}
+
+/* ----------------------------------------------------------- a4: hash */
+/* Bucket of frequency f after scaling: round-half-up of (sigma f mod N)/(N/B),
+   the rule of the worked example (bucket 1 = round(64/128)). */
+void oracle_hash(int64_t N, int64_t B, int64_t sigma, int64_t f, int64_t *h, int64_t *o)
+{
+    int64_t NB = N / B, half = NB / 2;
+    int64_t p = mod_pos(sigma * f, N);
+    int64_t hh = (p + half) / NB; /* in [0, B] */
+    *o = p - hh * NB;             /* in [-half, NB - half) */
+    *h = hh % B;
+}
+
+void oracle_permute(int64_t N, int64_t sigma, int64_t tau, const double *x, double *out)
+{
+    for (int64_t m = 0; m < N; ++m) {
+        int64_t i = mod_pos(sigma * m + tau, N);
+        out[2 * m] = x[2 * i];
+        out[2 * m + 1] = x[2 * i + 1];
+    }
+}
+
+/* ------------------------------------------------------ a1 + a2 */
+void oracle_bucketize(int64_t N, int64_t B, int64_t w, int L, const int64_t *sigma,
+                      const int64_t *tau, const double *g, const double *x, double *z,
+                      double *zhat)
+{
+    double complex *zl = (double complex *)malloc(sizeof(double complex) * (size_t)B);
+    double complex *wB = (double complex *)malloc(sizeof(double complex) * (size_t)B);
+    for (int64_t t = 0; t < B; ++t) {
+        double a = -2.0 * M_PI * (double)t / (double)B;
+        wB[t] = cos(a) + I * sin(a); /* omega_B^t */
+    }
+    for (int l = 0; l < L; ++l) {
+        for (int64_t j = 0; j < B; ++j) zl[j] = 0;
+        /* multiply by the window and fold (Eq. 11) the permuted signal */
+        for (int64_t q = 0; q < w; ++q) {
+            int64_t m = q - w / 2;
+            int64_t i = mod_pos(sigma[l] * m + tau[l], N);
+            int64_t j = mod_pos(m, B);
+            zl[j] += g[q] * (x[2 * i] + I * x[2 * i + 1]);
+        }
+        if (z) {
+            for (int64_t j = 0; j < B; ++j) {
+                z[2 * (l * B + j)] = creal(zl[j]);
+                z[2 * (l * B + j) + 1] = cimag(zl[j]);
+            }
+        }
+        /* B-point DFT, unnormalised */
+        for (int64_t k = 0; k < B; ++k) {
+            double complex s = 0;
+            for (int64_t j = 0; j < B; ++j) s += zl[j] * wB[(j * k) % B];
+            zhat[2 * (l * B + k)] = creal(s);
+            zhat[2 * (l * B + k) + 1] = cimag(s);
+        }
+    }
+    free(zl);
+    free(wB);
+}
+
+/* ---------------------------------------------------------- a3: select */
+typedef struct {
+    float key;
+    int64_t id;  /* tie-break: smaller id ranks first */
+    int64_t pos; /* where the entry came from */
+} keyed;
+
+/* larger key first, then smaller id */
+static int keyed_cmp(const void *a, const void *b)
+{
+    const keyed *x = (const keyed *)a, *y = (const keyed *)b;
+    if (x->key > y->key) return -1;
+    if (x->key < y->key) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+int64_t oracle_select(int64_t B, int64_t cK, const double *zhat_loop, int32_t *sel)
+{
+    keyed *k = (keyed *)malloc(sizeof(keyed) * (size_t)B);
+    for (int64_t j = 0; j < B; ++j) {
+        double re = zhat_loop[2 * j], im = zhat_loop[2 * j + 1];
+        k[j].key = (float)(re * re + im * im);
+        k[j].id = j;
+        k[j].pos = j;
+    }
+    qsort(k, (size_t)B, sizeof(keyed), keyed_cmp);
+    int64_t n = cK < B ? cK : B;
+    for (int64_t s = 0; s < n; ++s) sel[s] = (int32_t)k[s].id;
+    free(k);
+    return n;
+}
+
+/* ------------------------------------------------------ a4 + a5: vote */
+/* Every frequency hashed (via sigma^-1) into one of the selected buckets of a
+   loop receives one vote; candidates are those with at least T votes. */
+int64_t oracle_vote(int64_t N, int64_t B, int L, int64_t nsel, int T, const int64_t *sigma_inv,
+                    const int32_t *sel, int32_t *score, int32_t *cand)
+{
+    int64_t NB = N / B, half = NB / 2;
+    int32_t *sc = score ? score : (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    memset(sc, 0, sizeof(int32_t) * (size_t)N);
+    for (int l = 0; l < L; ++l) {
+        for (int64_t s = 0; s < nsel; ++s) {
+            int64_t j = sel[l * nsel + s];
+            for (int64_t o = -half; o < NB - half; ++o) {
+                int64_t p = mod_pos(j * NB + o, N);
+                int64_t f = mod_pos(sigma_inv[l] * p, N);
+                sc[f] += 1;
+            }
+        }
+    }
+    int64_t n = 0;
+    for (int64_t f = 0; f < N; ++f)
+        if (sc[f] >= T) cand[n++] = (int32_t)f;
+    if (!score) free(sc);
+    return n;
+}
+
+/* ------------------------------------------------------ a6: estimate */
+static int dbl_cmp(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+static double median_of(double *v, int n)
+{
+    qsort(v, (size_t)n, sizeof(double), dbl_cmp);
+    if (n % 2) return v[n / 2];
+    return 0.5 * (v[n / 2 - 1] + v[n / 2]);
+}
+
+void oracle_estimate(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau,
+                     const double *Gt, const double *zhat, int64_t ncand, const int32_t *cand,
+                     double *est, double *per_loop)
+{
+    int64_t half = (N / B) / 2;
+    double *re = (double *)malloc(sizeof(double) * (size_t)L);
+    double *im = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int64_t c = 0; c < ncand; ++c) {
+        int64_t f = cand[c];
+        for (int l = 0; l < L; ++l) {
+            int64_t h, o;
+            oracle_hash(N, B, sigma[l], f, &h, &o);
+            double complex zb = zhat[2 * (l * B + h)] + I * zhat[2 * (l * B + h) + 1];
+            double complex G = Gt[2 * (o + half)] + I * Gt[2 * (o + half) + 1];
+            /* undo the time-shift phase exp(+2 pi i tau f / N) and the
+               filter's gain at offset o */
+            double complex v = zb * unit_root(-(tau[l] * f), N) / G;
+            re[l] = creal(v);
+            im[l] = cimag(v);
+            if (per_loop) {
+                per_loop[2 * (c * L + l)] = re[l];
+                per_loop[2 * (c * L + l) + 1] = im[l];
+            }
+        }
+        est[2 * c] = median_of(re, L);
+        est[2 * c + 1] = median_of(im, L);
+    }
+    free(re);
+    free(im);
+}
+
+/* --------------------------------------------------------- a7: top-K */
+int64_t oracle_topk(int64_t ncand, const int32_t *cand, const double *est, int64_t K,
+                    int32_t *idx, double *val)
+{
+    keyed *k = (keyed *)malloc(sizeof(keyed) * (size_t)(ncand > 0 ? ncand : 1));
+    for (int64_t c = 0; c < ncand; ++c) {
+        double re = est[2 * c], im = est[2 * c + 1];
+        k[c].key = (float)(re * re + im * im);
+        k[c].id = cand[c];
+        k[c].pos = c;
+    }
+    qsort(k, (size_t)ncand, sizeof(keyed), keyed_cmp);
+    int64_t n = K < ncand ? K : ncand;
+    /* the n winners, back in increasing f */
+    keyed *win = (keyed *)malloc(sizeof(keyed) * (size_t)(n > 0 ? n : 1));
+    for (int64_t s = 0; s < n; ++s) {
+        win[s] = k[s];
+        win[s].key = 0.0f; /* equal keys: the comparator falls back to id = f */
+    }
+    qsort(win, (size_t)n, sizeof(keyed), keyed_cmp);
+    for (int64_t s = 0; s < n; ++s) {
+        idx[s] = (int32_t)win[s].id;
+        val[2 * s] = est[2 * win[s].pos];
+        val[2 * s + 1] = est[2 * win[s].pos + 1];
+    }
+    free(win);
+    free(k);
+    return n;
+}
+
+/* ---------------------------------------------------- sampling ratio */
+int64_t oracle_samples_touched(int64_t N, int64_t w, int L, const int64_t *sigma,
+                               const int64_t *tau)
+{
+    unsigned char *seen = (unsigned char *)calloc((size_t)N, 1);
+    int64_t n = 0;
+    for (int l = 0; l < L; ++l)
+        for (int64_t q = 0; q < w; ++q) {
+            int64_t i = mod_pos(sigma[l] * (q - w / 2) + tau[l], N);
+            if (!seen[i]) {
+                seen[i] = 1;
+                ++n;
+            }
+        }
+    free(seen);
+    return n;
+}
+
+/* ------------------------------------------------------------- Eq. 2 */
+void oracle_dft(int64_t N, const double *x, double *xhat)
+{
+    for (int64_t i = 0; i < N; ++i) {
+        double complex s = 0;
+        for (int64_t j = 0; j < N; ++j)
+            s += (x[2 * j] + I * x[2 * j + 1]) * unit_root(-mod_pos(i * j, N), N);
+        s /= (double)N;
+        xhat[2 * i] = creal(s);
+        xhat[2 * i + 1] = cimag(s);
+    }
+}
+
+/* --------------------------------------------------------- pipeline */
+int64_t oracle_sfft(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T,
+                    uint64_t seed, const double *g, const double *Gt, const double *x,
+                    int32_t *idx, double *val, double *zhat_out, int32_t *sel_out,
+                    int32_t *cand_out, double *est_out, int64_t *ncand_out)
+{
+    if (!is_pow2(N) || N < 2 || !is_pow2(B) || B > N || w < B || w > N || w % B || L < 1 ||
+        K < 1 || c < 1 || T < 1 || T > L)
+        return -1;
+    int64_t *sigma = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
+    int64_t *tau = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
+    int64_t *sinv = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
+    oracle_loop_params(N, L, seed, sigma, tau, sinv);
+
+    double *zhat = zhat_out ? zhat_out : (double *)malloc(sizeof(double) * 2 * (size_t)(L * B));
+    oracle_bucketize(N, B, w, L, sigma, tau, g, x, NULL, zhat);
+
+    int64_t cK = (int64_t)c * K;
+    int64_t nsel = cK < B ? cK : B;
+    int32_t *sel = sel_out ? sel_out : (int32_t *)malloc(sizeof(int32_t) * (size_t)(L * nsel));
+    for (int l = 0; l < L; ++l) oracle_select(B, cK, zhat + 2 * l * B, sel + l * nsel);
+
+    int32_t *cand = cand_out ? cand_out : (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int64_t ncand = oracle_vote(N, B, L, nsel, T, sinv, sel, NULL, cand);
+
+    double *est = est_out ? est_out : (double *)malloc(sizeof(double) * 2 * (size_t)(ncand ? ncand : 1));
+    oracle_estimate(N, B, L, sigma, tau, Gt, zhat, ncand, cand, est, NULL);
+
+    int64_t kout = oracle_topk(ncand, cand, est, K, idx, val);
+    if (ncand_out) *ncand_out = ncand;
+
+    if (!est_out) free(est);
+    if (!cand_out) free(cand);
+    if (!sel_out) free(sel);
+    if (!zhat_out) free(zhat);
+    free(sigma);
+    free(tau);
+    free(sinv);
+    return kout;
+}

@@ -1,0 +1,112 @@
+/*
+ * FP64 CPU oracle for the flat-window voting sparse FFT (sFFT1.0-style).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may include, link or
+ * call this code: only the tests, the package smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header, table or constant with
+ * the CUDA implementation.
+ *
+ * Every routine is a plain, slow restatement of one step of the method, in the
+ * order the paper describes it ("Empirical Evaluation of Typical Sparse Fast
+ * Fourier Transform Algorithms", arXiv:2012.08238):
+ *   Eq. 2          forward DFT with the 1/N factor (oracle_dft)
+ *   Eq. 6-7        time shift / time scaling -> the permuted gather
+ *   Eq. 11         time-domain aliasing (fold into B buckets)
+ *   Eq. 12-13      flat window = sinc x Gaussian (oracle_window_taps)
+ *   Eq. 14         flat-filter bucket composition, rounding rule of the
+ *                  worked example (oracle_hash)
+ *   "Method of probability and statistics": top-2K buckets + voting
+ *   "Energy concentration method": per-loop estimate, combined by median
+ *   "Scaling method": random odd sigma
+ *   Table 2        sampling complexity (oracle_samples_touched)
+ *
+ * Conventions.  Complex arrays are interleaved (re, im) doubles.  Window index
+ * q in [0, w) stands for window position m = q - w/2.  Loop parameters are
+ * sigma (odd), tau, and sigma^-1 mod N.  All indices are int64.
+ */
+#ifndef SFFT_ORACLE_H
+#define SFFT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x64-10 block (Salmon et al., SC'11): 4x64-bit counter, 2x64 key. */
+void oracle_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+
+/* Per-loop parameters: block = Philox(ctr=(l,0,0,0), key=(seed,0));
+   sigma_l = 2*(out0 mod N/2) + 1, tau_l = out1 mod N, sigma_inv_l by the
+   extended Euclidean algorithm.  Returns 0, or -1 if N is not a power of two
+   >= 2. */
+int oracle_loop_params(int64_t N, int L, uint64_t seed, int64_t *sigma, int64_t *tau,
+                       int64_t *sigma_inv);
+
+/* Multiplicative inverse of odd a modulo N (power of two), extended Euclid. */
+int64_t oracle_modinv(int64_t a, int64_t N);
+
+/* Eq. 12 x Eq. 13 taps g[q], q in [0,w). */
+void oracle_window_taps(int64_t N, int64_t B, int64_t w, double *g);
+
+/* Flat-filter gain G~(o) = sum_m g(m) exp(+2 pi i m o / N) for one offset o. */
+void oracle_filter_gain_at(int64_t N, int64_t w, const double *g, int64_t o, double out[2]);
+
+/* All N/B gains, o in [-N/2B, N/2B) stored at index o + N/2B. */
+void oracle_filter_gain(int64_t N, int64_t B, int64_t w, const double *g, double *Gt);
+
+/* Flat-filter hash (Eq. 14 rounding): p = sigma f mod N,
+   h = round_half_up(p B / N) mod B, o = p - round_half_up(p B / N) * N/B. */
+void oracle_hash(int64_t N, int64_t B, int64_t sigma, int64_t f, int64_t *h, int64_t *o);
+
+/* out[m'] = x[(sigma m' + tau) mod N] for m' in [0, N): Eq. 6-7 composed. */
+void oracle_permute(int64_t N, int64_t sigma, int64_t tau, const double *x, double *out);
+
+/* Steps a1+a2: z[l][j] (fold of the windowed permuted signal, Eq. 11) and
+   zhat[l][k] = sum_j z[l][j] exp(-2 pi i j k / B).  z may be NULL. */
+void oracle_bucketize(int64_t N, int64_t B, int64_t w, int L, const int64_t *sigma,
+                      const int64_t *tau, const double *g, const double *x, double *z,
+                      double *zhat);
+
+/* Step a3: the cK buckets of one loop with largest |zhat|^2 (key rounded to
+   binary32), ties to the lower bucket.  Writes min(cK, B) indices in rank
+   order and returns that count. */
+int64_t oracle_select(int64_t B, int64_t cK, const double *zhat_loop, int32_t *sel);
+
+/* Steps a4+a5: explicit score[N] histogram of hashed-back votes; writes the
+   candidates {f : score >= T} in increasing f and returns their count.
+   sel is [L][nsel]. score may be NULL (then allocated internally). */
+int64_t oracle_vote(int64_t N, int64_t B, int L, int64_t nsel, int T, const int64_t *sigma_inv,
+                    const int32_t *sel, int32_t *score, int32_t *cand);
+
+/* Step a6: v_l(f) = zhat_l[h_l(f)] exp(-2 pi i tau_l f / N) / G~(o_l(f)),
+   combined by coordinate-wise median (even L: mean of the two middle values).
+   per_loop ([ncand][L] complex) may be NULL. */
+void oracle_estimate(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau,
+                     const double *Gt, const double *zhat, int64_t ncand, const int32_t *cand,
+                     double *est, double *per_loop);
+
+/* Step a7: the K candidates with largest |est|^2 (key rounded to binary32),
+   ties to the lower f, returned sorted by f.  Returns min(K, ncand). */
+int64_t oracle_topk(int64_t ncand, const int32_t *cand, const double *est, int64_t K,
+                    int32_t *idx, double *val);
+
+/* Distinct sample indices touched by all L loops (Table 2 sampling). */
+int64_t oracle_samples_touched(int64_t N, int64_t w, int L, const int64_t *sigma,
+                               const int64_t *tau);
+
+/* Eq. 2: xhat_i = (1/N) sum_j x_j exp(-2 pi i i j / N), O(N^2). */
+void oracle_dft(int64_t N, const double *x, double *xhat);
+
+/* Whole pipeline a0..a7 for one signal.  g (w taps) and Gt (N/B gains) come
+   from oracle_window_taps / oracle_filter_gain.  Intermediates may be NULL:
+   zhat [L][B] complex, sel [L][min(cK,B)], cand/est (capacity N).
+   Returns k_out = min(K, |I|), or -1 on invalid parameters. */
+int64_t oracle_sfft(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T,
+                    uint64_t seed, const double *g, const double *Gt, const double *x,
+                    int32_t *idx, double *val, double *zhat_out, int32_t *sel_out,
+                    int32_t *cand_out, double *est_out, int64_t *ncand_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,75 @@
+"""The oracle's pins catch plausible mistakes (CPU only).
+
+Each case plants one mistake in a temporary copy of the oracle's C source
+(a dropped term, a flipped sign, a wrong rounding, a shifted index, a swapped
+operand), builds it, and runs the pin suite against it: at least one pin must
+fail.  The committed oracle is never modified.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "sfft_oracle.c")
+
+# (name, original text, mutated text)
+MUTANTS = [
+    ("phase sign", "unit_root(-(tau[l] * f), N)", "unit_root((tau[l] * f), N)"),
+    ("gain dropped", "unit_root(-(tau[l] * f), N) / G;", "unit_root(-(tau[l] * f), N);"),
+    ("hash floors", "int64_t hh = (p + half) / NB;", "int64_t hh = p / NB;"),
+    ("dft sign", "double a = -2.0 * M_PI * (double)t / (double)B;",
+     "double a = 2.0 * M_PI * (double)t / (double)B;"),
+    ("sinc centre", "(m == 0) ? 1.0 / (double)B", "(m == 0) ? 1.0"),
+    ("gaussian width", "(double)B * sqrt(log2((double)N))", "(double)B * log2((double)N)"),
+    ("fold index", "int64_t j = mod_pos(m, B);", "int64_t j = mod_pos(q, B);"),
+    ("gather shift sign", "mod_pos(sigma[l] * m + tau[l], N);\n            int64_t j",
+     "mod_pos(sigma[l] * m - tau[l], N);\n            int64_t j"),
+    ("vote without inverse", "int64_t f = mod_pos(sigma_inv[l] * p, N);", "int64_t f = p;"),
+    ("even median", "return 0.5 * (v[n / 2 - 1] + v[n / 2]);", "return v[n / 2];"),
+    ("tie order", "return (x->id > y->id) - (x->id < y->id);", "return (x->id < y->id) - (x->id > y->id);"),
+    ("philox multiplier", "M1 = 0xCA5A826395121157ULL", "M1 = 0xCA5A826395121159ULL"),
+    ("sigma parity", "int64_t s = 2 * (int64_t)(out[0] % (uint64_t)(N / 2)) + 1;",
+     "int64_t s = (int64_t)(out[0] % (uint64_t)N) | 1;"),
+    ("threshold off by one", "if (sc[f] >= T) cand[n++]", "if (sc[f] > T) cand[n++]"),
+]
+
+PIN_CHECKS = [
+    pins.test_philox_known_answer,
+    lambda: pins.test_loop_params_stream_and_inverse(1 << 16),
+    pins.test_flat_bucket_worked_example,
+    pins.test_scaling_worked_example,
+    pins.test_gaussian_width_example,
+    lambda: pins.test_window_taps_shape(1 << 12, 16),
+    lambda: pins.test_filter_gain_against_fft(1 << 12, 16),
+    pins.test_hash_rounding_brute_force,
+    lambda: pins.test_bucketize_closed_form(1 << 10, 16, 3),
+    pins.test_select_brute_force_with_ties,
+    lambda: pins.test_vote_brute_force(1 << 10, 16, 6, 5, 3),
+    lambda: pins.test_estimate_exact_for_one_sparse(1 << 12, 16, 5),
+    pins.test_median_combination,
+    pins.test_topk_brute_force,
+    pins.test_exact_recovery_noiseless,
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name!r} not unique"
+    mut = tmp_path / "sfft_oracle.c"
+    mut.write_text(src.replace(old, new))
+    hdr = os.path.join(os.path.dirname(SRC), "sfft_oracle.h")
+    (tmp_path / "sfft_oracle.h").write_text(open(hdr).read())
+    so = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-o", str(so), str(mut), "-lm"])
+    failed = []
+    with oracle.use_library(str(so)):
+        for check in PIN_CHECKS:
+            try:
+                check()
+            except (AssertionError, ValueError, IndexError):
+                failed.append(getattr(check, "__name__", "lambda"))
+    assert failed, f"no pin caught the planted mistake {name!r}"
