@@ -1,0 +1,218 @@
+/*
+ * sfft.h -- C ABI of the GB300-native flat-window voting sparse FFT.
+ *
+ * The library computes, for a length-N complex signal x whose spectrum is
+ * (approximately) K-sparse, the K largest Fourier coefficients
+ *
+ *     xhat_f = (1/N) sum_j x_j exp(-2 pi i f j / N)          (Eq. 2)
+ *
+ * with the voting framework of sFFT1.0 as surveyed in "Empirical Evaluation of
+ * Typical Sparse Fast Fourier Transform Algorithms" (arXiv:2012.08238).  Per
+ * location loop l < L it
+ *   a0  draws a random odd scaling sigma_l and shift tau_l (scaling method,
+ *       Eq. 6-7) from Philox4x64-10 keyed by the plan seed;
+ *   a1  gathers x[(sigma_l m + tau_l) mod N] for window positions
+ *       m in [-w/2, w/2), multiplies by the flat window g (sinc x Gaussian,
+ *       Eq. 12-13) and folds the product into B buckets (Eq. 11);
+ *   a2  takes a B-point FFT of the fold (bucket values, Eq. 14);
+ *   a3  keeps the c*K buckets of largest energy (probability-and-statistics
+ *       location method: "2K large buckets");
+ *   a4  hashes every frequency f to bucket round(sigma_l f B / N) mod B;
+ *   a5  votes: frequencies hashed into kept buckets in at least T loops are
+ *       candidates;
+ *   a6  estimates each candidate per loop by energy concentration, undoing
+ *       the time-shift phase and the window gain, and takes the median over
+ *       loops (real and imaginary parts separately);
+ *   a7  returns the K candidates of largest magnitude, sorted by frequency.
+ *
+ * Conventions shared by every entry point:
+ *   - complex64 arrays are interleaved (re, im) float pairs;
+ *   - x_dev / outputs are DEVICE pointers owned by the caller unless the
+ *     function name ends in _host; the library never frees caller memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); work is enqueued asynchronously and results are valid once
+ *     the stream reaches that point;
+ *   - every call returns an sfft_status; no call aborts or throws.  A failed
+ *     call writes a one-line reason readable with sfft_last_error();
+ *   - a plan owns device scratch: one plan must not be executed by two
+ *     streams at once (use separate plans, sfft_execute_batch or the server).
+ *
+ * Sizes (checked, SFFT_EINVAL otherwise): N a power of two in [2, 2^30];
+ * B a power of two in [2, min(N, 16384)]; w a multiple of B in [B, N];
+ * 1 <= L <= 32; 1 <= K <= min(N, 16384); c >= 1; 1 <= T <= L.
+ */
+#ifndef SFFT_H
+#define SFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFFT_OK = 0,
+    SFFT_EINVAL = 1,    /* invalid argument or size */
+    SFFT_ENOMEM = 2,    /* device or host allocation failed */
+    SFFT_ECUDA = 3,     /* a CUDA runtime call failed (see sfft_last_error) */
+    SFFT_EBUSY = 4,     /* admission refused: server budget or slots exhausted */
+    SFFT_ETIMEDOUT = 5, /* a bounded wait expired */
+    SFFT_EPENDING = 6,  /* request not finished yet (sfft_poll) */
+    SFFT_ENOTIMPL = 7   /* option not implemented in this build */
+} sfft_status;
+
+typedef struct sfft_plan sfft_plan;
+typedef struct sfft_server sfft_server;
+
+/* Plan options.  Zero-initialised fields take the defaults listed. */
+typedef struct {
+    int32_t c;         /* buckets kept per loop = min(c*K, B); 0 -> 2 ("2K large buckets") */
+    int32_t T;         /* vote threshold; 0 -> ceil(L/2) */
+    int32_t precision; /* 0 -> FP32 B-point FFT (the only precision in this build) */
+    int32_t reserved;  /* must be 0 */
+} sfft_opts;
+
+/* Read-only description of a plan (host struct filled by sfft_plan_get_info). */
+typedef struct {
+    int64_t N, w;
+    int32_t K, B, L, c, T, nsel; /* nsel = min(c*K, B) */
+    uint64_t seed;
+    int64_t samples_touched;     /* distinct sample indices read per execute (Table 2) */
+    int64_t candidate_capacity;  /* min(N, (L-T+1)*nsel*N/B): bound on the candidate set */
+    size_t device_bytes;         /* device memory held by the plan */
+} sfft_plan_info;
+
+/* ------------------------------------------------------------------ plans */
+
+/* Create a plan: validates sizes, derives sigma_l, tau_l (a0), computes the
+   window taps, the gain table and the FFT twiddles on the GPU in FP64 (a0'),
+   and allocates scratch on the current CUDA device.  *plan is NULL on failure.
+   Blocks until the plan-time kernels finish.  Errors: SFFT_EINVAL, SFFT_ENOMEM,
+   SFFT_ECUDA. */
+sfft_status sfft_plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t B, int64_t w,
+                             int32_t L, uint64_t seed);
+
+/* As sfft_plan_create with explicit options (opts may be NULL). */
+sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t K, int32_t B, int64_t w,
+                                int32_t L, uint64_t seed, const sfft_opts *opts);
+
+/* Release a plan and its device memory (NULL is a no-op).  The caller must
+   ensure no enqueued work still uses it. */
+void sfft_plan_destroy(sfft_plan *plan);
+
+sfft_status sfft_plan_get_info(const sfft_plan *plan, sfft_plan_info *info);
+
+/* Copy the L loop parameters (host arrays of length L; any may be NULL):
+   sigma (odd), tau, and sigma^-1 mod N.  Pure host call. */
+sfft_status sfft_plan_get_loops(const sfft_plan *plan, uint32_t *sigma, uint32_t *tau,
+                                uint32_t *sigma_inv);
+
+/* Loop parameters without a plan (host only, no GPU needed): block
+   Philox4x64-10(counter = (l,0,0,0), key = (seed,0)) gives words r0, r1;
+   sigma_l = 2 (r0 mod N/2) + 1, tau_l = r1 mod N.  Errors: SFFT_EINVAL. */
+sfft_status sfft_loop_params(int64_t N, int32_t L, uint64_t seed, uint32_t *sigma, uint32_t *tau,
+                             uint32_t *sigma_inv);
+
+/* ---------------------------------------------------------------- execute */
+
+/* Whole hot path a1..a7 on one signal.
+   x_dev:     complex64[N], device.
+   idx_dev:   int32[K], device; the k_out recovered frequencies, ascending;
+              entries past k_out are left untouched.
+   val_dev:   complex64[K], device; estimates of xhat_f (Eq. 2 scale).
+   k_out_dev: int32[1], device; k_out = min(K, number of candidates).
+   Errors: SFFT_EINVAL (NULL pointer), SFFT_ECUDA (launch failure). */
+sfft_status sfft_execute(sfft_plan *plan, const float *x_dev, int32_t *idx_dev, float *val_dev,
+                         int32_t *k_out_dev, void *stream);
+
+/* The same with HOST buffers: copies x_host (complex64[N]) to a device buffer
+   owned by the plan, executes, copies the outputs back and synchronises the
+   stream.  Pinned host memory gives the fastest copies. */
+sfft_status sfft_execute_host(sfft_plan *plan, const float *x_host, int32_t *idx_host,
+                              float *val_host, int32_t *k_out_host, void *stream);
+
+/* Many signals in one pass: every stage is one launch over all `count` jobs
+   (plans may differ in N, K, B, w, L).  Arrays have `count` entries; plans
+   must be distinct (each owns its scratch).  k_out_dev is int32[count] on the
+   device.  A job list seen before replays a cached CUDA graph.
+   Errors: SFFT_EINVAL, SFFT_ENOMEM, SFFT_ECUDA. */
+sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_dev,
+                               int32_t *const *idx_dev, float *const *val_dev, int32_t *k_out_dev,
+                               int32_t count, void *stream);
+
+/* ------------------------------------------------- single stages (tests) */
+/* Each runs one step on caller buffers; the plan's scratch is used for the
+   rest.  They exist so that every kernel can be checked on its own. */
+
+/* a1+a2: zhat_dev = complex64[L][B], bucket values of every loop. */
+sfft_status sfft_bucketize(sfft_plan *plan, const float *x_dev, float *zhat_dev, void *stream);
+
+/* a3: sel_dev = int32[L][nsel], per loop the kept buckets in rank order
+   (energy descending, ties to the lower bucket); zhat_dev as above. */
+sfft_status sfft_select(sfft_plan *plan, const float *zhat_dev, int32_t *sel_dev, void *stream);
+
+/* a4+a5: candidates {f : votes >= T} from the kept buckets sel_dev
+   (int32[L][nsel]); cand_dev int32[cap] receives them in no particular
+   order and n_cand_dev int32[1] their count.  The count never exceeds
+   candidate_capacity; cap must be at least that (SFFT_EINVAL otherwise). */
+sfft_status sfft_vote(sfft_plan *plan, const int32_t *sel_dev, int32_t *cand_dev,
+                      int32_t *n_cand_dev, int64_t cap, void *stream);
+
+/* a6: est_dev complex64[n_cand] = median estimates of the n_cand frequencies
+   cand_dev (any order) from bucket values zhat_dev (complex64[L][B]). */
+sfft_status sfft_estimate(sfft_plan *plan, const float *zhat_dev, const int32_t *cand_dev,
+                          int64_t n_cand, float *est_dev, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct {
+    int64_t N, w;
+    int32_t K, B, L;
+    uint64_t seed;
+    sfft_opts opts;        /* zero -> defaults */
+    const float *x_dev;    /* complex64[N], device, caller-owned, valid until done */
+    int32_t *idx_dev;      /* int32[K], device */
+    float *val_dev;        /* complex64[K], device */
+} sfft_request;
+
+typedef struct {
+    int32_t k_out;          /* number of frequencies written */
+    int32_t status;         /* sfft_status of the request */
+    int64_t samples_touched;
+    int64_t latency_ns;     /* submit -> completion observed by the server */
+} sfft_result;
+
+/* Start a serving loop on the current device: a host thread admits submitted
+   requests while their plans fit in hbm_budget_bytes and at most max_slots
+   are in flight, batches whatever is admitted, and launches it while earlier
+   batches still run (continuous batching).  Plans are cached and reused. */
+sfft_status sfft_server_create(sfft_server **srv, size_t hbm_budget_bytes, int32_t max_slots);
+
+/* Queue one request; *ticket identifies it.  SFFT_EBUSY if its plan alone
+   exceeds the budget; SFFT_EINVAL for bad sizes. */
+sfft_status sfft_submit(sfft_server *srv, const sfft_request *req, uint64_t *ticket);
+
+/* SFFT_EPENDING until the request has finished, then SFFT_OK (result filled;
+   the ticket is released) or the request's error. */
+sfft_status sfft_poll(sfft_server *srv, uint64_t ticket, sfft_result *result);
+
+/* Block until the ticket finishes or timeout_ms passes (SFFT_ETIMEDOUT). */
+sfft_status sfft_wait(sfft_server *srv, uint64_t ticket, int64_t timeout_ms, sfft_result *result);
+
+/* Pause (paused != 0) or resume admission: paused requests stay queued.
+   Used to drain a server or to hold requests back deliberately. */
+sfft_status sfft_server_set_paused(sfft_server *srv, int32_t paused);
+
+/* Drain outstanding work and stop the loop (NULL is a no-op). */
+void sfft_server_destroy(sfft_server *srv);
+
+/* ------------------------------------------------------------------ misc */
+const char *sfft_status_string(sfft_status s);
+/* Reason for the calling thread's most recent failure ("" if none). */
+const char *sfft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFFT_H */

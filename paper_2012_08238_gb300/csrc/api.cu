@@ -1,0 +1,756 @@
+// Host side of the C ABI: plans, execute, batched execute with cached CUDA
+// graphs, single-stage entry points, errors.
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstddef>
+#include <list>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sfft_internal.cuh"
+
+struct sfft_plan {
+    uint64_t id;  // unique per plan, keys the batch-graph cache
+    int device;
+    int64_t N, w;
+    int32_t K, B, L, c, T, nsel;
+    uint64_t seed;
+    uint32_t sigma_inv[sfft::kMaxL];
+    int64_t samples_touched;
+    int64_t cap;
+    size_t device_bytes;
+    sfft::PlanDev h;         // host mirror of the device descriptor
+    sfft::PlanDev *d;        // device descriptor
+    void *dmem;              // single allocation holding everything
+    // staging for sfft_execute_host (allocated on first use)
+    void *stage;
+};
+
+namespace sfft {
+
+namespace {
+thread_local std::string g_err;
+std::atomic<uint64_t> g_next_id{1};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+uint32_t ilog2(uint64_t v) {
+    uint32_t r = 0;
+    while ((1ull << r) < v) ++r;
+    return r;
+}
+
+// Philox4x64-10 block function (Salmon et al., SC'11): ten rounds of two
+// 64x64->128-bit multiplies with the published multipliers, the key bumped by
+// the published Weyl increments after every round.
+void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+    for (int r = 0; r < 10; ++r) {
+        const unsigned __int128 p0 = (unsigned __int128)0xD2E7470EE14C6C93ULL * c[0];
+        const unsigned __int128 p1 = (unsigned __int128)0xCA5A826395121157ULL * c[2];
+        const uint64_t n0 = (uint64_t)(p1 >> 64) ^ c[1] ^ k0;
+        const uint64_t n1 = (uint64_t)p1;
+        const uint64_t n2 = (uint64_t)(p0 >> 64) ^ c[3] ^ k1;
+        const uint64_t n3 = (uint64_t)p0;
+        c[0] = n0;
+        c[1] = n1;
+        c[2] = n2;
+        c[3] = n3;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+}
+
+// inverse of an odd number modulo 2^32 by Newton's iteration x <- x (2 - a x)
+uint32_t inv_odd_u32(uint32_t a) {
+    uint32_t x = a;  // correct to 3 bits
+    for (int i = 0; i < 4; ++i) x *= 2u - a * x;
+    return x;
+}
+
+void loop_params_host(int64_t N, int32_t L, uint64_t seed, uint32_t *sigma, uint32_t *tau, uint32_t *sinv) {
+    const uint64_t half = (uint64_t)N / 2;
+    for (int32_t l = 0; l < L; ++l) {
+        uint64_t c[4] = {(uint64_t)l, 0, 0, 0};
+        philox4x64_10(c, seed, 0);
+        const uint32_t s = (uint32_t)(2 * (c[0] % half) + 1);
+        if (sigma) sigma[l] = s;
+        if (tau) tau[l] = (uint32_t)(c[1] % (uint64_t)N);
+        if (sinv) sinv[l] = inv_odd_u32(s) & (uint32_t)(N - 1);
+    }
+}
+
+sfft_status check_sizes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T) {
+    if (!is_pow2(N) || N < 2 || N > (1ll << kMaxLogN)) {
+        set_error("N must be a power of two in [2, 2^30]");
+        return SFFT_EINVAL;
+    }
+    if (!is_pow2(B) || B < 2 || B > kMaxB || B > N) {
+        set_error("B must be a power of two in [2, min(N, 16384)]");
+        return SFFT_EINVAL;
+    }
+    if (w < B || w > N || w % B) {
+        set_error("w must be a multiple of B in [B, N]");
+        return SFFT_EINVAL;
+    }
+    if (L < 1 || L > kMaxL) {
+        set_error("L must lie in [1, 32]");
+        return SFFT_EINVAL;
+    }
+    if (K < 1 || K > kMaxK || K > N) {
+        set_error("K must lie in [1, min(N, 16384)]");
+        return SFFT_EINVAL;
+    }
+    if (c < 1 || T < 1 || T > L) {
+        set_error("c must be >= 1 and T in [1, L]");
+        return SFFT_EINVAL;
+    }
+    if (N / B > (1ll << 24) || (double)(N / B) * (double)w > 68719476736.0) {
+        set_error("plan too large: N/B must be <= 2^24 and (N/B)*w <= 2^36");
+        return SFFT_EINVAL;
+    }
+    return SFFT_OK;
+}
+
+constexpr int kNumSms = 152;  // GB300; only shapes the default work split
+
+// Work split of one plan for the gather and vote kernels.
+void decompose(PlanDev &P) {
+    P.tb = std::min<uint32_t>(P.B, 256);
+    P.tiles = P.B / P.tb;
+    P.rounds = P.w / P.B;
+    uint32_t want = (2 * kNumSms + P.tiles * P.L - 1) / (P.tiles * P.L);
+    want = std::max<uint32_t>(1, std::min<uint32_t>(want, P.rounds));
+    P.rpc = (P.rounds + want - 1) / want;
+    P.nchunk = (P.rounds + P.rpc - 1) / P.rpc;
+    P.vtiles = std::max<uint32_t>(1, std::min<uint32_t>((P.N + 4095) / 4096, 8 * kNumSms));
+}
+
+struct Layout {
+    size_t plan, taps, tw, ginv, part, zhat, en, topk, sel, flags, surv, ctr, total;
+};
+
+Layout layout_of(const PlanDev &P, int64_t cap) {
+    Layout o;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off += align256(bytes);
+        return at;
+    };
+    const size_t L = P.L, B = P.B;
+    o.plan = take(sizeof(PlanDev));
+    o.taps = take(sizeof(float) * P.w);
+    o.tw = take(sizeof(float2) * (B / 2));
+    o.ginv = take(sizeof(float2) * (P.N / B));
+    o.part = take(sizeof(float2) * P.nchunk * L * B);
+    o.zhat = take(sizeof(float2) * L * B);
+    o.en = take(sizeof(float) * L * B);
+    o.topk = take(sizeof(float) * L * P.Kl);
+    o.sel = take(sizeof(int32_t) * L * P.nsel);
+    o.flags = take(sizeof(uint16_t) * L * B);
+    o.surv = take(sizeof(uint4) * (size_t)cap);
+    o.ctr = take(sizeof(uint32_t) * kNumCounters);
+    o.total = off;
+    return o;
+}
+
+// Sizes and work split of a plan, without touching the device.
+void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
+                   int64_t *cap) {
+    memset(&P, 0, sizeof(P));
+    const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
+    P.N = (uint32_t)N;
+    P.mask = (uint32_t)(N - 1);
+    P.logN = ilog2(N);
+    P.B = (uint32_t)B;
+    P.logB = ilog2(B);
+    P.shift = P.logN - P.logB;
+    P.half = (uint32_t)((N / B) / 2);
+    P.w = (uint32_t)w;
+    P.halfw = (uint32_t)(w / 2);
+    P.L = (uint32_t)L;
+    P.K = (uint32_t)K;
+    P.Kl = (uint32_t)std::min<int32_t>(K, B);
+    P.nsel = (uint32_t)nsel;
+    P.T = (uint32_t)T;
+    P.M = (uint32_t)((L + 1) / 2);
+    decompose(P);
+    *cap = std::min<int64_t>(N, (int64_t)(L - T + 1) * nsel * (N / B));
+    P.cap = (uint32_t)*cap;
+    P.flags_smem = (uint32_t)(L * B * 2) <= (uint32_t)kFlagsSmemBytes;
+}
+
+}  // namespace
+
+size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T) {
+    if (check_sizes(N, K, B, w, L, c, T) != SFFT_OK) return 0;
+    PlanDev P;
+    int64_t cap;
+    fill_plan_dev(P, N, K, B, w, L, c, T, &cap);
+    return layout_of(P, cap).total;
+}
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+sfft_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return SFFT_ENOMEM;
+    return SFFT_ECUDA;
+}
+
+// ------------------------------------------------------------ launch helpers
+namespace {
+
+struct Sizes {
+    uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
+    uint32_t max_B = 0, max_flags = 0, L_uniform = 0;
+};
+
+Sizes plan_sizes(const sfft_plan *p) {
+    Sizes z;
+    z.gather = p->h.tiles * p->h.L * p->h.nchunk;
+    z.select = p->h.L;
+    z.vote = p->h.vtiles;
+    z.jobs = 1;
+    z.max_B = p->h.B;
+    z.max_flags = p->h.L * p->h.B * 2;
+    z.L_uniform = p->h.L;
+    return z;
+}
+
+// G -> S -> V(prune) -> V(fallback) -> top-K, all stream-ordered.
+cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &lk,
+                            const Sizes &z, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = launch_gather(lg, z.gather, s)) != cudaSuccess) return e;
+    if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.max_flags, nullptr, nullptr, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_vote(lv, z.vote, kVoteFallback, z.L_uniform, z.max_flags, nullptr, nullptr, s)) != cudaSuccess)
+        return e;
+    return launch_topk(lk, z.jobs, s);
+}
+
+Job make_job(const sfft_plan *p, const float *x, int32_t *idx, float *val, int32_t *kout) {
+    Job j;
+    j.p = p->d;
+    j.x = reinterpret_cast<const float2 *>(x);
+    j.idx = idx;
+    j.val = reinterpret_cast<float2 *>(val);
+    j.kout = kout;
+    return j;
+}
+
+Launch single(const Job &j) {
+    Launch ln;
+    ln.jobs = nullptr;
+    ln.offs = nullptr;
+    ln.njobs = 1;
+    ln.one = j;
+    return ln;
+}
+
+// ---- batch buffers: a small ring of (pinned host, device) pairs for one-off
+// job lists, and a cache of captured graphs for job lists seen again.
+struct Slot {
+    void *host = nullptr;
+    void *dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    int device = -1;
+};
+
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    void *dev = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int seen = 0;
+    int device = -1;
+};
+
+std::mutex g_batch_mu;
+Slot g_slots[4];
+int g_next_slot = 0;
+std::list<GraphEntry> g_graphs;  // most recent first
+constexpr size_t kMaxGraphs = 16;
+
+void drop_entry(GraphEntry &e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.dev) cudaFree(e.dev);
+    e.exec = nullptr;
+    e.dev = nullptr;
+}
+
+}  // namespace
+
+void forget_plan_graphs(uint64_t id) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        bool uses = false;
+        for (size_t i = 1; i < it->key.size(); i += 4)
+            if (it->key[i] == id) uses = true;
+        if (uses) {
+            drop_entry(*it);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+}  // namespace sfft
+
+using namespace sfft;
+
+// ------------------------------------------------------------------- plans
+extern "C" sfft_status sfft_loop_params(int64_t N, int32_t L, uint64_t seed, uint32_t *sigma, uint32_t *tau,
+                                        uint32_t *sigma_inv) {
+    if (!is_pow2(N) || N < 2 || N > (1ll << kMaxLogN) || L < 1 || L > kMaxL) {
+        set_error("N must be a power of two in [2, 2^30] and L in [1, 32]");
+        return SFFT_EINVAL;
+    }
+    loop_params_host(N, L, seed, sigma, tau, sigma_inv);
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L,
+                                        uint64_t seed) {
+    return sfft_plan_create_ex(plan, N, K, B, w, L, seed, nullptr);
+}
+
+extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t K, int32_t B, int64_t w,
+                                           int32_t L, uint64_t seed, const sfft_opts *opts) {
+    if (!plan) {
+        set_error("plan pointer is NULL");
+        return SFFT_EINVAL;
+    }
+    *plan = nullptr;
+    sfft_opts o = {};
+    if (opts) o = *opts;
+    if (o.precision != 0) {
+        set_error("only precision 0 (FP32 FFT) is implemented");
+        return SFFT_ENOTIMPL;
+    }
+    if (o.reserved != 0) {
+        set_error("sfft_opts.reserved must be 0");
+        return SFFT_EINVAL;
+    }
+    const int32_t c = o.c > 0 ? o.c : 2;
+    const int32_t T = o.T > 0 ? o.T : (L + 1) / 2;
+    sfft_status st = check_sizes(N, K, B, w, L, c, T);
+    if (st != SFFT_OK) return st;
+
+    sfft_plan *p = new (std::nothrow) sfft_plan();
+    if (!p) {
+        set_error("host allocation failed");
+        return SFFT_ENOMEM;
+    }
+    p->id = g_next_id.fetch_add(1);
+    cudaGetDevice(&p->device);
+    p->N = N;
+    p->w = w;
+    p->K = K;
+    p->B = B;
+    p->L = L;
+    p->c = c;
+    p->T = T;
+    p->nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
+    p->seed = seed;
+
+    PlanDev &P = p->h;
+    fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap);
+    loop_params_host(N, L, seed, P.sigma, P.tau, p->sigma_inv);
+    const Layout lay = layout_of(P, p->cap);
+    p->device_bytes = lay.total;
+    const size_t off = lay.total;
+    cudaError_t e = cudaMalloc(&p->dmem, off);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaMalloc(plan)");
+    }
+    char *base = static_cast<char *>(p->dmem);
+    p->d = reinterpret_cast<PlanDev *>(base + lay.plan);
+    P.taps = reinterpret_cast<float *>(base + lay.taps);
+    P.tw = reinterpret_cast<float2 *>(base + lay.tw);
+    P.ginv = reinterpret_cast<float2 *>(base + lay.ginv);
+    P.partial = reinterpret_cast<float2 *>(base + lay.part);
+    P.zhat = reinterpret_cast<float2 *>(base + lay.zhat);
+    P.energy = reinterpret_cast<float *>(base + lay.en);
+    P.topkeys = reinterpret_cast<float *>(base + lay.topk);
+    P.sel = reinterpret_cast<int32_t *>(base + lay.sel);
+    P.flags = reinterpret_cast<uint16_t *>(base + lay.flags);
+    P.surv = reinterpret_cast<uint4 *>(base + lay.surv);
+    P.ctr = reinterpret_cast<uint32_t *>(base + lay.ctr);
+
+    // plan-time tables on a private stream
+    cudaStream_t s = nullptr;
+    double *ginv2 = nullptr;
+    void *tmp = nullptr;  // bitmap + counters
+    const size_t nb = (size_t)(N / B);
+    const size_t bitmap_bytes = align256(((size_t)N + 31) / 32 * 4);
+    auto fail = [&](cudaError_t err, const char *what) {
+        if (s) cudaStreamDestroy(s);
+        if (ginv2) cudaFree(ginv2);
+        if (tmp) cudaFree(tmp);
+        cudaFree(p->dmem);
+        delete p;
+        return cuda_fail(err, what);
+    };
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+    if ((e = cudaMalloc(&ginv2, sizeof(double) * nb)) != cudaSuccess) return fail(e, "cudaMalloc(gain)");
+    if ((e = cudaMalloc(&tmp, bitmap_bytes + 256)) != cudaSuccess) return fail(e, "cudaMalloc(bitmap)");
+    if ((e = cudaMemcpyAsync(p->d, &P, sizeof(PlanDev), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(e, "upload plan");
+    if ((e = cudaMemsetAsync(P.ctr, 0, sizeof(uint32_t) * kNumCounters, s)) != cudaSuccess)
+        return fail(e, "clear counters");
+    if ((e = plan_tables(P.N, P.B, P.w, const_cast<float *>(P.taps), const_cast<float2 *>(P.tw),
+                         const_cast<float2 *>(P.ginv), ginv2, s)) != cudaSuccess)
+        return fail(e, "plan tables");
+    unsigned long long *d_count = reinterpret_cast<unsigned long long *>(static_cast<char *>(tmp) + bitmap_bytes);
+    unsigned long long *d_max = d_count + 1;
+    if ((e = plan_max_bits(ginv2, (uint32_t)nb, d_max, s)) != cudaSuccess) return fail(e, "gain max");
+    const uint32_t *d_sigma = reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(p->d) + offsetof(PlanDev, sigma));
+    const uint32_t *d_tau = reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(p->d) + offsetof(PlanDev, tau));
+    if ((e = plan_samples_touched(P.N, P.w, P.L, d_sigma, d_tau, static_cast<uint32_t *>(tmp), d_count, s)) !=
+        cudaSuccess)
+        return fail(e, "samples touched");
+    unsigned long long host2[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(host2, d_count, sizeof(host2), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return fail(e, "download stats");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "plan kernels");
+    p->samples_touched = (int64_t)host2[0];
+    double gmax;
+    memcpy(&gmax, &host2[1], sizeof(double));
+    float gf = (float)gmax;
+    if ((double)gf < gmax) gf = nextafterf(gf, INFINITY);
+    P.ginv2max = gf;
+    // second upload with the gain bound filled in
+    if ((e = cudaMemcpyAsync(p->d, &P, sizeof(PlanDev), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(e, "upload plan");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "upload plan");
+    cudaStreamDestroy(s);
+    cudaFree(ginv2);
+    cudaFree(tmp);
+    *plan = p;
+    return SFFT_OK;
+}
+
+extern "C" void sfft_plan_destroy(sfft_plan *plan) {
+    if (!plan) return;
+    forget_plan_graphs(plan->id);
+    if (plan->stage) cudaFree(plan->stage);
+    cudaFree(plan->dmem);
+    delete plan;
+}
+
+extern "C" sfft_status sfft_plan_get_info(const sfft_plan *p, sfft_plan_info *info) {
+    if (!p || !info) {
+        set_error("NULL argument");
+        return SFFT_EINVAL;
+    }
+    info->N = p->N;
+    info->w = p->w;
+    info->K = p->K;
+    info->B = p->B;
+    info->L = p->L;
+    info->c = p->c;
+    info->T = p->T;
+    info->nsel = p->nsel;
+    info->seed = p->seed;
+    info->samples_touched = p->samples_touched;
+    info->candidate_capacity = p->cap;
+    info->device_bytes = p->device_bytes;
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_plan_get_loops(const sfft_plan *p, uint32_t *sigma, uint32_t *tau,
+                                           uint32_t *sigma_inv) {
+    if (!p) {
+        set_error("NULL plan");
+        return SFFT_EINVAL;
+    }
+    for (int l = 0; l < p->L; ++l) {
+        if (sigma) sigma[l] = p->h.sigma[l];
+        if (tau) tau[l] = p->h.tau[l];
+        if (sigma_inv) sigma_inv[l] = p->sigma_inv[l];
+    }
+    return SFFT_OK;
+}
+
+// ----------------------------------------------------------------- execute
+extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *idx_dev, float *val_dev,
+                                    int32_t *k_out_dev, void *stream) {
+    if (!p || !x_dev || !idx_dev || !val_dev || !k_out_dev) {
+        set_error("NULL argument");
+        return SFFT_EINVAL;
+    }
+    const Launch ln = single(make_job(p, x_dev, idx_dev, val_dev, k_out_dev));
+    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_execute_host(sfft_plan *p, const float *x_host, int32_t *idx_host, float *val_host,
+                                         int32_t *k_out_host, void *stream) {
+    if (!p || !x_host || !idx_host || !val_host || !k_out_host) {
+        set_error("NULL argument");
+        return SFFT_EINVAL;
+    }
+    const size_t xb = align256(sizeof(float2) * p->N), ib = align256(sizeof(int32_t) * p->K),
+                 vb = align256(sizeof(float2) * p->K);
+    if (!p->stage) SFFT_CUDA_TRY(cudaMalloc(&p->stage, xb + ib + vb + 256));
+    char *b = static_cast<char *>(p->stage);
+    float *x = reinterpret_cast<float *>(b);
+    int32_t *idx = reinterpret_cast<int32_t *>(b + xb);
+    float *val = reinterpret_cast<float *>(b + xb + ib);
+    int32_t *kout = reinterpret_cast<int32_t *>(b + xb + ib + vb);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SFFT_CUDA_TRY(cudaMemcpyAsync(x, x_host, sizeof(float2) * p->N, cudaMemcpyHostToDevice, s));
+    sfft_status st = sfft_execute(p, x, idx, val, kout, stream);
+    if (st != SFFT_OK) return st;
+    SFFT_CUDA_TRY(cudaMemcpyAsync(k_out_host, kout, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SFFT_CUDA_TRY(cudaMemcpyAsync(idx_host, idx, sizeof(int32_t) * p->K, cudaMemcpyDeviceToHost, s));
+    SFFT_CUDA_TRY(cudaMemcpyAsync(val_host, val, sizeof(float2) * p->K, cudaMemcpyDeviceToHost, s));
+    SFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return SFFT_OK;
+}
+
+// ------------------------------------------------------------------- batch
+namespace {
+
+struct BatchLayout {
+    std::vector<unsigned char> bytes;  // jobs, then four prefix arrays
+    size_t off_offs[4];
+    Sizes z;
+};
+
+BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t *const *idx,
+                        float *const *val, int32_t *kout, int32_t count) {
+    BatchLayout b;
+    const size_t jb = align256(sizeof(Job) * count), ob = align256(sizeof(uint32_t) * (count + 1));
+    b.bytes.assign(jb + 4 * ob, 0);
+    Job *jobs = reinterpret_cast<Job *>(b.bytes.data());
+    uint32_t *offs[4];
+    for (int k = 0; k < 4; ++k) {
+        b.off_offs[k] = jb + k * ob;
+        offs[k] = reinterpret_cast<uint32_t *>(b.bytes.data() + b.off_offs[k]);
+        offs[k][0] = 0;
+    }
+    Sizes &z = b.z;
+    z.L_uniform = plans[0]->h.L;
+    for (int32_t i = 0; i < count; ++i) {
+        const sfft_plan *p = plans[i];
+        jobs[i] = make_job(p, x[i], idx[i], val[i], kout + i);
+        const Sizes s = plan_sizes(p);
+        offs[0][i + 1] = offs[0][i] + s.gather;
+        offs[1][i + 1] = offs[1][i] + s.select;
+        offs[2][i + 1] = offs[2][i] + s.vote;
+        offs[3][i + 1] = offs[3][i] + 1;
+        z.max_B = std::max(z.max_B, s.max_B);
+        z.max_flags = std::max(z.max_flags, s.max_flags);
+        if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
+    }
+    z.gather = offs[0][count];
+    z.select = offs[1][count];
+    z.vote = offs[2][count];
+    z.jobs = (uint32_t)count;
+    return b;
+}
+
+cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, cudaStream_t s) {
+    const char *base = static_cast<const char *>(dev);
+    Launch ln[4];
+    for (int k = 0; k < 4; ++k) {
+        ln[k].jobs = reinterpret_cast<const Job *>(base);
+        ln[k].offs = reinterpret_cast<const uint32_t *>(base + b.off_offs[k]);
+        ln[k].njobs = count;
+        memset(&ln[k].one, 0, sizeof(Job));
+    }
+    return launch_pipeline(ln[0], ln[1], ln[2], ln[3], b.z, s);
+}
+
+}  // namespace
+
+extern "C" sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_dev,
+                                          int32_t *const *idx_dev, float *const *val_dev, int32_t *k_out_dev,
+                                          int32_t count, void *stream) {
+    if (count < 0 || (count > 0 && (!plans || !x_dev || !idx_dev || !val_dev || !k_out_dev))) {
+        set_error("NULL argument or negative count");
+        return SFFT_EINVAL;
+    }
+    if (count == 0) return SFFT_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        if (!plans[i] || !x_dev[i] || !idx_dev[i] || !val_dev[i]) {
+            set_error("NULL entry in batch arrays");
+            return SFFT_EINVAL;
+        }
+        for (int32_t j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) {
+                set_error("a plan appears twice in one batch (each plan owns its scratch)");
+                return SFFT_EINVAL;
+            }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int device = 0;
+    cudaGetDevice(&device);
+    BatchLayout b = build_batch(plans, x_dev, idx_dev, val_dev, k_out_dev, count);
+
+    // key: count, then (plan id, x, idx, val) per job, then k_out
+    std::vector<uint64_t> key;
+    key.reserve(2 + 4 * count);
+    key.push_back((uint64_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        key.push_back(plans[i]->id);
+        key.push_back((uint64_t)(uintptr_t)x_dev[i]);
+        key.push_back((uint64_t)(uintptr_t)idx_dev[i]);
+        key.push_back((uint64_t)(uintptr_t)val_dev[i]);
+    }
+    key.push_back((uint64_t)(uintptr_t)k_out_dev);
+
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+        if (it->device != device || it->key != key) continue;
+        GraphEntry &ge = *it;
+        if (!ge.exec) {
+            // second sighting: keep a persistent job buffer and capture the pipeline
+            cudaError_t e = cudaMalloc(&ge.dev, b.bytes.size());
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch graph)");
+            SFFT_CUDA_TRY(cudaMemcpy(ge.dev, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice));
+            cudaStream_t cap = nullptr;
+            SFFT_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                cudaError_t le = launch_batch(b, ge.dev, count, cap);
+                e = cudaStreamEndCapture(cap, &g);
+                if (le != cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) {
+                drop_entry(ge);
+                g_graphs.erase(it);
+                return cuda_fail(e, "capture batch graph");
+            }
+        }
+        g_graphs.splice(g_graphs.begin(), g_graphs, it);
+        SFFT_CUDA_TRY(cudaGraphLaunch(g_graphs.front().exec, s));
+        return SFFT_OK;
+    }
+    // first sighting: remember the key, run through a staging slot
+    GraphEntry ne;
+    ne.key = key;
+    ne.device = device;
+    g_graphs.push_front(ne);
+    while (g_graphs.size() > kMaxGraphs) {
+        drop_entry(g_graphs.back());
+        g_graphs.pop_back();
+    }
+    Slot &sl = g_slots[g_next_slot];
+    g_next_slot = (g_next_slot + 1) % 4;
+    if (sl.done) SFFT_CUDA_TRY(cudaEventSynchronize(sl.done));
+    if (sl.device != device || sl.cap < b.bytes.size()) {
+        if (sl.host) cudaFreeHost(sl.host);
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.done) cudaEventDestroy(sl.done);
+        sl = Slot();
+        const size_t cap = std::max<size_t>(b.bytes.size(), 64 * 1024);
+        SFFT_CUDA_TRY(cudaMallocHost(&sl.host, cap));
+        SFFT_CUDA_TRY(cudaMalloc(&sl.dev, cap));
+        SFFT_CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+        sl.cap = cap;
+        sl.device = device;
+    }
+    memcpy(sl.host, b.bytes.data(), b.bytes.size());
+    SFFT_CUDA_TRY(cudaMemcpyAsync(sl.dev, sl.host, b.bytes.size(), cudaMemcpyHostToDevice, s));
+    SFFT_CUDA_TRY(launch_batch(b, sl.dev, count, s));
+    SFFT_CUDA_TRY(cudaEventRecord(sl.done, s));
+    return SFFT_OK;
+}
+
+// ------------------------------------------------------------ single stages
+extern "C" sfft_status sfft_bucketize(sfft_plan *p, const float *x_dev, float *zhat_dev, void *stream) {
+    if (!p || !x_dev || !zhat_dev) {
+        set_error("NULL argument");
+        return SFFT_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Launch ln = single(make_job(p, x_dev, nullptr, nullptr, nullptr));
+    const Sizes z = plan_sizes(p);
+    SFFT_CUDA_TRY(launch_gather(ln, z.gather, s));
+    SFFT_CUDA_TRY(launch_fft_select(ln, z.select, z.max_B, 0, s));
+    SFFT_CUDA_TRY(cudaMemcpyAsync(zhat_dev, p->h.zhat, sizeof(float2) * p->L * p->B, cudaMemcpyDeviceToDevice, s));
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_select(sfft_plan *p, const float *zhat_dev, int32_t *sel_dev, void *stream) {
+    if (!p || !zhat_dev || !sel_dev) {
+        set_error("NULL argument");
+        return SFFT_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
+    SFFT_CUDA_TRY(cudaMemcpyAsync(p->h.zhat, zhat_dev, sizeof(float2) * p->L * p->B, cudaMemcpyDeviceToDevice, s));
+    SFFT_CUDA_TRY(launch_fft_select(ln, p->h.L, p->h.B, 1, s));
+    SFFT_CUDA_TRY(
+        cudaMemcpyAsync(sel_dev, p->h.sel, sizeof(int32_t) * p->L * p->nsel, cudaMemcpyDeviceToDevice, s));
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_vote(sfft_plan *p, const int32_t *sel_dev, int32_t *cand_dev, int32_t *n_cand_dev,
+                                 int64_t cap, void *stream) {
+    if (!p || !sel_dev || !cand_dev || !n_cand_dev) {
+        set_error("NULL argument");
+        return SFFT_EINVAL;
+    }
+    if (cap < p->cap) {
+        set_error("candidate buffer smaller than the plan's candidate capacity");
+        return SFFT_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
+    SFFT_CUDA_TRY(cudaMemsetAsync(n_cand_dev, 0, sizeof(int32_t), s));
+    SFFT_CUDA_TRY(launch_flags_from_sel(p->d, p->h.L, sel_dev, s));
+    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, p->h.L * p->h.B * 2, cand_dev,
+                              n_cand_dev, s));
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_estimate(sfft_plan *p, const float *zhat_dev, const int32_t *cand_dev, int64_t n_cand,
+                                     float *est_dev, void *stream) {
+    if (!p || n_cand < 0 || (n_cand > 0 && (!zhat_dev || !cand_dev || !est_dev))) {
+        set_error("NULL argument or negative count");
+        return SFFT_EINVAL;
+    }
+    if (n_cand > (int64_t)p->N) {
+        set_error("more candidates than frequencies");
+        return SFFT_EINVAL;
+    }
+    SFFT_CUDA_TRY(launch_estimate_list(p->d, p->h.L, reinterpret_cast<const float2 *>(zhat_dev), cand_dev,
+                                       (uint32_t)n_cand, reinterpret_cast<float2 *>(est_dev),
+                                       static_cast<cudaStream_t>(stream)));
+    return SFFT_OK;
+}
+
+// -------------------------------------------------------------------- misc
+extern "C" const char *sfft_status_string(sfft_status s) {
+    switch (s) {
+        case SFFT_OK: return "ok";
+        case SFFT_EINVAL: return "invalid argument";
+        case SFFT_ENOMEM: return "out of memory";
+        case SFFT_ECUDA: return "CUDA error";
+        case SFFT_EBUSY: return "busy";
+        case SFFT_ETIMEDOUT: return "timed out";
+        case SFFT_EPENDING: return "pending";
+        case SFFT_ENOTIMPL: return "not implemented";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *sfft_last_error(void) { return g_err.c_str(); }

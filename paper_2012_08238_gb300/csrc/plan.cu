@@ -1,0 +1,144 @@
+// Plan-time kernels: flat-window taps, window gain table and FFT twiddles in
+// FP64 (step a0'), and the count of distinct samples a plan reads.
+#include <math_constants.h>
+
+#include <algorithm>
+
+#include "sfft_internal.cuh"
+
+namespace sfft {
+
+namespace {
+
+// Eq. 12 (sinc of width B with centre value 1/B) times Eq. 13 (Gaussian of
+// width sigma_g = B sqrt(log2 N)), window position m = q - w/2.
+__device__ double flat_tap(int64_t m, uint32_t B, double sg) {
+    const double sinc = (m == 0) ? 1.0 / (double)B : sinpi((double)m / (double)B) / (CUDART_PI * (double)m);
+    const double t = (double)m / sg;
+    return sinc * exp(-0.5 * t * t);
+}
+
+__global__ void k_taps(uint32_t N, uint32_t B, uint32_t w, double sg, double *g64, float *g32) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < w; q += gridDim.x * blockDim.x) {
+        const double g = flat_tap((int64_t)q - (int64_t)(w / 2), B, sg);
+        g64[q] = g;
+        g32[q] = (float)g;
+    }
+}
+
+// G~(o) = sum_m g(m) exp(+2 pi i m o / N), one CTA per offset o in
+// [-N/2B, N/2B); stores 1/G~(o) (FP32) and |1/G~(o)|^2 (FP64).
+__global__ void k_gain(uint32_t N, uint32_t B, uint32_t w, const double *g64, float2 *ginv, double *ginv2) {
+    __shared__ double sre[256], sim[256];
+    const uint32_t NB = N / B, half = NB / 2;
+    const int64_t o = (int64_t)blockIdx.x - (int64_t)half;
+    double re = 0.0, im = 0.0;
+    for (uint32_t q = threadIdx.x; q < w; q += blockDim.x) {
+        const int64_t m = (int64_t)q - (int64_t)(w / 2);
+        int64_t r = (m * o) % (int64_t)N;
+        if (r < 0) r += N;
+        double sn, cs;
+        sincospi(2.0 * (double)r / (double)N, &sn, &cs);
+        re += g64[q] * cs;
+        im += g64[q] * sn;
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (uint32_t s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sre[threadIdx.x] += sre[threadIdx.x + s];
+            sim[threadIdx.x] += sim[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double gr = sre[0], gi = sim[0], n2 = gr * gr + gi * gi;
+        ginv[blockIdx.x] = make_float2((float)(gr / n2), (float)(-gi / n2));
+        ginv2[blockIdx.x] = 1.0 / n2;
+    }
+}
+
+__global__ void k_twiddle(uint32_t B, float2 *tw) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < B / 2; k += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(-2.0 * (double)k / (double)B, &sn, &cs);
+        tw[k] = make_float2((float)cs, (float)sn);
+    }
+}
+
+__global__ void k_mark(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma, const uint32_t *tau,
+                       uint32_t *bitmap) {
+    const uint64_t total = (uint64_t)L * w;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t l = (uint32_t)(t / w), q = (uint32_t)(t % w);
+        const uint32_t i = (sigma[l] * (q - w / 2) + tau[l]) & (N - 1);
+        atomicOr(bitmap + (i >> 5), 1u << (i & 31));
+    }
+}
+
+__global__ void k_popc(const uint32_t *bitmap, uint32_t nwords, unsigned long long *count) {
+    unsigned long long c = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x)
+        c += __popc(bitmap[i]);
+    c = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// max of non-negative doubles through their (monotone) bit patterns
+__global__ void k_max_bits(const double *v, uint32_t n, unsigned long long *out) {
+    unsigned long long m = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double d = v[i];
+        const unsigned long long b = (d >= 0.0) ? (unsigned long long)__double_as_longlong(d) : 0ull;
+        m = b > m ? b : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_down_sync(0xFFFFFFFFu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+}  // namespace
+
+cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_max_bits<<<std::min<uint32_t>((n + 255) / 256, 4096), 256, 0, s>>>(v, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
+                        double *ginv2, cudaStream_t s) {
+    double *g64 = nullptr;
+    cudaError_t e = cudaMallocAsync(&g64, sizeof(double) * w, s);
+    if (e != cudaSuccess) return e;
+    const uint32_t logN = 31 - __builtin_clz(N);
+    const double sg = (double)B * sqrt((double)logN);
+    k_taps<<<(w + 255) / 256, 256, 0, s>>>(N, B, w, sg, g64, taps);
+    k_gain<<<N / B, 256, 0, s>>>(N, B, w, g64, ginv, ginv2);
+    k_twiddle<<<(B / 2 + 255) / 256, 256, 0, s>>>(B, tw);
+    e = cudaGetLastError();
+    cudaError_t e2 = cudaFreeAsync(g64, s);
+    return e != cudaSuccess ? e : e2;
+}
+
+cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
+                                 const uint32_t *tau, uint32_t *bitmap, unsigned long long *count,
+                                 cudaStream_t s) {
+    const uint32_t nwords = (N + 31) / 32;
+    cudaError_t e = cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * nwords, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const uint64_t total = (uint64_t)L * w;
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>((total + 255) / 256, 65535);
+    k_mark<<<blocks, 256, 0, s>>>(N, w, L, sigma, tau, bitmap);
+    const uint32_t pb = std::min<uint32_t>((nwords + 255) / 256, 65535);
+    k_popc<<<pb, 256, 0, s>>>(bitmap, nwords, count);
+    return cudaGetLastError();
+}
+
+}  // namespace sfft

@@ -1,0 +1,112 @@
+// Internal declarations of the CUDA sparse-FFT library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sfft.h"
+
+namespace sfft {
+
+constexpr int kMaxL = 32;
+constexpr int kMaxB = 16384;
+constexpr int kMaxK = 16384;
+constexpr int kMaxLogN = 30;
+constexpr int kTopkSmem = 16384;       // survivors sorted in shared memory up to this count
+constexpr int kFlagsSmemBytes = 96 * 1024;
+
+// Per-plan counters in device memory (uint32 slots).
+enum Counter : int {
+    kNCand = 0,    // candidates (score >= T) found by the vote scan
+    kNSurv = 1,    // survivors of the pruned pass (estimated)
+    kNGe = 2,      // survivors whose key >= theta
+    kNSurv2 = 3,   // entries written by the unpruned fallback pass
+    kSelDone = 4,  // loops finished by the FFT/select kernel (last-block pattern)
+    kTheta = 5,    // prune threshold theta (float bits)
+    kErr = 6,      // device-side error word (0 = none)
+    kNumCounters = 16
+};
+
+// Everything a kernel needs to know about one plan; lives in device memory and
+// is copied into shared memory by every CTA that works on the plan.
+struct PlanDev {
+    uint32_t N, mask, logN;
+    uint32_t B, logB;
+    uint32_t shift;   // log2(N/B)
+    uint32_t half;    // (N/B)/2 : round-half-up offset of the hash
+    uint32_t w, halfw;
+    uint32_t L, K, Kl;  // Kl = min(K, B)
+    uint32_t nsel, T, M;  // M = ceil(L/2): strong loops needed by the median bound
+    uint32_t nchunk, rounds, rpc, tb, tiles;  // gather decomposition
+    uint32_t vtiles;                          // vote CTAs per job
+    uint32_t flags_smem;                      // vote table fits in shared memory
+    uint32_t cap;                             // candidate capacity
+    float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
+    uint32_t sigma[kMaxL], tau[kMaxL];
+    const float *taps;     // [w]
+    const float2 *tw;      // [B/2] exp(-2 pi i k / B)
+    const float2 *ginv;    // [N/B] 1 / G~(o), o + half
+    float2 *partial;       // [nchunk][L][B]
+    float2 *zhat;          // [L][B]
+    float *energy;         // [L][B]
+    float *topkeys;        // [L][Kl], descending
+    int32_t *sel;          // [L][nsel]
+    uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
+    uint4 *surv;           // [cap] {f, key bits, re bits, im bits}
+    uint32_t *ctr;         // [kNumCounters]
+};
+
+// One signal of a launch: which plan, which input, where the outputs go.
+struct Job {
+    const PlanDev *p;
+    const float2 *x;
+    int32_t *idx;
+    float2 *val;
+    int32_t *kout;
+};
+
+// Launch descriptor shared by all stage kernels: either one job passed by
+// value, or `njobs` jobs in device memory with a CTA-offset prefix per kernel.
+struct Launch {
+    const Job *jobs;        // nullptr -> use `one`
+    const uint32_t *offs;   // [njobs + 1] CTA prefix for this kernel (batch only)
+    int njobs;
+    Job one;
+};
+
+enum VoteMode : int { kVotePrune = 0, kVoteFallback = 1, kVoteCandidates = 2 };
+
+// ---------------------------------------------------------------- host side
+void set_error(const std::string &msg);
+sfft_status cuda_fail(cudaError_t e, const char *what);
+
+// Kernel launchers (stream-ordered, no synchronisation).
+cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
+cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
+                              cudaStream_t s);
+// L_uniform: common L of every job (0 when they differ).
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform,
+                        uint32_t max_flags_bytes, int32_t *cand_out, int32_t *ncand_out,
+                        cudaStream_t s);
+cudaError_t launch_topk(const Launch &ln, uint32_t njobs, cudaStream_t s);
+cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
+                                 uint32_t n, float2 *est, cudaStream_t s);
+cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *sel, cudaStream_t s);
+
+// Plan-time FP64 kernels (plan.cu).
+cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
+                        double *ginv2, cudaStream_t s);
+cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, cudaStream_t s);
+cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
+                                 const uint32_t *tau, uint32_t *bitmap, unsigned long long *count,
+                                 cudaStream_t s);
+
+}  // namespace sfft
+
+#define SFFT_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return sfft::cuda_fail(_e, #expr); \
+    } while (0)

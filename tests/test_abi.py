@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every declared symbol (CPU only).
+
+Also checks the host-only parts of the library: the loop parameters it
+derives from a seed (against the oracle and numpy's Philox) and the size
+validation that runs before any device call.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_08238_gb300 import build, sfft
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(sfft_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    assert os.path.exists(path)
+    so = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(so, name), f"{name} declared in include/ but not exported"
+    assert set(names) == set(sfft.EXPORTED), "binding and header disagree"
+
+
+@pytest.mark.parametrize("N,L,seed", [(1 << 16, 8, 0), (1 << 20, 12, 12345), (2, 3, 7), (1 << 30, 32, 2**63 + 1)])
+def test_loop_params_match_oracle(N, L, seed):
+    s, t, si = sfft.sfft_loop_params(N, L, seed)
+    os_, ot, osi = oracle.loop_params(N, L, seed)
+    assert list(os_) == s and list(ot) == t and list(osi) == si
+
+
+@pytest.mark.parametrize("args", [
+    (1000, 10, 64, 2368, 8),        # N not a power of two
+    (1 << 16, 10, 48, 2400, 8),     # B not a power of two
+    (1 << 16, 10, 64, 2370, 8),     # w not a multiple of B
+    (1 << 16, 10, 64, 32, 8),       # w < B
+    (1 << 16, 10, 64, 2368, 0),     # L = 0
+    (1 << 16, 10, 64, 2368, 33),    # L > 32
+    (1 << 16, 0, 64, 2368, 8),      # K = 0
+    (1 << 16, 20000, 64, 2368, 8),  # K > 16384
+    (1 << 31, 10, 64, 2368, 8),     # N > 2^30
+    (1 << 16, 10, 1 << 15, 1 << 15, 8),  # B > 16384
+])
+def test_invalid_sizes_rejected_before_any_device_call(args):
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_plan_create(*args, seed=0)
+    assert ei.value.status == sfft.SFFT_EINVAL
+
+
+def test_invalid_options_rejected():
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_plan_create_ex(1 << 16, 10, 64, 2368, 8, 0, c=1, T=9)
+    assert ei.value.status == sfft.SFFT_EINVAL
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_plan_create_ex(1 << 16, 10, 64, 2368, 8, 0, precision=1)
+    assert ei.value.status == sfft.SFFT_ENOTIMPL
+
+
+def test_status_strings():
+    assert sfft.status_string(sfft.SFFT_OK) == "ok"
+    assert sfft.status_string(sfft.SFFT_EPENDING) == "pending"

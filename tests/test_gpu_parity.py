@@ -1,0 +1,264 @@
+"""Parity of the CUDA path with the FP64 oracle, stage by stage and end to end.
+
+Tolerances (FP32 arithmetic on the GPU, FP64 in the oracle):
+  * bucket values zhat: relative L2 <= 1e-5;
+  * kept buckets, candidates: identical wherever the decision is not a near
+    tie of FP32 energies (relative gap 1e-5); exact ties go to the lower index
+    on both sides;
+  * votes given the same kept buckets: bit-exact candidate sets;
+  * estimates and output values: relative L2 <= 1e-4;
+  * recovered support: identical on exactly sparse inputs, >= 99.9 %
+    agreement on noisy ones.
+Each GPU stage is fed the oracle's own intermediate arrays, so a stage is
+checked independently of the ones before it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import rel_l2, run_bucketize, run_estimate, run_execute, run_select, run_vote
+from paper_2012_08238_gb300 import configs, sfft, signals
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _pair(N, K, B, w, L, seed, c=2, T=None):
+    plan = sfft.sfft_plan_create_ex(N, K, B, w, L, seed, c=c, T=T or 0)
+    oplan = oracle.Plan(N, K, B, w, L, seed, c=c, T=T)
+    return plan, oplan
+
+
+def _sparse(N, freqs, coefs):
+    j = np.arange(N)
+    x = np.zeros(N, np.complex128)
+    for f, a in zip(freqs, coefs):
+        x += a * np.exp(2j * np.pi * j * f / N)
+    return x.astype(np.complex64)
+
+
+# (N, K, B, w, L, seed, c, T, signal kind)
+SHAPES = [
+    (1 << 10, 3, 16, 16 * 31, 3, 1, 2, None, "exact"),            # tiny
+    (1 << 12, 4, 32, 32 * 33, 5, 2, 2, None, "exact"),            # B < 256: threads share buckets, odd L
+    (1 << 14, 6, 1024, 2048, 4, 3, 2, None, "noisy"),             # B > 256: several bucket tiles
+    (256, 4, 256, 256, 2, 4, 2, None, "exact"),                   # B = N: one frequency per bucket
+    (4, 1, 2, 4, 1, 5, 2, None, "exact"),                         # smallest sizes
+    (1 << 16, 10, 64, 2368, 8, 6, 2, None, "exact"),              # exactly sparse workload shape
+    (1 << 13, 8, 64, 64 * 34, 16, 7, 2, None, "noisy"),           # L = 16 specialisation
+    (1 << 13, 8, 64, 64 * 34, 7, 8, 2, 7, "noisy"),               # T = L, generic L
+    (1 << 13, 8, 64, 64 * 34, 32, 9, 3, 10, "noisy"),             # L = 32, c = 3
+]
+
+
+def _signal(N, K, seed, kind):
+    if kind == "exact":
+        return signals.make_signal(N, K, seed).x
+    return signals.make_signal(N, K, seed, snr_db=15.0).x
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"N{s[0]}_K{s[1]}_B{s[2]}_L{s[4]}")
+def test_bucketize_matches_oracle(shape):
+    N, K, B, w, L, seed, c, T, kind = shape
+    plan, op = _pair(N, K, B, w, L, seed, c, T)
+    x = _signal(N, K, seed, kind)
+    _, zo = oracle.bucketize(N, B, w, op.sigma, op.tau, op.g, x)
+    zg = run_bucketize(plan, x)
+    assert rel_l2(zg, zo) <= 1e-5
+
+
+def _select_consistent(zo_loop, sel_gpu, nsel):
+    key = np.abs(zo_loop) ** 2
+    order = np.lexsort((np.arange(len(key)), -key))
+    cut = key[order[nsel - 1]]
+    chosen = set(int(k) for k in sel_gpu)
+    assert len(chosen) == nsel
+    for k in range(len(key)):
+        if key[k] > cut * (1 + 1e-5) + 1e-30:
+            assert k in chosen, "a clearly larger bucket was not kept"
+        if key[k] < cut * (1 - 1e-5):
+            assert k not in chosen, "a clearly smaller bucket was kept"
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"N{s[0]}_K{s[1]}_B{s[2]}_L{s[4]}")
+def test_select_matches_oracle(shape):
+    N, K, B, w, L, seed, c, T, kind = shape
+    plan, op = _pair(N, K, B, w, L, seed, c, T)
+    x = _signal(N, K, seed, kind)
+    _, zo = oracle.bucketize(N, B, w, op.sigma, op.tau, op.g, x)
+    zin = zo.astype(np.complex64)
+    sg = run_select(plan, zin)
+    for l in range(L):
+        _select_consistent(zin[l].astype(np.complex128), sg[l], op.nsel)
+
+
+def test_select_exact_ties_go_to_lower_index():
+    N, K, B, w, L = 1 << 12, 5, 64, 64 * 33, 3
+    plan, op = _pair(N, K, B, w, L, 0)
+    rng = np.random.default_rng(0)
+    z = (rng.integers(0, 3, (L, B)) * np.exp(0j)).astype(np.complex64)  # many equal energies
+    sg = run_select(plan, z)
+    for l in range(L):
+        assert np.array_equal(sg[l], oracle.select(B, 2 * K, z[l]))
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"N{s[0]}_K{s[1]}_B{s[2]}_L{s[4]}")
+def test_vote_bit_exact_given_oracle_selection(shape):
+    N, K, B, w, L, seed, c, T, kind = shape
+    plan, op = _pair(N, K, B, w, L, seed, c, T)
+    x = _signal(N, K, seed, kind)
+    ref = oracle.sfft(op, x, intermediates=True)
+    cand = run_vote(plan, ref["sel"])
+    assert np.array_equal(cand, ref["cand"])
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"N{s[0]}_K{s[1]}_B{s[2]}_L{s[4]}")
+def test_estimate_matches_oracle(shape):
+    N, K, B, w, L, seed, c, T, kind = shape
+    plan, op = _pair(N, K, B, w, L, seed, c, T)
+    x = _signal(N, K, seed, kind)
+    ref = oracle.sfft(op, x, intermediates=True)
+    est = run_estimate(plan, ref["zhat"].astype(np.complex64), ref["cand"])
+    assert rel_l2(est, ref["est"]) <= 1e-4
+
+
+def _valid_topk(ref_est_of, gpu_idx, ref_idx, K):
+    """GPU output is a valid top-K of the oracle's estimates: agreement on
+    every rank that is not a near tie."""
+    keys = {f: abs(v) ** 2 for f, v in ref_est_of.items()}
+    ranked = sorted(keys, key=lambda f: (-keys[f], f))
+    kth = keys[ranked[min(K, len(ranked)) - 1]] if ranked else 0.0
+    for f in ranked:
+        if keys[f] > kth * (1 + 1e-4) + 1e-30:
+            assert f in gpu_idx
+    for f in gpu_idx:
+        assert f in keys and keys[f] >= kth * (1 - 1e-4)
+
+
+def _rank_gap(est, K):
+    """Relative gap between the K-th and (K+1)-th largest |est|^2 (inf if fewer)."""
+    keys = np.sort(np.abs(np.asarray(est)) ** 2)[::-1]
+    if len(keys) <= K:
+        return np.inf
+    return (keys[K - 1] - keys[K]) / max(keys[K - 1], 1e-300)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"N{s[0]}_K{s[1]}_B{s[2]}_L{s[4]}")
+def test_execute_matches_oracle(shape):
+    N, K, B, w, L, seed, c, T, kind = shape
+    plan, op = _pair(N, K, B, w, L, seed, c, T)
+    x = _signal(N, K, seed, kind)
+    ref = oracle.sfft(op, x, intermediates=True)
+    idx, val, k = run_execute(plan, x)
+    assert np.all(np.diff(idx) > 0), "output must be sorted by frequency"
+    est_of = dict(zip(ref["cand"].tolist(), ref["est"].tolist()))
+    _valid_topk(est_of, set(idx.tolist()), ref["idx"], K)
+    if _rank_gap(ref["est"], K) > 1e-4:  # no near tie at the K-th rank: unique answer
+        assert k == ref["k_out"]
+        assert np.array_equal(idx, ref["idx"])
+    common, gi, oi = np.intersect1d(idx, ref["idx"], return_indices=True)
+    assert len(common) >= len(ref["idx"]) - 1
+    assert rel_l2(val[gi], ref["val"][oi]) <= 1e-4
+
+
+def test_exact_recovery_workload_seeds():
+    W = configs.EXACT_N16
+    for seed in range(8):
+        sig = signals.make_signal(W.N, W.K, seed)
+        plan = sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, seed)
+        op = oracle.Plan(W.N, W.K, W.B, W.window, W.L, seed)
+        ref = oracle.sfft(op, sig.x)
+        idx, val, k = run_execute(plan, sig.x)
+        assert np.array_equal(idx, sig.freqs) and np.array_equal(idx, ref["idx"])
+        assert rel_l2(val, ref["val"]) <= 1e-4
+
+
+def test_general_sparse_workload_support_agreement():
+    W = configs.GENERAL_N20
+    agree = total = 0
+    for seed in range(3):
+        sig = signals.make_signal(W.N, W.K, seed, W.snr_db)
+        plan = sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, seed)
+        op = oracle.Plan(W.N, W.K, W.B, W.window, W.L, seed)
+        ref = oracle.sfft(op, sig.x)
+        idx, val, k = run_execute(plan, sig.x)
+        common, gi, oi = np.intersect1d(idx, ref["idx"], return_indices=True)
+        agree += len(common)
+        total += len(ref["idx"])
+        assert rel_l2(val[gi], ref["val"][oi]) <= 1e-4
+    assert agree >= 0.999 * total
+
+
+def test_all_zero_signal_ties_by_frequency():
+    # every energy is zero: every selection and every ranking is a tie
+    N, K, B, w, L = 1 << 12, 5, 64, 64 * 33, 4
+    plan, op = _pair(N, K, B, w, L, 3)
+    x = np.zeros(N, np.complex64)
+    ref = oracle.sfft(op, x)
+    idx, val, k = run_execute(plan, x)
+    assert k == ref["k_out"]
+    assert np.array_equal(idx, ref["idx"])
+    assert np.all(val == 0)
+
+
+def test_all_buckets_kept_large_candidate_set():
+    # c*K >= B keeps every bucket: every frequency is a candidate (N > 16384
+    # exercises the multi-pass selection of the top K)
+    N, K, B, w, L = 1 << 15, 10, 16, 16 * 36, 3
+    plan, op = _pair(N, K, B, w, L, 5)
+    for x in (np.zeros(N, np.complex64), signals.make_signal(N, K, 5).x):
+        ref = oracle.sfft(op, x)
+        idx, val, k = run_execute(plan, x)
+        assert k == ref["k_out"] == K
+        assert np.array_equal(idx, ref["idx"])
+        assert rel_l2(val, ref["val"]) <= 1e-4
+
+
+@pytest.mark.parametrize("seed", [0, 3, 5])
+def test_fewer_candidates_than_K(seed):
+    # a zero signal makes every energy an exact tie (kept buckets 0..cK-1 on
+    # both sides), so the candidate set is unique and here smaller than K
+    N, K, B, w, L = 1 << 14, 8, 64, 64 * 35, 4
+    plan, op = _pair(N, K, B, w, L, seed, c=1, T=4)
+    x = np.zeros(N, np.complex64)
+    ref = oracle.sfft(op, x)
+    assert ref["k_out"] < K
+    idx, val, k = run_execute(plan, x)
+    assert k == ref["k_out"]
+    assert np.array_equal(idx, ref["idx"])
+    assert np.all(val == 0)
+
+
+def test_dense_spectrum_forces_unpruned_path():
+    # far more large coefficients than K: bucket energies overstate the
+    # estimates, so the pruned pass cannot certify K survivors
+    N, K, B, w, L = 1 << 12, 6, 64, 64 * 33, 6
+    plan, op = _pair(N, K, B, w, L, 13)
+    x = signals.make_signal(N, 600, 13).x
+    ref = oracle.sfft(op, x, intermediates=True)
+    idx, val, k = run_execute(plan, x)
+    est_of = dict(zip(ref["cand"].tolist(), ref["est"].tolist()))
+    _valid_topk(est_of, set(idx.tolist()), ref["idx"], K)
+    common, gi, oi = np.intersect1d(idx, ref["idx"], return_indices=True)
+    assert rel_l2(val[gi], ref["val"][oi]) <= 1e-4
+
+
+def test_repeat_execute_is_deterministic():
+    W = configs.EXACT_N16
+    plan = sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, 1)
+    x = signals.make_signal(W.N, W.K, 1, snr_db=10.0).x
+    a = run_execute(plan, x)
+    b = run_execute(plan, x)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_plan_info_and_sampling_count():
+    W = configs.GENERAL_N20
+    plan = sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, 2)
+    info = plan.info
+    op = oracle.Plan(W.N, W.K, W.B, W.window, W.L, 2)
+    assert info.samples_touched == oracle.samples_touched(W.N, W.window, op.sigma, op.tau)
+    assert info.nsel == 200 and info.T == 6
+    s, t, si = sfft.sfft_plan_get_loops(plan)
+    assert s == list(op.sigma) and t == list(op.tau) and si == list(op.sigma_inv)
