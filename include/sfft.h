@@ -141,6 +141,25 @@ sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_de
                                int32_t *const *idx_dev, float *const *val_dev, int32_t *k_out_dev,
                                int32_t count, void *stream);
 
+/* Measurement form of sfft_execute_batch: enqueues `steps` back-to-back runs
+   of the batch on `stream` (no graph) with CUDA events recorded on that
+   stream around each of the five stage launches (gather-fold, FFT+select,
+   vote, vote fallback, top-K), waits for the last one, and returns the
+   device time from the first event to the last (*total_ms) and the summed
+   time of each stage over all steps (stage_ms[5]).  Errors as for
+   sfft_execute_batch. */
+sfft_status sfft_execute_batch_timed(sfft_plan *const *plans, const float *const *x_dev,
+                                     int32_t *const *idx_dev, float *const *val_dev,
+                                     int32_t *k_out_dev, int32_t count, int32_t steps,
+                                     float *total_ms, float *stage_ms, void *stream);
+
+/* Batch with HOST buffers: copies each x_host[i] (complex64[N_i]) into a
+   device buffer owned by plans[i], runs the batch, copies idx/val/k_out back
+   to x's host arrays (k_out_host int32[count]) and synchronises the stream. */
+sfft_status sfft_execute_batch_host(sfft_plan *const *plans, const float *const *x_host,
+                                    int32_t *const *idx_host, float *const *val_host,
+                                    int32_t *k_out_host, int32_t count, void *stream);
+
 /* ------------------------------------------------- single stages (tests) */
 /* Each runs one step on caller buffers; the plan's scratch is used for the
    rest.  They exist so that every kernel can be checked on its own. */

@@ -224,17 +224,25 @@ Sizes plan_sizes(const sfft_plan *p) {
     return z;
 }
 
-// G -> S -> V(prune) -> V(fallback) -> top-K, all stream-ordered.
+// G -> S -> V(prune) -> V(fallback) -> top-K, all stream-ordered.  With ev
+// (6 events) the events are recorded around the five launches.
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &lk,
-                            const Sizes &z, cudaStream_t s) {
+                            const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
+    auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+    if ((e = mark(0)) != cudaSuccess) return e;
     if ((e = launch_gather(lg, z.gather, s)) != cudaSuccess) return e;
+    if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
+    if ((e = mark(2)) != cudaSuccess) return e;
     if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.max_flags, nullptr, nullptr, s)) != cudaSuccess)
         return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
     if ((e = launch_vote(lv, z.vote, kVoteFallback, z.L_uniform, z.max_flags, nullptr, nullptr, s)) != cudaSuccess)
         return e;
-    return launch_topk(lk, z.jobs, s);
+    if ((e = mark(4)) != cudaSuccess) return e;
+    if ((e = launch_topk(lk, z.jobs, s)) != cudaSuccess) return e;
+    return mark(5);
 }
 
 Job make_job(const sfft_plan *p, const float *x, int32_t *idx, float *val, int32_t *kout) {
@@ -562,7 +570,8 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
     return b;
 }
 
-cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, cudaStream_t s) {
+cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, cudaStream_t s,
+                         cudaEvent_t *ev = nullptr) {
     const char *base = static_cast<const char *>(dev);
     Launch ln[4];
     for (int k = 0; k < 4; ++k) {
@@ -571,21 +580,17 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         ln[k].njobs = count;
         memset(&ln[k].one, 0, sizeof(Job));
     }
-    return launch_pipeline(ln[0], ln[1], ln[2], ln[3], b.z, s);
+    return launch_pipeline(ln[0], ln[1], ln[2], ln[3], b.z, s, ev);
 }
 
-}  // namespace
-
-extern "C" sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_dev,
-                                          int32_t *const *idx_dev, float *const *val_dev, int32_t *k_out_dev,
-                                          int32_t count, void *stream) {
-    if (count < 0 || (count > 0 && (!plans || !x_dev || !idx_dev || !val_dev || !k_out_dev))) {
+sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,
+                             const void *const *val, const void *kout, int32_t count) {
+    if (count < 0 || (count > 0 && (!plans || !x || !idx || !val || !kout))) {
         set_error("NULL argument or negative count");
         return SFFT_EINVAL;
     }
-    if (count == 0) return SFFT_OK;
     for (int32_t i = 0; i < count; ++i) {
-        if (!plans[i] || !x_dev[i] || !idx_dev[i] || !val_dev[i]) {
+        if (!plans[i] || !x[i] || !idx[i] || !val[i]) {
             set_error("NULL entry in batch arrays");
             return SFFT_EINVAL;
         }
@@ -595,6 +600,17 @@ extern "C" sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *
                 return SFFT_EINVAL;
             }
     }
+    return SFFT_OK;
+}
+
+}  // namespace
+
+extern "C" sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_dev,
+                                          int32_t *const *idx_dev, float *const *val_dev, int32_t *k_out_dev,
+                                          int32_t count, void *stream) {
+    sfft_status st = check_batch_args(plans, (const void *const *)x_dev, (const void *const *)idx_dev,
+                                      (const void *const *)val_dev, k_out_dev, count);
+    if (st != SFFT_OK || count == 0) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int device = 0;
     cudaGetDevice(&device);
@@ -671,6 +687,91 @@ extern "C" sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *
     SFFT_CUDA_TRY(cudaMemcpyAsync(sl.dev, sl.host, b.bytes.size(), cudaMemcpyHostToDevice, s));
     SFFT_CUDA_TRY(launch_batch(b, sl.dev, count, s));
     SFFT_CUDA_TRY(cudaEventRecord(sl.done, s));
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_execute_batch_timed(sfft_plan *const *plans, const float *const *x_dev,
+                                                int32_t *const *idx_dev, float *const *val_dev,
+                                                int32_t *k_out_dev, int32_t count, int32_t steps,
+                                                float *total_ms, float *stage_ms, void *stream) {
+    sfft_status st = check_batch_args(plans, (const void *const *)x_dev, (const void *const *)idx_dev,
+                                      (const void *const *)val_dev, k_out_dev, count);
+    if (st != SFFT_OK) return st;
+    if (count == 0 || steps < 1 || !total_ms || !stage_ms) {
+        set_error("timed batch needs count >= 1, steps >= 1 and output pointers");
+        return SFFT_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchLayout b = build_batch(plans, x_dev, idx_dev, val_dev, k_out_dev, count);
+    void *dev = nullptr;
+    SFFT_CUDA_TRY(cudaMalloc(&dev, b.bytes.size()));
+    std::vector<cudaEvent_t> ev((size_t)steps * 6, nullptr);
+    cudaError_t e = cudaMemcpy(dev, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice);
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    for (int32_t k = 0; k < steps && e == cudaSuccess; ++k) e = launch_batch(b, dev, count, s, &ev[(size_t)k * 6]);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+    if (e == cudaSuccess) {
+        for (int i = 0; i < 5; ++i) stage_ms[i] = 0.f;
+        for (int32_t k = 0; k < steps && e == cudaSuccess; ++k)
+            for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
+                float ms = 0.f;
+                e = cudaEventElapsedTime(&ms, ev[(size_t)k * 6 + i], ev[(size_t)k * 6 + i + 1]);
+                stage_ms[i] += ms;
+            }
+        if (e == cudaSuccess) e = cudaEventElapsedTime(total_ms, ev.front(), ev.back());
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    cudaFree(dev);
+    if (e != cudaSuccess) return cuda_fail(e, "timed batch");
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_execute_batch_host(sfft_plan *const *plans, const float *const *x_host,
+                                               int32_t *const *idx_host, float *const *val_host,
+                                               int32_t *k_out_host, int32_t count, void *stream) {
+    sfft_status st = check_batch_args(plans, (const void *const *)x_host, (const void *const *)idx_host,
+                                      (const void *const *)val_host, k_out_host, count);
+    if (st != SFFT_OK || count == 0) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<const float *> xd(count);
+    std::vector<int32_t *> id(count);
+    std::vector<float *> vd(count);
+    int32_t *kd = nullptr;
+    for (int32_t i = 0; i < count; ++i) {
+        sfft_plan *p = plans[i];
+        const size_t xb = align256(sizeof(float2) * p->N), ib = align256(sizeof(int32_t) * p->K),
+                     vb = align256(sizeof(float2) * p->K);
+        if (!p->stage) SFFT_CUDA_TRY(cudaMalloc(&p->stage, xb + ib + vb + 256));
+        char *b = static_cast<char *>(p->stage);
+        xd[i] = reinterpret_cast<const float *>(b);
+        id[i] = reinterpret_cast<int32_t *>(b + xb);
+        vd[i] = reinterpret_cast<float *>(b + xb + ib);
+        SFFT_CUDA_TRY(cudaMemcpyAsync(b, x_host[i], sizeof(float2) * p->N, cudaMemcpyHostToDevice, s));
+    }
+    // k_out of the batch lands in the first plan's staging tail, one int per job
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        static thread_local void *kbuf = nullptr;
+        static thread_local int32_t kcap = 0;
+        if (kcap < count) {
+            if (kbuf) cudaFree(kbuf);
+            kbuf = nullptr;
+            kcap = 0;
+            SFFT_CUDA_TRY(cudaMalloc(&kbuf, sizeof(int32_t) * count));
+            kcap = count;
+        }
+        kd = static_cast<int32_t *>(kbuf);
+    }
+    st = sfft_execute_batch(plans, xd.data(), id.data(), vd.data(), kd, count, stream);
+    if (st != SFFT_OK) return st;
+    SFFT_CUDA_TRY(cudaMemcpyAsync(k_out_host, kd, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
+    for (int32_t i = 0; i < count; ++i) {
+        const sfft_plan *p = plans[i];
+        SFFT_CUDA_TRY(cudaMemcpyAsync(idx_host[i], id[i], sizeof(int32_t) * p->K, cudaMemcpyDeviceToHost, s));
+        SFFT_CUDA_TRY(cudaMemcpyAsync(val_host[i], vd[i], sizeof(float2) * p->K, cudaMemcpyDeviceToHost, s));
+    }
+    SFFT_CUDA_TRY(cudaStreamSynchronize(s));
     return SFFT_OK;
 }
 

@@ -1,4 +1,4 @@
-"""L0 / L1 / L2 error of a recovered sparse spectrum (test infrastructure).
+"""L0 / L1 / L2 error of a recovered sparse spectrum against the exact one.
 
 The paper's platform reports L0, L1 and L2 errors of each result against the
 best result but never defines them (Experimental Setup).  The reading used

@@ -56,6 +56,9 @@ _SIGS = {
     "sfft_execute": (_i32, [_p, _p, _p, _p, _p, _p]),
     "sfft_execute_host": (_i32, [_p, _p, _p, _p, _p, _p]),
     "sfft_execute_batch": (_i32, [_p, _p, _p, _p, _p, _i32, _p]),
+    "sfft_execute_batch_timed": (_i32, [_p, _p, _p, _p, _p, _i32, _i32, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float), _p]),
+    "sfft_execute_batch_host": (_i32, [_p, _p, _p, _p, _p, _i32, _p]),
     "sfft_bucketize": (_i32, [_p, _p, _p, _p]),
     "sfft_select": (_i32, [_p, _p, _p, _p]),
     "sfft_vote": (_i32, [_p, _p, _p, _p, _i64, _p]),
@@ -215,6 +218,36 @@ def sfft_execute_batch(plans, xs, idxs, vals, k_out, stream=None):
     _check(lib().sfft_execute_batch(arr([p.handle for p in plans]), arr([_addr(x) for x in xs]),
                                     arr([_addr(i) for i in idxs]), arr([_addr(v) for v in vals]),
                                     _addr(k_out), n, _stream(stream)))
+
+
+STAGES = ("gather_fold", "fft_select", "vote", "vote_fallback", "topk")
+
+
+def sfft_execute_batch_timed(plans, xs, idxs, vals, k_out, steps, stream=None):
+    """Returns (total_ms, {stage: summed ms}) over `steps` back-to-back runs."""
+    n = len(plans)
+    arr = lambda vals_: (_p * n)(*vals_)  # noqa: E731
+    total = ctypes.c_float()
+    stages = (ctypes.c_float * 5)()
+    _check(lib().sfft_execute_batch_timed(arr([p.handle for p in plans]), arr([_addr(x) for x in xs]),
+                                          arr([_addr(i) for i in idxs]), arr([_addr(v) for v in vals]),
+                                          _addr(k_out), n, steps, ctypes.byref(total), stages, _stream(stream)))
+    return total.value, dict(zip(STAGES, list(stages)))
+
+
+def _host_addr(a):
+    if hasattr(a, "ctypes"):
+        return a.ctypes.data
+    return _addr(a)
+
+
+def sfft_execute_batch_host(plans, xs, idxs, vals, k_out, stream=None):
+    """Host-buffer batch: numpy arrays or (pinned) CPU tensors."""
+    n = len(plans)
+    arr = lambda vals_: (_p * n)(*vals_)  # noqa: E731
+    _check(lib().sfft_execute_batch_host(arr([p.handle for p in plans]), arr([_host_addr(x) for x in xs]),
+                                         arr([_host_addr(i) for i in idxs]), arr([_host_addr(v) for v in vals]),
+                                         _host_addr(k_out), n, _stream(stream)))
 
 
 def sfft_bucketize(plan: Plan, x, zhat, stream=None):

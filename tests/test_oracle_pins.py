@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import metrics
+from paper_2012_08238_gb300 import metrics
 from paper_2012_08238_gb300 import configs, signals
 from golden_io import ints, records
 
