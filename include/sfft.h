@@ -183,6 +183,26 @@ sfft_status sfft_vote(sfft_plan *plan, const int32_t *sel_dev, int32_t *cand_dev
 sfft_status sfft_estimate(sfft_plan *plan, const float *zhat_dev, const int32_t *cand_dev,
                           int64_t n_cand, float *est_dev, void *stream);
 
+/* Bucket values (a1+a2, same output as sfft_bucketize) for callers that
+   cannot allocate device memory.  The paper has no counterpart: this exists
+   for processes whose device memory belongs to another allocator (a
+   framework's caching pool, a fixed arena reserved at start-up) or whose
+   steady state cannot afford an allocation that may block, and which
+   therefore cannot create a plan.  Takes the plan sizes and seed directly;
+   x_dev complex64[N] and zhat_dev complex64[L][B] are the caller's device
+   buffers.  Calls no cudaMalloc/cudaFree and no allocating library routine:
+   its only scratch is a 2 MiB array in the library's static device memory
+   (2^18 complex64 partial sums; every device that loads the library holds
+   it until the process exits).  Sizes as for plans, plus L*B <= 262144
+   (SFFT_EINVAL otherwise, with the reason in sfft_last_error).  The first
+   call on each device looks up that array's device address; make that first
+   call before any stream capture.  All calls share the array: calls whose
+   work overlaps on the GPU (different streams, different host threads) race
+   and must be serialised by the caller.  Every scratch entry a call reads
+   is written earlier in the same call, so no clearing is needed. */
+sfft_status sfft_bucketize_noalloc(int64_t N, int32_t B, int64_t w, int32_t L, uint64_t seed,
+                                   const float *x_dev, float *zhat_dev, void *stream);
+
 /* ---------------------------------------------------------------- serving */
 
 typedef struct {

@@ -63,6 +63,7 @@ _SIGS = {
     "sfft_select": (_i32, [_p, _p, _p, _p]),
     "sfft_vote": (_i32, [_p, _p, _p, _p, _i64, _p]),
     "sfft_estimate": (_i32, [_p, _p, _p, _i64, _p, _p]),
+    "sfft_bucketize_noalloc": (_i32, [_i64, _i32, _i64, _i32, _u64, _p, _p, _p]),
     "sfft_server_create": (_i32, [ctypes.POINTER(_p), ctypes.c_size_t, _i32]),
     "sfft_submit": (_i32, [_p, ctypes.POINTER(sfft_request), ctypes.POINTER(_u64)]),
     "sfft_poll": (_i32, [_p, _u64, ctypes.POINTER(sfft_result)]),
@@ -264,6 +265,12 @@ def sfft_vote(plan: Plan, sel, cand, n_cand, cap, stream=None):
 
 def sfft_estimate(plan: Plan, zhat, cand, n_cand, est, stream=None):
     _check(lib().sfft_estimate(plan.handle, _addr(zhat), _addr(cand), n_cand, _addr(est), _stream(stream)))
+
+
+def sfft_bucketize_noalloc(N, B, w, L, seed, x, zhat, stream=None):
+    """Bucket values without allocating (scratch in the library's static
+    device memory); see include/sfft.h for the limits and the sharing rule."""
+    _check(lib().sfft_bucketize_noalloc(N, B, w, L, seed, _addr(x), _addr(zhat), _stream(stream)))
 
 
 class Server:
