@@ -173,7 +173,8 @@ def run_ours(args):
 
     # the oracle pool starts before any GPU work (spawned workers)
     cores = host_cores()
-    pool = oracle_pool(min(cores, args.cpu_signals)) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu and not args.profile
+    pool = oracle_pool(min(cores, args.cpu_signals)) if want_cpu else None
 
     W = WORKLOAD
     S = args.signals
@@ -219,6 +220,12 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed = float(tt.item())
     value = world * S * args.steps / elapsed
+    if args.profile:
+        if pool is not None:
+            pool.close()
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "value": value, "stage_ms": stage_ms}), flush=True)
+        return
 
     # ---- graph replay of the same batch (context)
     torch.cuda.synchronize(dev)
@@ -366,6 +373,8 @@ def main():
     ap.add_argument("--signals", type=int, default=64, help="signals per step (per GPU)")
     ap.add_argument("--cpu-signals", type=int, default=32, help="oracle sample size for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiler runs: only the warm-up and timed steps (no context runs, no CPU baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

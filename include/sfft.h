@@ -108,6 +108,19 @@ sfft_status sfft_plan_get_info(const sfft_plan *plan, sfft_plan_info *info);
 sfft_status sfft_plan_get_loops(const sfft_plan *plan, uint32_t *sigma, uint32_t *tau,
                                 uint32_t *sigma_inv);
 
+/* Counters of the plan's most recent execution (host struct).  Reads device
+   memory synchronously: call after the stream that ran the plan has reached
+   the end of that execution. */
+typedef struct {
+    int64_t candidates;  /* |{f : votes >= T}| */
+    int64_t estimated;   /* candidates the median bound could not exclude */
+    int64_t recorded;    /* estimates kept for the top-K (key >= theta) */
+    int32_t fallback;    /* 1 if the unpruned pass ran (fewer than K recorded) */
+    float theta;         /* prune threshold: 1/4 of the K-th largest bucket energy */
+} sfft_exec_stats;
+
+sfft_status sfft_plan_last_stats(const sfft_plan *plan, sfft_exec_stats *stats);
+
 /* Loop parameters without a plan (host only, no GPU needed): block
    Philox4x64-10(counter = (l,0,0,0), key = (seed,0)) gives words r0, r1;
    sigma_l = 2 (r0 mod N/2) + 1, tau_l = r1 mod N.  Errors: SFFT_EINVAL. */

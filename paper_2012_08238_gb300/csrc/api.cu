@@ -128,7 +128,9 @@ void decompose(PlanDev &P) {
     want = std::max<uint32_t>(1, std::min<uint32_t>(want, P.rounds));
     P.rpc = (P.rounds + want - 1) / want;
     P.nchunk = (P.rounds + P.rpc - 1) / P.rpc;
-    P.vtiles = std::max<uint32_t>(1, std::min<uint32_t>((P.N + 4095) / 4096, 8 * kNumSms));
+    P.vtiles = (P.N + kVoteTileF - 1) / kVoteTileF;  // each tile's survivors fit the CTA's queue
+    P.use_shfl = (P.B >= 32 && P.B <= 512) ? 1u : 0u;
+    P.lbpl = P.use_shfl ? P.logB - 5 : 0u;
 }
 
 struct Layout {
@@ -151,7 +153,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.part = take(sizeof(float2) * P.nchunk * L * B);
     o.zhat = take(sizeof(float2) * L * B);
     o.en = take(sizeof(float) * L * B);
-    o.topk = take(sizeof(float) * L * P.Kl);
+    o.topk = take(sizeof(uint32_t) * L * 32);
     o.sel = take(sizeof(int32_t) * L * P.nsel);
     o.flags = take(sizeof(uint16_t) * L * B);
     o.surv = take(sizeof(uint4) * (size_t)cap);
@@ -183,7 +185,6 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     decompose(P);
     *cap = std::min<int64_t>(N, (int64_t)(L - T + 1) * nsel * (N / B));
     P.cap = (uint32_t)*cap;
-    P.flags_smem = (uint32_t)(L * B * 2) <= (uint32_t)kFlagsSmemBytes;
 }
 
 }  // namespace
@@ -210,6 +211,7 @@ namespace {
 struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0;
+    bool shfl = true;
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -221,13 +223,14 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.max_B = p->h.B;
     z.max_flags = p->h.L * p->h.B * 2;
     z.L_uniform = p->h.L;
+    z.shfl = p->h.use_shfl != 0;
     return z;
 }
 
 // G -> S -> V(prune) -> V(fallback) -> top-K, all stream-ordered.  With ev
 // (6 events) the events are recorded around the five launches.
-cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &lk,
-                            const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &lf,
+                            const Launch &lk, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
@@ -235,10 +238,12 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.max_flags, nullptr, nullptr, s)) != cudaSuccess)
+    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.shfl, z.max_flags, 0, nullptr, nullptr, s)) !=
+        cudaSuccess)
         return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_vote(lv, z.vote, kVoteFallback, z.L_uniform, z.max_flags, nullptr, nullptr, s)) != cudaSuccess)
+    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.shfl, z.max_flags, kFallbackCtas,
+                         nullptr, nullptr, s)) != cudaSuccess)
         return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = launch_topk(lk, z.jobs, s)) != cudaSuccess) return e;
@@ -390,7 +395,7 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     P.partial = reinterpret_cast<float2 *>(base + lay.part);
     P.zhat = reinterpret_cast<float2 *>(base + lay.zhat);
     P.energy = reinterpret_cast<float *>(base + lay.en);
-    P.topkeys = reinterpret_cast<float *>(base + lay.topk);
+    P.packed = reinterpret_cast<uint32_t *>(base + lay.topk);
     P.sel = reinterpret_cast<int32_t *>(base + lay.sel);
     P.flags = reinterpret_cast<uint16_t *>(base + lay.flags);
     P.surv = reinterpret_cast<uint4 *>(base + lay.surv);
@@ -491,6 +496,24 @@ extern "C" sfft_status sfft_plan_get_loops(const sfft_plan *p, uint32_t *sigma, 
     return SFFT_OK;
 }
 
+extern "C" sfft_status sfft_plan_last_stats(const sfft_plan *p, sfft_exec_stats *st) {
+    if (!p || !st) {
+        set_error("NULL argument");
+        return SFFT_EINVAL;
+    }
+    uint32_t c[kNumCounters];
+    SFFT_CUDA_TRY(cudaMemcpy(c, p->h.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    const bool fb = (c[kNGe] < (uint32_t)p->K) && (c[kNGe] < c[kNCand]);
+    st->candidates = c[kNCand];
+    st->estimated = fb ? c[kNSurv2] : c[kNSurv];
+    st->recorded = fb ? c[kNSurv2] : c[kNGe];
+    st->fallback = fb ? 1 : 0;
+    float th;
+    memcpy(&th, &c[kTheta], sizeof(th));
+    st->theta = th;
+    return SFFT_OK;
+}
+
 // ----------------------------------------------------------------- execute
 extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *idx_dev, float *val_dev,
                                     int32_t *k_out_dev, void *stream) {
@@ -499,7 +522,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
         return SFFT_EINVAL;
     }
     const Launch ln = single(make_job(p, x_dev, idx_dev, val_dev, k_out_dev));
-    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
 }
 
@@ -532,8 +555,8 @@ extern "C" sfft_status sfft_execute_host(sfft_plan *p, const float *x_host, int3
 namespace {
 
 struct BatchLayout {
-    std::vector<unsigned char> bytes;  // jobs, then four prefix arrays
-    size_t off_offs[4];
+    std::vector<unsigned char> bytes;  // jobs, then five prefix arrays
+    size_t off_offs[5];
     Sizes z;
 };
 
@@ -541,10 +564,10 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
                         float *const *val, int32_t *kout, int32_t count) {
     BatchLayout b;
     const size_t jb = align256(sizeof(Job) * count), ob = align256(sizeof(uint32_t) * (count + 1));
-    b.bytes.assign(jb + 4 * ob, 0);
+    b.bytes.assign(jb + 5 * ob, 0);
     Job *jobs = reinterpret_cast<Job *>(b.bytes.data());
-    uint32_t *offs[4];
-    for (int k = 0; k < 4; ++k) {
+    uint32_t *offs[5];
+    for (int k = 0; k < 5; ++k) {
         b.off_offs[k] = jb + k * ob;
         offs[k] = reinterpret_cast<uint32_t *>(b.bytes.data() + b.off_offs[k]);
         offs[k][0] = 0;
@@ -559,7 +582,9 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         offs[1][i + 1] = offs[1][i] + s.select;
         offs[2][i + 1] = offs[2][i] + s.vote;
         offs[3][i + 1] = offs[3][i] + 1;
+        offs[4][i + 1] = offs[4][i] + kFallbackCtas;
         z.max_B = std::max(z.max_B, s.max_B);
+        z.shfl = z.shfl && s.shfl;
         z.max_flags = std::max(z.max_flags, s.max_flags);
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
     }
@@ -573,14 +598,14 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
 cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, cudaStream_t s,
                          cudaEvent_t *ev = nullptr) {
     const char *base = static_cast<const char *>(dev);
-    Launch ln[4];
-    for (int k = 0; k < 4; ++k) {
+    Launch ln[5];
+    for (int k = 0; k < 5; ++k) {
         ln[k].jobs = reinterpret_cast<const Job *>(base);
         ln[k].offs = reinterpret_cast<const uint32_t *>(base + b.off_offs[k]);
         ln[k].njobs = count;
         memset(&ln[k].one, 0, sizeof(Job));
     }
-    return launch_pipeline(ln[0], ln[1], ln[2], ln[3], b.z, s, ev);
+    return launch_pipeline(ln[0], ln[1], ln[2], ln[4], ln[3], b.z, s, ev);
 }
 
 sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,
@@ -818,7 +843,7 @@ extern "C" sfft_status sfft_vote(sfft_plan *p, const int32_t *sel_dev, int32_t *
     const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
     SFFT_CUDA_TRY(cudaMemsetAsync(n_cand_dev, 0, sizeof(int32_t), s));
     SFFT_CUDA_TRY(launch_flags_from_sel(p->d, p->h.L, sel_dev, s));
-    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, p->h.L * p->h.B * 2, cand_dev,
+    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, 0, cand_dev,
                               n_cand_dev, s));
     return SFFT_OK;
 }

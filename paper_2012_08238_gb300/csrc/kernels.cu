@@ -168,15 +168,38 @@ __device__ void bitonic_pairs(unsigned long long *a, uint32_t *pay, uint32_t n, 
     }
 }
 
-// Number of entries >= t in a descending list of float bit patterns.
-__device__ uint32_t count_ge(const float *list, uint32_t n, uint32_t t) {
-    uint32_t lo = 0, hi = n;  // answer in [lo, hi]
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (__float_as_uint(__ldcg(list + mid)) >= t) lo = mid + 1;
-        else hi = mid;
+// K-th largest of n non-negative floats (as bit patterns) by four 8-bit radix
+// passes over a 256-bin shared histogram; called by all threads of a block.
+__device__ uint32_t radix_kth_largest(const float *v, uint32_t n, uint32_t k, uint32_t *hist,
+                                      uint32_t *s_prefix, uint32_t *s_need) {
+    if (threadIdx.x == 0) {
+        *s_prefix = 0;
+        *s_need = k;
     }
-    return lo;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int sh = 24 - 8 * pass;
+        const uint32_t pmask = pass == 0 ? 0u : (0xFFFFFFFFu << (sh + 8));
+        for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        const uint32_t prefix = *s_prefix;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t u = __float_as_uint(__ldcg(v + i));
+            if ((u & pmask) == prefix) atomicAdd(&hist[(u >> sh) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t need = *s_need, cum = 0;
+            int d = 255;
+            for (; d > 0; --d) {
+                if (cum + hist[d] >= need) break;
+                cum += hist[d];
+            }
+            *s_need = need - cum;
+            *s_prefix = prefix | ((uint32_t)d << sh);
+        }
+        __syncthreads();
+    }
+    return *s_prefix;
 }
 
 // -------------------------------------------------------------- a2 + a3
@@ -192,6 +215,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_fft_select(Launch ln, int se
     __shared__ uint32_t s_local;
     __shared__ int s_last;
     __shared__ float s_theta;
+    __shared__ uint32_t s_hist[256], s_prefix, s_need;
     if (threadIdx.x == 0) {
         Job j;
         uint32_t loc;
@@ -250,54 +274,58 @@ __global__ void __launch_bounds__(kSelectThreads) k_fft_select(Launch ln, int se
     bitonic_desc(sm, B);
     for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x)
         P.sel[(size_t)l * P.nsel + s] = (int32_t)(~(uint32_t)sm[s]);
-    for (uint32_t s = threadIdx.x; s < P.Kl; s += blockDim.x)
-        P.topkeys[(size_t)l * P.Kl + s] = __uint_as_float((uint32_t)(sm[s] >> 32));
     uint16_t *frow = P.flags + (size_t)l * B;
     for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) frow[k] = 0;
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x) frow[~(uint32_t)sm[s]] = 1;
 
-    // ---- last CTA of the job: theta and strong flags
+    // ---- last CTA of the job: theta and the kept/strong tables
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(P.ctr + kSelDone, 1u) == P.L - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (threadIdx.x < 32) {
-        // theta = 1/4 of the K-th largest bucket energy over all loops: a
-        // guess at a lower bound of the K-th largest estimate (exactness never
-        // depends on it; a guess that is too high triggers the fallback pass)
-        const uint32_t lane = threadIdx.x;
-        float theta = 0.f;
-        if ((uint64_t)P.K <= (uint64_t)P.L * P.Kl) {
-            uint32_t lo = 0, hi = 0xFFFFFFFFu;  // lo satisfies count >= K
-            while (hi - lo > 1) {
-                uint32_t mid = lo + ((hi - lo) >> 1);
-                uint32_t c = lane < P.L ? count_ge(P.topkeys + (size_t)lane * P.Kl, P.Kl, mid) : 0;
-                c = __reduce_add_sync(0xFFFFFFFFu, c);
-                if (c >= P.K) lo = mid;
-                else hi = mid;
-            }
-            theta = 0.25f * __uint_as_float(lo);
+    const uint32_t total = P.L * B;
+    // theta = 1/4 of the K-th largest bucket energy over all loops: a guess at
+    // a lower bound of the K-th largest estimate.  Exactness never depends on
+    // it; a guess that is too high only sends the job to the fallback pass.
+    if (P.K <= total) {
+        const uint32_t kth = radix_kth_largest(P.energy, total, P.K, s_hist, &s_prefix, &s_need);
+        if (threadIdx.x == 0) {
+            float theta = 0.25f * __uint_as_float(kth);
             if (!(theta >= 0.f) || isinf(theta)) theta = 0.f;
-        }
-        if (lane == 0) {
             s_theta = theta;
-            P.ctr[kTheta] = __float_as_uint(theta);
         }
+    } else if (threadIdx.x == 0) {
+        s_theta = 0.f;
     }
     __syncthreads();
+    if (threadIdx.x == 0) P.ctr[kTheta] = __float_as_uint(s_theta);
     // a loop is "strong" for f when |zhat|^2 * max|1/G~|^2 >= theta/2; with
     // fewer than M strong loops the median estimate is provably below theta
     const float thr = 0.5f * s_theta;
     const float gmul = P.ginv2max * (1.0f + 1.0f / 1024.0f);
-    const uint32_t total = P.L * B;
     for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
         const float en = __ldcg(P.energy + e);
-        uint16_t f = __ldcg(reinterpret_cast<const unsigned short *>(P.flags) + e);
+        uint16_t f = __ldcg(reinterpret_cast<const unsigned short *>(P.flags) + e) & 1u;
         if (en * gmul >= thr) f |= 256;
         P.flags[e] = f;
+    }
+    if (P.use_shfl) {
+        __syncthreads();
+        const uint32_t bpl = 1u << P.lbpl;
+        for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
+            const uint32_t ll = idx >> 5, j = idx & 31;
+            const uint16_t *fr = P.flags + (size_t)ll * B + j * bpl;
+            uint32_t word = 0;
+            for (uint32_t b = 0; b < bpl; ++b) {
+                const uint32_t fl = fr[b];
+                word |= (fl & 1u) << b;
+                word |= ((fl >> 8) & 1u) << (16 + b);
+            }
+            P.packed[idx] = word;
+        }
     }
     if (threadIdx.x == 0) {
         P.ctr[kSelDone] = 0;
@@ -380,17 +408,37 @@ __device__ float2 median_estimate(const PlanDev &P, const float2 *zhat, uint32_t
 // --------------------------------------------------------------- a4 + a5
 // Vote scan over all f of a job tile: score(f) = #{l : h_l(f) kept} and the
 // number of strong loops, both from one table lookup per loop.  Candidates
-// (score >= T) are counted; those that can still reach the top K (strong
-// count >= M in the pruned pass, all in the fallback pass) are estimated and
-// appended to the survivor list.
-template <int LT, bool SMEM>
-__global__ void __launch_bounds__(kVoteThreads) k_vote(Launch ln, int mode, int32_t *cand_out,
+// (score >= T) are counted.  Candidates that can still reach the top K
+// (strong count >= M in the pruned pass; every candidate in the fallback
+// pass) are queued in shared memory and estimated by all threads together;
+// the pruned pass records only estimates with key >= theta, the fallback
+// pass records all.
+template <int LT>
+__device__ void flush_queue(const PlanDev &P, const uint32_t *queue, uint32_t qn, int mode, float theta,
+                            uint32_t &my_rec) {
+    for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) {
+        const uint32_t f = queue[i];
+        const float2 v = median_estimate<LT>(P, P.zhat, f);
+        const float key = v.x * v.x + v.y * v.y;
+        if (mode == kVoteFallback || key >= theta) {
+            const uint32_t pos = atomicAdd(P.ctr + (mode == kVotePrune ? kNGe : kNSurv2), 1u);
+            P.surv[pos] = make_uint4(f, __float_as_uint(key), __float_as_uint(v.x), __float_as_uint(v.y));
+            ++my_rec;
+        }
+    }
+}
+
+enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabShfl = 2 };
+
+template <int LT, int TAB>
+__global__ void __launch_bounds__(kVoteThreads) k_vote(Launch ln, int mode, uint32_t fb_ctas, int32_t *cand_out,
                                                        int32_t *ncand_out) {
     extern __shared__ uint16_t tab_s[];
     __shared__ PlanDev P;
     __shared__ Job J;
-    __shared__ uint32_t s_local, s_cand, s_ge;
+    __shared__ uint32_t s_local, s_cand, s_est, s_qn;
     __shared__ int s_skip;
+    __shared__ uint32_t queue[kVoteTileF];
     if (threadIdx.x == 0) {
         Job j;
         uint32_t loc;
@@ -398,7 +446,8 @@ __global__ void __launch_bounds__(kVoteThreads) k_vote(Launch ln, int mode, int3
         J = j;
         s_local = loc;
         s_cand = 0;
-        s_ge = 0;
+        s_est = 0;
+        s_qn = 0;
     }
     __syncthreads();
     load_plan(P, J.p);
@@ -406,8 +455,8 @@ __global__ void __launch_bounds__(kVoteThreads) k_vote(Launch ln, int mode, int3
     if (threadIdx.x == 0) {
         int skip = 0;
         if (mode == kVoteFallback) {
-            const uint32_t nge = P.ctr[kNGe], ns = P.ctr[kNSurv], nc = P.ctr[kNCand];
-            skip = (nge >= P.K) || (ns == nc);
+            const uint32_t nge = P.ctr[kNGe], nc = P.ctr[kNCand];
+            skip = (nge >= P.K) || (nge >= nc);  // the recorded set already decides the top K
         }
         s_skip = skip;
     }
@@ -416,8 +465,9 @@ __global__ void __launch_bounds__(kVoteThreads) k_vote(Launch ln, int mode, int3
 
     const uint32_t L = LT > 0 ? (uint32_t)LT : P.L;
     const uint32_t B = P.B;
+    const uint32_t lane = threadIdx.x & 31;
     const uint16_t *tab = P.flags;
-    if constexpr (SMEM) {
+    if constexpr (TAB == kTabSmem) {
         const uint32_t nw = (L * B) / 2;  // B is even
         const uint32_t *src = reinterpret_cast<const uint32_t *>(P.flags);
         uint32_t *dst = reinterpret_cast<uint32_t *>(tab_s);
@@ -425,73 +475,95 @@ __global__ void __launch_bounds__(kVoteThreads) k_vote(Launch ln, int mode, int3
         __syncthreads();
         tab = tab_s;
     }
+    // register copies of the loop scalings and (shuffle table) of this lane's bucket bits
+    constexpr int LR = LT > 0 ? LT : 1;
+    uint32_t sg[LR], pw[LR];
+    if constexpr (LT > 0) {
+#pragma unroll
+        for (int l = 0; l < LT; ++l) {
+            sg[l] = P.sigma[l];
+            pw[l] = TAB == kTabShfl ? __ldcg(P.packed + l * 32 + lane) : 0u;
+        }
+    }
     const float theta = mode == kVotePrune ? __uint_as_float(P.ctr[kTheta]) : 0.f;
     const uint32_t Mreq = mode == kVotePrune ? P.M : 0u;
     const uint32_t T = P.T, N = P.N, mask = P.mask, half = P.half, shift = P.shift;
-    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lshift = shift + P.lbpl, bmask = (1u << P.lbpl) - 1u;
+    // fields of the per-frequency accumulator: score | strong << sfield
+    constexpr uint32_t sfield = TAB == kTabShfl ? 16 : 8;
+    constexpr uint32_t smask = (1u << sfield) - 1u;
 
     uint32_t per = (N + P.vtiles - 1) / P.vtiles;
-    per = (per + kVoteThreads - 1) / kVoteThreads * kVoteThreads;
-    const uint32_t f0 = s_local * per;
-    const uint32_t f1 = min(N, f0 + per);
-    uint32_t my_cand = 0, my_ge = 0;
-    for (uint32_t base = f0; base < f1; base += kVoteThreads) {
-        const uint32_t f = base + threadIdx.x;
-        const bool valid = f < f1;
-        uint32_t acc = 0;
-        if constexpr (LT > 0) {
+    per = (per + kVoteThreads - 1) / kVoteThreads * kVoteThreads;  // <= kVoteTileF
+    const uint32_t stride = mode == kVoteFallback ? fb_ctas : P.vtiles;
+    uint32_t my_cand = 0, my_rec = 0;
+    for (uint32_t tile = s_local; tile < P.vtiles; tile += stride) {
+        const uint32_t f0 = tile * per;
+        const uint32_t f1 = min(N, f0 + per);
+        for (uint32_t base = f0; base < f1; base += kVoteThreads) {
+            const uint32_t f = base + threadIdx.x;
+            const bool valid = f < f1;
+            uint32_t acc = 0;
+            if constexpr (TAB == kTabShfl) {
 #pragma unroll
-            for (int l = 0; l < LT; ++l) {
-                const uint32_t h = ((P.sigma[l] * f + half) & mask) >> shift;
-                acc += tab[l * B + h];
+                for (int l = 0; l < LT; ++l) {
+                    // bits [logN-5, logN) of q pick the lane, the next lbpl bits down the bucket in it
+                    const uint32_t q = sg[l] * f + half;
+                    const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], q >> lshift);
+                    acc += (w >> ((q >> shift) & bmask)) & 0x10001u;
+                }
+            } else if constexpr (LT > 0) {
+#pragma unroll
+                for (int l = 0; l < LT; ++l) {
+                    const uint32_t h = ((sg[l] * f + half) & mask) >> shift;
+                    acc += tab[l * B + h];
+                }
+            } else {
+                for (uint32_t l = 0; l < L; ++l) {
+                    const uint32_t h = ((P.sigma[l] * f + half) & mask) >> shift;
+                    acc += tab[l * B + h];
+                }
             }
-        } else {
-            for (uint32_t l = 0; l < L; ++l) {
-                const uint32_t h = ((P.sigma[l] * f + half) & mask) >> shift;
-                acc += tab[l * B + h];
+            const bool cand = valid && (acc & smask) >= T;
+            my_cand += cand;
+            if (mode == kVoteCandidates) {
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, cand);
+                if (bal) {
+                    uint32_t b0 = 0;
+                    if (lane == 0) b0 = atomicAdd(reinterpret_cast<uint32_t *>(ncand_out), __popc(bal));
+                    b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+                    if (cand) cand_out[b0 + __popc(bal & lanemask_lt())] = (int32_t)f;
+                }
+                continue;
             }
-        }
-        const bool cand = valid && (acc & 0xFFu) >= T;
-        my_cand += cand;
-        if (mode == kVoteCandidates) {
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, cand);
-            if (bal) {
+            const bool surv = cand && (acc >> sfield) >= Mreq;
+            const uint32_t bs = __ballot_sync(0xFFFFFFFFu, surv);
+            if (bs) {
                 uint32_t b0 = 0;
-                if (lane == 0) b0 = atomicAdd(reinterpret_cast<uint32_t *>(ncand_out), __popc(bal));
+                if (lane == 0) b0 = atomicAdd(&s_qn, __popc(bs));
                 b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-                if (cand) cand_out[b0 + __popc(bal & lanemask_lt())] = (int32_t)f;
-            }
-            continue;
-        }
-        const bool surv = cand && (acc >> 8) >= Mreq;
-        const uint32_t bs = __ballot_sync(0xFFFFFFFFu, surv);
-        if (bs) {
-            uint32_t b0 = 0;
-            const int leader = __ffs(bs) - 1;
-            if (lane == (uint32_t)leader)
-                b0 = atomicAdd(P.ctr + (mode == kVotePrune ? kNSurv : kNSurv2), __popc(bs));
-            b0 = __shfl_sync(0xFFFFFFFFu, b0, leader);
-            if (surv) {
-                const float2 v = median_estimate<LT>(P, P.zhat, f);
-                const float key = v.x * v.x + v.y * v.y;
-                P.surv[b0 + __popc(bs & lanemask_lt())] =
-                    make_uint4(f, __float_as_uint(key), __float_as_uint(v.x), __float_as_uint(v.y));
-                my_ge += key >= theta;
+                if (surv) queue[b0 + __popc(bs & lanemask_lt())] = f;  // < kVoteTileF: one slot per f of the tile
             }
         }
+        if (mode == kVoteCandidates) continue;
+        __syncthreads();
+        const uint32_t qn = s_qn;
+        flush_queue<LT>(P, queue, qn, mode, theta, my_rec);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_est += qn;
+            s_qn = 0;
+        }
+        __syncthreads();
     }
     if (mode == kVoteCandidates) return;
     // block totals
     my_cand = __reduce_add_sync(0xFFFFFFFFu, my_cand);
-    my_ge = __reduce_add_sync(0xFFFFFFFFu, my_ge);
-    if (lane == 0) {
-        if (my_cand) atomicAdd(&s_cand, my_cand);
-        if (my_ge) atomicAdd(&s_ge, my_ge);
-    }
+    if (lane == 0 && my_cand) atomicAdd(&s_cand, my_cand);
     __syncthreads();
     if (threadIdx.x == 0 && mode == kVotePrune) {
         if (s_cand) atomicAdd(P.ctr + kNCand, s_cand);
-        if (s_ge) atomicAdd(P.ctr + kNGe, s_ge);
+        atomicAdd(P.ctr + kNSurv, s_est);
     }
 }
 
@@ -500,8 +572,12 @@ __device__ __forceinline__ unsigned long long surv_key(uint4 r) {
     return ((unsigned long long)r.y << 32) | (uint32_t)(~r.x);  // key desc, then f asc
 }
 
-// One CTA per job: the k_out = min(K, candidates) survivors of largest
-// estimate magnitude (ties to the lower f), written sorted by f.
+// One CTA per job: the k_out = min(K, candidates) recorded estimates of
+// largest magnitude (ties to the lower f), written sorted by f.  Records are
+// those of the pruned pass (key >= theta) when at least K of them exist or
+// they are all the candidates; otherwise those of the fallback pass (every
+// candidate).  Pruned candidates have key < theta, so either set contains
+// the top K of all candidates.
 __global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
     extern __shared__ unsigned long long tk[];  // kTopkSmem keys + kTopkSmem payloads
     uint32_t *pay = reinterpret_cast<uint32_t *>(tk + kTopkSmem);
@@ -519,9 +595,9 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
     load_plan(P, J.p);
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t nge = P.ctr[kNGe], ns = P.ctr[kNSurv], nc = P.ctr[kNCand];
-        const bool fallback = !((nge >= P.K) || (ns == nc));
-        s_S = fallback ? P.ctr[kNSurv2] : ns;
+        const uint32_t nge = P.ctr[kNGe], nc = P.ctr[kNCand];
+        const bool fallback = (nge < P.K) && (nge < nc);
+        s_S = fallback ? P.ctr[kNSurv2] : nge;
         s_kout = min(P.K, nc);
     }
     __syncthreads();
@@ -629,26 +705,29 @@ __global__ void k_flags_from_sel(const PlanDev *pd, const int32_t *sel) {
     }
 }
 
-template <int LT, bool SMEM>
-cudaError_t vote_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, int32_t *cand_out,
-                         int32_t *ncand_out, cudaStream_t s) {
-    auto kern = k_vote<LT, SMEM>;
-    if (SMEM) {
+template <int LT, int TAB>
+cudaError_t vote_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, uint32_t fb_ctas,
+                         int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
+    auto kern = k_vote<LT, TAB>;
+    if (TAB == kTabSmem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<ctas, kVoteThreads, SMEM ? smem : 0, s>>>(ln, mode, cand_out, ncand_out);
+    kern<<<ctas, kVoteThreads, TAB == kTabSmem ? smem : 0, s>>>(ln, mode, fb_ctas, cand_out, ncand_out);
     return cudaGetLastError();
 }
 
-template <bool SMEM>
-cudaError_t vote_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t L, uint32_t smem,
+template <int TAB>
+cudaError_t vote_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t L, uint32_t smem, uint32_t fb_ctas,
                             int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
     switch (L) {
-        case 8: return vote_variant<8, SMEM>(ln, ctas, mode, smem, cand_out, ncand_out, s);
-        case 12: return vote_variant<12, SMEM>(ln, ctas, mode, smem, cand_out, ncand_out, s);
-        case 16: return vote_variant<16, SMEM>(ln, ctas, mode, smem, cand_out, ncand_out, s);
-        default: return vote_variant<0, SMEM>(ln, ctas, mode, smem, cand_out, ncand_out, s);
+        case 8: return vote_variant<8, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 12: return vote_variant<12, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 16: return vote_variant<16, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        default:
+            if (TAB == kTabShfl) return cudaErrorInvalidValue;
+            return vote_variant<0, TAB == kTabShfl ? kTabGlobal : TAB>(ln, ctas, mode, smem, fb_ctas, cand_out,
+                                                                      ncand_out, s);
     }
 }
 
@@ -670,14 +749,16 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
     return cudaGetLastError();
 }
 
-// L_uniform: the common L of all jobs, or 0 when they differ.
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform,
-                        uint32_t max_flags_bytes, int32_t *cand_out, int32_t *ncand_out,
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool shfl,
+                        uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
+    if (shfl && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16))
+        return vote_dispatch_l<kTabShfl>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
-        return vote_dispatch_l<true>(ln, total_ctas, mode, L_uniform, max_flags_bytes, cand_out, ncand_out, s);
-    return vote_dispatch_l<false>(ln, total_ctas, mode, L_uniform, 0, cand_out, ncand_out, s);
+        return vote_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,
+                                         ncand_out, s);
+    return vote_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
 }
 
 cudaError_t launch_topk(const Launch &ln, uint32_t njobs, cudaStream_t s) {

