@@ -1,0 +1,216 @@
+"""Batched execution and the serving loop against the plain per-signal path.
+
+Every stage kernel computes a job's values the same way whether it runs alone
+or inside a batch (integer votes, comparisons-only medians, the same FP32
+arithmetic per job), so batched and served results must equal the plain
+results bit for bit.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from gpu_helpers import run_execute
+from paper_2012_08238_gb300 import configs, sfft, signals
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# (N, K, B, w, L, seed, snr): shuffle-table, shared-table and generic-L jobs mixed
+MIX = [
+    (1 << 16, 10, 64, 2368, 8, 0, None),
+    (1 << 14, 6, 1024, 2048, 4, 1, 15.0),
+    (1 << 15, 12, 128, 128 * 36, 12, 2, 20.0),
+    (1 << 13, 5, 32, 32 * 34, 5, 3, 10.0),
+    (1 << 16, 10, 64, 2368, 8, 4, 30.0),
+]
+
+
+def _setup(mix):
+    plans, xs, idxs, vals, sigs = [], [], [], [], []
+    for N, K, B, w, L, seed, snr in mix:
+        sig = signals.make_signal(N, K, seed, snr)
+        sigs.append(sig)
+        plans.append(sfft.sfft_plan_create(N, K, B, w, L, seed))
+        xs.append(torch.from_numpy(sig.x).cuda())
+        idxs.append(torch.full((K,), -1, dtype=torch.int32, device="cuda"))
+        vals.append(torch.zeros(K, dtype=torch.complex64, device="cuda"))
+    kout = torch.zeros(len(mix), dtype=torch.int32, device="cuda")
+    return plans, xs, idxs, vals, kout, sigs
+
+
+def _collect(idxs, vals, kout):
+    torch.cuda.synchronize()
+    k = kout.cpu().numpy()
+    return [(idxs[i].cpu().numpy()[: k[i]], vals[i].cpu().numpy()[: k[i]]) for i in range(len(idxs))]
+
+
+def _same(a, b):
+    return np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_batch_of_mixed_plans_equals_plain_execute():
+    plans, xs, idxs, vals, kout, sigs = _setup(MIX)
+    ref = [run_execute(p, s.x)[:2] for p, s in zip(plans, sigs)]
+    sfft.sfft_execute_batch(plans, xs, idxs, vals, kout)
+    got = _collect(idxs, vals, kout)
+    for r, g in zip(ref, got):
+        assert _same(r, g)
+
+
+def test_batch_graph_replay_reads_current_inputs():
+    plans, xs, idxs, vals, kout, sigs = _setup(MIX)
+    ref = [run_execute(p, s.x)[:2] for p, s in zip(plans, sigs)]
+    for _ in range(3):  # staging run, graph capture, graph replay
+        for t in idxs:
+            t.fill_(-1)
+        sfft.sfft_execute_batch(plans, xs, idxs, vals, kout)
+        got = _collect(idxs, vals, kout)
+        for r, g in zip(ref, got):
+            assert _same(r, g)
+    # new contents in the same buffers: the replayed graph must see them
+    new = [signals.make_signal(N, K, seed + 100, snr) for (N, K, B, w, L, seed, snr) in MIX]
+    for t, s in zip(xs, new):
+        t.copy_(torch.from_numpy(s.x).cuda())
+    ref2 = [run_execute(p, s.x)[:2] for p, s in zip(plans, new)]
+    sfft.sfft_execute_batch(plans, xs, idxs, vals, kout)
+    got = _collect(idxs, vals, kout)
+    for r, g in zip(ref2, got):
+        assert _same(r, g)
+
+
+def test_batch_rejects_repeated_plan():
+    plans, xs, idxs, vals, kout, sigs = _setup(MIX[:2])
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_execute_batch([plans[0], plans[0]], xs, idxs, vals, kout)
+    assert ei.value.status == sfft.SFFT_EINVAL
+
+
+def test_host_buffer_paths_equal_device_paths():
+    plans, xs, idxs, vals, kout, sigs = _setup(MIX)
+    ref = [run_execute(p, s.x)[:2] for p, s in zip(plans, sigs)]
+    # single plan, host buffers
+    N, K = MIX[0][0], MIX[0][1]
+    ih = np.zeros(K, np.int32)
+    vh = np.zeros(K, np.complex64)
+    kh = np.zeros(1, np.int32)
+    sfft.sfft_execute_host(plans[0], np.ascontiguousarray(sigs[0].x), ih, vh, kh)
+    assert _same(ref[0], (ih[: kh[0]], vh[: kh[0]]))
+    # batch, pinned host buffers
+    xh = [torch.from_numpy(s.x).pin_memory() for s in sigs]
+    ihs = [torch.zeros(m[1], dtype=torch.int32).pin_memory() for m in MIX]
+    vhs = [torch.zeros(m[1], dtype=torch.complex64).pin_memory() for m in MIX]
+    khs = torch.zeros(len(MIX), dtype=torch.int32).pin_memory()
+    sfft.sfft_execute_batch_host(plans, xh, ihs, vhs, khs)
+    for i, r in enumerate(ref):
+        k = int(khs[i])
+        assert _same(r, (ihs[i].numpy()[:k], vhs[i].numpy()[:k]))
+
+
+def test_timed_batch_reports_stage_times():
+    plans, xs, idxs, vals, kout, sigs = _setup(MIX)
+    ref = [run_execute(p, s.x)[:2] for p, s in zip(plans, sigs)]
+    total, stages = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, 3)
+    assert total > 0 and all(v >= 0 for v in stages.values())
+    assert sum(stages.values()) <= total * 1.01
+    got = _collect(idxs, vals, kout)
+    for r, g in zip(ref, got):
+        assert _same(r, g)
+
+
+# ------------------------------------------------------------------ serving
+def _request_buffers(N, K, seed, snr):
+    sig = signals.make_signal(N, K, seed, snr)
+    x = torch.from_numpy(sig.x).cuda()
+    idx = torch.full((K,), -1, dtype=torch.int32, device="cuda")
+    val = torch.zeros(K, dtype=torch.complex64, device="cuda")
+    return sig, x, idx, val
+
+
+def _serve(srv, reqs):
+    """Submit every request, wait for all; returns [(idx, val, result)]."""
+    bufs, tickets = [], []
+    for (N, K, B, w, L, seed, snr) in reqs:
+        sig, x, idx, val = _request_buffers(N, K, seed, snr)
+        bufs.append((x, idx, val))
+        tickets.append(sfft.sfft_submit(srv, N, K, B, w, L, seed, x, idx, val))
+    out = []
+    for t, (x, idx, val) in zip(tickets, bufs):
+        res = sfft.sfft_wait(srv, t, 60000)
+        torch.cuda.synchronize()
+        out.append((idx.cpu().numpy()[: res.k_out], val.cpu().numpy()[: res.k_out], res))
+    return out
+
+
+def test_server_results_equal_alone_and_in_the_mix():
+    srv = sfft.sfft_server_create(4 << 30, 16)
+    probe = (1 << 16, 10, 64, 2368, 8, 77, 20.0)
+    alone = _serve(srv, [probe])[0]
+    rng = np.random.default_rng(0)
+    mix = [MIX[i % len(MIX)][:5] + (1000 + i, float(rng.uniform(0, 40))) for i in range(30)]
+    mix.insert(13, probe)
+    served = _serve(srv, mix)
+    in_mix = served[13]
+    assert np.array_equal(alone[0], in_mix[0]) and np.array_equal(alone[1], in_mix[1])
+    # every served result equals the plain path
+    for (N, K, B, w, L, seed, snr), (idx, val, res) in zip(mix, served):
+        assert res.status == sfft.SFFT_OK and res.latency_ns > 0
+        plan = sfft.sfft_plan_create(N, K, B, w, L, seed)
+        ref = run_execute(plan, signals.make_signal(N, K, seed, snr).x)
+        assert np.array_equal(ref[0], idx) and np.array_equal(ref[1], val)
+        assert res.samples_touched == plan.info.samples_touched
+    srv.destroy()
+
+
+def test_server_pause_wait_timeout_and_resume():
+    srv = sfft.sfft_server_create(1 << 30, 4)
+    sfft.sfft_server_set_paused(srv, True)
+    N, K, B, w, L = 1 << 14, 5, 64, 64 * 35, 6
+    sig, x, idx, val = _request_buffers(N, K, 5, None)
+    t = sfft.sfft_submit(srv, N, K, B, w, L, 5, x, idx, val)
+    assert sfft.sfft_poll(srv, t) is None  # pending
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_wait(srv, t, 100)
+    assert ei.value.status == sfft.SFFT_ETIMEDOUT
+    sfft.sfft_server_set_paused(srv, False)
+    res = sfft.sfft_wait(srv, t, 60000)
+    assert res.status == sfft.SFFT_OK and res.k_out == K
+    torch.cuda.synchronize()
+    assert np.array_equal(idx.cpu().numpy(), sig.freqs)
+    srv.destroy()
+
+
+def test_server_rejects_request_beyond_budget_and_evicts_idle_plans():
+    small = sfft.sfft_server_create(1 << 20, 4)  # 1 MiB: no N=2^20 plan fits
+    W = configs.GENERAL_N20
+    sig, x, idx, val = _request_buffers(1 << 12, 4, 1, None)
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_submit(small, W.N, W.K, W.B, W.window, W.L, 0, x, idx, val)
+    assert ei.value.status == sfft.SFFT_EBUSY
+    small.destroy()
+    # room for about two N=2^16 plans: four different plans must still all be served
+    srv = sfft.sfft_server_create(5 << 20, 2)
+    reqs = [(1 << 16, 10, 64, 2368, 8, s, 20.0) for s in range(4)]
+    out = []
+    for r in reqs:  # one at a time, so each new plan must evict an idle one
+        out += _serve(srv, [r])
+    for (N, K, B, w, L, seed, snr), (i, v, res) in zip(reqs, out):
+        assert res.status == sfft.SFFT_OK
+        plan = sfft.sfft_plan_create(N, K, B, w, L, seed)
+        ref = run_execute(plan, signals.make_signal(N, K, seed, snr).x)
+        assert np.array_equal(ref[0], i)
+    srv.destroy()
+
+
+def test_server_destroy_drains_outstanding_work():
+    srv = sfft.sfft_server_create(2 << 30, 8)
+    bufs = []
+    for s in range(12):
+        sig, x, idx, val = _request_buffers(1 << 14, 5, s, None)
+        bufs.append((sig, x, idx, val))  # buffers stay alive until the server is done
+        sfft.sfft_submit(srv, 1 << 14, 5, 64, 64 * 35, 6, s, x, idx, val)
+    srv.destroy()  # must finish every queued request before returning
+    torch.cuda.synchronize()
+    for sig, x, idx, val in bufs:
+        assert np.array_equal(idx.cpu().numpy(), sig.freqs)
