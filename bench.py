@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2012_08238_gb300 import configs, signals  # noqa: E402
+from paper_2012_08238_gb300 import configs, replicas, signals  # noqa: E402
 
 METRIC = "spectra/s batched+served vs plain at fixed L1 error; p50/p99 ms; HBM GB/s"
 UNIT = "spectra/s"
@@ -147,6 +147,43 @@ def time_oracle(pool, seeds) -> float:
     return max(per.values())
 
 
+def measure_served(sfft, torch, W, xs, dev, n_req, rate, seed=0):
+    """Requests through sfft_submit/sfft_wait: a saturation run (all
+    submitted at once) and a Poisson run at `rate` requests/s; latencies are
+    the server's submit-to-completion times."""
+    S = len(xs)
+    srv = sfft.sfft_server_create(16 << 30, 64)
+    idx = torch.zeros((n_req, W.K), dtype=torch.int32, device=dev)
+    val = torch.zeros((n_req, W.K), dtype=torch.complex64, device=dev)
+
+    def submit(i):
+        return sfft.sfft_submit(srv, W.N, W.K, W.B, W.window, W.L, i % S, xs[i % S], idx[i], val[i])
+
+    def drain(tickets):
+        return [sfft.sfft_wait(srv, t, 120000).latency_ns for t in tickets]
+
+    drain([submit(i) for i in range(min(n_req, 2 * S))])  # plan cache warm-up
+    t0 = time.perf_counter()
+    lat_sat = drain([submit(i) for i in range(n_req)])
+    sat_value = n_req / (time.perf_counter() - t0)
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, n_req)
+    arrivals = np.cumsum(gaps)
+    tickets = []
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        tickets.append(submit(i))
+    lat = drain(tickets)
+    span = time.perf_counter() - t0
+    srv.destroy()
+    lat_ms = np.asarray(lat) / 1e6
+    return {"unit": UNIT, "saturated_value": sat_value,
+            "saturated_p50_ms": float(np.percentile(np.asarray(lat_sat) / 1e6, 50)),
+            "offered_per_s": rate, "value": n_req / span, "requests": n_req,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99))}
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -178,7 +215,7 @@ def run_ours(args):
 
     W = WORKLOAD
     S = args.signals
-    seeds = [rank * S + i for i in range(S)]
+    seeds = replicas.shard(rank, world, S)
     sigs = [signals.make_signal(W.N, W.K, s, W.snr_db) for s in seeds]
     plans = [sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, s) for s in seeds]
     info = plans[0].info
@@ -214,12 +251,8 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop() if clocks else None
-    elapsed = total_ms / 1e3
-    if dist:
-        tt = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    value = world * S * args.steps / elapsed
+    elapsed = replicas.max_over_ranks(total_ms / 1e3, dist, dev)
+    value = replicas.throughput(world * S * args.steps, elapsed)
     if args.profile:
         if pool is not None:
             pool.close()
@@ -251,6 +284,9 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plain_value = S * reps / (e0.elapsed_time(e1) / 1e3)
+
+    # ---- served: requests through the continuous-batching server
+    served = measure_served(sfft, torch, W, xs, dev, args.served_requests, args.served_rate)
 
     # ---- end to end through the host-buffer batch call (pinned host memory)
     xh = [torch.from_numpy(sg.x).pin_memory() for sg in sigs]
@@ -315,7 +351,7 @@ def run_ours(args):
                    "l2": f"no flush: inputs {S * W.N * 8 / 2**20:.0f} MiB and touched sectors "
                          f"{sector_bytes / 2**20:.0f} MiB per step exceed the 129 MB L2"},
         "l1_error": l1, "support_recall": recall,
-        "plain_value": plain_value, "graph_value": graph_value,
+        "plain_value": plain_value, "graph_value": graph_value, "served": served,
         "stage_ms_per_step": per_launch, "stage_share": {k: v / sum(per_launch.values()) for k, v in per_launch.items()},
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
         "roofline": roofline, "roofline_gather": gather_roof,
@@ -373,6 +409,8 @@ def main():
     ap.add_argument("--signals", type=int, default=64, help="signals per step (per GPU)")
     ap.add_argument("--cpu-signals", type=int, default=32, help="oracle sample size for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--served-requests", type=int, default=4096, help="requests per serving run")
+    ap.add_argument("--served-rate", type=float, default=20000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--profile", action="store_true",
                     help="profiler runs: only the warm-up and timed steps (no context runs, no CPU baseline)")
     args = ap.parse_args()
