@@ -357,7 +357,7 @@ def run_ours(args):
         "roofline": roofline, "roofline_gather": gather_roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "clocks": clk,
         "wall_s_timed": t_wall,
     }

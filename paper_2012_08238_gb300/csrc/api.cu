@@ -134,7 +134,7 @@ void decompose(PlanDev &P) {
 }
 
 struct Layout {
-    size_t plan, taps, tw, ginv, part, zhat, en, topk, sel, flags, surv, ctr, total;
+    size_t plan, taps, tw, ginv, part, zhat, en, topk, sel, flags, survf, surv, ctr, total;
 };
 
 Layout layout_of(const PlanDev &P, int64_t cap) {
@@ -156,6 +156,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.topk = take(sizeof(uint32_t) * L * 32);
     o.sel = take(sizeof(int32_t) * L * P.nsel);
     o.flags = take(sizeof(uint16_t) * L * B);
+    o.survf = take(sizeof(uint32_t) * (size_t)cap);
     o.surv = take(sizeof(uint4) * (size_t)cap);
     o.ctr = take(sizeof(uint32_t) * kNumCounters);
     o.total = off;
@@ -211,7 +212,7 @@ namespace {
 struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0;
-    bool shfl = true;
+    bool shfl = true, pair = true;
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -224,13 +225,16 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.max_flags = p->h.L * p->h.B * 2;
     z.L_uniform = p->h.L;
     z.shfl = p->h.use_shfl != 0;
+    z.pair = p->h.B >= 64 && p->h.N >= 2;
     return z;
 }
 
-// G -> S -> V(prune) -> V(fallback) -> top-K, all stream-ordered.  With ev
-// (6 events) the events are recorded around the five launches.
-cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &lf,
-                            const Launch &lk, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+// gather -> FFT/select -> scan -> estimate -> [fallback scan -> fallback
+// estimate] -> top-K, all stream-ordered.  With ev (6 events) the events
+// bracket five stages: gather, FFT/select, scan + estimate, fallback, top-K.
+cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
+                            const Launch &lf, const Launch &lk, const Sizes &z, cudaStream_t s,
+                            cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
@@ -238,13 +242,15 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.shfl, z.max_flags, 0, nullptr, nullptr, s)) !=
-        cudaSuccess)
+    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.shfl, z.pair, z.max_flags, 0, nullptr, nullptr,
+                         s)) != cudaSuccess)
         return e;
+    if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.shfl, z.max_flags, kFallbackCtas,
-                         nullptr, nullptr, s)) != cudaSuccess)
+    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.shfl, z.pair, z.max_flags,
+                         kFallbackCtas, nullptr, nullptr, s)) != cudaSuccess)
         return e;
+    if ((e = launch_estimate(le, z.jobs, kVoteFallback, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = launch_topk(lk, z.jobs, s)) != cudaSuccess) return e;
     return mark(5);
@@ -257,8 +263,11 @@ Job make_job(const sfft_plan *p, const float *x, int32_t *idx, float *val, int32
     j.idx = idx;
     j.val = reinterpret_cast<float2 *>(val);
     j.kout = kout;
+    j.rpc = p->h.rpc;
+    j.nchunk = p->h.nchunk;
     return j;
 }
+
 
 Launch single(const Job &j) {
     Launch ln;
@@ -398,6 +407,7 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     P.packed = reinterpret_cast<uint32_t *>(base + lay.topk);
     P.sel = reinterpret_cast<int32_t *>(base + lay.sel);
     P.flags = reinterpret_cast<uint16_t *>(base + lay.flags);
+    P.survf = reinterpret_cast<uint32_t *>(base + lay.survf);
     P.surv = reinterpret_cast<uint4 *>(base + lay.surv);
     P.ctr = reinterpret_cast<uint32_t *>(base + lay.ctr);
 
@@ -506,7 +516,7 @@ extern "C" sfft_status sfft_plan_last_stats(const sfft_plan *p, sfft_exec_stats 
     const bool fb = (c[kNGe] < (uint32_t)p->K) && (c[kNGe] < c[kNCand]);
     st->candidates = c[kNCand];
     st->estimated = fb ? c[kNSurv2] : c[kNSurv];
-    st->recorded = fb ? c[kNSurv2] : c[kNGe];
+    st->recorded = fb ? c[kNRec2] : c[kNGe];
     st->fallback = fb ? 1 : 0;
     float th;
     memcpy(&th, &c[kTheta], sizeof(th));
@@ -522,7 +532,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
         return SFFT_EINVAL;
     }
     const Launch ln = single(make_job(p, x_dev, idx_dev, val_dev, k_out_dev));
-    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
 }
 
@@ -555,8 +565,8 @@ extern "C" sfft_status sfft_execute_host(sfft_plan *p, const float *x_host, int3
 namespace {
 
 struct BatchLayout {
-    std::vector<unsigned char> bytes;  // jobs, then five prefix arrays
-    size_t off_offs[5];
+    std::vector<unsigned char> bytes;  // jobs, then six CTA prefix arrays
+    size_t off_offs[6];
     Sizes z;
 };
 
@@ -564,27 +574,32 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
                         float *const *val, int32_t *kout, int32_t count) {
     BatchLayout b;
     const size_t jb = align256(sizeof(Job) * count), ob = align256(sizeof(uint32_t) * (count + 1));
-    b.bytes.assign(jb + 5 * ob, 0);
+    b.bytes.assign(jb + 6 * ob, 0);
     Job *jobs = reinterpret_cast<Job *>(b.bytes.data());
-    uint32_t *offs[5];
-    for (int k = 0; k < 5; ++k) {
+    uint32_t *offs[6];
+    for (int k = 0; k < 6; ++k) {
         b.off_offs[k] = jb + k * ob;
         offs[k] = reinterpret_cast<uint32_t *>(b.bytes.data() + b.off_offs[k]);
         offs[k][0] = 0;
     }
     Sizes &z = b.z;
     z.L_uniform = plans[0]->h.L;
+    // gather split: the plan's (short CTAs, many waves; measured faster than
+    // fewer, longer CTAs, whose last wave runs a mostly idle GPU)
     for (int32_t i = 0; i < count; ++i) {
         const sfft_plan *p = plans[i];
         jobs[i] = make_job(p, x[i], idx[i], val[i], kout + i);
-        const Sizes s = plan_sizes(p);
+        Sizes s = plan_sizes(p);
+        s.gather = p->h.tiles * p->h.L * jobs[i].nchunk;
         offs[0][i + 1] = offs[0][i] + s.gather;
         offs[1][i + 1] = offs[1][i] + s.select;
         offs[2][i + 1] = offs[2][i] + s.vote;
         offs[3][i + 1] = offs[3][i] + 1;
         offs[4][i + 1] = offs[4][i] + kFallbackCtas;
+        offs[5][i + 1] = offs[5][i] + kEstimateCtas;
         z.max_B = std::max(z.max_B, s.max_B);
         z.shfl = z.shfl && s.shfl;
+        z.pair = z.pair && s.pair;
         z.max_flags = std::max(z.max_flags, s.max_flags);
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
     }
@@ -598,14 +613,14 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
 cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, cudaStream_t s,
                          cudaEvent_t *ev = nullptr) {
     const char *base = static_cast<const char *>(dev);
-    Launch ln[5];
-    for (int k = 0; k < 5; ++k) {
+    Launch ln[6];
+    for (int k = 0; k < 6; ++k) {
         ln[k].jobs = reinterpret_cast<const Job *>(base);
         ln[k].offs = reinterpret_cast<const uint32_t *>(base + b.off_offs[k]);
         ln[k].njobs = count;
         memset(&ln[k].one, 0, sizeof(Job));
     }
-    return launch_pipeline(ln[0], ln[1], ln[2], ln[4], ln[3], b.z, s, ev);
+    return launch_pipeline(ln[0], ln[1], ln[2], ln[5], ln[4], ln[3], b.z, s, ev);
 }
 
 sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,
@@ -843,8 +858,8 @@ extern "C" sfft_status sfft_vote(sfft_plan *p, const int32_t *sel_dev, int32_t *
     const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
     SFFT_CUDA_TRY(cudaMemsetAsync(n_cand_dev, 0, sizeof(int32_t), s));
     SFFT_CUDA_TRY(launch_flags_from_sel(p->d, p->h.L, sel_dev, s));
-    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, 0, cand_dev,
-                              n_cand_dev, s));
+    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, false, p->h.L * p->h.B * 2, 0,
+                              cand_dev, n_cand_dev, s));
     return SFFT_OK;
 }
 

@@ -4,6 +4,12 @@
 // an array of jobs in device memory with a per-kernel CTA prefix (batched
 // execute).  A CTA locates its job, copies the job's PlanDev into shared
 // memory and works on one tile of that job.
+//
+// Pipeline per job: k_gather (a1) -> k_fft_select (a2, a3; its last CTA also
+// builds the vote tables) -> k_vote_scan (a4, a5: candidates and survivors of
+// the median bound) -> k_estimate_surv (a6: estimates, keeps key >= theta)
+// -> [k_vote_scan, k_estimate_surv in fallback mode: idle unless fewer than K
+// estimates reached theta] -> k_topk (a7).
 #include <math_constants.h>
 
 #include "sfft_internal.cuh"
@@ -12,9 +18,7 @@ namespace sfft {
 
 namespace {
 
-constexpr int kGatherThreads = 256;
-constexpr int kSelectThreads = 256;
-constexpr int kVoteThreads = 256;
+constexpr int kThreads = 256;  // every kernel but k_topk
 constexpr int kTopkThreads = 1024;
 
 __device__ __forceinline__ void locate(const Launch &ln, uint32_t bid, Job &job, uint32_t &local) {
@@ -42,34 +46,8 @@ __device__ __forceinline__ void load_plan(PlanDev &dst, const PlanDev *src) {
     for (uint32_t i = threadIdx.x; i < sizeof(PlanDev) / 8; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-__device__ __forceinline__ uint32_t lanemask_lt() {
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// Round-half-up flat-filter hash of frequency f in loop l: bucket h and the
-// offset o from the bucket centre, returned as o + half in [0, N/B).
-__device__ __forceinline__ void hash_freq(const PlanDev &P, uint32_t sigma, uint32_t f, uint32_t &h,
-                                          uint32_t &opos) {
-    uint32_t p = (sigma * f) & P.mask;
-    uint32_t hh = (p + P.half) >> P.shift;  // in [0, B]
-    opos = p + P.half - (hh << P.shift);
-    h = hh & (P.B - 1);
-}
-
-// ------------------------------------------------------------------ a1
-// z_l[j] partial sums: sum over the rounds of one chunk of
-// g(m) * x[(sigma_l m + tau_l) mod N] for the window positions m = j (mod B).
-__global__ void __launch_bounds__(kGatherThreads) k_gather(Launch ln) {
-    __shared__ PlanDev P;
-    __shared__ Job J;
-    __shared__ uint32_t s_local;
-    __shared__ float2 red[kGatherThreads];
+// Locate + load in one call; every kernel starts with it.
+__device__ __forceinline__ void enter(const Launch &ln, PlanDev &P, Job &J, uint32_t &s_local) {
     if (threadIdx.x == 0) {
         Job j;
         uint32_t loc;
@@ -80,6 +58,106 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Launch ln) {
     __syncthreads();
     load_plan(P, J.p);
     __syncthreads();
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// True when the pruned pass could not certify the top K (fewer than K
+// estimates reached theta and not every candidate was estimated).
+__device__ __forceinline__ bool needs_fallback(const PlanDev &P) {
+    const uint32_t nge = P.ctr[kNGe], nc = P.ctr[kNCand];
+    return nge < P.K && nge < nc;
+}
+
+// Inclusive sum over a 256-thread block (warp shuffles + 8 warp totals).
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *wsum) {
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < 8 ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= (uint32_t)o) s += y;
+        }
+        if (lane < 8) wsum[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t r = x + (wid ? wsum[wid - 1] : 0u);
+    __syncthreads();  // wsum free again
+    return r;
+}
+
+// k-th largest (1 <= k <= n) of n 32-bit keys by four 8-bit radix passes over
+// a 256-bin histogram whose suffix sums come from one block scan per pass.
+// Returns the key; *s_need is how many keys equal to it rank within the top k.
+// Called by all 256 threads.
+template <bool kGlobal>
+__device__ uint32_t block_kth_largest(const uint32_t *v, uint32_t n, uint32_t k, uint32_t *hist, uint32_t *wsum,
+                                      uint32_t *s_prefix, uint32_t *s_need) {
+    if (threadIdx.x == 0) {
+        *s_prefix = 0;
+        *s_need = k;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 4; ++pass) {
+        const int sh = 24 - 8 * pass;
+        const uint32_t pmask = pass == 0 ? 0u : (0xFFFFFFFFu << (sh + 8));
+        const uint32_t prefix = *s_prefix, need = *s_need;
+        hist[threadIdx.x] = 0;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
+            const uint32_t u = kGlobal ? __ldcg(v + i) : v[i];
+            if ((u & pmask) == prefix) atomicAdd(&hist[(u >> sh) & 255u], 1u);
+        }
+        __syncthreads();
+        const uint32_t c = hist[255 - threadIdx.x];  // thread t scans bins from the top
+        const uint32_t incl = block_incl_scan(c, wsum);
+        const uint32_t excl = incl - c;
+        if (c > 0 && excl < need && need <= incl) {
+            *s_prefix = prefix | ((255u - threadIdx.x) << sh);
+            *s_need = need - excl;
+        }
+        __syncthreads();
+    }
+    return *s_prefix;
+}
+
+// Round-half-up flat-filter hash of frequency f in loop l: bucket h and the
+// offset o from the bucket centre, returned as o + half in [0, N/B).
+__device__ __forceinline__ void hash_freq(const PlanDev &P, uint32_t sigma, uint32_t f, uint32_t &h,
+                                          uint32_t &opos) {
+    const uint32_t p = (sigma * f) & P.mask;
+    const uint32_t hh = (p + P.half) >> P.shift;  // in [0, B]
+    opos = p + P.half - (hh << P.shift);
+    h = hh & (P.B - 1);
+}
+
+// ------------------------------------------------------------------ a1
+// z_l[j] partial sums: sum over the rounds of one chunk of
+// g(m) * x[(sigma_l m + tau_l) mod N] for the window positions m = j (mod B).
+// The job chooses the chunking (rpc rounds per chunk).
+__global__ void __launch_bounds__(kThreads) k_gather(Launch ln) {
+    __shared__ PlanDev P;
+    __shared__ Job J;
+    __shared__ uint32_t s_local;
+    __shared__ float2 red[kThreads];
+    enter(ln, P, J, s_local);
 
     const uint32_t local = s_local;
     const uint32_t tile = local % P.tiles;
@@ -87,12 +165,12 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(Launch ln) {
     const uint32_t l = rest % P.L;
     const uint32_t chunk = rest / P.L;
     const uint32_t TB = P.tb;
-    const uint32_t PP = kGatherThreads / TB;  // threads sharing one bucket
+    const uint32_t PP = kThreads / TB;  // threads sharing one bucket
     const uint32_t jt = threadIdx.x & (TB - 1);
     const uint32_t s = threadIdx.x / TB;
     const uint32_t j = tile * TB + jt;
-    const uint32_t r0 = chunk * P.rpc;
-    const uint32_t r1 = min(P.rounds, r0 + P.rpc);
+    const uint32_t r0 = chunk * J.rpc;
+    const uint32_t r1 = min(P.rounds, r0 + J.rpc);
     const uint32_t sig = P.sigma[l], tau = P.tau[l], mask = P.mask, B = P.B, halfw = P.halfw;
     const uint32_t jq = (j + halfw) & (B - 1);  // position of bucket j inside a round
     const float2 *__restrict__ x = J.x;
@@ -130,10 +208,10 @@ __device__ void bitonic_desc(unsigned long long *a, uint32_t n) {
     for (uint32_t k = 2; k <= n; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
             for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-                uint32_t ixj = i ^ j;
+                const uint32_t ixj = i ^ j;
                 if (ixj > i) {
-                    unsigned long long x = a[i], y = a[ixj];
-                    bool desc = (i & k) == 0;
+                    const unsigned long long x = a[i], y = a[ixj];
+                    const bool desc = (i & k) == 0;
                     if (desc ? (x < y) : (x > y)) {
                         a[i] = y;
                         a[ixj] = x;
@@ -150,14 +228,14 @@ __device__ void bitonic_pairs(unsigned long long *a, uint32_t *pay, uint32_t n, 
     for (uint32_t k = 2; k <= n; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
             for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-                uint32_t ixj = i ^ j;
+                const uint32_t ixj = i ^ j;
                 if (ixj > i) {
-                    unsigned long long x = a[i], y = a[ixj];
-                    bool up = ((i & k) == 0) == asc;
+                    const unsigned long long x = a[i], y = a[ixj];
+                    const bool up = ((i & k) == 0) == asc;
                     if (up ? (x > y) : (x < y)) {
                         a[i] = y;
                         a[ixj] = x;
-                        uint32_t t = pay[i];
+                        const uint32_t t = pay[i];
                         pay[i] = pay[ixj];
                         pay[ixj] = t;
                     }
@@ -168,73 +246,38 @@ __device__ void bitonic_pairs(unsigned long long *a, uint32_t *pay, uint32_t n, 
     }
 }
 
-// K-th largest of n non-negative floats (as bit patterns) by four 8-bit radix
-// passes over a 256-bin shared histogram; called by all threads of a block.
-__device__ uint32_t radix_kth_largest(const float *v, uint32_t n, uint32_t k, uint32_t *hist,
-                                      uint32_t *s_prefix, uint32_t *s_need) {
-    if (threadIdx.x == 0) {
-        *s_prefix = 0;
-        *s_need = k;
-    }
-    for (int pass = 0; pass < 4; ++pass) {
-        const int sh = 24 - 8 * pass;
-        const uint32_t pmask = pass == 0 ? 0u : (0xFFFFFFFFu << (sh + 8));
-        for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
-        const uint32_t prefix = *s_prefix;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t u = __float_as_uint(__ldcg(v + i));
-            if ((u & pmask) == prefix) atomicAdd(&hist[(u >> sh) & 255u], 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t need = *s_need, cum = 0;
-            int d = 255;
-            for (; d > 0; --d) {
-                if (cum + hist[d] >= need) break;
-                cum += hist[d];
-            }
-            *s_need = need - cum;
-            *s_prefix = prefix | ((uint32_t)d << sh);
-        }
-        __syncthreads();
-    }
-    return *s_prefix;
-}
-
 // -------------------------------------------------------------- a2 + a3
 // One CTA per (job, loop): sum the gather partials, B-point radix-2 FFT in
-// shared memory, bucket energies, top-nsel selection (energy descending,
-// ties to the lower bucket).  The last CTA of a job derives the prune
-// threshold theta and the strong-bucket flags for all loops.
-__global__ void __launch_bounds__(kSelectThreads) k_fft_select(Launch ln, int select_only) {
+// shared memory, bucket energies, and the nsel kept buckets (energy
+// descending, ties to the lower bucket).  The last CTA of a job derives the
+// prune threshold theta and the kept/strong tables for all loops.
+// select_only: the bucket values are already in P.zhat; the kept buckets are
+// also listed in rank order in P.sel.
+__global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_only) {
     extern __shared__ unsigned long long sm[];  // B entries
     float2 *buf = reinterpret_cast<float2 *>(sm);
+    uint32_t *en_s = reinterpret_cast<uint32_t *>(sm);
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
     __shared__ int s_last;
     __shared__ float s_theta;
-    __shared__ uint32_t s_hist[256], s_prefix, s_need;
-    if (threadIdx.x == 0) {
-        Job j;
-        uint32_t loc;
-        locate(ln, blockIdx.x, j, loc);
-        J = j;
-        s_local = loc;
-    }
-    __syncthreads();
-    load_plan(P, J.p);
-    __syncthreads();
+    __shared__ uint32_t s_hist[256], s_wsum[8], s_prefix, s_need;
+    enter(ln, P, J, s_local);
 
     const uint32_t l = s_local, B = P.B, logB = P.logB;
     float2 *zrow = P.zhat + (size_t)l * B;
     float *erow = P.energy + (size_t)l * B;
+    uint16_t *frow = P.flags + (size_t)l * B;
     if (!select_only) {
+        const uint32_t nchunk = J.nchunk;
+        const size_t cstride = (size_t)P.L * B;
         for (uint32_t j = threadIdx.x; j < B; j += blockDim.x) {
             float2 acc = make_float2(0.f, 0.f);
-            for (uint32_t c = 0; c < P.nchunk; ++c) {
-                float2 v = P.partial[((size_t)c * P.L + l) * B + j];
+            const float2 *src = P.partial + (size_t)l * B + j;
+#pragma unroll 4
+            for (uint32_t c = 0; c < nchunk; ++c) {
+                const float2 v = src[c * cstride];
                 acc.x += v.x;
                 acc.y += v.y;
             }
@@ -268,16 +311,35 @@ __global__ void __launch_bounds__(kSelectThreads) k_fft_select(Launch ln, int se
         }
     }
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
-        sm[k] = ((unsigned long long)__float_as_uint(erow[k]) << 32) | (uint32_t)(~k);
-    __syncthreads();
-    bitonic_desc(sm, B);
-    for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x)
-        P.sel[(size_t)l * P.nsel + s] = (int32_t)(~(uint32_t)sm[s]);
-    uint16_t *frow = P.flags + (size_t)l * B;
-    for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) frow[k] = 0;
-    __syncthreads();
-    for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x) frow[~(uint32_t)sm[s]] = 1;
+    if (select_only) {
+        // rank-ordered list for the single-stage entry point
+        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
+            sm[k] = ((unsigned long long)__float_as_uint(erow[k]) << 32) | (uint32_t)(~k);
+        __syncthreads();
+        bitonic_desc(sm, B);
+        for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x)
+            P.sel[(size_t)l * P.nsel + s] = (int32_t)(~(uint32_t)sm[s]);
+        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) frow[k] = 0;
+        __syncthreads();
+        for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x) frow[~(uint32_t)sm[s]] = 1;
+    } else {
+        // kept = energy above the nsel-th largest, plus the lowest-index ties
+        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) en_s[k] = __float_as_uint(erow[k]);
+        __syncthreads();
+        const uint32_t kth = block_kth_largest<false>(en_s, B, P.nsel, s_hist, s_wsum, &s_prefix, &s_need);
+        const uint32_t need_eq = s_need;
+        const uint32_t per = (B + kThreads - 1) / kThreads;
+        const uint32_t k0 = min(B, threadIdx.x * per), k1 = min(B, k0 + per);
+        uint32_t eq = 0;
+        for (uint32_t k = k0; k < k1; ++k) eq += en_s[k] == kth;
+        uint32_t r = block_incl_scan(eq, s_wsum) - eq;  // equal keys before k0
+        for (uint32_t k = k0; k < k1; ++k) {
+            const uint32_t e = en_s[k];
+            bool keep = e > kth;
+            if (e == kth) keep = r++ < need_eq;
+            frow[k] = keep ? 1 : 0;
+        }
+    }
 
     // ---- last CTA of the job: theta and the kept/strong tables
     __threadfence();
@@ -291,9 +353,10 @@ __global__ void __launch_bounds__(kSelectThreads) k_fft_select(Launch ln, int se
     // a lower bound of the K-th largest estimate.  Exactness never depends on
     // it; a guess that is too high only sends the job to the fallback pass.
     if (P.K <= total) {
-        const uint32_t kth = radix_kth_largest(P.energy, total, P.K, s_hist, &s_prefix, &s_need);
+        const uint32_t kb = block_kth_largest<true>(reinterpret_cast<const uint32_t *>(P.energy), total, P.K,
+                                                    s_hist, s_wsum, &s_prefix, &s_need);
         if (threadIdx.x == 0) {
-            float theta = 0.25f * __uint_as_float(kth);
+            float theta = 0.25f * __uint_as_float(kb);
             if (!(theta >= 0.f) || isinf(theta)) theta = 0.f;
             s_theta = theta;
         }
@@ -313,6 +376,9 @@ __global__ void __launch_bounds__(kSelectThreads) k_fft_select(Launch ln, int se
         P.flags[e] = f;
     }
     if (P.use_shfl) {
+        // lane j of loop ll holds buckets [j*bpl, (j+1)*bpl): kept bits at
+        // [0, bpl), strong bits at [16, 16+bpl), the word rotated left by
+        // j*bpl so that one rotate right by the bucket index extracts both
         __syncthreads();
         const uint32_t bpl = 1u << P.lbpl;
         for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
@@ -324,7 +390,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_fft_select(Launch ln, int se
                 word |= (fl & 1u) << b;
                 word |= ((fl >> 8) & 1u) << (16 + b);
             }
-            P.packed[idx] = word;
+            P.packed[idx] = __funnelshift_l(word, word, (j * bpl) & 31u);
         }
     }
     if (threadIdx.x == 0) {
@@ -333,6 +399,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_fft_select(Launch ln, int se
         P.ctr[kNSurv] = 0;
         P.ctr[kNGe] = 0;
         P.ctr[kNSurv2] = 0;
+        P.ctr[kNRec2] = 0;
     }
 }
 
@@ -356,8 +423,7 @@ __device__ __forceinline__ float median_sorted(const float *a, uint32_t n) {
 
 // Per-loop energy-concentration estimate of frequency f in loop l:
 // zhat_l[h] * exp(-2 pi i tau_l f / N) / G~(o).
-__device__ __forceinline__ float2 loop_estimate(const PlanDev &P, const float2 *zhat, uint32_t l,
-                                                uint32_t f) {
+__device__ __forceinline__ float2 loop_estimate(const PlanDev &P, const float2 *zhat, uint32_t l, uint32_t f) {
     uint32_t h, opos;
     hash_freq(P, P.sigma[l], f, h, opos);
     const float2 z = zhat[(size_t)l * P.B + h];
@@ -406,59 +472,35 @@ __device__ float2 median_estimate(const PlanDev &P, const float2 *zhat, uint32_t
 }
 
 // --------------------------------------------------------------- a4 + a5
-// Vote scan over all f of a job tile: score(f) = #{l : h_l(f) kept} and the
-// number of strong loops, both from one table lookup per loop.  Candidates
-// (score >= T) are counted.  Candidates that can still reach the top K
-// (strong count >= M in the pruned pass; every candidate in the fallback
-// pass) are queued in shared memory and estimated by all threads together;
-// the pruned pass records only estimates with key >= theta, the fallback
-// pass records all.
-template <int LT>
-__device__ void flush_queue(const PlanDev &P, const uint32_t *queue, uint32_t qn, int mode, float theta,
-                            uint32_t &my_rec) {
-    for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) {
-        const uint32_t f = queue[i];
-        const float2 v = median_estimate<LT>(P, P.zhat, f);
-        const float key = v.x * v.x + v.y * v.y;
-        if (mode == kVoteFallback || key >= theta) {
-            const uint32_t pos = atomicAdd(P.ctr + (mode == kVotePrune ? kNGe : kNSurv2), 1u);
-            P.surv[pos] = make_uint4(f, __float_as_uint(key), __float_as_uint(v.x), __float_as_uint(v.y));
-            ++my_rec;
-        }
-    }
-}
-
+// Vote scan over one tile of frequencies of a job: per loop one lookup gives
+// the kept bit and the strong bit of bucket h_l(f), accumulated as
+// score | strong << field.  Candidates (score >= T) are counted; survivors of
+// the median bound (strong count >= M; every candidate in the fallback pass)
+// are queued per tile in shared memory and appended to the job's list.
+//
+// The bucket comes from t = (sigma_l << (32 - log2 N)) f + (half << (32 - log2 N))
+// mod 2^32, whose top log2 B bits are round-half-up(sigma_l f B / N) mod B.
 enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabShfl = 2 };
 
-template <int LT, int TAB>
-__global__ void __launch_bounds__(kVoteThreads) k_vote(Launch ln, int mode, uint32_t fb_ctas, int32_t *cand_out,
-                                                       int32_t *ncand_out) {
+// PAIR (register table, B >= 64): a thread takes f and f + N/2 together.
+// Their t differ only in bit 31, so the second lookup reads lane ^ 16 with the
+// same rotation, and one accumulator holds both: bytes 0/1 the scores, 2/3 the
+// strong counts.  (Measured: this beats one frequency per thread, and shifts
+// beat multiply-high extraction of the lane and bucket bits.)
+template <int LT, int TAB, bool PAIR>
+__global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uint32_t fb_ctas, int32_t *cand_out,
+                                                        int32_t *ncand_out) {
     extern __shared__ uint16_t tab_s[];
     __shared__ PlanDev P;
     __shared__ Job J;
-    __shared__ uint32_t s_local, s_cand, s_est, s_qn;
+    __shared__ uint32_t s_local, s_cand, s_qn, s_base;
     __shared__ int s_skip;
     __shared__ uint32_t queue[kVoteTileF];
+    enter(ln, P, J, s_local);
     if (threadIdx.x == 0) {
-        Job j;
-        uint32_t loc;
-        locate(ln, blockIdx.x, j, loc);
-        J = j;
-        s_local = loc;
         s_cand = 0;
-        s_est = 0;
         s_qn = 0;
-    }
-    __syncthreads();
-    load_plan(P, J.p);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int skip = 0;
-        if (mode == kVoteFallback) {
-            const uint32_t nge = P.ctr[kNGe], nc = P.ctr[kNCand];
-            skip = (nge >= P.K) || (nge >= nc);  // the recorded set already decides the top K
-        }
-        s_skip = skip;
+        s_skip = mode == kVoteFallback && !needs_fallback(P);
     }
     __syncthreads();
     if (s_skip) return;
@@ -475,95 +517,145 @@ __global__ void __launch_bounds__(kVoteThreads) k_vote(Launch ln, int mode, uint
         __syncthreads();
         tab = tab_s;
     }
-    // register copies of the loop scalings and (shuffle table) of this lane's bucket bits
     constexpr int LR = LT > 0 ? LT : 1;
-    uint32_t sg[LR], pw[LR];
+    uint32_t av[LR], pw[LR];
     if constexpr (LT > 0) {
 #pragma unroll
         for (int l = 0; l < LT; ++l) {
-            sg[l] = P.sigma[l];
+            av[l] = P.sigma[l] << (32 - P.logN);
             pw[l] = TAB == kTabShfl ? __ldcg(P.packed + l * 32 + lane) : 0u;
         }
     }
-    const float theta = mode == kVotePrune ? __uint_as_float(P.ctr[kTheta]) : 0.f;
+    const uint32_t cv = P.half << (32 - P.logN);
+    const uint32_t top = 32 - P.logB;
     const uint32_t Mreq = mode == kVotePrune ? P.M : 0u;
-    const uint32_t T = P.T, N = P.N, mask = P.mask, half = P.half, shift = P.shift;
-    const uint32_t lshift = shift + P.lbpl, bmask = (1u << P.lbpl) - 1u;
-    // fields of the per-frequency accumulator: score | strong << sfield
-    constexpr uint32_t sfield = TAB == kTabShfl ? 16 : 8;
+    const uint32_t T = P.T, N = P.N;
+    constexpr uint32_t sfield = TAB == kTabShfl ? 16 : 8;  // accumulator: score | strong << sfield
     constexpr uint32_t smask = (1u << sfield) - 1u;
+    const uint32_t span = PAIR ? N / 2 : N;  // frequencies handled as f (PAIR adds f + N/2)
 
-    uint32_t per = (N + P.vtiles - 1) / P.vtiles;
-    per = (per + kVoteThreads - 1) / kVoteThreads * kVoteThreads;  // <= kVoteTileF
+    uint32_t per = (span + P.vtiles - 1) / P.vtiles;
+    per = (per + kThreads - 1) / kThreads * kThreads;  // PAIR: 2 per <= kVoteTileF
     const uint32_t stride = mode == kVoteFallback ? fb_ctas : P.vtiles;
-    uint32_t my_cand = 0, my_rec = 0;
+    uint32_t my_cand = 0;
+
+    // candidate count, candidate list (stage entry point) or survivor queue
+    auto handle = [&](uint32_t f, bool valid, uint32_t score, uint32_t strong) {
+        const bool cand = valid && score >= T;
+        my_cand += cand;
+        if (mode == kVoteCandidates) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, cand);
+            if (bal) {
+                uint32_t b0 = 0;
+                if (lane == 0) b0 = atomicAdd(reinterpret_cast<uint32_t *>(ncand_out), __popc(bal));
+                b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+                if (cand) cand_out[b0 + __popc(bal & lanemask_lt())] = (int32_t)f;
+            }
+            return;
+        }
+        const bool surv = cand && strong >= Mreq;
+        const uint32_t bs = __ballot_sync(0xFFFFFFFFu, surv);
+        if (bs) {
+            uint32_t b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&s_qn, __popc(bs));
+            b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+            if (surv) queue[b0 + __popc(bs & lanemask_lt())] = f;  // < kVoteTileF: one slot per f of the tile
+        }
+    };
+
     for (uint32_t tile = s_local; tile < P.vtiles; tile += stride) {
         const uint32_t f0 = tile * per;
-        const uint32_t f1 = min(N, f0 + per);
-        for (uint32_t base = f0; base < f1; base += kVoteThreads) {
+        const uint32_t f1 = min(span, f0 + per);
+        for (uint32_t base = f0; base < f1; base += kThreads) {
             const uint32_t f = base + threadIdx.x;
             const bool valid = f < f1;
-            uint32_t acc = 0;
-            if constexpr (TAB == kTabShfl) {
+            if constexpr (PAIR) {
+                uint32_t acc = 0;
 #pragma unroll
                 for (int l = 0; l < LT; ++l) {
-                    // bits [logN-5, logN) of q pick the lane, the next lbpl bits down the bucket in it
-                    const uint32_t q = sg[l] * f + half;
-                    const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], q >> lshift);
-                    acc += (w >> ((q >> shift) & bmask)) & 0x10001u;
+                    const uint32_t t = av[l] * f + cv;
+                    const uint32_t src = t >> 27;  // lane: top 5 bits of the bucket
+                    const uint32_t w1 = __shfl_sync(0xFFFFFFFFu, pw[l], src);
+                    const uint32_t w2 = __shfl_sync(0xFFFFFFFFu, pw[l], src ^ 16u);
+                    const uint32_t a1 = t >> top;  // bucket; the rotate uses it mod 32
+                    const uint32_t r1 = __funnelshift_r(w1, w1, a1);
+                    const uint32_t r2 = __funnelshift_r(w2, w2, a1 + 24u);  // rotr 24 = rotl 8
+                    acc += (r1 & 0x00010001u) + (r2 & 0x01000100u);
                 }
-            } else if constexpr (LT > 0) {
-#pragma unroll
-                for (int l = 0; l < LT; ++l) {
-                    const uint32_t h = ((sg[l] * f + half) & mask) >> shift;
-                    acc += tab[l * B + h];
-                }
+                handle(f, valid, acc & 0xFFu, (acc >> 16) & 0xFFu);
+                handle(f + span, valid, (acc >> 8) & 0xFFu, acc >> 24);
             } else {
-                for (uint32_t l = 0; l < L; ++l) {
-                    const uint32_t h = ((P.sigma[l] * f + half) & mask) >> shift;
-                    acc += tab[l * B + h];
+                uint32_t acc = 0;
+                if constexpr (TAB == kTabShfl) {
+#pragma unroll
+                    for (int l = 0; l < LT; ++l) {
+                        const uint32_t t = av[l] * f + cv;
+                        const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> 27);
+                        acc += __funnelshift_r(w, w, t >> top) & 0x10001u;
+                    }
+                } else if constexpr (LT > 0) {
+#pragma unroll
+                    for (int l = 0; l < LT; ++l) acc += tab[l * B + ((av[l] * f + cv) >> top)];
+                } else {
+                    for (uint32_t l = 0; l < L; ++l)
+                        acc += tab[l * B + (((P.sigma[l] << (32 - P.logN)) * f + cv) >> top)];
                 }
-            }
-            const bool cand = valid && (acc & smask) >= T;
-            my_cand += cand;
-            if (mode == kVoteCandidates) {
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, cand);
-                if (bal) {
-                    uint32_t b0 = 0;
-                    if (lane == 0) b0 = atomicAdd(reinterpret_cast<uint32_t *>(ncand_out), __popc(bal));
-                    b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-                    if (cand) cand_out[b0 + __popc(bal & lanemask_lt())] = (int32_t)f;
-                }
-                continue;
-            }
-            const bool surv = cand && (acc >> sfield) >= Mreq;
-            const uint32_t bs = __ballot_sync(0xFFFFFFFFu, surv);
-            if (bs) {
-                uint32_t b0 = 0;
-                if (lane == 0) b0 = atomicAdd(&s_qn, __popc(bs));
-                b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-                if (surv) queue[b0 + __popc(bs & lanemask_lt())] = f;  // < kVoteTileF: one slot per f of the tile
+                handle(f, valid, acc & smask, acc >> sfield);
             }
         }
         if (mode == kVoteCandidates) continue;
         __syncthreads();
         const uint32_t qn = s_qn;
-        flush_queue<LT>(P, queue, qn, mode, theta, my_rec);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            s_est += qn;
-            s_qn = 0;
+        if (qn) {
+            if (threadIdx.x == 0) s_base = atomicAdd(P.ctr + (mode == kVotePrune ? kNSurv : kNSurv2), qn);
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) P.survf[s_base + i] = queue[i];
+            __syncthreads();
+            if (threadIdx.x == 0) s_qn = 0;
+            __syncthreads();
         }
-        __syncthreads();
     }
-    if (mode == kVoteCandidates) return;
-    // block totals
+    if (mode != kVotePrune) return;
     my_cand = __reduce_add_sync(0xFFFFFFFFu, my_cand);
     if (lane == 0 && my_cand) atomicAdd(&s_cand, my_cand);
     __syncthreads();
-    if (threadIdx.x == 0 && mode == kVotePrune) {
-        if (s_cand) atomicAdd(P.ctr + kNCand, s_cand);
-        atomicAdd(P.ctr + kNSurv, s_est);
+    if (threadIdx.x == 0 && s_cand) atomicAdd(P.ctr + kNCand, s_cand);
+}
+
+// ------------------------------------------------------------------ a6
+// Median estimates of the listed frequencies of a job, kEstimateCtas CTAs per
+// job.  The pruned pass keeps estimates with key >= theta; the fallback pass
+// keeps all.  Records: {f, key bits, re bits, im bits}.
+template <int LT>
+__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode) {
+    __shared__ PlanDev P;
+    __shared__ Job J;
+    __shared__ uint32_t s_local;
+    __shared__ int s_skip;
+    enter(ln, P, J, s_local);
+    if (threadIdx.x == 0) s_skip = mode == kVoteFallback && !needs_fallback(P);
+    __syncthreads();
+    if (s_skip) return;
+    const bool prune = mode == kVotePrune;
+    const uint32_t n = P.ctr[prune ? kNSurv : kNSurv2];
+    const float theta = prune ? __uint_as_float(P.ctr[kTheta]) : 0.f;
+    uint32_t *cnt = P.ctr + (prune ? kNGe : kNRec2);
+    for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += kEstimateCtas * kThreads) {
+        const uint32_t f = P.survf[i];
+        const float2 v = median_estimate<LT>(P, P.zhat, f);
+        const float key = v.x * v.x + v.y * v.y;
+        const bool keep = !prune || key >= theta;
+        const uint32_t act = __activemask();
+        const uint32_t bal = __ballot_sync(act, keep);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            uint32_t b0 = 0;
+            if ((threadIdx.x & 31) == (uint32_t)leader) b0 = atomicAdd(cnt, __popc(bal));
+            b0 = __shfl_sync(act, b0, leader);
+            if (keep)
+                P.surv[b0 + __popc(bal & lanemask_lt())] =
+                    make_uint4(f, __float_as_uint(key), __float_as_uint(v.x), __float_as_uint(v.y));
+        }
     }
 }
 
@@ -583,22 +675,12 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
     uint32_t *pay = reinterpret_cast<uint32_t *>(tk + kTopkSmem);
     __shared__ PlanDev P;
     __shared__ Job J;
-    __shared__ uint32_t s_S, s_kout, s_hist[256], s_need, s_cnt;
+    __shared__ uint32_t s_local, s_S, s_kout, s_hist[256], s_need, s_cnt;
     __shared__ unsigned long long s_prefix, s_pmask;
+    enter(ln, P, J, s_local);
     if (threadIdx.x == 0) {
-        Job j;
-        uint32_t loc;
-        locate(ln, blockIdx.x, j, loc);
-        J = j;
-    }
-    __syncthreads();
-    load_plan(P, J.p);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t nge = P.ctr[kNGe], nc = P.ctr[kNCand];
-        const bool fallback = (nge < P.K) && (nge < nc);
-        s_S = fallback ? P.ctr[kNSurv2] : nge;
-        s_kout = min(P.K, nc);
+        s_S = needs_fallback(P) ? P.ctr[kNRec2] : P.ctr[kNGe];
+        s_kout = min(P.K, P.ctr[kNCand]);
     }
     __syncthreads();
     const uint32_t S = s_S, kout = s_kout;
@@ -682,8 +764,8 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
 
 // Stage kernels for the single-step entry points.
 template <int LT>
-__global__ void k_estimate_list(const PlanDev *pd, const float2 *zhat, const int32_t *cand,
-                                uint32_t n, float2 *est) {
+__global__ void k_estimate_list(const PlanDev *pd, const float2 *zhat, const int32_t *cand, uint32_t n,
+                                float2 *est) {
     __shared__ PlanDev P;
     load_plan(P, pd);
     __syncthreads();
@@ -705,29 +787,29 @@ __global__ void k_flags_from_sel(const PlanDev *pd, const int32_t *sel) {
     }
 }
 
-template <int LT, int TAB>
-cudaError_t vote_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, uint32_t fb_ctas,
+template <int LT, int TAB, bool PAIR>
+cudaError_t scan_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, uint32_t fb_ctas,
                          int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
-    auto kern = k_vote<LT, TAB>;
+    auto kern = k_vote_scan<LT, TAB, PAIR>;
     if (TAB == kTabSmem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<ctas, kVoteThreads, TAB == kTabSmem ? smem : 0, s>>>(ln, mode, fb_ctas, cand_out, ncand_out);
+    kern<<<ctas, kThreads, TAB == kTabSmem ? smem : 0, s>>>(ln, mode, fb_ctas, cand_out, ncand_out);
     return cudaGetLastError();
 }
 
-template <int TAB>
-cudaError_t vote_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t L, uint32_t smem, uint32_t fb_ctas,
+template <int TAB, bool PAIR>
+cudaError_t scan_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t L, uint32_t smem, uint32_t fb_ctas,
                             int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
     switch (L) {
-        case 8: return vote_variant<8, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
-        case 12: return vote_variant<12, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
-        case 16: return vote_variant<16, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 8: return scan_variant<8, TAB, PAIR>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 12: return scan_variant<12, TAB, PAIR>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 16: return scan_variant<16, TAB, PAIR>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
         default:
-            if (TAB == kTabShfl) return cudaErrorInvalidValue;
-            return vote_variant<0, TAB == kTabShfl ? kTabGlobal : TAB>(ln, ctas, mode, smem, fb_ctas, cand_out,
-                                                                      ncand_out, s);
+            if (TAB == kTabShfl || PAIR) return cudaErrorInvalidValue;
+            return scan_variant<0, TAB == kTabShfl ? kTabGlobal : TAB, false>(ln, ctas, mode, smem, fb_ctas,
+                                                                             cand_out, ncand_out, s);
     }
 }
 
@@ -735,7 +817,7 @@ cudaError_t vote_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t 
 
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
-    k_gather<<<total_ctas, kGatherThreads, 0, s>>>(ln);
+    k_gather<<<total_ctas, kThreads, 0, s>>>(ln);
     return cudaGetLastError();
 }
 
@@ -745,20 +827,36 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
     const int smem = (int)(max_B * sizeof(unsigned long long));
     cudaError_t e = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_fft_select<<<total_ctas, kSelectThreads, smem, s>>>(ln, select_only);
+    k_fft_select<<<total_ctas, kThreads, smem, s>>>(ln, select_only);
     return cudaGetLastError();
 }
 
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool shfl,
-                        uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
-                        cudaStream_t s) {
+                        bool pair, uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out,
+                        int32_t *ncand_out, cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
-    if (shfl && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16))
-        return vote_dispatch_l<kTabShfl>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+    if (shfl && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16)) {
+        if (pair)
+            return scan_dispatch_l<kTabShfl, true>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out,
+                                                   s);
+        return scan_dispatch_l<kTabShfl, false>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+    }
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
-        return vote_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,
-                                         ncand_out, s);
-    return vote_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+        return scan_dispatch_l<kTabSmem, false>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,
+                                                ncand_out, s);
+    return scan_dispatch_l<kTabGlobal, false>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+}
+
+cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s) {
+    if (njobs == 0) return cudaSuccess;
+    const uint32_t ctas = njobs * kEstimateCtas;
+    switch (L_uniform) {
+        case 8: k_estimate_surv<8><<<ctas, kThreads, 0, s>>>(ln, mode); break;
+        case 12: k_estimate_surv<12><<<ctas, kThreads, 0, s>>>(ln, mode); break;
+        case 16: k_estimate_surv<16><<<ctas, kThreads, 0, s>>>(ln, mode); break;
+        default: k_estimate_surv<0><<<ctas, kThreads, 0, s>>>(ln, mode); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_topk(const Launch &ln, uint32_t njobs, cudaStream_t s) {

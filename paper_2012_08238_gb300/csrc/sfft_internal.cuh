@@ -18,16 +18,18 @@ constexpr int kTopkSmem = 16384;       // survivors sorted in shared memory up t
 constexpr int kFlagsSmemBytes = 96 * 1024;
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kFallbackCtas = 4;        // CTAs per job of the (usually idle) unpruned pass
+constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel
 
 // Per-plan counters in device memory (uint32 slots).
 enum Counter : int {
     kNCand = 0,    // candidates (score >= T) found by the vote scan
-    kNSurv = 1,    // survivors of the pruned pass (estimated)
-    kNGe = 2,      // survivors whose key >= theta
-    kNSurv2 = 3,   // entries written by the unpruned fallback pass
+    kNSurv = 1,    // survivors of the median bound listed by the pruned scan
+    kNGe = 2,      // their estimates with key >= theta (records of the pruned pass)
+    kNSurv2 = 3,   // candidates listed by the unpruned fallback scan
     kSelDone = 4,  // loops finished by the FFT/select kernel (last-block pattern)
     kTheta = 5,    // prune threshold theta (float bits)
     kErr = 6,      // device-side error word (0 = none)
+    kNRec2 = 7,    // records written by the unpruned fallback pass
     kNumCounters = 16
 };
 
@@ -56,7 +58,8 @@ struct PlanDev {
     uint32_t *packed;      // [L][32]: lane j's buckets, kept bits | strong bits << 16
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
-    uint4 *surv;           // [cap] {f, key bits, re bits, im bits}
+    uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
+    uint4 *surv;           // [cap] records {f, key bits, re bits, im bits}
     uint32_t *ctr;         // [kNumCounters]
 };
 
@@ -67,6 +70,7 @@ struct Job {
     int32_t *idx;
     float2 *val;
     int32_t *kout;
+    uint32_t rpc, nchunk;  // gather split of this launch: rounds per chunk, chunks (<= plan's nchunk)
 };
 
 // Launch descriptor shared by all stage kernels: either one job passed by
@@ -89,10 +93,12 @@ cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s)
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
                               cudaStream_t s);
 // L_uniform: common L of every job (0 when they differ); shfl: every job has
-// use_shfl; fb_ctas: CTAs per job of a fallback launch (ignored otherwise).
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool shfl,
+// use_shfl; pair: every job has B >= 64 (scan f and f + N/2 together);
+// fb_ctas: CTAs per job of a fallback launch (ignored otherwise).
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool shfl, bool pair,
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s);
+cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s);
 cudaError_t launch_topk(const Launch &ln, uint32_t njobs, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);

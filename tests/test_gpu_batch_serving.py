@@ -1,9 +1,11 @@
 """Batched execution and the serving loop against the plain per-signal path.
 
-Every stage kernel computes a job's values the same way whether it runs alone
-or inside a batch (integer votes, comparisons-only medians, the same FP32
-arithmetic per job), so batched and served results must equal the plain
-results bit for bit.
+Votes, selections and medians are integer or comparison-only work, but a
+batch may split a job's gather into a different number of chunks than a plain
+call, which reorders FP32 additions.  So the recovered frequencies must be
+identical and the values equal within relative L2 1e-5 (the bucket-value
+tolerance of the parity tests); a batch replayed with the same job list is
+bit-for-bit deterministic.
 """
 import time
 
@@ -47,6 +49,14 @@ def _collect(idxs, vals, kout):
 
 
 def _same(a, b):
+    """Identical support; values within relative L2 1e-5."""
+    if not np.array_equal(a[0], b[0]):
+        return False
+    va, vb = np.asarray(a[1], np.complex128), np.asarray(b[1], np.complex128)
+    return np.linalg.norm(va - vb) <= 1e-5 * max(np.linalg.norm(vb), 1e-30)
+
+
+def _identical(a, b):
     return np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
@@ -62,6 +72,7 @@ def test_batch_of_mixed_plans_equals_plain_execute():
 def test_batch_graph_replay_reads_current_inputs():
     plans, xs, idxs, vals, kout, sigs = _setup(MIX)
     ref = [run_execute(p, s.x)[:2] for p, s in zip(plans, sigs)]
+    first = None
     for _ in range(3):  # staging run, graph capture, graph replay
         for t in idxs:
             t.fill_(-1)
@@ -69,6 +80,10 @@ def test_batch_graph_replay_reads_current_inputs():
         got = _collect(idxs, vals, kout)
         for r, g in zip(ref, got):
             assert _same(r, g)
+        if first is None:
+            first = got
+        for a, b in zip(first, got):
+            assert _identical(a, b)  # same job list: same arithmetic
     # new contents in the same buffers: the replayed graph must see them
     new = [signals.make_signal(N, K, seed + 100, snr) for (N, K, B, w, L, seed, snr) in MIX]
     for t, s in zip(xs, new):
@@ -152,13 +167,13 @@ def test_server_results_equal_alone_and_in_the_mix():
     mix.insert(13, probe)
     served = _serve(srv, mix)
     in_mix = served[13]
-    assert np.array_equal(alone[0], in_mix[0]) and np.array_equal(alone[1], in_mix[1])
+    assert _same((alone[0], alone[1]), (in_mix[0], in_mix[1]))
     # every served result equals the plain path
     for (N, K, B, w, L, seed, snr), (idx, val, res) in zip(mix, served):
         assert res.status == sfft.SFFT_OK and res.latency_ns > 0
         plan = sfft.sfft_plan_create(N, K, B, w, L, seed)
         ref = run_execute(plan, signals.make_signal(N, K, seed, snr).x)
-        assert np.array_equal(ref[0], idx) and np.array_equal(ref[1], val)
+        assert _same(ref[:2], (idx, val))
         assert res.samples_touched == plan.info.samples_touched
     srv.destroy()
 
