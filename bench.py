@@ -311,15 +311,18 @@ def run_ours(args):
     distinct = S * 8 * info.samples_touched  # algorithmic bytes: distinct samples read
     gather_gbs = distinct / (per_launch["gather_fold"] / 1e3) / 1e9
     sector_bytes = S * W.L * W.window * 32
-    lookups = S * W.N * W.L
-    lds_peak = 152 * 32 * sm_max_mhz * 1e6  # conflict-free shared-memory lookups per second
-    vote_rate = lookups / (per_launch["vote"] / 1e3)
-    if dominant == "vote":
-        roofline = {"kernel": "k_vote (vote scan + pruned estimate)", "bound": "alu",
-                    "achieved": vote_rate / 1e12, "peak": lds_peak / 1e12, "unit": "T lookups/s",
-                    "frac": vote_rate / lds_peak, "traffic": None,
-                    "per_unit": f"N*L = {W.N * W.L} table lookups per spectrum",
-                    "peak_source": f"152 SMs x 32 lanes x {sm_max_mhz:.0f} MHz (derived)"}
+    # vote scan: N*L table lookups per spectrum, at least 4 integer lane-ops
+    # each (hash multiply-add, bucket shift, bit extraction, accumulate);
+    # peak = one lane-op per lane per clock on 152 SMs x 128 lanes
+    scan_ops = S * W.N * W.L * 4
+    alu_peak = 152 * 128 * sm_max_mhz * 1e6
+    scan_rate = scan_ops / (per_launch["vote_scan"] / 1e3)
+    if dominant == "vote_scan":
+        roofline = {"kernel": "k_vote_scan (vote scan)", "bound": "alu",
+                    "achieved": scan_rate / 1e12, "peak": alu_peak / 1e12, "unit": "T int lane-ops/s",
+                    "frac": scan_rate / alu_peak, "traffic": None,
+                    "per_unit": f"4 x N x L = {4 * W.N * W.L} lane-ops per spectrum",
+                    "peak_source": f"152 SMs x 128 lanes x {sm_max_mhz:.0f} MHz (derived, recipe unit counts)"}
     else:
         roofline = {"kernel": "k_gather (gather-window-fold)", "bound": "hbm", "achieved": gather_gbs,
                     "peak": hbm_peak, "unit": "GB/s", "frac": gather_gbs / hbm_peak, "traffic": None,

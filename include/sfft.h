@@ -156,11 +156,11 @@ sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_de
 
 /* Measurement form of sfft_execute_batch: enqueues `steps` back-to-back runs
    of the batch on `stream` (no graph) with CUDA events recorded on that
-   stream around each of the five stage launches (gather-fold, FFT+select,
-   vote, vote fallback, top-K), waits for the last one, and returns the
-   device time from the first event to the last (*total_ms) and the summed
-   time of each stage over all steps (stage_ms[5]).  Errors as for
-   sfft_execute_batch. */
+   stream around each of its six stages (gather-fold, FFT+select, vote scan,
+   survivor estimate, fallback scan + estimate, top-K), waits for the last
+   one, and returns the device time from the first event to the last
+   (*total_ms) and the summed time of each stage over all steps
+   (stage_ms[6]).  Errors as for sfft_execute_batch. */
 sfft_status sfft_execute_batch_timed(sfft_plan *const *plans, const float *const *x_dev,
                                      int32_t *const *idx_dev, float *const *val_dev,
                                      int32_t *k_out_dev, int32_t count, int32_t steps,

@@ -230,8 +230,9 @@ Sizes plan_sizes(const sfft_plan *p) {
 }
 
 // gather -> FFT/select -> scan -> estimate -> [fallback scan -> fallback
-// estimate] -> top-K, all stream-ordered.  With ev (6 events) the events
-// bracket five stages: gather, FFT/select, scan + estimate, fallback, top-K.
+// estimate] -> top-K, all stream-ordered.  With ev (kStages + 1 events) the
+// events bracket the stages: gather, FFT/select, scan, estimate, fallback
+// (scan + estimate), top-K.
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
                             const Launch &lf, const Launch &lk, const Sizes &z, cudaStream_t s,
                             cudaEvent_t *ev = nullptr) {
@@ -245,15 +246,16 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.shfl, z.pair, z.max_flags, 0, nullptr, nullptr,
                          s)) != cudaSuccess)
         return e;
-    if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
+    if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess) return e;
+    if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.shfl, z.pair, z.max_flags,
                          kFallbackCtas, nullptr, nullptr, s)) != cudaSuccess)
         return e;
     if ((e = launch_estimate(le, z.jobs, kVoteFallback, z.L_uniform, s)) != cudaSuccess) return e;
-    if ((e = mark(4)) != cudaSuccess) return e;
+    if ((e = mark(5)) != cudaSuccess) return e;
     if ((e = launch_topk(lk, z.jobs, s)) != cudaSuccess) return e;
-    return mark(5);
+    return mark(6);
 }
 
 Job make_job(const sfft_plan *p, const float *x, int32_t *idx, float *val, int32_t *kout) {
@@ -745,17 +747,20 @@ extern "C" sfft_status sfft_execute_batch_timed(sfft_plan *const *plans, const f
     BatchLayout b = build_batch(plans, x_dev, idx_dev, val_dev, k_out_dev, count);
     void *dev = nullptr;
     SFFT_CUDA_TRY(cudaMalloc(&dev, b.bytes.size()));
-    std::vector<cudaEvent_t> ev((size_t)steps * 6, nullptr);
+    constexpr int kStages = 6;
+    std::vector<cudaEvent_t> ev((size_t)steps * (kStages + 1), nullptr);
     cudaError_t e = cudaMemcpy(dev, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice);
     for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
-    for (int32_t k = 0; k < steps && e == cudaSuccess; ++k) e = launch_batch(b, dev, count, s, &ev[(size_t)k * 6]);
+    for (int32_t k = 0; k < steps && e == cudaSuccess; ++k)
+        e = launch_batch(b, dev, count, s, &ev[(size_t)k * (kStages + 1)]);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
     if (e == cudaSuccess) {
-        for (int i = 0; i < 5; ++i) stage_ms[i] = 0.f;
+        for (int i = 0; i < kStages; ++i) stage_ms[i] = 0.f;
         for (int32_t k = 0; k < steps && e == cudaSuccess; ++k)
-            for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
+            for (int i = 0; i < kStages && e == cudaSuccess; ++i) {
                 float ms = 0.f;
-                e = cudaEventElapsedTime(&ms, ev[(size_t)k * 6 + i], ev[(size_t)k * 6 + i + 1]);
+                e = cudaEventElapsedTime(&ms, ev[(size_t)k * (kStages + 1) + i],
+                                         ev[(size_t)k * (kStages + 1) + i + 1]);
                 stage_ms[i] += ms;
             }
         if (e == cudaSuccess) e = cudaEventElapsedTime(total_ms, ev.front(), ev.back());

@@ -404,15 +404,27 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
 }
 
 // ------------------------------------------------------------------ a6
+// Batcher's odd-even merge sort on the next power-of-two number of slots, with
+// every comparator that touches a slot >= N dropped (those slots would hold
+// +inf and never move): 24 comparators for N = 8, 42 for 12, 63 for 16.
 template <int N>
 __device__ __forceinline__ void sort_net(float *a) {
+    constexpr int S = N <= 8 ? 8 : (N <= 16 ? 16 : 32);
 #pragma unroll
-    for (int pass = 0; pass < N; ++pass) {
+    for (int p = 1; p < S; p <<= 1) {
 #pragma unroll
-        for (int i = pass & 1; i + 1 < N; i += 2) {
-            const float x = a[i], y = a[i + 1];
-            a[i] = fminf(x, y);
-            a[i + 1] = fmaxf(x, y);
+        for (int k = p; k >= 1; k >>= 1) {
+#pragma unroll
+            for (int j = k % p; j <= S - 1 - k; j += 2 * k) {
+#pragma unroll
+                for (int i = 0; i < k; ++i) {
+                    if (i + j + k < N && (i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+                        const float x = a[i + j], y = a[i + j + k];
+                        a[i + j] = fminf(x, y);
+                        a[i + j + k] = fmaxf(x, y);
+                    }
+                }
+            }
         }
     }
 }
@@ -431,7 +443,9 @@ __device__ __forceinline__ float2 loop_estimate(const PlanDev &P, const float2 *
     const uint32_t r = (P.tau[l] * f) & P.mask;
     const int32_t rs = (int32_t)(r << (32 - P.logN)) >> (32 - P.logN);  // in [-N/2, N/2)
     float sn, cs;
-    sincospif(2.0f * (float)rs / (float)P.N, &sn, &cs);
+    // the integer reduction above leaves an angle in [-pi, pi), where the
+    // fast intrinsic's absolute error (~2^-21) is far inside the value tolerance
+    __sincosf((float)rs * (2.0f * CUDART_PI_F / (float)P.N), &sn, &cs);
     const float2 zp = make_float2(z.x * cs + z.y * sn, z.y * cs - z.x * sn);
     return cmul(zp, g);
 }

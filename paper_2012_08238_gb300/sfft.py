@@ -233,7 +233,7 @@ def sfft_execute_batch(plans, xs, idxs, vals, k_out, stream=None):
                                     _addr(k_out), n, _stream(stream)))
 
 
-STAGES = ("gather_fold", "fft_select", "vote", "vote_fallback", "topk")
+STAGES = ("gather_fold", "fft_select", "vote_scan", "estimate", "fallback", "topk")
 
 
 def sfft_execute_batch_timed(plans, xs, idxs, vals, k_out, steps, stream=None):
@@ -241,7 +241,7 @@ def sfft_execute_batch_timed(plans, xs, idxs, vals, k_out, steps, stream=None):
     n = len(plans)
     arr = lambda vals_: (_p * n)(*vals_)  # noqa: E731
     total = ctypes.c_float()
-    stages = (ctypes.c_float * 5)()
+    stages = (ctypes.c_float * len(STAGES))()
     _check(lib().sfft_execute_batch_timed(arr([p.handle for p in plans]), arr([_addr(x) for x in xs]),
                                           arr([_addr(i) for i in idxs]), arr([_addr(v) for v in vals]),
                                           _addr(k_out), n, steps, ctypes.byref(total), stages, _stream(stream)))
