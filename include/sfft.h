@@ -112,9 +112,10 @@ sfft_status sfft_plan_get_loops(const sfft_plan *plan, uint32_t *sigma, uint32_t
    memory synchronously: call after the stream that ran the plan has reached
    the end of that execution. */
 typedef struct {
-    int64_t candidates;  /* |{f : votes >= T}| */
-    int64_t estimated;   /* candidates the median bound could not exclude */
-    int64_t recorded;    /* estimates kept for the top-K (key >= theta) */
+    int64_t candidates;  /* |{f : votes >= T}| when the fallback pass ran (it counts
+                            them); -1 otherwise (then at least K exist) */
+    int64_t estimated;   /* frequencies the median bound could not exclude */
+    int64_t recorded;    /* estimates kept for the top-K (candidates, key >= theta) */
     int32_t fallback;    /* 1 if the unpruned pass ran (fewer than K recorded) */
     float theta;         /* prune threshold: 1/4 of the K-th largest bucket energy */
 } sfft_exec_stats;

@@ -129,8 +129,8 @@ void decompose(PlanDev &P) {
     P.rpc = (P.rounds + want - 1) / want;
     P.nchunk = (P.rounds + P.rpc - 1) / P.rpc;
     P.vtiles = (P.N + kVoteTileF - 1) / kVoteTileF;  // each tile's survivors fit the CTA's queue
-    P.use_shfl = (P.B >= 32 && P.B <= 512) ? 1u : 0u;
-    P.lbpl = P.use_shfl ? P.logB - 5 : 0u;
+    P.use_pair = (P.B >= 64 && P.B <= 512) ? 1u : 0u;
+    P.lbpl = P.use_pair ? P.logB - 5 : 0u;
 }
 
 struct Layout {
@@ -212,7 +212,7 @@ namespace {
 struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0;
-    bool shfl = true, pair = true;
+    bool pair = true;
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -224,8 +224,7 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.max_B = p->h.B;
     z.max_flags = p->h.L * p->h.B * 2;
     z.L_uniform = p->h.L;
-    z.shfl = p->h.use_shfl != 0;
-    z.pair = p->h.B >= 64 && p->h.N >= 2;
+    z.pair = p->h.use_pair != 0;
     return z;
 }
 
@@ -243,14 +242,14 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.shfl, z.pair, z.max_flags, 0, nullptr, nullptr,
-                         s)) != cudaSuccess)
+    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.pair, z.max_flags, 0, nullptr, nullptr, s)) !=
+        cudaSuccess)
         return e;
     if ((e = mark(3)) != cudaSuccess) return e;
     if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.shfl, z.pair, z.max_flags,
-                         kFallbackCtas, nullptr, nullptr, s)) != cudaSuccess)
+    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.pair, z.max_flags, kFallbackCtas,
+                         nullptr, nullptr, s)) != cudaSuccess)
         return e;
     if ((e = launch_estimate(le, z.jobs, kVoteFallback, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
@@ -515,8 +514,8 @@ extern "C" sfft_status sfft_plan_last_stats(const sfft_plan *p, sfft_exec_stats 
     }
     uint32_t c[kNumCounters];
     SFFT_CUDA_TRY(cudaMemcpy(c, p->h.ctr, sizeof(c), cudaMemcpyDeviceToHost));
-    const bool fb = (c[kNGe] < (uint32_t)p->K) && (c[kNGe] < c[kNCand]);
-    st->candidates = c[kNCand];
+    const bool fb = c[kNGe] < (uint32_t)p->K;
+    st->candidates = fb ? (int64_t)c[kNCand] : -1;
     st->estimated = fb ? c[kNSurv2] : c[kNSurv];
     st->recorded = fb ? c[kNRec2] : c[kNGe];
     st->fallback = fb ? 1 : 0;
@@ -600,7 +599,6 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         offs[4][i + 1] = offs[4][i] + kFallbackCtas;
         offs[5][i + 1] = offs[5][i] + kEstimateCtas;
         z.max_B = std::max(z.max_B, s.max_B);
-        z.shfl = z.shfl && s.shfl;
         z.pair = z.pair && s.pair;
         z.max_flags = std::max(z.max_flags, s.max_flags);
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
@@ -863,8 +861,8 @@ extern "C" sfft_status sfft_vote(sfft_plan *p, const int32_t *sel_dev, int32_t *
     const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
     SFFT_CUDA_TRY(cudaMemsetAsync(n_cand_dev, 0, sizeof(int32_t), s));
     SFFT_CUDA_TRY(launch_flags_from_sel(p->d, p->h.L, sel_dev, s));
-    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, false, p->h.L * p->h.B * 2, 0,
-                              cand_dev, n_cand_dev, s));
+    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, 0, cand_dev,
+                              n_cand_dev, s));
     return SFFT_OK;
 }
 

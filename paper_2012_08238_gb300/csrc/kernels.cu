@@ -70,12 +70,10 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// True when the pruned pass could not certify the top K (fewer than K
-// estimates reached theta and not every candidate was estimated).
-__device__ __forceinline__ bool needs_fallback(const PlanDev &P) {
-    const uint32_t nge = P.ctr[kNGe], nc = P.ctr[kNCand];
-    return nge < P.K && nge < nc;
-}
+// True when the pruned pass could not certify the top K: fewer than K
+// candidates reached theta.  The fallback pass then records (and counts)
+// every candidate.
+__device__ __forceinline__ bool needs_fallback(const PlanDev &P) { return P.ctr[kNGe] < P.K; }
 
 // Inclusive sum over a 256-thread block (warp shuffles + 8 warp totals).
 __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *wsum) {
@@ -375,20 +373,21 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         if (en * gmul >= thr) f |= 256;
         P.flags[e] = f;
     }
-    if (P.use_shfl) {
-        // lane j of loop ll holds buckets [j*bpl, (j+1)*bpl): kept bits at
-        // [0, bpl), strong bits at [16, 16+bpl), the word rotated left by
-        // j*bpl so that one rotate right by the bucket index extracts both
+    if (P.use_pair) {
+        // lane j of loop ll: strong bits of its buckets [j*bpl, (j+1)*bpl) at
+        // [0, bpl) and of their partners (bucket ^ B/2, lane j ^ 16) at
+        // [16, 16+bpl), the word rotated left by j*bpl so that one rotate right
+        // by the bucket index puts f's bit at 0 and f+N/2's bit at 16
         __syncthreads();
         const uint32_t bpl = 1u << P.lbpl;
         for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
             const uint32_t ll = idx >> 5, j = idx & 31;
-            const uint16_t *fr = P.flags + (size_t)ll * B + j * bpl;
+            const uint16_t *fr = P.flags + (size_t)ll * B;
             uint32_t word = 0;
             for (uint32_t b = 0; b < bpl; ++b) {
-                const uint32_t fl = fr[b];
-                word |= (fl & 1u) << b;
-                word |= ((fl >> 8) & 1u) << (16 + b);
+                const uint32_t h = j * bpl + b;
+                word |= ((fr[h] >> 8) & 1u) << b;
+                word |= ((fr[h ^ (B / 2)] >> 8) & 1u) << (16 + b);
             }
             P.packed[idx] = __funnelshift_l(word, word, (j * bpl) & 31u);
         }
@@ -486,22 +485,23 @@ __device__ float2 median_estimate(const PlanDev &P, const float2 *zhat, uint32_t
 }
 
 // --------------------------------------------------------------- a4 + a5
-// Vote scan over one tile of frequencies of a job: per loop one lookup gives
-// the kept bit and the strong bit of bucket h_l(f), accumulated as
-// score | strong << field.  Candidates (score >= T) are counted; survivors of
-// the median bound (strong count >= M; every candidate in the fallback pass)
-// are queued per tile in shared memory and appended to the job's list.
+// Vote scan over one tile of frequencies of a job.
+//
+// Pruned pass: only frequencies with at least M strong loops can reach the top
+// K (median bound), so they are queued per tile in shared memory and appended
+// to the job's survivor list; whether they are candidates (kept in >= T
+// loops) is checked when they are estimated.  With the register table
+// (64 <= B <= 512, L in {8, 12, 16}) a thread takes f and f + N/2: their hash
+// words differ only in bit 31, so one warp shuffle of the lane's word and one
+// rotate give both strong bits (f at bit 0, f + N/2 at bit 16).
+// Fallback pass and candidate listing: the u16 kept/strong table (shared or
+// global memory); every candidate is counted and listed.
 //
 // The bucket comes from t = (sigma_l << (32 - log2 N)) f + (half << (32 - log2 N))
 // mod 2^32, whose top log2 B bits are round-half-up(sigma_l f B / N) mod B.
-enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabShfl = 2 };
+enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabPair = 2 };
 
-// PAIR (register table, B >= 64): a thread takes f and f + N/2 together.
-// Their t differ only in bit 31, so the second lookup reads lane ^ 16 with the
-// same rotation, and one accumulator holds both: bytes 0/1 the scores, 2/3 the
-// strong counts.  (Measured: this beats one frequency per thread, and shifts
-// beat multiply-high extraction of the lane and bucket bits.)
-template <int LT, int TAB, bool PAIR>
+template <int LT, int TAB>
 __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uint32_t fb_ctas, int32_t *cand_out,
                                                         int32_t *ncand_out) {
     extern __shared__ uint16_t tab_s[];
@@ -537,43 +537,26 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
 #pragma unroll
         for (int l = 0; l < LT; ++l) {
             av[l] = P.sigma[l] << (32 - P.logN);
-            pw[l] = TAB == kTabShfl ? __ldcg(P.packed + l * 32 + lane) : 0u;
+            pw[l] = TAB == kTabPair ? __ldcg(P.packed + l * 32 + lane) : 0u;
         }
     }
     const uint32_t cv = P.half << (32 - P.logN);
     const uint32_t top = 32 - P.logB;
-    const uint32_t Mreq = mode == kVotePrune ? P.M : 0u;
-    const uint32_t T = P.T, N = P.N;
-    constexpr uint32_t sfield = TAB == kTabShfl ? 16 : 8;  // accumulator: score | strong << sfield
-    constexpr uint32_t smask = (1u << sfield) - 1u;
-    const uint32_t span = PAIR ? N / 2 : N;  // frequencies handled as f (PAIR adds f + N/2)
+    const uint32_t M = P.M, T = P.T, N = P.N;
+    const uint32_t span = TAB == kTabPair ? N / 2 : N;  // f; the pair path adds f + N/2
 
     uint32_t per = (span + P.vtiles - 1) / P.vtiles;
-    per = (per + kThreads - 1) / kThreads * kThreads;  // PAIR: 2 per <= kVoteTileF
+    per = (per + kThreads - 1) / kThreads * kThreads;  // pair path: 2 per <= kVoteTileF
     const uint32_t stride = mode == kVoteFallback ? fb_ctas : P.vtiles;
     uint32_t my_cand = 0;
 
-    // candidate count, candidate list (stage entry point) or survivor queue
-    auto handle = [&](uint32_t f, bool valid, uint32_t score, uint32_t strong) {
-        const bool cand = valid && score >= T;
-        my_cand += cand;
-        if (mode == kVoteCandidates) {
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, cand);
-            if (bal) {
-                uint32_t b0 = 0;
-                if (lane == 0) b0 = atomicAdd(reinterpret_cast<uint32_t *>(ncand_out), __popc(bal));
-                b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-                if (cand) cand_out[b0 + __popc(bal & lanemask_lt())] = (int32_t)f;
-            }
-            return;
-        }
-        const bool surv = cand && strong >= Mreq;
-        const uint32_t bs = __ballot_sync(0xFFFFFFFFu, surv);
+    auto enqueue = [&](uint32_t f, bool take) {
+        const uint32_t bs = __ballot_sync(0xFFFFFFFFu, take);
         if (bs) {
             uint32_t b0 = 0;
             if (lane == 0) b0 = atomicAdd(&s_qn, __popc(bs));
             b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-            if (surv) queue[b0 + __popc(bs & lanemask_lt())] = f;  // < kVoteTileF: one slot per f of the tile
+            if (take) queue[b0 + __popc(bs & lanemask_lt())] = f;  // < kVoteTileF: one slot per f of the tile
         }
     };
 
@@ -583,38 +566,38 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
         for (uint32_t base = f0; base < f1; base += kThreads) {
             const uint32_t f = base + threadIdx.x;
             const bool valid = f < f1;
-            if constexpr (PAIR) {
+            if constexpr (TAB == kTabPair) {
                 uint32_t acc = 0;
 #pragma unroll
                 for (int l = 0; l < LT; ++l) {
                     const uint32_t t = av[l] * f + cv;
-                    const uint32_t src = t >> 27;  // lane: top 5 bits of the bucket
-                    const uint32_t w1 = __shfl_sync(0xFFFFFFFFu, pw[l], src);
-                    const uint32_t w2 = __shfl_sync(0xFFFFFFFFu, pw[l], src ^ 16u);
-                    const uint32_t a1 = t >> top;  // bucket; the rotate uses it mod 32
-                    const uint32_t r1 = __funnelshift_r(w1, w1, a1);
-                    const uint32_t r2 = __funnelshift_r(w2, w2, a1 + 24u);  // rotr 24 = rotl 8
-                    acc += (r1 & 0x00010001u) + (r2 & 0x01000100u);
+                    const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> 27);  // lane: top 5 bucket bits
+                    acc += __funnelshift_r(w, w, t >> top) & 0x10001u;            // rotate by bucket mod 32
                 }
-                handle(f, valid, acc & 0xFFu, (acc >> 16) & 0xFFu);
-                handle(f + span, valid, (acc >> 8) & 0xFFu, acc >> 24);
+                enqueue(f, valid && (acc & 0xFFFFu) >= M);
+                enqueue(f + span, valid && (acc >> 16) >= M);
             } else {
-                uint32_t acc = 0;
-                if constexpr (TAB == kTabShfl) {
-#pragma unroll
-                    for (int l = 0; l < LT; ++l) {
-                        const uint32_t t = av[l] * f + cv;
-                        const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> 27);
-                        acc += __funnelshift_r(w, w, t >> top) & 0x10001u;
-                    }
-                } else if constexpr (LT > 0) {
+                uint32_t acc = 0;  // score | strong << 8
+                if constexpr (LT > 0) {
 #pragma unroll
                     for (int l = 0; l < LT; ++l) acc += tab[l * B + ((av[l] * f + cv) >> top)];
                 } else {
                     for (uint32_t l = 0; l < L; ++l)
                         acc += tab[l * B + (((P.sigma[l] << (32 - P.logN)) * f + cv) >> top)];
                 }
-                handle(f, valid, acc & smask, acc >> sfield);
+                const bool cand = valid && (acc & 0xFFu) >= T;
+                if (mode == kVoteCandidates) {
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, cand);
+                    if (bal) {
+                        uint32_t b0 = 0;
+                        if (lane == 0) b0 = atomicAdd(reinterpret_cast<uint32_t *>(ncand_out), __popc(bal));
+                        b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+                        if (cand) cand_out[b0 + __popc(bal & lanemask_lt())] = (int32_t)f;
+                    }
+                    continue;
+                }
+                my_cand += cand;
+                enqueue(f, mode == kVoteFallback ? cand : cand && (acc >> 8) >= M);
             }
         }
         if (mode == kVoteCandidates) continue;
@@ -629,16 +612,25 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
             __syncthreads();
         }
     }
-    if (mode != kVotePrune) return;
+    if (mode != kVoteFallback) return;
     my_cand = __reduce_add_sync(0xFFFFFFFFu, my_cand);
     if (lane == 0 && my_cand) atomicAdd(&s_cand, my_cand);
     __syncthreads();
     if (threadIdx.x == 0 && s_cand) atomicAdd(P.ctr + kNCand, s_cand);
 }
 
+// kept in at least T loops (the candidate test the register-table scan defers)
+__device__ __forceinline__ bool is_candidate(const PlanDev &P, uint32_t f) {
+    const uint32_t cv = P.half << (32 - P.logN), top = 32 - P.logB;
+    uint32_t score = 0;
+    for (uint32_t l = 0; l < P.L; ++l)
+        score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << (32 - P.logN)) * f + cv) >> top)) & 1u;
+    return score >= P.T;
+}
+
 // ------------------------------------------------------------------ a6
 // Median estimates of the listed frequencies of a job, kEstimateCtas CTAs per
-// job.  The pruned pass keeps estimates with key >= theta; the fallback pass
+// job.  The pruned pass keeps candidates whose key >= theta; the fallback pass
 // keeps all.  Records: {f, key bits, re bits, im bits}.
 template <int LT>
 __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode) {
@@ -656,9 +648,14 @@ __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode)
     uint32_t *cnt = P.ctr + (prune ? kNGe : kNRec2);
     for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += kEstimateCtas * kThreads) {
         const uint32_t f = P.survf[i];
-        const float2 v = median_estimate<LT>(P, P.zhat, f);
-        const float key = v.x * v.x + v.y * v.y;
-        const bool keep = !prune || key >= theta;
+        bool keep = !prune || is_candidate(P, f);
+        float2 v = make_float2(0.f, 0.f);
+        float key = 0.f;
+        if (keep) {
+            v = median_estimate<LT>(P, P.zhat, f);
+            key = v.x * v.x + v.y * v.y;
+            keep = !prune || key >= theta;
+        }
         const uint32_t act = __activemask();
         const uint32_t bal = __ballot_sync(act, keep);
         if (bal) {
@@ -680,10 +677,9 @@ __device__ __forceinline__ unsigned long long surv_key(uint4 r) {
 
 // One CTA per job: the k_out = min(K, candidates) recorded estimates of
 // largest magnitude (ties to the lower f), written sorted by f.  Records are
-// those of the pruned pass (key >= theta) when at least K of them exist or
-// they are all the candidates; otherwise those of the fallback pass (every
-// candidate).  Pruned candidates have key < theta, so either set contains
-// the top K of all candidates.
+// those of the pruned pass (candidates with key >= theta) when at least K of
+// them exist; otherwise those of the fallback pass (every candidate).  Pruned
+// candidates have key < theta, so either set contains the top K.
 __global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
     extern __shared__ unsigned long long tk[];  // kTopkSmem keys + kTopkSmem payloads
     uint32_t *pay = reinterpret_cast<uint32_t *>(tk + kTopkSmem);
@@ -693,8 +689,9 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
     __shared__ unsigned long long s_prefix, s_pmask;
     enter(ln, P, J, s_local);
     if (threadIdx.x == 0) {
-        s_S = needs_fallback(P) ? P.ctr[kNRec2] : P.ctr[kNGe];
-        s_kout = min(P.K, P.ctr[kNCand]);
+        const bool fb = needs_fallback(P);
+        s_S = fb ? P.ctr[kNRec2] : P.ctr[kNGe];
+        s_kout = fb ? min(P.K, P.ctr[kNCand]) : P.K;  // without fallback >= K candidates exist
     }
     __syncthreads();
     const uint32_t S = s_S, kout = s_kout;
@@ -801,10 +798,10 @@ __global__ void k_flags_from_sel(const PlanDev *pd, const int32_t *sel) {
     }
 }
 
-template <int LT, int TAB, bool PAIR>
+template <int LT, int TAB>
 cudaError_t scan_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, uint32_t fb_ctas,
                          int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
-    auto kern = k_vote_scan<LT, TAB, PAIR>;
+    auto kern = k_vote_scan<LT, TAB>;
     if (TAB == kTabSmem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -813,17 +810,17 @@ cudaError_t scan_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t sme
     return cudaGetLastError();
 }
 
-template <int TAB, bool PAIR>
+template <int TAB>
 cudaError_t scan_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t L, uint32_t smem, uint32_t fb_ctas,
                             int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
     switch (L) {
-        case 8: return scan_variant<8, TAB, PAIR>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
-        case 12: return scan_variant<12, TAB, PAIR>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
-        case 16: return scan_variant<16, TAB, PAIR>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 8: return scan_variant<8, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 12: return scan_variant<12, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 16: return scan_variant<16, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
         default:
-            if (TAB == kTabShfl || PAIR) return cudaErrorInvalidValue;
-            return scan_variant<0, TAB == kTabShfl ? kTabGlobal : TAB, false>(ln, ctas, mode, smem, fb_ctas,
-                                                                             cand_out, ncand_out, s);
+            if (TAB == kTabPair) return cudaErrorInvalidValue;
+            return scan_variant<0, TAB == kTabPair ? kTabGlobal : TAB>(ln, ctas, mode, smem, fb_ctas, cand_out,
+                                                                      ncand_out, s);
     }
 }
 
@@ -845,20 +842,16 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
     return cudaGetLastError();
 }
 
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool shfl,
-                        bool pair, uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out,
-                        int32_t *ncand_out, cudaStream_t s) {
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool pair,
+                        uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
+                        cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
-    if (shfl && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16)) {
-        if (pair)
-            return scan_dispatch_l<kTabShfl, true>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out,
-                                                   s);
-        return scan_dispatch_l<kTabShfl, false>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
-    }
+    if (mode == kVotePrune && pair && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16))
+        return scan_dispatch_l<kTabPair>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
-        return scan_dispatch_l<kTabSmem, false>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,
-                                                ncand_out, s);
-    return scan_dispatch_l<kTabGlobal, false>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+        return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,
+                                         ncand_out, s);
+    return scan_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
 }
 
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s) {

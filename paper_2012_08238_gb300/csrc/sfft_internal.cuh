@@ -22,7 +22,7 @@ constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate
 
 // Per-plan counters in device memory (uint32 slots).
 enum Counter : int {
-    kNCand = 0,    // candidates (score >= T) found by the vote scan
+    kNCand = 0,    // candidates (score >= T), counted by the fallback scan only
     kNSurv = 1,    // survivors of the median bound listed by the pruned scan
     kNGe = 2,      // their estimates with key >= theta (records of the pruned pass)
     kNSurv2 = 3,   // candidates listed by the unpruned fallback scan
@@ -45,7 +45,7 @@ struct PlanDev {
     uint32_t nsel, T, M;  // M = ceil(L/2): strong loops needed by the median bound
     uint32_t nchunk, rounds, rpc, tb, tiles;  // gather decomposition
     uint32_t vtiles;                          // vote tiles per job (<= kVoteTileF frequencies each)
-    uint32_t use_shfl, lbpl;                  // 32 <= B <= 512: bucket bits in registers, log2(B/32)
+    uint32_t use_pair, lbpl;                  // 64 <= B <= 512: strong bits in registers, log2(B/32)
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
     uint32_t sigma[kMaxL], tau[kMaxL];
@@ -55,7 +55,7 @@ struct PlanDev {
     float2 *partial;       // [nchunk][L][B]
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
-    uint32_t *packed;      // [L][32]: lane j's buckets, kept bits | strong bits << 16
+    uint32_t *packed;      // [L][32]: lane j's strong bits, its buckets' and their partners' (+B/2)
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
     uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
@@ -92,10 +92,10 @@ sfft_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
                               cudaStream_t s);
-// L_uniform: common L of every job (0 when they differ); shfl: every job has
-// use_shfl; pair: every job has B >= 64 (scan f and f + N/2 together);
+// L_uniform: common L of every job (0 when they differ); pair: every job has
+// use_pair (the pruned scan then uses the register table of strong bits);
 // fb_ctas: CTAs per job of a fallback launch (ignored otherwise).
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool shfl, bool pair,
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool pair,
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s);
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s);
