@@ -134,7 +134,7 @@ void decompose(PlanDev &P) {
 }
 
 struct Layout {
-    size_t plan, taps, tw, ginv, part, zhat, en, topk, sel, flags, survf, surv, ctr, total;
+    size_t plan, taps, tw, ginv, part, zhat, en, lkth, topk, sel, flags, survf, surv, ctr, total;
 };
 
 Layout layout_of(const PlanDev &P, int64_t cap) {
@@ -153,6 +153,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.part = take(sizeof(float2) * P.nchunk * L * B);
     o.zhat = take(sizeof(float2) * L * B);
     o.en = take(sizeof(float) * L * B);
+    o.lkth = take(sizeof(float) * L);
     o.topk = take(sizeof(uint32_t) * L * 32);
     o.sel = take(sizeof(int32_t) * L * P.nsel);
     o.flags = take(sizeof(uint16_t) * L * B);
@@ -211,7 +212,7 @@ namespace {
 
 struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
-    uint32_t max_B = 0, max_flags = 0, L_uniform = 0;
+    uint32_t max_B = 0, max_flags = 0, L_uniform = 0, max_K = 0;
     bool pair = true;
 };
 
@@ -222,6 +223,7 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.vote = p->h.vtiles;
     z.jobs = 1;
     z.max_B = p->h.B;
+    z.max_K = p->h.K;
     z.max_flags = p->h.L * p->h.B * 2;
     z.L_uniform = p->h.L;
     z.pair = p->h.use_pair != 0;
@@ -251,9 +253,9 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.pair, z.max_flags, kFallbackCtas,
                          nullptr, nullptr, s)) != cudaSuccess)
         return e;
-    if ((e = launch_estimate(le, z.jobs, kVoteFallback, z.L_uniform, s)) != cudaSuccess) return e;
+    if ((e = launch_estimate(lf, z.jobs, kVoteFallback, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
-    if ((e = launch_topk(lk, z.jobs, s)) != cudaSuccess) return e;
+    if ((e = launch_topk(lk, z.jobs, z.max_K, s)) != cudaSuccess) return e;
     return mark(6);
 }
 
@@ -274,6 +276,7 @@ Launch single(const Job &j) {
     Launch ln;
     ln.jobs = nullptr;
     ln.offs = nullptr;
+    ln.map = nullptr;
     ln.njobs = 1;
     ln.one = j;
     return ln;
@@ -405,6 +408,7 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     P.partial = reinterpret_cast<float2 *>(base + lay.part);
     P.zhat = reinterpret_cast<float2 *>(base + lay.zhat);
     P.energy = reinterpret_cast<float *>(base + lay.en);
+    P.loopkth = reinterpret_cast<float *>(base + lay.lkth);
     P.packed = reinterpret_cast<uint32_t *>(base + lay.topk);
     P.sel = reinterpret_cast<int32_t *>(base + lay.sel);
     P.flags = reinterpret_cast<uint16_t *>(base + lay.flags);
@@ -566,23 +570,17 @@ extern "C" sfft_status sfft_execute_host(sfft_plan *p, const float *x_host, int3
 namespace {
 
 struct BatchLayout {
-    std::vector<unsigned char> bytes;  // jobs, then six CTA prefix arrays
-    size_t off_offs[6];
+    std::vector<unsigned char> bytes;  // jobs, then per kernel a CTA prefix and a CTA -> job map
+    size_t off_offs[6], off_map[6];
     Sizes z;
 };
 
 BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t *const *idx,
                         float *const *val, int32_t *kout, int32_t count) {
     BatchLayout b;
-    const size_t jb = align256(sizeof(Job) * count), ob = align256(sizeof(uint32_t) * (count + 1));
-    b.bytes.assign(jb + 6 * ob, 0);
-    Job *jobs = reinterpret_cast<Job *>(b.bytes.data());
-    uint32_t *offs[6];
-    for (int k = 0; k < 6; ++k) {
-        b.off_offs[k] = jb + k * ob;
-        offs[k] = reinterpret_cast<uint32_t *>(b.bytes.data() + b.off_offs[k]);
-        offs[k][0] = 0;
-    }
+    // CTA counts per job and kernel: gather, select, vote, top-K, fallback, estimate
+    std::vector<uint32_t> cnt((size_t)count * 6);
+    std::vector<Job> jobs(count);
     Sizes &z = b.z;
     z.L_uniform = plans[0]->h.L;
     // gather split: the plan's (short CTAs, many waves; measured faster than
@@ -590,22 +588,46 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
     for (int32_t i = 0; i < count; ++i) {
         const sfft_plan *p = plans[i];
         jobs[i] = make_job(p, x[i], idx[i], val[i], kout + i);
-        Sizes s = plan_sizes(p);
-        s.gather = p->h.tiles * p->h.L * jobs[i].nchunk;
-        offs[0][i + 1] = offs[0][i] + s.gather;
-        offs[1][i + 1] = offs[1][i] + s.select;
-        offs[2][i + 1] = offs[2][i] + s.vote;
-        offs[3][i + 1] = offs[3][i] + 1;
-        offs[4][i + 1] = offs[4][i] + kFallbackCtas;
-        offs[5][i + 1] = offs[5][i] + kEstimateCtas;
+        const Sizes s = plan_sizes(p);
+        uint32_t *c = &cnt[(size_t)i * 6];
+        c[0] = s.gather;
+        c[1] = s.select;
+        c[2] = s.vote;
+        c[3] = 1;
+        c[4] = kFallbackCtas;
+        c[5] = kEstimateCtas;
         z.max_B = std::max(z.max_B, s.max_B);
+        z.max_K = std::max(z.max_K, s.max_K);
         z.pair = z.pair && s.pair;
         z.max_flags = std::max(z.max_flags, s.max_flags);
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
     }
-    z.gather = offs[0][count];
-    z.select = offs[1][count];
-    z.vote = offs[2][count];
+    uint64_t tot[6] = {0, 0, 0, 0, 0, 0};
+    for (int32_t i = 0; i < count; ++i)
+        for (int k = 0; k < 6; ++k) tot[k] += cnt[(size_t)i * 6 + k];
+    const size_t jb = align256(sizeof(Job) * count), ob = align256(sizeof(uint32_t) * (count + 1));
+    size_t off = jb;
+    for (int k = 0; k < 6; ++k) {
+        b.off_offs[k] = off;
+        off += ob;
+        b.off_map[k] = off;
+        off += align256(sizeof(uint32_t) * tot[k]);
+    }
+    b.bytes.assign(off, 0);
+    memcpy(b.bytes.data(), jobs.data(), sizeof(Job) * count);
+    for (int k = 0; k < 6; ++k) {
+        uint32_t *offs = reinterpret_cast<uint32_t *>(b.bytes.data() + b.off_offs[k]);
+        uint32_t *map = reinterpret_cast<uint32_t *>(b.bytes.data() + b.off_map[k]);
+        offs[0] = 0;
+        for (int32_t i = 0; i < count; ++i) {
+            const uint32_t c = cnt[(size_t)i * 6 + k];
+            offs[i + 1] = offs[i] + c;
+            for (uint32_t t = 0; t < c; ++t) map[offs[i] + t] = (uint32_t)i;
+        }
+    }
+    z.gather = (uint32_t)tot[0];
+    z.select = (uint32_t)tot[1];
+    z.vote = (uint32_t)tot[2];
     z.jobs = (uint32_t)count;
     return b;
 }
@@ -617,6 +639,7 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
     for (int k = 0; k < 6; ++k) {
         ln[k].jobs = reinterpret_cast<const Job *>(base);
         ln[k].offs = reinterpret_cast<const uint32_t *>(base + b.off_offs[k]);
+        ln[k].map = reinterpret_cast<const uint32_t *>(base + b.off_map[k]);
         ln[k].njobs = count;
         memset(&ln[k].one, 0, sizeof(Job));
     }

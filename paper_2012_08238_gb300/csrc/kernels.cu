@@ -18,8 +18,8 @@ namespace sfft {
 
 namespace {
 
-constexpr int kThreads = 256;  // every kernel but k_topk
-constexpr int kTopkThreads = 1024;
+constexpr int kThreads = 256;  // every kernel
+constexpr uint32_t kTwSmemMaxB = 8192;  // FFT twiddles staged in shared memory up to this B
 
 __device__ __forceinline__ void locate(const Launch &ln, uint32_t bid, Job &job, uint32_t &local) {
     if (ln.jobs == nullptr) {
@@ -27,14 +27,9 @@ __device__ __forceinline__ void locate(const Launch &ln, uint32_t bid, Job &job,
         local = bid;
         return;
     }
-    int lo = 0, hi = ln.njobs;  // offs[lo] <= bid < offs[hi]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (__ldg(ln.offs + mid) <= bid) lo = mid;
-        else hi = mid;
-    }
-    job = ln.jobs[lo];
-    local = bid - __ldg(ln.offs + lo);
+    const uint32_t jid = __ldg(ln.map + bid);
+    job = ln.jobs[jid];
+    local = bid - __ldg(ln.offs + jid);
 }
 
 // Copy the job's plan descriptor into shared memory (call from all threads,
@@ -252,9 +247,10 @@ __device__ void bitonic_pairs(unsigned long long *a, uint32_t *pay, uint32_t n, 
 // select_only: the bucket values are already in P.zhat; the kept buckets are
 // also listed in rank order in P.sel.
 __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_only) {
-    extern __shared__ unsigned long long sm[];  // B entries
+    extern __shared__ unsigned long long sm[];  // B values, B energies, B/2 twiddles (B <= kTwSmemMaxB)
     float2 *buf = reinterpret_cast<float2 *>(sm);
-    uint32_t *en_s = reinterpret_cast<uint32_t *>(sm);
+    uint32_t *en_s;
+    const float2 *tw;
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
@@ -264,11 +260,16 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
     enter(ln, P, J, s_local);
 
     const uint32_t l = s_local, B = P.B, logB = P.logB;
+    en_s = reinterpret_cast<uint32_t *>(buf + B);
+    float2 *tw_s = B <= kTwSmemMaxB ? reinterpret_cast<float2 *>(en_s + B) : nullptr;
+    tw = tw_s ? tw_s : P.tw;
     float2 *zrow = P.zhat + (size_t)l * B;
     float *erow = P.energy + (size_t)l * B;
     uint16_t *frow = P.flags + (size_t)l * B;
     if (!select_only) {
         const uint32_t nchunk = J.nchunk;
+        if (tw_s)
+            for (uint32_t k = threadIdx.x; k < B / 2; k += blockDim.x) tw_s[k] = __ldg(P.tw + k);
         const size_t cstride = (size_t)P.L * B;
         for (uint32_t j = threadIdx.x; j < B; j += blockDim.x) {
             float2 acc = make_float2(0.f, 0.f);
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
                 const uint32_t k = bf & (h - 1);
                 const uint32_t i0 = ((bf >> hs) << (hs + 1)) + k;
                 const uint32_t i1 = i0 + h;
-                const float2 w = __ldg(P.tw + (k << (logB - 1 - hs)));
+                const float2 w = tw[k << (logB - 1 - hs)];
                 const float2 a = buf[i0];
                 const float2 t = cmul(w, buf[i1]);
                 buf[i0] = make_float2(a.x + t.x, a.y + t.y);
@@ -299,20 +300,24 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         }
         for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
             const float2 z = buf[k];
+            const float e = z.x * z.x + z.y * z.y;
             zrow[k] = z;
-            erow[k] = z.x * z.x + z.y * z.y;
+            erow[k] = e;
+            en_s[k] = __float_as_uint(e);
         }
     } else {
         for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
             const float2 z = zrow[k];
-            erow[k] = z.x * z.x + z.y * z.y;
+            const float e = z.x * z.x + z.y * z.y;
+            erow[k] = e;
+            en_s[k] = __float_as_uint(e);
         }
     }
     __syncthreads();
     if (select_only) {
         // rank-ordered list for the single-stage entry point
         for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
-            sm[k] = ((unsigned long long)__float_as_uint(erow[k]) << 32) | (uint32_t)(~k);
+            sm[k] = ((unsigned long long)en_s[k] << 32) | (uint32_t)(~k);
         __syncthreads();
         bitonic_desc(sm, B);
         for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x)
@@ -322,8 +327,6 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x) frow[~(uint32_t)sm[s]] = 1;
     } else {
         // kept = energy above the nsel-th largest, plus the lowest-index ties
-        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) en_s[k] = __float_as_uint(erow[k]);
-        __syncthreads();
         const uint32_t kth = block_kth_largest<false>(en_s, B, P.nsel, s_hist, s_wsum, &s_prefix, &s_need);
         const uint32_t need_eq = s_need;
         const uint32_t per = (B + kThreads - 1) / kThreads;
@@ -337,6 +340,12 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
             if (e == kth) keep = r++ < need_eq;
             frow[k] = keep ? 1 : 0;
         }
+        // this loop's ceil(K/L)-th largest energy: their minimum over loops is
+        // at most the K-th largest energy of all loops (each loop has
+        // ceil(K/L) values at or above it)
+        const uint32_t kq = (P.K + P.L - 1) / P.L;
+        const uint32_t kqv = kq <= B ? block_kth_largest<false>(en_s, B, kq, s_hist, s_wsum, &s_prefix, &s_need) : 0u;
+        if (threadIdx.x == 0) P.loopkth[l] = __uint_as_float(kqv);
     }
 
     // ---- last CTA of the job: theta and the kept/strong tables
@@ -347,26 +356,27 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
     if (!s_last) return;
     __threadfence();
     const uint32_t total = P.L * B;
-    // theta = 1/4 of the K-th largest bucket energy over all loops: a guess at
-    // a lower bound of the K-th largest estimate.  Exactness never depends on
-    // it; a guess that is too high only sends the job to the fallback pass.
-    if (P.K <= total) {
-        const uint32_t kb = block_kth_largest<true>(reinterpret_cast<const uint32_t *>(P.energy), total, P.K,
-                                                    s_hist, s_wsum, &s_prefix, &s_need);
+    // theta = 1/4 of a lower bound of the K-th largest bucket energy over all
+    // loops: a guess at a lower bound of the K-th largest estimate.  Exactness
+    // never depends on it; a guess that is too high only sends the job to the
+    // fallback pass.
+    if (threadIdx.x < 32) {
+        float mn = INFINITY;
+        for (uint32_t ll = threadIdx.x; ll < P.L; ll += 32) mn = fminf(mn, __ldcg(P.loopkth + ll));
+        for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
         if (threadIdx.x == 0) {
-            float theta = 0.25f * __uint_as_float(kb);
+            float theta = select_only ? 0.f : 0.25f * mn;  // single-stage select: no pruning downstream
             if (!(theta >= 0.f) || isinf(theta)) theta = 0.f;
             s_theta = theta;
+            P.ctr[kTheta] = __float_as_uint(theta);
         }
-    } else if (threadIdx.x == 0) {
-        s_theta = 0.f;
     }
     __syncthreads();
-    if (threadIdx.x == 0) P.ctr[kTheta] = __float_as_uint(s_theta);
     // a loop is "strong" for f when |zhat|^2 * max|1/G~|^2 >= theta/2; with
     // fewer than M strong loops the median estimate is provably below theta
     const float thr = 0.5f * s_theta;
     const float gmul = P.ginv2max * (1.0f + 1.0f / 1024.0f);
+#pragma unroll 4
     for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
         const float en = __ldcg(P.energy + e);
         uint16_t f = __ldcg(reinterpret_cast<const unsigned short *>(P.flags) + e) & 1u;
@@ -378,16 +388,18 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         // [0, bpl) and of their partners (bucket ^ B/2, lane j ^ 16) at
         // [16, 16+bpl), the word rotated left by j*bpl so that one rotate right
         // by the bucket index puts f's bit at 0 and f+N/2's bit at 16
-        __syncthreads();
         const uint32_t bpl = 1u << P.lbpl;
         for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
             const uint32_t ll = idx >> 5, j = idx & 31;
-            const uint16_t *fr = P.flags + (size_t)ll * B;
+            const float *er = P.energy + (size_t)ll * B;
             uint32_t word = 0;
-            for (uint32_t b = 0; b < bpl; ++b) {
-                const uint32_t h = j * bpl + b;
-                word |= ((fr[h] >> 8) & 1u) << b;
-                word |= ((fr[h ^ (B / 2)] >> 8) & 1u) << (16 + b);
+#pragma unroll
+            for (uint32_t b = 0; b < 16; ++b) {
+                if (b < bpl) {
+                    const uint32_t h = j * bpl + b;
+                    word |= (uint32_t)(__ldcg(er + h) * gmul >= thr) << b;
+                    word |= (uint32_t)(__ldcg(er + (h ^ (B / 2))) * gmul >= thr) << (16 + b);
+                }
             }
             P.packed[idx] = __funnelshift_l(word, word, (j * bpl) & 31u);
         }
@@ -633,7 +645,7 @@ __device__ __forceinline__ bool is_candidate(const PlanDev &P, uint32_t f) {
 // job.  The pruned pass keeps candidates whose key >= theta; the fallback pass
 // keeps all.  Records: {f, key bits, re bits, im bits}.
 template <int LT>
-__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode) {
+__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode, uint32_t ctas_per_job) {
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
@@ -646,7 +658,7 @@ __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode)
     const uint32_t n = P.ctr[prune ? kNSurv : kNSurv2];
     const float theta = prune ? __uint_as_float(P.ctr[kTheta]) : 0.f;
     uint32_t *cnt = P.ctr + (prune ? kNGe : kNRec2);
-    for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += kEstimateCtas * kThreads) {
+    for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += ctas_per_job * kThreads) {
         const uint32_t f = P.survf[i];
         bool keep = !prune || is_candidate(P, f);
         float2 v = make_float2(0.f, 0.f);
@@ -680,9 +692,10 @@ __device__ __forceinline__ unsigned long long surv_key(uint4 r) {
 // those of the pruned pass (candidates with key >= theta) when at least K of
 // them exist; otherwise those of the fallback pass (every candidate).  Pruned
 // candidates have key < theta, so either set contains the top K.
-__global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
-    extern __shared__ unsigned long long tk[];  // kTopkSmem keys + kTopkSmem payloads
-    uint32_t *pay = reinterpret_cast<uint32_t *>(tk + kTopkSmem);
+// cap: shared-memory entries (a power of two >= every job's K).
+__global__ void __launch_bounds__(kThreads) k_topk(Launch ln, uint32_t cap) {
+    extern __shared__ unsigned long long tk[];  // cap keys + cap payloads
+    uint32_t *pay = reinterpret_cast<uint32_t *>(tk + cap);
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local, s_S, s_kout, s_hist[256], s_need, s_cnt;
@@ -696,7 +709,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
     __syncthreads();
     const uint32_t S = s_S, kout = s_kout;
     const uint4 *surv = P.surv;
-    if (S <= (uint32_t)kTopkSmem) {
+    if (S <= cap) {
         uint32_t n2 = 1;
         while (n2 < S) n2 <<= 1;
         for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
@@ -748,7 +761,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(Launch ln) {
             const unsigned long long k = surv_key(surv[i]);
             if (kout > 0 && k >= kth) {
                 const uint32_t pos = atomicAdd(&s_cnt, 1u);
-                if (pos < (uint32_t)kTopkSmem) {
+                if (pos < cap) {
                     tk[pos] = k;
                     pay[pos] = i;
                 }
@@ -835,7 +848,8 @@ cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s)
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
                               cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
-    const int smem = (int)(max_B * sizeof(unsigned long long));
+    const int smem = (int)(max_B * (sizeof(float2) + sizeof(uint32_t)) +
+                           (max_B <= kTwSmemMaxB ? max_B / 2 * sizeof(float2) : 0));
     cudaError_t e = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_fft_select<<<total_ctas, kThreads, smem, s>>>(ln, select_only);
@@ -854,24 +868,29 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
     return scan_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
 }
 
+// kEstimateCtas CTAs per job for the pruned pass, kFallbackCtas for the
+// (usually idle) fallback pass; ln's prefix array must match.
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
-    const uint32_t ctas = njobs * kEstimateCtas;
+    const uint32_t per = mode == kVoteFallback ? kFallbackCtas : kEstimateCtas;
+    const uint32_t ctas = njobs * per;
     switch (L_uniform) {
-        case 8: k_estimate_surv<8><<<ctas, kThreads, 0, s>>>(ln, mode); break;
-        case 12: k_estimate_surv<12><<<ctas, kThreads, 0, s>>>(ln, mode); break;
-        case 16: k_estimate_surv<16><<<ctas, kThreads, 0, s>>>(ln, mode); break;
-        default: k_estimate_surv<0><<<ctas, kThreads, 0, s>>>(ln, mode); break;
+        case 8: k_estimate_surv<8><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
+        case 12: k_estimate_surv<12><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
+        case 16: k_estimate_surv<16><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
+        default: k_estimate_surv<0><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_topk(const Launch &ln, uint32_t njobs, cudaStream_t s) {
+cudaError_t launch_topk(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
-    const int smem = kTopkSmem * (int)(sizeof(unsigned long long) + sizeof(uint32_t));
+    uint32_t cap = kTopkSmemMin;
+    while (cap < max_K) cap <<= 1;  // the radix path compacts K winners into the buffer
+    const int smem = (int)(cap * (sizeof(unsigned long long) + sizeof(uint32_t)));
     cudaError_t e = cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_topk<<<njobs, kTopkThreads, smem, s>>>(ln);
+    k_topk<<<njobs, kThreads, smem, s>>>(ln, cap);
     return cudaGetLastError();
 }
 

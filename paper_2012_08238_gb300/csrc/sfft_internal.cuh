@@ -14,7 +14,7 @@ constexpr int kMaxL = 32;
 constexpr int kMaxB = 16384;
 constexpr int kMaxK = 16384;
 constexpr int kMaxLogN = 30;
-constexpr int kTopkSmem = 16384;       // survivors sorted in shared memory up to this count
+constexpr int kTopkSmemMin = 4096;     // top-K sorts up to max(this, K) records in shared memory
 constexpr int kFlagsSmemBytes = 96 * 1024;
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kFallbackCtas = 4;        // CTAs per job of the (usually idle) unpruned pass
@@ -55,6 +55,7 @@ struct PlanDev {
     float2 *partial;       // [nchunk][L][B]
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
+    float *loopkth;        // [L] ceil(K/L)-th largest energy of each loop
     uint32_t *packed;      // [L][32]: lane j's strong bits, its buckets' and their partners' (+B/2)
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
@@ -74,10 +75,12 @@ struct Job {
 };
 
 // Launch descriptor shared by all stage kernels: either one job passed by
-// value, or `njobs` jobs in device memory with a CTA-offset prefix per kernel.
+// value, or `njobs` jobs in device memory with, per kernel, a CTA-offset
+// prefix and a CTA -> job map.
 struct Launch {
     const Job *jobs;        // nullptr -> use `one`
     const uint32_t *offs;   // [njobs + 1] CTA prefix for this kernel (batch only)
+    const uint32_t *map;    // [total CTAs] job of each CTA (batch only)
     int njobs;
     Job one;
 };
@@ -99,7 +102,7 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s);
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s);
-cudaError_t launch_topk(const Launch &ln, uint32_t njobs, cudaStream_t s);
+cudaError_t launch_topk(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);
 cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *sel, cudaStream_t s);
