@@ -32,6 +32,14 @@ sys.path.insert(0, ROOT)
 from paper_2012_08238_gb300 import configs, replicas, signals  # noqa: E402
 
 METRIC = "spectra/s batched+served vs plain at fixed L1 error; p50/p99 ms; HBM GB/s"
+
+# DRAM bytes per spectrum of the two kernels that can dominate, from one ncu
+# capture each (dram__bytes_read.sum + dram__bytes_write.sum, 8-signal case,
+# scaled per spectrum); the summaries are under profiles/.
+NCU_TRAFFIC_PER_SPECTRUM = {
+    "k_vote_scan": 36_096 / 8,
+    "k_gather": (66_689_024 + 2_041_600) / 8,
+}
 UNIT = "spectra/s"
 WORKLOAD = configs.GENERAL_N20
 
@@ -309,9 +317,7 @@ def run_ours(args):
     per_launch = {k: v / args.steps for k, v in stage_ms.items()}
     dominant = max(per_launch, key=per_launch.get)
     distinct = S * 8 * info.samples_touched  # algorithmic bytes: distinct samples read
-    # the gather's time here includes the FFT/select kernel that sums its
-    # partials (a conservative figure for the gather)
-    bucket_ms = per_launch["gather_fold"] + per_launch["fft_select"]
+    bucket_ms = per_launch["gather_fold"]
     gather_gbs = distinct / (bucket_ms / 1e3) / 1e9
     sector_bytes = S * W.L * W.window * 32
     # vote scan: N*L table lookups per spectrum, at least 4 integer lane-ops
@@ -320,19 +326,21 @@ def run_ours(args):
     scan_ops = S * W.N * W.L * 4
     alu_peak = 152 * 128 * sm_max_mhz * 1e6
     scan_rate = scan_ops / (per_launch["vote_scan"] / 1e3)
-    gather_roof = {"kernel": "k_gather + k_fft_select",
+    gather_roof = {"kernel": "k_gather",
                    "achieved": gather_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gather_gbs / hbm_peak,
                    "sector_gbs": sector_bytes / (bucket_ms / 1e3) / 1e9,
-                   "sector_efficiency": distinct / sector_bytes, "peak_source": peak_kind}
+                   "sector_efficiency": distinct / sector_bytes, "peak_source": peak_kind,
+                   "traffic": S * NCU_TRAFFIC_PER_SPECTRUM["k_gather"]}
     if dominant == "vote_scan":
         roofline = {"kernel": "k_vote_scan (vote scan)", "bound": "alu",
                     "achieved": scan_rate / 1e12, "peak": alu_peak / 1e12, "unit": "T int lane-ops/s",
-                    "frac": scan_rate / alu_peak, "traffic": None,
+                    "frac": scan_rate / alu_peak, "traffic": S * NCU_TRAFFIC_PER_SPECTRUM["k_vote_scan"],
                     "per_unit": f"4 x N x L = {4 * W.N * W.L} lane-ops per spectrum",
                     "peak_source": f"152 SMs x 128 lanes x {sm_max_mhz:.0f} MHz (derived, recipe unit counts)"}
     else:
         roofline = {"kernel": gather_roof["kernel"], "bound": "hbm", "achieved": gather_gbs,
-                    "peak": hbm_peak, "unit": "GB/s", "frac": gather_gbs / hbm_peak, "traffic": None,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": gather_gbs / hbm_peak,
+                    "traffic": S * NCU_TRAFFIC_PER_SPECTRUM["k_gather"],
                     "per_unit": f"8 B x {info.samples_touched} distinct samples per spectrum",
                     "peak_source": peak_kind}
 
