@@ -129,7 +129,8 @@ void decompose(PlanDev &P) {
     P.rpc = (P.rounds + want - 1) / want;
     P.nchunk = (P.rounds + P.rpc - 1) / P.rpc;
     P.vtiles = (P.N + kVoteTileF - 1) / kVoteTileF;  // each tile's survivors fit the CTA's queue
-    P.use_pair = (P.B >= 64 && P.B <= 512) ? 1u : 0u;
+    P.use_quad = (P.B >= 128 && P.B <= 512) ? 1u : 0u;
+    P.use_pair = P.B == 64 ? 1u : 0u;
     P.lbpl = P.use_pair ? P.logB - 5 : 0u;
 }
 
@@ -213,7 +214,7 @@ namespace {
 struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0, max_K = 0;
-    bool pair = true;
+    bool pair = true, quad = true;
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -227,6 +228,7 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.max_flags = p->h.L * p->h.B * 2;
     z.L_uniform = p->h.L;
     z.pair = p->h.use_pair != 0;
+    z.quad = p->h.use_quad != 0;
     return z;
 }
 
@@ -244,14 +246,14 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.pair, z.max_flags, 0, nullptr, nullptr, s)) !=
-        cudaSuccess)
+    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.pair, z.quad, z.max_flags, 0, nullptr, nullptr,
+                         s)) != cudaSuccess)
         return e;
     if ((e = mark(3)) != cudaSuccess) return e;
     if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.pair, z.max_flags, kFallbackCtas,
-                         nullptr, nullptr, s)) != cudaSuccess)
+    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.pair, z.quad, z.max_flags,
+                         kFallbackCtas, nullptr, nullptr, s)) != cudaSuccess)
         return e;
     if ((e = launch_estimate(lf, z.jobs, kVoteFallback, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
@@ -599,6 +601,7 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         z.max_B = std::max(z.max_B, s.max_B);
         z.max_K = std::max(z.max_K, s.max_K);
         z.pair = z.pair && s.pair;
+        z.quad = z.quad && s.quad;
         z.max_flags = std::max(z.max_flags, s.max_flags);
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
     }
@@ -884,8 +887,8 @@ extern "C" sfft_status sfft_vote(sfft_plan *p, const int32_t *sel_dev, int32_t *
     const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
     SFFT_CUDA_TRY(cudaMemsetAsync(n_cand_dev, 0, sizeof(int32_t), s));
     SFFT_CUDA_TRY(launch_flags_from_sel(p->d, p->h.L, sel_dev, s));
-    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, 0, cand_dev,
-                              n_cand_dev, s));
+    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, false, p->h.L * p->h.B * 2, 0,
+                              cand_dev, n_cand_dev, s));
     return SFFT_OK;
 }
 

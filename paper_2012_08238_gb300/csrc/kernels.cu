@@ -383,6 +383,23 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         if (en * gmul >= thr) f |= 256;
         P.flags[e] = f;
     }
+    if (P.use_quad) {
+        // lane j of loop ll: strong bit of every bucket h = j (mod 32) at bit
+        // (h >> (log2 B - 5)) mod 32; the buckets of f + kN/4 (k = 0..3) share
+        // f's lane and sit 8 bits apart in rotation order
+        const uint32_t sh = P.logB - 5;
+        for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
+            const uint32_t ll = idx >> 5, j = idx & 31;
+            const float *er = P.energy + (size_t)ll * B;
+            uint32_t word = 0;
+#pragma unroll
+            for (uint32_t m = 0; m < 16; ++m) {
+                const uint32_t h = j + 32 * m;
+                if (h < B) word |= (uint32_t)(__ldcg(er + h) * gmul >= thr) << ((h >> sh) & 31u);
+            }
+            P.packed[idx] = word;
+        }
+    }
     if (P.use_pair) {
         // lane j of loop ll: strong bits of its buckets [j*bpl, (j+1)*bpl) at
         // [0, bpl) and of their partners (bucket ^ B/2, lane j ^ 16) at
@@ -499,6 +516,13 @@ __device__ float2 median_estimate(const PlanDev &P, const float2 *zhat, uint32_t
 // --------------------------------------------------------------- a4 + a5
 // Vote scan over one tile of frequencies of a job.
 //
+// Quad path (128 <= B <= 512): a thread takes f + kN/4, k = 0..3.  Their
+// hash words differ by k*sigma_l*2^30, so their buckets are the members of
+// one group {h + i B/4}: same lane (h mod 32), bit positions 8 apart after
+// one rotate by h >> (log2 B - 5).  The four strong bits land in the four
+// bytes of one accumulator (a byte permute swaps bytes 1 and 3 for loops with
+// sigma = 3 mod 4, whose member order runs backwards).
+//
 // Pruned pass: only frequencies with at least M strong loops can reach the top
 // K (median bound), so they are queued per tile in shared memory and appended
 // to the job's survivor list; whether they are candidates (kept in >= T
@@ -511,7 +535,7 @@ __device__ float2 median_estimate(const PlanDev &P, const float2 *zhat, uint32_t
 //
 // The bucket comes from t = (sigma_l << (32 - log2 N)) f + (half << (32 - log2 N))
 // mod 2^32, whose top log2 B bits are round-half-up(sigma_l f B / N) mod B.
-enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabPair = 2 };
+enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabPair = 2, kTabQuad = 3 };
 
 template <int LT, int TAB>
 __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uint32_t fb_ctas, int32_t *cand_out,
@@ -544,21 +568,23 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
         tab = tab_s;
     }
     constexpr int LR = LT > 0 ? LT : 1;
-    uint32_t av[LR], pw[LR];
+    uint32_t av[LR], pw[LR], ps[LR];
     if constexpr (LT > 0) {
 #pragma unroll
         for (int l = 0; l < LT; ++l) {
             av[l] = P.sigma[l] << (32 - P.logN);
-            pw[l] = TAB == kTabPair ? __ldcg(P.packed + l * 32 + lane) : 0u;
+            pw[l] = (TAB == kTabPair || TAB == kTabQuad) ? __ldcg(P.packed + l * 32 + lane) : 0u;
+            ps[l] = (P.sigma[l] & 2u) ? 0x1230u : 0x3210u;
         }
     }
     const uint32_t cv = P.half << (32 - P.logN);
     const uint32_t top = 32 - P.logB;
     const uint32_t M = P.M, T = P.T, N = P.N;
-    const uint32_t span = TAB == kTabPair ? N / 2 : N;  // f; the pair path adds f + N/2
+    // frequencies per thread and iteration: f (+ N/2 pair) (+ kN/4 quad)
+    const uint32_t span = TAB == kTabQuad ? N / 4 : (TAB == kTabPair ? N / 2 : N);
 
     uint32_t per = (span + P.vtiles - 1) / P.vtiles;
-    per = (per + kThreads - 1) / kThreads * kThreads;  // pair path: 2 per <= kVoteTileF
+    per = (per + kThreads - 1) / kThreads * kThreads;  // (N / span) * per <= kVoteTileF
     const uint32_t stride = mode == kVoteFallback ? fb_ctas : P.vtiles;
     uint32_t my_cand = 0;
 
@@ -578,7 +604,20 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
         for (uint32_t base = f0; base < f1; base += kThreads) {
             const uint32_t f = base + threadIdx.x;
             const bool valid = f < f1;
-            if constexpr (TAB == kTabPair) {
+            if constexpr (TAB == kTabQuad) {
+                uint32_t acc = 0;  // byte k: strong count of f + kN/4
+#pragma unroll
+                for (int l = 0; l < LT; ++l) {
+                    const uint32_t t = av[l] * f + cv;
+                    const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> top);  // lane = bucket mod 32
+                    const uint32_t r = __funnelshift_r(w, w, t >> 27);
+                    acc += __byte_perm(r & 0x01010101u, 0, ps[l]);
+                }
+                enqueue(f, valid && (acc & 0xFFu) >= M);
+                enqueue(f + span, valid && ((acc >> 8) & 0xFFu) >= M);
+                enqueue(f + 2 * span, valid && ((acc >> 16) & 0xFFu) >= M);
+                enqueue(f + 3 * span, valid && (acc >> 24) >= M);
+            } else if constexpr (TAB == kTabPair) {
                 uint32_t acc = 0;
 #pragma unroll
                 for (int l = 0; l < LT; ++l) {
@@ -831,9 +870,9 @@ cudaError_t scan_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t 
         case 12: return scan_variant<12, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
         case 16: return scan_variant<16, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
         default:
-            if (TAB == kTabPair) return cudaErrorInvalidValue;
-            return scan_variant<0, TAB == kTabPair ? kTabGlobal : TAB>(ln, ctas, mode, smem, fb_ctas, cand_out,
-                                                                      ncand_out, s);
+            if (TAB == kTabPair || TAB == kTabQuad) return cudaErrorInvalidValue;
+            return scan_variant<0, (TAB == kTabPair || TAB == kTabQuad) ? kTabGlobal : TAB>(
+                ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
     }
 }
 
@@ -856,11 +895,14 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
     return cudaGetLastError();
 }
 
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool pair,
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool pair, bool quad,
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
-    if (mode == kVotePrune && pair && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16))
+    const bool lt = L_uniform == 8 || L_uniform == 12 || L_uniform == 16;
+    if (mode == kVotePrune && quad && lt)
+        return scan_dispatch_l<kTabQuad>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+    if (mode == kVotePrune && pair && lt)
         return scan_dispatch_l<kTabPair>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
         return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,

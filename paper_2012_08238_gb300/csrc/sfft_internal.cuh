@@ -45,7 +45,8 @@ struct PlanDev {
     uint32_t nsel, T, M;  // M = ceil(L/2): strong loops needed by the median bound
     uint32_t nchunk, rounds, rpc, tb, tiles;  // gather decomposition
     uint32_t vtiles;                          // vote tiles per job (<= kVoteTileF frequencies each)
-    uint32_t use_pair, lbpl;                  // 64 <= B <= 512: strong bits in registers, log2(B/32)
+    uint32_t use_pair, lbpl;                  // B == 64: strong bits in registers (pairs), log2(B/32)
+    uint32_t use_quad;                        // 128 <= B <= 512: strong bits in registers (quads)
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
     uint32_t sigma[kMaxL], tau[kMaxL];
@@ -56,7 +57,7 @@ struct PlanDev {
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
     float *loopkth;        // [L] ceil(K/L)-th largest energy of each loop
-    uint32_t *packed;      // [L][32]: lane j's strong bits, its buckets' and their partners' (+B/2)
+    uint32_t *packed;      // [L][32]: lane j's strong bits (layout of the pair or quad scan)
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
     uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
@@ -95,10 +96,10 @@ sfft_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
                               cudaStream_t s);
-// L_uniform: common L of every job (0 when they differ); pair: every job has
-// use_pair (the pruned scan then uses the register table of strong bits);
-// fb_ctas: CTAs per job of a fallback launch (ignored otherwise).
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool pair,
+// L_uniform: common L of every job (0 when they differ); pair / quad: every
+// job has use_pair / use_quad (the pruned scan then uses the register table
+// of strong bits); fb_ctas: CTAs per job of a fallback launch (else ignored).
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool pair, bool quad,
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s);
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s);
