@@ -118,6 +118,8 @@ sfft_status check_sizes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, i
 }
 
 constexpr int kNumSms = 152;  // GB300; only shapes the default work split
+constexpr int kScanCtasPerSm = 8;  // resident 256-thread scan CTAs per SM
+constexpr int kScanWaves = 3;
 
 // Work split of one plan for the gather and vote kernels.
 void decompose(PlanDev &P) {
@@ -129,9 +131,7 @@ void decompose(PlanDev &P) {
     P.rpc = (P.rounds + want - 1) / want;
     P.nchunk = (P.rounds + P.rpc - 1) / P.rpc;
     P.vtiles = (P.N + kVoteTileF - 1) / kVoteTileF;  // each tile's survivors fit the CTA's queue
-    P.use_quad = (P.B >= 128 && P.B <= 512) ? 1u : 0u;
-    P.use_pair = P.B == 64 ? 1u : 0u;
-    P.lbpl = P.use_pair ? P.logB - 5 : 0u;
+    P.use_bits = (P.B >= 32 && P.B <= 512) ? 1u : 0u;
 }
 
 struct Layout {
@@ -214,7 +214,7 @@ namespace {
 struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0, max_K = 0;
-    bool pair = true, quad = true;
+    bool bits = true;
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -227,8 +227,7 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.max_K = p->h.K;
     z.max_flags = p->h.L * p->h.B * 2;
     z.L_uniform = p->h.L;
-    z.pair = p->h.use_pair != 0;
-    z.quad = p->h.use_quad != 0;
+    z.bits = p->h.use_bits != 0;
     return z;
 }
 
@@ -246,13 +245,13 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.pair, z.quad, z.max_flags, 0, nullptr, nullptr,
+    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.bits, z.max_flags, 0, nullptr, nullptr,
                          s)) != cudaSuccess)
         return e;
     if ((e = mark(3)) != cudaSuccess) return e;
     if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.pair, z.quad, z.max_flags,
+    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.bits, z.max_flags,
                          kFallbackCtas, nullptr, nullptr, s)) != cudaSuccess)
         return e;
     if ((e = launch_estimate(lf, z.jobs, kVoteFallback, z.L_uniform, s)) != cudaSuccess) return e;
@@ -270,6 +269,7 @@ Job make_job(const sfft_plan *p, const float *x, int32_t *idx, float *val, int32
     j.kout = kout;
     j.rpc = p->h.rpc;
     j.nchunk = p->h.nchunk;
+    j.vctas = p->h.vtiles;
     return j;
 }
 
@@ -600,10 +600,23 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         c[5] = kEstimateCtas;
         z.max_B = std::max(z.max_B, s.max_B);
         z.max_K = std::max(z.max_K, s.max_K);
-        z.pair = z.pair && s.pair;
-        z.quad = z.quad && s.quad;
+        z.bits = z.bits && s.bits;
         z.max_flags = std::max(z.max_flags, s.max_flags);
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
+    }
+    // pruned scan: up to 4 vote tiles per CTA while the launch keeps at least
+    // kScanWaves waves of resident CTAs (fewer CTAs amortise the per-CTA
+    // set-up; too few leave a mostly idle last wave)
+    {
+        uint64_t vt = 0;
+        for (int32_t i = 0; i < count; ++i) vt += cnt[(size_t)i * 6 + 2];
+        uint32_t tpc = 4;
+        while (tpc > 1 && vt / tpc < (uint64_t)kScanWaves * kNumSms * kScanCtasPerSm) tpc >>= 1;
+        for (int32_t i = 0; i < count; ++i) {
+            uint32_t &c2 = cnt[(size_t)i * 6 + 2];
+            c2 = (c2 + tpc - 1) / tpc;
+            jobs[i].vctas = c2;
+        }
     }
     uint64_t tot[6] = {0, 0, 0, 0, 0, 0};
     for (int32_t i = 0; i < count; ++i)
@@ -887,7 +900,7 @@ extern "C" sfft_status sfft_vote(sfft_plan *p, const int32_t *sel_dev, int32_t *
     const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
     SFFT_CUDA_TRY(cudaMemsetAsync(n_cand_dev, 0, sizeof(int32_t), s));
     SFFT_CUDA_TRY(launch_flags_from_sel(p->d, p->h.L, sel_dev, s));
-    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, false, p->h.L * p->h.B * 2, 0,
+    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, 0,
                               cand_dev, n_cand_dev, s));
     return SFFT_OK;
 }

@@ -59,6 +59,10 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// sigma^-1 mod 32 for odd sigma: sigma^2 = 1 (mod 8) holds 3 bits, one
+// Newton step doubles them
+__device__ __forceinline__ uint32_t inv_mod32(uint32_t sigma) { return sigma * (2u - sigma * sigma); }
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -383,42 +387,22 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         if (en * gmul >= thr) f |= 256;
         P.flags[e] = f;
     }
-    if (P.use_quad) {
+    if (P.use_bits) {
         // lane j of loop ll: strong bit of every bucket h = j (mod 32) at bit
-        // (h >> (log2 B - 5)) mod 32; the buckets of f + kN/4 (k = 0..3) share
-        // f's lane and sit 8 bits apart in rotation order
+        // (sigma^-1 * (h >> (log2 B - 5))) mod 32, so that the scan's one
+        // rotate puts the bit of f + kN/G (G = B/32) at position k * 32/G
         const uint32_t sh = P.logB - 5;
         for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
             const uint32_t ll = idx >> 5, j = idx & 31;
+            const uint32_t si = inv_mod32(P.sigma[ll]);
             const float *er = P.energy + (size_t)ll * B;
             uint32_t word = 0;
 #pragma unroll
             for (uint32_t m = 0; m < 16; ++m) {
                 const uint32_t h = j + 32 * m;
-                if (h < B) word |= (uint32_t)(__ldcg(er + h) * gmul >= thr) << ((h >> sh) & 31u);
+                if (h < B) word |= (uint32_t)(__ldcg(er + h) * gmul >= thr) << ((si * (h >> sh)) & 31u);
             }
             P.packed[idx] = word;
-        }
-    }
-    if (P.use_pair) {
-        // lane j of loop ll: strong bits of its buckets [j*bpl, (j+1)*bpl) at
-        // [0, bpl) and of their partners (bucket ^ B/2, lane j ^ 16) at
-        // [16, 16+bpl), the word rotated left by j*bpl so that one rotate right
-        // by the bucket index puts f's bit at 0 and f+N/2's bit at 16
-        const uint32_t bpl = 1u << P.lbpl;
-        for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
-            const uint32_t ll = idx >> 5, j = idx & 31;
-            const float *er = P.energy + (size_t)ll * B;
-            uint32_t word = 0;
-#pragma unroll
-            for (uint32_t b = 0; b < 16; ++b) {
-                if (b < bpl) {
-                    const uint32_t h = j * bpl + b;
-                    word |= (uint32_t)(__ldcg(er + h) * gmul >= thr) << b;
-                    word |= (uint32_t)(__ldcg(er + (h ^ (B / 2))) * gmul >= thr) << (16 + b);
-                }
-            }
-            P.packed[idx] = __funnelshift_l(word, word, (j * bpl) & 31u);
         }
     }
     if (threadIdx.x == 0) {
@@ -516,26 +500,75 @@ __device__ float2 median_estimate(const PlanDev &P, const float2 *zhat, uint32_t
 // --------------------------------------------------------------- a4 + a5
 // Vote scan over one tile of frequencies of a job.
 //
-// Quad path (128 <= B <= 512): a thread takes f + kN/4, k = 0..3.  Their
-// hash words differ by k*sigma_l*2^30, so their buckets are the members of
-// one group {h + i B/4}: same lane (h mod 32), bit positions 8 apart after
-// one rotate by h >> (log2 B - 5).  The four strong bits land in the four
-// bytes of one accumulator (a byte permute swaps bytes 1 and 3 for loops with
-// sigma = 3 mod 4, whose member order runs backwards).
-//
 // Pruned pass: only frequencies with at least M strong loops can reach the top
 // K (median bound), so they are queued per tile in shared memory and appended
 // to the job's survivor list; whether they are candidates (kept in >= T
-// loops) is checked when they are estimated.  With the register table
-// (64 <= B <= 512, L in {8, 12, 16}) a thread takes f and f + N/2: their hash
-// words differ only in bit 31, so one warp shuffle of the lane's word and one
-// rotate give both strong bits (f at bit 0, f + N/2 at bit 16).
+// loops) is checked when they are estimated.
+//
+// Register table (32 <= B <= 512, L in {8, 12, 16}): a thread takes the G =
+// B/32 frequencies f + kN/G.  Their hash words differ by k sigma_l 2^32/G,
+// so their buckets h + k sigma_l 32 share the lane h mod 32 of the packed
+// table, and one warp shuffle fetches the word holding all G strong bits.
+// A rotate by sigma^-1 * (h >> (log2 B - 5)) (the table's positions are
+// scaled by sigma^-1 to match) puts member k's bit at position k * 32/G in
+// every loop, so carry-save adders over the L rotated words count the
+// strong loops of all 32 positions at once (bit-sliced counters).
 // Fallback pass and candidate listing: the u16 kept/strong table (shared or
 // global memory); every candidate is counted and listed.
 //
 // The bucket comes from t = (sigma_l << (32 - log2 N)) f + (half << (32 - log2 N))
 // mod 2^32, whose top log2 B bits are round-half-up(sigma_l f B / N) mod B.
-enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabPair = 2, kTabQuad = 3 };
+enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabBits = 2 };
+
+// Full adder over 32 bit-lanes: a + b + c = s + 2 cy.
+__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &sum, uint32_t &cy) {
+    sum = a ^ b ^ c;
+    cy = (a & b) | (c & (a ^ b));
+}
+
+// Bit-sliced population count of N words: pl[i] holds bit i of the per-position
+// count.  One column of N words of equal weight is reduced to one word by
+// full adders (a half adder for an even remainder); the floor(N/2) carries
+// form the next column.
+template <int N, int P, int AT = 0>
+__device__ __forceinline__ void count_planes(const uint32_t (&col)[N], uint32_t (&pl)[P]) {
+    constexpr int NC = N / 2;
+    uint32_t cy[NC > 0 ? NC : 1];
+    uint32_t acc = col[0];
+#pragma unroll
+    for (int k = 0; k < (N - 1) / 2; ++k) full_add(acc, col[1 + 2 * k], col[2 + 2 * k], acc, cy[k]);
+    if constexpr (N > 1 && (N - 1) % 2 == 1) {
+        cy[NC - 1] = acc & col[N - 1];
+        acc ^= col[N - 1];
+    }
+    pl[AT] = acc;
+    if constexpr (NC > 0) count_planes<NC, P, AT + 1>(cy, pl);
+}
+
+// Positions whose count (planes pl, least significant first) is >= M.
+template <int M, int P>
+__device__ __forceinline__ uint32_t count_at_least(const uint32_t (&pl)[P]) {
+    uint32_t ge = 0, eq = 0xFFFFFFFFu;
+#pragma unroll
+    for (int b = P - 1; b >= 0; --b) {
+        if ((M >> b) & 1) {
+            eq &= pl[b];
+        } else {
+            ge |= eq & pl[b];
+            eq &= ~pl[b];
+        }
+    }
+    return ge | eq;
+}
+
+constexpr int bit_length(int v) { return v > 0 ? 1 + bit_length(v >> 1) : 0; }
+
+// Bits k * 32/G, k < G = 2^lgG (lgG <= 5): the member counters.
+__device__ __forceinline__ uint32_t member_mask(uint32_t lgG) {
+    uint32_t m = 1u;
+    for (uint32_t w = 32u >> lgG; w < 32u; w <<= 1) m |= m << w;
+    return m;
+}
 
 template <int LT, int TAB>
 __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uint32_t fb_ctas, int32_t *cand_out,
@@ -568,24 +601,28 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
         tab = tab_s;
     }
     constexpr int LR = LT > 0 ? LT : 1;
-    uint32_t av[LR], pw[LR], ps[LR];
+    uint32_t av[LR], pw[LR], si[LR];
     if constexpr (LT > 0) {
 #pragma unroll
         for (int l = 0; l < LT; ++l) {
             av[l] = P.sigma[l] << (32 - P.logN);
-            pw[l] = (TAB == kTabPair || TAB == kTabQuad) ? __ldcg(P.packed + l * 32 + lane) : 0u;
-            ps[l] = (P.sigma[l] & 2u) ? 0x1230u : 0x3210u;
+            pw[l] = TAB == kTabBits ? __ldcg(P.packed + l * 32 + lane) : 0u;
+            si[l] = inv_mod32(P.sigma[l]);
         }
     }
     const uint32_t cv = P.half << (32 - P.logN);
     const uint32_t top = 32 - P.logB;
     const uint32_t M = P.M, T = P.T, N = P.N;
-    // frequencies per thread and iteration: f (+ N/2 pair) (+ kN/4 quad)
-    const uint32_t span = TAB == kTabQuad ? N / 4 : (TAB == kTabPair ? N / 2 : N);
+    // register table: G = B/32 frequencies f + k span per thread, member k's
+    // counter at bit k << gsh
+    const uint32_t lgG = TAB == kTabBits ? P.logB - 5 : 0u;
+    const uint32_t gsh = 5 - lgG;
+    const uint32_t span = N >> lgG;
+    const uint32_t members = TAB == kTabBits ? member_mask(lgG) : 1u;
 
     uint32_t per = (span + P.vtiles - 1) / P.vtiles;
-    per = (per + kThreads - 1) / kThreads * kThreads;  // (N / span) * per <= kVoteTileF
-    const uint32_t stride = mode == kVoteFallback ? fb_ctas : P.vtiles;
+    per = (per + kThreads - 1) / kThreads * kThreads;  // (N / span) * per <= kVoteTileF (G <= 16)
+    const uint32_t stride = mode == kVoteFallback ? fb_ctas : (mode == kVotePrune ? J.vctas : P.vtiles);
     uint32_t my_cand = 0;
 
     auto enqueue = [&](uint32_t f, bool take) {
@@ -604,29 +641,27 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
         for (uint32_t base = f0; base < f1; base += kThreads) {
             const uint32_t f = base + threadIdx.x;
             const bool valid = f < f1;
-            if constexpr (TAB == kTabQuad) {
-                uint32_t acc = 0;  // byte k: strong count of f + kN/4
+            if constexpr (TAB == kTabBits) {
+                uint32_t x[LT];
 #pragma unroll
                 for (int l = 0; l < LT; ++l) {
                     const uint32_t t = av[l] * f + cv;
                     const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> top);  // lane = bucket mod 32
-                    const uint32_t r = __funnelshift_r(w, w, t >> 27);
-                    acc += __byte_perm(r & 0x01010101u, 0, ps[l]);
+                    x[l] = __funnelshift_r(w, w, (t >> 27) * si[l]);
                 }
-                enqueue(f, valid && (acc & 0xFFu) >= M);
-                enqueue(f + span, valid && ((acc >> 8) & 0xFFu) >= M);
-                enqueue(f + 2 * span, valid && ((acc >> 16) & 0xFFu) >= M);
-                enqueue(f + 3 * span, valid && (acc >> 24) >= M);
-            } else if constexpr (TAB == kTabPair) {
-                uint32_t acc = 0;
-#pragma unroll
-                for (int l = 0; l < LT; ++l) {
-                    const uint32_t t = av[l] * f + cv;
-                    const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> 27);  // lane: top 5 bucket bits
-                    acc += __funnelshift_r(w, w, t >> top) & 0x10001u;            // rotate by bucket mod 32
+                // at least M = ceil(L/2) strong loops (the plan's M for this L)
+                constexpr int NP = bit_length(LT);
+                uint32_t pl[NP];
+                count_planes<LT, NP>(x, pl);
+                uint32_t m = valid ? count_at_least<(LT + 1) / 2, NP>(pl) & members : 0u;
+                if (m) {
+                    uint32_t q = atomicAdd(&s_qn, (uint32_t)__popc(m));  // < kVoteTileF: one slot per f of the tile
+                    do {
+                        const uint32_t b = __ffs(m) - 1;
+                        m &= m - 1;
+                        queue[q++] = f + (b >> gsh) * span;
+                    } while (m);
                 }
-                enqueue(f, valid && (acc & 0xFFFFu) >= M);
-                enqueue(f + span, valid && (acc >> 16) >= M);
             } else {
                 uint32_t acc = 0;  // score | strong << 8
                 if constexpr (LT > 0) {
@@ -870,9 +905,9 @@ cudaError_t scan_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t 
         case 12: return scan_variant<12, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
         case 16: return scan_variant<16, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
         default:
-            if (TAB == kTabPair || TAB == kTabQuad) return cudaErrorInvalidValue;
-            return scan_variant<0, (TAB == kTabPair || TAB == kTabQuad) ? kTabGlobal : TAB>(
-                ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+            if (TAB == kTabBits) return cudaErrorInvalidValue;
+            return scan_variant<0, TAB == kTabBits ? kTabGlobal : TAB>(ln, ctas, mode, smem, fb_ctas, cand_out,
+                                                                      ncand_out, s);
     }
 }
 
@@ -895,15 +930,13 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
     return cudaGetLastError();
 }
 
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool pair, bool quad,
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
     const bool lt = L_uniform == 8 || L_uniform == 12 || L_uniform == 16;
-    if (mode == kVotePrune && quad && lt)
-        return scan_dispatch_l<kTabQuad>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
-    if (mode == kVotePrune && pair && lt)
-        return scan_dispatch_l<kTabPair>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+    if (mode == kVotePrune && bits && lt)
+        return scan_dispatch_l<kTabBits>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
         return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,
                                          ncand_out, s);

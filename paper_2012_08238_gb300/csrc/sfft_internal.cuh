@@ -45,8 +45,7 @@ struct PlanDev {
     uint32_t nsel, T, M;  // M = ceil(L/2): strong loops needed by the median bound
     uint32_t nchunk, rounds, rpc, tb, tiles;  // gather decomposition
     uint32_t vtiles;                          // vote tiles per job (<= kVoteTileF frequencies each)
-    uint32_t use_pair, lbpl;                  // B == 64: strong bits in registers (pairs), log2(B/32)
-    uint32_t use_quad;                        // 128 <= B <= 512: strong bits in registers (quads)
+    uint32_t use_bits;                        // 32 <= B <= 512: strong bits in registers (pruned scan)
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
     uint32_t sigma[kMaxL], tau[kMaxL];
@@ -57,7 +56,7 @@ struct PlanDev {
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
     float *loopkth;        // [L] ceil(K/L)-th largest energy of each loop
-    uint32_t *packed;      // [L][32]: lane j's strong bits (layout of the pair or quad scan)
+    uint32_t *packed;      // [L][32]: lane j's strong bits (register-table scan)
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
     uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
@@ -73,6 +72,7 @@ struct Job {
     float2 *val;
     int32_t *kout;
     uint32_t rpc, nchunk;  // gather split of this launch: rounds per chunk, chunks (<= plan's nchunk)
+    uint32_t vctas;        // pruned-scan CTAs of this job (each takes every vctas-th vote tile)
 };
 
 // Launch descriptor shared by all stage kernels: either one job passed by
@@ -96,10 +96,10 @@ sfft_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
                               cudaStream_t s);
-// L_uniform: common L of every job (0 when they differ); pair / quad: every
-// job has use_pair / use_quad (the pruned scan then uses the register table
-// of strong bits); fb_ctas: CTAs per job of a fallback launch (else ignored).
-cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool pair, bool quad,
+// L_uniform: common L of every job (0 when they differ); bits: every job has
+// use_bits (the pruned scan then uses the register table of strong bits);
+// fb_ctas: CTAs per job of a fallback launch (else ignored).
+cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s);
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s);
