@@ -231,8 +231,9 @@ Sizes plan_sizes(const sfft_plan *p) {
     return z;
 }
 
-// gather -> FFT/select -> scan -> estimate -> [fallback scan -> fallback
-// estimate] -> top-K, all stream-ordered.  With ev (kStages + 1 events) the
+// gather -> FFT/select -> scan -> estimate (inside the scan when it uses the
+// register table) -> [fallback scan -> fallback estimate] -> top-K, all
+// stream-ordered.  With ev (kStages + 1 events) the
 // events bracket the stages: gather, FFT/select, scan, estimate, fallback
 // (scan + estimate), top-K.
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
@@ -249,7 +250,9 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
                          s)) != cudaSuccess)
         return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess) return e;
+    if (!scan_estimates(z.L_uniform, z.bits) &&
+        (e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess)
+        return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.bits, z.max_flags,
                          kFallbackCtas, nullptr, nullptr, s)) != cudaSuccess)

@@ -497,6 +497,49 @@ __device__ float2 median_estimate(const PlanDev &P, const float2 *zhat, uint32_t
     }
 }
 
+// kept in at least T loops (the candidate test the register-table scan defers)
+template <int LT>
+__device__ __forceinline__ bool is_candidate(const PlanDev &P, uint32_t f) {
+    const uint32_t cv = P.half << (32 - P.logN), top = 32 - P.logB;
+    uint32_t score = 0;
+    if constexpr (LT > 0) {
+#pragma unroll
+        for (int l = 0; l < LT; ++l)
+            score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << (32 - P.logN)) * f + cv) >> top)) & 1u;
+    } else {
+        for (uint32_t l = 0; l < P.L; ++l)
+            score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << (32 - P.logN)) * f + cv) >> top)) & 1u;
+    }
+    return score >= P.T;
+}
+
+// Median estimate of f, appended to the job's records {f, key bits, re bits,
+// im bits} at *cnt when kept: by the pruned pass when f is a candidate whose
+// key reaches theta, by the fallback pass always (f is a listed candidate).
+template <int LT>
+__device__ __forceinline__ void estimate_record(const PlanDev &P, uint32_t f, bool prune, float theta,
+                                                uint32_t *cnt) {
+    bool keep = !prune || is_candidate<LT>(P, f);
+    float2 v = make_float2(0.f, 0.f);
+    float key = 0.f;
+    if (keep) {
+        v = median_estimate<LT>(P, P.zhat, f);
+        key = v.x * v.x + v.y * v.y;
+        keep = !prune || key >= theta;
+    }
+    const uint32_t act = __activemask();
+    const uint32_t bal = __ballot_sync(act, keep);
+    if (bal) {
+        const int leader = __ffs(bal) - 1;
+        uint32_t b0 = 0;
+        if ((threadIdx.x & 31) == (uint32_t)leader) b0 = atomicAdd(cnt, __popc(bal));
+        b0 = __shfl_sync(act, b0, leader);
+        if (keep)
+            P.surv[b0 + __popc(bal & lanemask_lt())] =
+                make_uint4(f, __float_as_uint(key), __float_as_uint(v.x), __float_as_uint(v.y));
+    }
+}
+
 // --------------------------------------------------------------- a4 + a5
 // Vote scan over one tile of frequencies of a job.
 //
@@ -578,7 +621,9 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
     __shared__ Job J;
     __shared__ uint32_t s_local, s_cand, s_qn, s_base;
     __shared__ int s_skip;
-    __shared__ uint32_t queue[kVoteTileF];
+    // register-table scan: survivors of several tiles wait for one estimate
+    // pass (flushed once more than a tile's worth is queued)
+    __shared__ uint32_t queue[TAB == kTabBits ? 2 * kVoteTileF : kVoteTileF];
     enter(ln, P, J, s_local);
     if (threadIdx.x == 0) {
         s_cand = 0;
@@ -655,7 +700,9 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
                 count_planes<LT, NP>(x, pl);
                 uint32_t m = valid ? count_at_least<(LT + 1) / 2, NP>(pl) & members : 0u;
                 if (m) {
-                    uint32_t q = atomicAdd(&s_qn, (uint32_t)__popc(m));  // < kVoteTileF: one slot per f of the tile
+                    // < 2 kVoteTileF: at most kVoteTileF queued before the tile,
+                    // one slot per f of the tile
+                    uint32_t q = atomicAdd(&s_qn, (uint32_t)__popc(m));
                     do {
                         const uint32_t b = __ffs(m) - 1;
                         m &= m - 1;
@@ -689,7 +736,19 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
         if (mode == kVoteCandidates) continue;
         __syncthreads();
         const uint32_t qn = s_qn;
-        if (qn) {
+        if constexpr (TAB == kTabBits) {
+            // pruned pass with the register table: queued survivors are
+            // estimated here (theta is final once the FFT/select stage ends)
+            if (qn > (uint32_t)kVoteTileF || (qn && tile + stride >= P.vtiles)) {
+                if (threadIdx.x == 0) atomicAdd(P.ctr + kNSurv, qn);
+                const float theta = __uint_as_float(P.ctr[kTheta]);
+                for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x)
+                    estimate_record<LT>(P, queue[i], true, theta, P.ctr + kNGe);
+                __syncthreads();
+                if (threadIdx.x == 0) s_qn = 0;
+                __syncthreads();
+            }
+        } else if (qn) {
             if (threadIdx.x == 0) s_base = atomicAdd(P.ctr + (mode == kVotePrune ? kNSurv : kNSurv2), qn);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) P.survf[s_base + i] = queue[i];
@@ -705,14 +764,6 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
     if (threadIdx.x == 0 && s_cand) atomicAdd(P.ctr + kNCand, s_cand);
 }
 
-// kept in at least T loops (the candidate test the register-table scan defers)
-__device__ __forceinline__ bool is_candidate(const PlanDev &P, uint32_t f) {
-    const uint32_t cv = P.half << (32 - P.logN), top = 32 - P.logB;
-    uint32_t score = 0;
-    for (uint32_t l = 0; l < P.L; ++l)
-        score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << (32 - P.logN)) * f + cv) >> top)) & 1u;
-    return score >= P.T;
-}
 
 // ------------------------------------------------------------------ a6
 // Median estimates of the listed frequencies of a job, kEstimateCtas CTAs per
@@ -732,28 +783,8 @@ __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode,
     const uint32_t n = P.ctr[prune ? kNSurv : kNSurv2];
     const float theta = prune ? __uint_as_float(P.ctr[kTheta]) : 0.f;
     uint32_t *cnt = P.ctr + (prune ? kNGe : kNRec2);
-    for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += ctas_per_job * kThreads) {
-        const uint32_t f = P.survf[i];
-        bool keep = !prune || is_candidate(P, f);
-        float2 v = make_float2(0.f, 0.f);
-        float key = 0.f;
-        if (keep) {
-            v = median_estimate<LT>(P, P.zhat, f);
-            key = v.x * v.x + v.y * v.y;
-            keep = !prune || key >= theta;
-        }
-        const uint32_t act = __activemask();
-        const uint32_t bal = __ballot_sync(act, keep);
-        if (bal) {
-            const int leader = __ffs(bal) - 1;
-            uint32_t b0 = 0;
-            if ((threadIdx.x & 31) == (uint32_t)leader) b0 = atomicAdd(cnt, __popc(bal));
-            b0 = __shfl_sync(act, b0, leader);
-            if (keep)
-                P.surv[b0 + __popc(bal & lanemask_lt())] =
-                    make_uint4(f, __float_as_uint(key), __float_as_uint(v.x), __float_as_uint(v.y));
-        }
-    }
+    for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += ctas_per_job * kThreads)
+        estimate_record<LT>(P, P.survf[i], prune, theta, cnt);
 }
 
 // ------------------------------------------------------------------ a7
@@ -934,8 +965,7 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
-    const bool lt = L_uniform == 8 || L_uniform == 12 || L_uniform == 16;
-    if (mode == kVotePrune && bits && lt)
+    if (mode == kVotePrune && scan_estimates(L_uniform, bits))
         return scan_dispatch_l<kTabBits>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
         return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,

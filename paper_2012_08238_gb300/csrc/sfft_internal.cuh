@@ -96,6 +96,13 @@ sfft_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
                               cudaStream_t s);
+// The pruned scan uses the register table of strong bits, and then also
+// estimates its survivors (no separate pruned estimate launch), when every
+// job has use_bits and they share L in {8, 12, 16}.
+inline bool scan_estimates(uint32_t L_uniform, bool bits) {
+    return bits && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16);
+}
+
 // L_uniform: common L of every job (0 when they differ); bits: every job has
 // use_bits (the pruned scan then uses the register table of strong bits);
 // fb_ctas: CTAs per job of a fallback launch (else ignored).
