@@ -214,6 +214,7 @@ namespace {
 struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0, max_K = 0;
+    uint32_t est_ctas = kEstimateCtas, est_smem = 0;  // pruned estimate: CTAs per job, staged table bytes
     bool bits = true;
 };
 
@@ -228,12 +229,12 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.max_flags = p->h.L * p->h.B * 2;
     z.L_uniform = p->h.L;
     z.bits = p->h.use_bits != 0;
+    z.est_smem = estimate_tab_bytes(p->h.N, p->h.B, p->h.L);
     return z;
 }
 
-// gather -> FFT/select -> scan -> estimate (inside the scan when it uses the
-// register table) -> [fallback scan -> fallback estimate] -> top-K, all
-// stream-ordered.  With ev (kStages + 1 events) the
+// gather -> FFT/select -> scan -> estimate -> [fallback scan -> fallback
+// estimate] -> top-K, all stream-ordered.  With ev (kStages + 1 events) the
 // events bracket the stages: gather, FFT/select, scan, estimate, fallback
 // (scan + estimate), top-K.
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
@@ -250,14 +251,13 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
                          s)) != cudaSuccess)
         return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    if (!scan_estimates(z.L_uniform, z.bits) &&
-        (e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, s)) != cudaSuccess)
+    if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, z.est_ctas, z.est_smem, s)) != cudaSuccess)
         return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.bits, z.max_flags,
                          kFallbackCtas, nullptr, nullptr, s)) != cudaSuccess)
         return e;
-    if ((e = launch_estimate(lf, z.jobs, kVoteFallback, z.L_uniform, s)) != cudaSuccess) return e;
+    if ((e = launch_estimate(lf, z.jobs, kVoteFallback, z.L_uniform, kFallbackCtas, 0, s)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     if ((e = launch_topk(lk, z.jobs, z.max_K, s)) != cudaSuccess) return e;
     return mark(6);
@@ -606,6 +606,15 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         z.bits = z.bits && s.bits;
         z.max_flags = std::max(z.max_flags, s.max_flags);
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
+        z.est_smem = (i == 0 || z.est_smem) && s.est_smem ? std::max(z.est_smem, s.est_smem) : 0u;
+    }
+    // pruned estimate with staged tables: one wave of resident CTAs over the
+    // batch (each CTA stages its job's tables once)
+    if (z.L_uniform != 8 && z.L_uniform != 12 && z.L_uniform != 16) z.est_smem = 0;
+    if (z.est_smem) {
+        const uint32_t fit = std::max<uint32_t>(1, kEstTabCtasPerSm * kNumSms / (uint32_t)count);
+        z.est_ctas = std::min<uint32_t>(kEstimateCtas, fit);
+        for (int32_t i = 0; i < count; ++i) cnt[(size_t)i * 6 + 5] = z.est_ctas;
     }
     // pruned scan: up to 4 vote tiles per CTA while the launch keeps at least
     // kScanWaves waves of resident CTAs (fewer CTAs amortise the per-CTA

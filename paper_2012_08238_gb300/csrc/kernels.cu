@@ -445,6 +445,18 @@ __device__ __forceinline__ float median_sorted(const float *a, uint32_t n) {
     return (n & 1) ? a[n / 2] : 0.5f * (a[n / 2 - 1] + a[n / 2]);
 }
 
+// Bucket value z of a frequency turned by exp(-2 pi i tau f / N) and scaled by
+// g = 1/G~(o); ph = (tau f mod N) 2^(32 - log2 N) is the turn as a 32-bit
+// fraction.
+__device__ __forceinline__ float2 turn_scale(float2 z, float2 g, uint32_t ph) {
+    float sn, cs;
+    // the signed fraction is an angle in [-pi, pi), where the fast intrinsic's
+    // absolute error (~2^-21) is far inside the value tolerance
+    __sincosf((float)(int32_t)ph * (2.0f * CUDART_PI_F / 4294967296.0f), &sn, &cs);
+    const float2 zp = make_float2(z.x * cs + z.y * sn, z.y * cs - z.x * sn);
+    return cmul(zp, g);
+}
+
 // Per-loop energy-concentration estimate of frequency f in loop l:
 // zhat_l[h] * exp(-2 pi i tau_l f / N) / G~(o).
 __device__ __forceinline__ float2 loop_estimate(const PlanDev &P, const float2 *zhat, uint32_t l, uint32_t f) {
@@ -452,14 +464,7 @@ __device__ __forceinline__ float2 loop_estimate(const PlanDev &P, const float2 *
     hash_freq(P, P.sigma[l], f, h, opos);
     const float2 z = zhat[(size_t)l * P.B + h];
     const float2 g = __ldg(P.ginv + opos);
-    const uint32_t r = (P.tau[l] * f) & P.mask;
-    const int32_t rs = (int32_t)(r << (32 - P.logN)) >> (32 - P.logN);  // in [-N/2, N/2)
-    float sn, cs;
-    // the integer reduction above leaves an angle in [-pi, pi), where the
-    // fast intrinsic's absolute error (~2^-21) is far inside the value tolerance
-    __sincosf((float)rs * (2.0f * CUDART_PI_F / (float)P.N), &sn, &cs);
-    const float2 zp = make_float2(z.x * cs + z.y * sn, z.y * cs - z.x * sn);
-    return cmul(zp, g);
+    return turn_scale(z, g, (P.tau[l] << (32 - P.logN)) * f);
 }
 
 template <int LT>
@@ -513,6 +518,103 @@ __device__ __forceinline__ bool is_candidate(const PlanDev &P, uint32_t f) {
     return score >= P.T;
 }
 
+// Pruned-pass estimate of survivor f with L = LT, appended to the records at
+// *cnt when f is a candidate whose key reaches theta.  One hash word per loop
+// feeds the kept-flag, bucket and gain loads, all issued before any is used.
+// Before the sort, f is dropped when neither median component can reach
+// a = sqrt(theta/2) (1 - 2^-10) in magnitude: a median >= a needs at least
+// M = ceil(L/2) values >= a, one <= -a as many <= -a, and with both medians
+// inside (-a, a) the computed key stays below theta.  Kept records are
+// bit-identical to median_estimate's.
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared-memory loads by 32-bit shared address (the staged estimate tables).
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+// Tables: the plan's in global memory (SM false), or copies in shared memory
+// (zt: zhat [L][B], gt: 1/G~ [N/B], kt: kept bits [L][B/32]).
+template <int LT, bool SM>
+__device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, float theta, float a,
+                                                uint32_t *cnt, const float2 *zt, const float2 *gt,
+                                                const uint32_t *kt) {
+    const uint32_t sN = 32 - P.logN, top = 32 - P.logB;
+    const uint32_t cv = P.half << sN;
+    const uint32_t osh = P.logB + sN;  // offset in the bucket: the word's bits below the bucket bits
+    const uint32_t B = P.B;
+    float2 z[LT], g[LT];
+    uint32_t ph[LT];
+    uint32_t kept = 0;
+#pragma unroll
+    for (int l = 0; l < LT; ++l) {
+        const uint32_t t = (P.sigma[l] << sN) * f + cv;
+        const uint32_t h = t >> top;
+        const uint32_t opos = osh < 32 ? (t << P.logB) >> osh : 0u;
+        if constexpr (SM) {
+            const uint32_t zb = (uint32_t)__cvta_generic_to_shared(zt);
+            const uint32_t gb = (uint32_t)__cvta_generic_to_shared(gt);
+            const uint32_t kb = (uint32_t)__cvta_generic_to_shared(kt);
+            kept += (lds_u32(kb + 4 * ((l * B + h) >> 5)) >> (h & 31u)) & 1u;
+            z[l] = lds_f2(zb + 8 * (l * B + h));
+            g[l] = lds_f2(gb + 8 * opos);
+        } else {
+            kept += __ldg(P.flags + l * B + h) & 1u;
+            z[l] = __ldg(P.zhat + l * B + h);
+            g[l] = __ldg(P.ginv + opos);
+        }
+        ph[l] = (P.tau[l] << sN) * f;
+    }
+    bool keep = kept >= P.T;
+    float re[LT], im[LT];
+    if (keep) {
+        uint32_t rp = 0, rn = 0, ip = 0, in = 0;
+#pragma unroll
+        for (int l = 0; l < LT; ++l) {
+            const float2 v = turn_scale(z[l], g[l], ph[l]);
+            re[l] = v.x;
+            im[l] = v.y;
+            rp += v.x >= a;
+            rn += v.x <= -a;
+            ip += v.y >= a;
+            in += v.y <= -a;
+        }
+        constexpr uint32_t M = (LT + 1) / 2;
+        keep = rp >= M || rn >= M || ip >= M || in >= M;
+    }
+    float2 v = make_float2(0.f, 0.f);
+    float key = 0.f;
+    if (keep) {
+        sort_net<LT>(re);
+        sort_net<LT>(im);
+        v = make_float2(median_sorted(re, LT), median_sorted(im, LT));
+        key = v.x * v.x + v.y * v.y;
+        keep = key >= theta;
+    }
+    const uint32_t act = __activemask();
+    const uint32_t bal = __ballot_sync(act, keep);
+    if (bal) {
+        const int leader = __ffs(bal) - 1;
+        uint32_t b0 = 0;
+        if ((threadIdx.x & 31) == (uint32_t)leader) b0 = atomicAdd(cnt, __popc(bal));
+        b0 = __shfl_sync(act, b0, leader);
+        if (keep)
+            P.surv[b0 + __popc(bal & lanemask_lt())] =
+                make_uint4(f, __float_as_uint(key), __float_as_uint(v.x), __float_as_uint(v.y));
+    }
+}
+
 // Median estimate of f, appended to the job's records {f, key bits, re bits,
 // im bits} at *cnt when kept: by the pruned pass when f is a candidate whose
 // key reaches theta, by the fallback pass always (f is a listed candidate).
@@ -541,27 +643,18 @@ __device__ __forceinline__ void estimate_record(const PlanDev &P, uint32_t f, bo
 }
 
 // --------------------------------------------------------------- a4 + a5
-// Vote scan over one tile of frequencies of a job.
+// Vote scan over the tiles of frequencies of a job.
 //
 // Pruned pass: only frequencies with at least M strong loops can reach the top
 // K (median bound), so they are queued per tile in shared memory and appended
-// to the job's survivor list; whether they are candidates (kept in >= T
-// loops) is checked when they are estimated.
-//
-// Register table (32 <= B <= 512, L in {8, 12, 16}): a thread takes the G =
-// B/32 frequencies f + kN/G.  Their hash words differ by k sigma_l 2^32/G,
-// so their buckets h + k sigma_l 32 share the lane h mod 32 of the packed
-// table, and one warp shuffle fetches the word holding all G strong bits.
-// A rotate by sigma^-1 * (h >> (log2 B - 5)) (the table's positions are
-// scaled by sigma^-1 to match) puts member k's bit at position k * 32/G in
-// every loop, so carry-save adders over the L rotated words count the
-// strong loops of all 32 positions at once (bit-sliced counters).
-// Fallback pass and candidate listing: the u16 kept/strong table (shared or
-// global memory); every candidate is counted and listed.
+// to the job's survivor list (k_scan_bits below does the same with a register
+// table and estimates them itself).  Fallback pass and candidate listing: the
+// u16 kept/strong table (shared or global memory); every candidate is
+// counted and listed.
 //
 // The bucket comes from t = (sigma_l << (32 - log2 N)) f + (half << (32 - log2 N))
 // mod 2^32, whose top log2 B bits are round-half-up(sigma_l f B / N) mod B.
-enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabBits = 2 };
+enum TableKind : int { kTabGlobal = 0, kTabSmem = 1 };
 
 // Full adder over 32 bit-lanes: a + b + c = s + 2 cy.
 __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &sum, uint32_t &cy) {
@@ -621,9 +714,7 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
     __shared__ Job J;
     __shared__ uint32_t s_local, s_cand, s_qn, s_base;
     __shared__ int s_skip;
-    // register-table scan: survivors of several tiles wait for one estimate
-    // pass (flushed once more than a tile's worth is queued)
-    __shared__ uint32_t queue[TAB == kTabBits ? 2 * kVoteTileF : kVoteTileF];
+    __shared__ uint32_t queue[kVoteTileF];
     enter(ln, P, J, s_local);
     if (threadIdx.x == 0) {
         s_cand = 0;
@@ -646,27 +737,17 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
         tab = tab_s;
     }
     constexpr int LR = LT > 0 ? LT : 1;
-    uint32_t av[LR], pw[LR], si[LR];
+    uint32_t av[LR];
     if constexpr (LT > 0) {
 #pragma unroll
-        for (int l = 0; l < LT; ++l) {
-            av[l] = P.sigma[l] << (32 - P.logN);
-            pw[l] = TAB == kTabBits ? __ldcg(P.packed + l * 32 + lane) : 0u;
-            si[l] = inv_mod32(P.sigma[l]);
-        }
+        for (int l = 0; l < LT; ++l) av[l] = P.sigma[l] << (32 - P.logN);
     }
     const uint32_t cv = P.half << (32 - P.logN);
     const uint32_t top = 32 - P.logB;
     const uint32_t M = P.M, T = P.T, N = P.N;
-    // register table: G = B/32 frequencies f + k span per thread, member k's
-    // counter at bit k << gsh
-    const uint32_t lgG = TAB == kTabBits ? P.logB - 5 : 0u;
-    const uint32_t gsh = 5 - lgG;
-    const uint32_t span = N >> lgG;
-    const uint32_t members = TAB == kTabBits ? member_mask(lgG) : 1u;
 
-    uint32_t per = (span + P.vtiles - 1) / P.vtiles;
-    per = (per + kThreads - 1) / kThreads * kThreads;  // (N / span) * per <= kVoteTileF (G <= 16)
+    uint32_t per = (N + P.vtiles - 1) / P.vtiles;
+    per = (per + kThreads - 1) / kThreads * kThreads;  // <= kVoteTileF
     const uint32_t stride = mode == kVoteFallback ? fb_ctas : (mode == kVotePrune ? J.vctas : P.vtiles);
     uint32_t my_cand = 0;
 
@@ -682,34 +763,11 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
 
     for (uint32_t tile = s_local; tile < P.vtiles; tile += stride) {
         const uint32_t f0 = tile * per;
-        const uint32_t f1 = min(span, f0 + per);
+        const uint32_t f1 = min(N, f0 + per);
         for (uint32_t base = f0; base < f1; base += kThreads) {
             const uint32_t f = base + threadIdx.x;
             const bool valid = f < f1;
-            if constexpr (TAB == kTabBits) {
-                uint32_t x[LT];
-#pragma unroll
-                for (int l = 0; l < LT; ++l) {
-                    const uint32_t t = av[l] * f + cv;
-                    const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> top);  // lane = bucket mod 32
-                    x[l] = __funnelshift_r(w, w, (t >> 27) * si[l]);
-                }
-                // at least M = ceil(L/2) strong loops (the plan's M for this L)
-                constexpr int NP = bit_length(LT);
-                uint32_t pl[NP];
-                count_planes<LT, NP>(x, pl);
-                uint32_t m = valid ? count_at_least<(LT + 1) / 2, NP>(pl) & members : 0u;
-                if (m) {
-                    // < 2 kVoteTileF: at most kVoteTileF queued before the tile,
-                    // one slot per f of the tile
-                    uint32_t q = atomicAdd(&s_qn, (uint32_t)__popc(m));
-                    do {
-                        const uint32_t b = __ffs(m) - 1;
-                        m &= m - 1;
-                        queue[q++] = f + (b >> gsh) * span;
-                    } while (m);
-                }
-            } else {
+            {
                 uint32_t acc = 0;  // score | strong << 8
                 if constexpr (LT > 0) {
 #pragma unroll
@@ -736,19 +794,7 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
         if (mode == kVoteCandidates) continue;
         __syncthreads();
         const uint32_t qn = s_qn;
-        if constexpr (TAB == kTabBits) {
-            // pruned pass with the register table: queued survivors are
-            // estimated here (theta is final once the FFT/select stage ends)
-            if (qn > (uint32_t)kVoteTileF || (qn && tile + stride >= P.vtiles)) {
-                if (threadIdx.x == 0) atomicAdd(P.ctr + kNSurv, qn);
-                const float theta = __uint_as_float(P.ctr[kTheta]);
-                for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x)
-                    estimate_record<LT>(P, queue[i], true, theta, P.ctr + kNGe);
-                __syncthreads();
-                if (threadIdx.x == 0) s_qn = 0;
-                __syncthreads();
-            }
-        } else if (qn) {
+        if (qn) {
             if (threadIdx.x == 0) s_base = atomicAdd(P.ctr + (mode == kVotePrune ? kNSurv : kNSurv2), qn);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) P.survf[s_base + i] = queue[i];
@@ -764,6 +810,85 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
     if (threadIdx.x == 0 && s_cand) atomicAdd(P.ctr + kNCand, s_cand);
 }
 
+
+// Pruned scan with the register table of strong bits (32 <= B <= 512, L in
+// {8, 12, 16}).
+//
+// A thread takes the G = B/32 frequencies f + kN/G.  Their hash words differ
+// by k sigma_l 2^32/G, so their buckets h + k sigma_l 32 share the lane
+// h mod 32 of the packed table, and one warp shuffle fetches the word holding
+// all G strong bits.  A rotate by sigma^-1 (h >> (log2 B - 5)) (the table's
+// positions are scaled by sigma^-1 to match) puts member k's bit at position
+// k 32/G in every loop, so carry-save adders over the L rotated words count
+// the strong loops of all 32 positions at once (bit-sliced counters).
+// Frequencies with at least M = ceil(L/2) strong loops are queued per tile in
+// shared memory and appended to the job's survivor list; candidacy is checked
+// when they are estimated.
+template <int LT>
+__global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
+    __shared__ PlanDev P;
+    __shared__ Job J;
+    __shared__ uint32_t s_local, s_qn, s_base;
+    __shared__ uint32_t queue[kVoteTileF];
+    enter(ln, P, J, s_local);
+    if (threadIdx.x == 0) s_qn = 0;
+
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t av[LT], pw[LT], si[LT];
+#pragma unroll
+    for (int l = 0; l < LT; ++l) {
+        av[l] = P.sigma[l] << (32 - P.logN);
+        pw[l] = __ldcg(P.packed + l * 32 + lane);
+        si[l] = inv_mod32(P.sigma[l]);
+    }
+    const uint32_t cv = P.half << (32 - P.logN);
+    const uint32_t top = 32 - P.logB;
+    // G = 2^lgG frequencies f + k span per thread, member k's counter at bit k << gsh
+    const uint32_t lgG = P.logB - 5;
+    const uint32_t gsh = 5 - lgG;
+    const uint32_t span = P.N >> lgG;
+    const uint32_t members = member_mask(lgG);
+    uint32_t per = (span + P.vtiles - 1) / P.vtiles;
+    per = (per + kThreads - 1) / kThreads * kThreads;  // G * per <= kVoteTileF (G <= 16)
+    __syncthreads();
+
+    for (uint32_t tile = s_local; tile < P.vtiles; tile += J.vctas) {
+        const uint32_t f0 = tile * per;
+        const uint32_t f1 = min(span, f0 + per);
+        for (uint32_t base = f0; base < f1; base += kThreads) {
+            const uint32_t f = base + threadIdx.x;
+            uint32_t x[LT];
+#pragma unroll
+            for (int l = 0; l < LT; ++l) {
+                const uint32_t t = av[l] * f + cv;
+                const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> top);  // lane = bucket mod 32
+                x[l] = __funnelshift_r(w, w, (t >> 27) * si[l]);
+            }
+            constexpr int NP = bit_length(LT);
+            uint32_t pl[NP];
+            count_planes<LT, NP>(x, pl);
+            uint32_t m = f < f1 ? count_at_least<(LT + 1) / 2, NP>(pl) & members : 0u;
+            if (m) {
+                uint32_t q = atomicAdd(&s_qn, (uint32_t)__popc(m));  // < kVoteTileF: one slot per f of the tile
+                do {
+                    const uint32_t b = __ffs(m) - 1;
+                    m &= m - 1;
+                    queue[q++] = f + (b >> gsh) * span;
+                } while (m);
+            }
+        }
+        __syncthreads();
+        const uint32_t qn = s_qn;
+        if (qn) {
+            if (threadIdx.x == 0) s_base = atomicAdd(P.ctr + kNSurv, qn);
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) P.survf[s_base + i] = queue[i];
+            __syncthreads();
+            if (threadIdx.x == 0) s_qn = 0;
+            __syncthreads();
+        }
+    }
+}
 
 // ------------------------------------------------------------------ a6
 // Median estimates of the listed frequencies of a job, kEstimateCtas CTAs per
@@ -783,8 +908,82 @@ __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode,
     const uint32_t n = P.ctr[prune ? kNSurv : kNSurv2];
     const float theta = prune ? __uint_as_float(P.ctr[kTheta]) : 0.f;
     uint32_t *cnt = P.ctr + (prune ? kNGe : kNRec2);
+    if constexpr (LT > 0) {
+        if (prune) {
+            const float a = sqrtf(0.5f * theta) * (1.0f - 1.0f / 1024.0f);
+            const uint32_t stride = ctas_per_job * kThreads;
+            uint32_t i = s_local * kThreads + threadIdx.x;
+            uint32_t fn = i < n ? __ldg(P.survf + i) : 0u;
+            for (; i < n; i += stride) {
+                const uint32_t f = fn;
+                if (i + stride < n) fn = __ldg(P.survf + i + stride);
+                estimate_pruned<LT, false>(P, f, theta, a, cnt, nullptr, nullptr, nullptr);
+            }
+            return;
+        }
+    }
     for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += ctas_per_job * kThreads)
         estimate_record<LT>(P, P.survf[i], prune, theta, cnt);
+}
+
+// Pruned-pass estimates with the job's tables staged in shared memory: zhat
+// (L B complex), 1/G~ (N/B complex) and the kept flags as bits.  A few CTAs
+// per job, each over a strided share of the survivors, so every lookup is a
+// shared-memory load.
+template <int LT>
+__global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t ctas_per_job) {
+    extern __shared__ float4 est_tab[];
+    __shared__ PlanDev P;
+    __shared__ Job J;
+    __shared__ uint32_t s_local;
+    enter(ln, P, J, s_local);
+    const uint32_t n = P.ctr[kNSurv];
+    if (s_local * kThreads >= n) return;  // nothing for this CTA (uniform)
+    const uint32_t LB = LT * P.B, NB = P.N >> P.logB;
+    float2 *zs = reinterpret_cast<float2 *>(est_tab);
+    float2 *gs = zs + LB;
+    uint32_t *ks = reinterpret_cast<uint32_t *>(gs + NB);
+    {
+        // zhat and 1/G~ by asynchronous 16-byte copies (all in flight at once;
+        // both tables start 256-byte aligned, LB is even)
+        const uint32_t zb = (uint32_t)__cvta_generic_to_shared(zs);
+        const uint32_t gb = (uint32_t)__cvta_generic_to_shared(gs);
+        for (uint32_t i = threadIdx.x; i < LB / 2; i += kThreads) cp_async16(zb + 16 * i, P.zhat + 2 * i);
+        for (uint32_t i = threadIdx.x; i < NB / 2; i += kThreads) cp_async16(gb + 16 * i, P.ginv + 2 * i);
+        if ((NB & 1u) && threadIdx.x == 0) gs[NB - 1] = __ldg(P.ginv + NB - 1);
+        // kept bits: word w from flags [32 w, 32 w + 32) (64 bytes, four 16-byte loads)
+        for (uint32_t w = threadIdx.x; w < LB / 32; w += kThreads) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(P.flags + 32 * w);
+            uint4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = __ldcg(src + k);
+            uint32_t word = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t c[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int b = 8 * k + 2 * j;
+                    word |= (c[j] & 1u) << b;
+                    word |= ((c[j] >> 16) & 1u) << (b + 1);
+                }
+            }
+            ks[w] = word;
+        }
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    const float theta = __uint_as_float(P.ctr[kTheta]);
+    const float a = sqrtf(0.5f * theta) * (1.0f - 1.0f / 1024.0f);
+    // the next survivor's frequency is fetched while this one is estimated
+    const uint32_t stride = ctas_per_job * kThreads;
+    uint32_t i = s_local * kThreads + threadIdx.x;
+    uint32_t fn = i < n ? __ldg(P.survf + i) : 0u;
+    for (; i < n; i += stride) {
+        const uint32_t f = fn;
+        if (i + stride < n) fn = __ldg(P.survf + i + stride);
+        estimate_pruned<LT, true>(P, f, theta, a, P.ctr + kNGe, zs, gs, ks);
+    }
 }
 
 // ------------------------------------------------------------------ a7
@@ -935,10 +1134,7 @@ cudaError_t scan_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t 
         case 8: return scan_variant<8, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
         case 12: return scan_variant<12, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
         case 16: return scan_variant<16, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
-        default:
-            if (TAB == kTabBits) return cudaErrorInvalidValue;
-            return scan_variant<0, TAB == kTabBits ? kTabGlobal : TAB>(ln, ctas, mode, smem, fb_ctas, cand_out,
-                                                                      ncand_out, s);
+        default: return scan_variant<0, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
     }
 }
 
@@ -965,20 +1161,32 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
-    if (mode == kVotePrune && scan_estimates(L_uniform, bits))
-        return scan_dispatch_l<kTabBits>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+    if (mode == kVotePrune && scan_uses_bits(L_uniform, bits)) {
+        switch (L_uniform) {
+            case 8: k_scan_bits<8><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 12: k_scan_bits<12><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            default: k_scan_bits<16><<<total_ctas, kThreads, 0, s>>>(ln); break;
+        }
+        return cudaGetLastError();
+    }
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
         return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,
                                          ncand_out, s);
     return scan_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
 }
 
-// kEstimateCtas CTAs per job for the pruned pass, kFallbackCtas for the
-// (usually idle) fallback pass; ln's prefix array must match.
-cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s) {
+cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, uint32_t prune_ctas,
+                            uint32_t tab_smem, cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
-    const uint32_t per = mode == kVoteFallback ? kFallbackCtas : kEstimateCtas;
+    const uint32_t per = mode == kVoteFallback ? kFallbackCtas : prune_ctas;
     const uint32_t ctas = njobs * per;
+    if (mode == kVotePrune && tab_smem && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16)) {
+        auto kern = L_uniform == 8 ? k_estimate_tab<8> : (L_uniform == 12 ? k_estimate_tab<12> : k_estimate_tab<16>);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_smem);
+        if (e != cudaSuccess) return e;
+        kern<<<ctas, kThreads, tab_smem, s>>>(ln, per);
+        return cudaGetLastError();
+    }
     switch (L_uniform) {
         case 8: k_estimate_surv<8><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
         case 12: k_estimate_surv<12><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;

@@ -18,7 +18,17 @@ constexpr int kTopkSmemMin = 4096;     // top-K sorts up to max(this, K) records
 constexpr int kFlagsSmemBytes = 96 * 1024;
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kFallbackCtas = 4;        // CTAs per job of the (usually idle) unpruned pass
-constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel
+constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
+constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
+constexpr int kEstTabCtasPerSm = 3;
+
+// Shared-memory bytes of a job's staged estimate tables: zhat (L B complex),
+// 1/G~ (N/B complex), kept bits (L B / 8 bytes); 0 when B < 32 (whole bit words).
+inline uint32_t estimate_tab_bytes(uint64_t N, uint32_t B, uint32_t L) {
+    if (B < 32) return 0;
+    const uint64_t b = 8ull * L * B + 8ull * (N / B) + (uint64_t)L * B / 8;
+    return b <= kEstTabMaxBytes ? (uint32_t)((b + 15) / 16 * 16) : 0;
+}
 
 // Per-plan counters in device memory (uint32 slots).
 enum Counter : int {
@@ -96,10 +106,9 @@ sfft_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
                               cudaStream_t s);
-// The pruned scan uses the register table of strong bits, and then also
-// estimates its survivors (no separate pruned estimate launch), when every
-// job has use_bits and they share L in {8, 12, 16}.
-inline bool scan_estimates(uint32_t L_uniform, bool bits) {
+// The pruned scan uses the register table of strong bits when every job has
+// use_bits and they share L in {8, 12, 16}.
+inline bool scan_uses_bits(uint32_t L_uniform, bool bits) {
     return bits && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16);
 }
 
@@ -109,7 +118,12 @@ inline bool scan_estimates(uint32_t L_uniform, bool bits) {
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
                         uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s);
-cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, cudaStream_t s);
+// prune_ctas: CTAs per job of the pruned pass (kFallbackCtas for the
+// fallback pass); ln's prefix array must match.  tab_smem > 0: every job's
+// tables fit that many bytes of shared memory (estimate_tab_bytes) and L is
+// uniform in {8, 12, 16}; the pruned pass then stages them there.
+cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, uint32_t prune_ctas,
+                            uint32_t tab_smem, cudaStream_t s);
 cudaError_t launch_topk(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);
