@@ -233,13 +233,12 @@ Sizes plan_sizes(const sfft_plan *p) {
     return z;
 }
 
-// gather -> FFT/select -> scan -> estimate -> [fallback scan -> fallback
-// estimate] -> top-K, all stream-ordered.  With ev (kStages + 1 events) the
-// events bracket the stages: gather, FFT/select, scan, estimate, fallback
-// (scan + estimate), top-K.
+// gather -> FFT/select -> scan -> estimate -> top-K (which runs a job's
+// fallback pass itself when needed), all stream-ordered.  With ev
+// (kStages + 1 events) the events bracket the stages: gather, FFT/select,
+// scan, estimate, fallback (empty: folded into top-K), top-K.
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
-                            const Launch &lf, const Launch &lk, const Sizes &z, cudaStream_t s,
-                            cudaEvent_t *ev = nullptr) {
+                            const Launch &lk, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
@@ -247,17 +246,12 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(1)) != cudaSuccess) return e;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.bits, z.max_flags, 0, nullptr, nullptr,
-                         s)) != cudaSuccess)
+    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.bits, z.max_flags, nullptr, nullptr, s)) !=
+        cudaSuccess)
         return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_estimate(le, z.jobs, kVotePrune, z.L_uniform, z.est_ctas, z.est_smem, s)) != cudaSuccess)
-        return e;
+    if ((e = launch_estimate(le, z.jobs, z.L_uniform, z.est_ctas, z.est_smem, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    if ((e = launch_vote(lf, z.jobs * kFallbackCtas, kVoteFallback, z.L_uniform, z.bits, z.max_flags,
-                         kFallbackCtas, nullptr, nullptr, s)) != cudaSuccess)
-        return e;
-    if ((e = launch_estimate(lf, z.jobs, kVoteFallback, z.L_uniform, kFallbackCtas, 0, s)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     if ((e = launch_topk(lk, z.jobs, z.max_K, s)) != cudaSuccess) return e;
     return mark(6);
@@ -525,7 +519,7 @@ extern "C" sfft_status sfft_plan_last_stats(const sfft_plan *p, sfft_exec_stats 
     SFFT_CUDA_TRY(cudaMemcpy(c, p->h.ctr, sizeof(c), cudaMemcpyDeviceToHost));
     const bool fb = c[kNGe] < (uint32_t)p->K;
     st->candidates = fb ? (int64_t)c[kNCand] : -1;
-    st->estimated = fb ? c[kNSurv2] : c[kNSurv];
+    st->estimated = fb ? c[kNCand] : c[kNSurv];  // the fallback pass estimates every candidate
     st->recorded = fb ? c[kNRec2] : c[kNGe];
     st->fallback = fb ? 1 : 0;
     float th;
@@ -542,7 +536,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
         return SFFT_EINVAL;
     }
     const Launch ln = single(make_job(p, x_dev, idx_dev, val_dev, k_out_dev));
-    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
 }
 
@@ -599,7 +593,7 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         c[1] = s.select;
         c[2] = s.vote;
         c[3] = 1;
-        c[4] = kFallbackCtas;
+        c[4] = 0;  // (unused slot)
         c[5] = kEstimateCtas;
         z.max_B = std::max(z.max_B, s.max_B);
         z.max_K = std::max(z.max_K, s.max_K);
@@ -671,7 +665,7 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         ln[k].njobs = count;
         memset(&ln[k].one, 0, sizeof(Job));
     }
-    return launch_pipeline(ln[0], ln[1], ln[2], ln[5], ln[4], ln[3], b.z, s, ev);
+    return launch_pipeline(ln[0], ln[1], ln[2], ln[5], ln[3], b.z, s, ev);
 }
 
 sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,
@@ -912,8 +906,8 @@ extern "C" sfft_status sfft_vote(sfft_plan *p, const int32_t *sel_dev, int32_t *
     const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
     SFFT_CUDA_TRY(cudaMemsetAsync(n_cand_dev, 0, sizeof(int32_t), s));
     SFFT_CUDA_TRY(launch_flags_from_sel(p->d, p->h.L, sel_dev, s));
-    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, 0,
-                              cand_dev, n_cand_dev, s));
+    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, cand_dev,
+                              n_cand_dev, s));
     return SFFT_OK;
 }
 

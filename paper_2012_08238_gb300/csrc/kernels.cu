@@ -6,10 +6,10 @@
 // memory and works on one tile of that job.
 //
 // Pipeline per job: k_gather (a1) -> k_fft_select (a2, a3; its last CTA also
-// builds the vote tables) -> k_vote_scan (a4, a5: candidates and survivors of
-// the median bound) -> k_estimate_surv (a6: estimates, keeps key >= theta)
-// -> [k_vote_scan, k_estimate_surv in fallback mode: idle unless fewer than K
-// estimates reached theta] -> k_topk (a7).
+// builds the vote tables) -> k_scan_bits or k_vote_scan (a4, a5: survivors of
+// the median bound) -> k_estimate_tab or k_estimate_surv (a6: estimates,
+// keeps key >= theta) -> k_topk (a7; runs the unpruned fallback pass first
+// when fewer than K estimates reached theta).
 #include <math_constants.h>
 
 #include "sfft_internal.cuh"
@@ -410,7 +410,6 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         P.ctr[kNCand] = 0;
         P.ctr[kNSurv] = 0;
         P.ctr[kNGe] = 0;
-        P.ctr[kNSurv2] = 0;
         P.ctr[kNRec2] = 0;
     }
 }
@@ -707,22 +706,15 @@ __device__ __forceinline__ uint32_t member_mask(uint32_t lgG) {
 }
 
 template <int LT, int TAB>
-__global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uint32_t fb_ctas, int32_t *cand_out,
-                                                        int32_t *ncand_out) {
+__global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int32_t *cand_out, int32_t *ncand_out) {
     extern __shared__ uint16_t tab_s[];
     __shared__ PlanDev P;
     __shared__ Job J;
-    __shared__ uint32_t s_local, s_cand, s_qn, s_base;
-    __shared__ int s_skip;
+    __shared__ uint32_t s_local, s_qn, s_base;
     __shared__ uint32_t queue[kVoteTileF];
     enter(ln, P, J, s_local);
-    if (threadIdx.x == 0) {
-        s_cand = 0;
-        s_qn = 0;
-        s_skip = mode == kVoteFallback && !needs_fallback(P);
-    }
+    if (threadIdx.x == 0) s_qn = 0;
     __syncthreads();
-    if (s_skip) return;
 
     const uint32_t L = LT > 0 ? (uint32_t)LT : P.L;
     const uint32_t B = P.B;
@@ -748,8 +740,7 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
 
     uint32_t per = (N + P.vtiles - 1) / P.vtiles;
     per = (per + kThreads - 1) / kThreads * kThreads;  // <= kVoteTileF
-    const uint32_t stride = mode == kVoteFallback ? fb_ctas : (mode == kVotePrune ? J.vctas : P.vtiles);
-    uint32_t my_cand = 0;
+    const uint32_t stride = mode == kVotePrune ? J.vctas : P.vtiles;
 
     auto enqueue = [&](uint32_t f, bool take) {
         const uint32_t bs = __ballot_sync(0xFFFFFFFFu, take);
@@ -787,15 +778,14 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
                     }
                     continue;
                 }
-                my_cand += cand;
-                enqueue(f, mode == kVoteFallback ? cand : cand && (acc >> 8) >= M);
+                enqueue(f, cand && (acc >> 8) >= M);
             }
         }
         if (mode == kVoteCandidates) continue;
         __syncthreads();
         const uint32_t qn = s_qn;
         if (qn) {
-            if (threadIdx.x == 0) s_base = atomicAdd(P.ctr + (mode == kVotePrune ? kNSurv : kNSurv2), qn);
+            if (threadIdx.x == 0) s_base = atomicAdd(P.ctr + kNSurv, qn);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) P.survf[s_base + i] = queue[i];
             __syncthreads();
@@ -803,11 +793,6 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, uin
             __syncthreads();
         }
     }
-    if (mode != kVoteFallback) return;
-    my_cand = __reduce_add_sync(0xFFFFFFFFu, my_cand);
-    if (lane == 0 && my_cand) atomicAdd(&s_cand, my_cand);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_cand) atomicAdd(P.ctr + kNCand, s_cand);
 }
 
 
@@ -891,39 +876,33 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
 }
 
 // ------------------------------------------------------------------ a6
-// Median estimates of the listed frequencies of a job, kEstimateCtas CTAs per
-// job.  The pruned pass keeps candidates whose key >= theta; the fallback pass
-// keeps all.  Records: {f, key bits, re bits, im bits}.
+// Pruned-pass median estimates of the job's survivors, ctas_per_job CTAs per
+// job: candidates whose key reaches theta are recorded as {f, key bits, re
+// bits, im bits}.
 template <int LT>
-__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, int mode, uint32_t ctas_per_job) {
+__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t ctas_per_job) {
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
-    __shared__ int s_skip;
     enter(ln, P, J, s_local);
-    if (threadIdx.x == 0) s_skip = mode == kVoteFallback && !needs_fallback(P);
-    __syncthreads();
-    if (s_skip) return;
-    const bool prune = mode == kVotePrune;
-    const uint32_t n = P.ctr[prune ? kNSurv : kNSurv2];
-    const float theta = prune ? __uint_as_float(P.ctr[kTheta]) : 0.f;
-    uint32_t *cnt = P.ctr + (prune ? kNGe : kNRec2);
+    const uint32_t n = P.ctr[kNSurv];
+    const float theta = __uint_as_float(P.ctr[kTheta]);
+    uint32_t *cnt = P.ctr + kNGe;
+    const uint32_t stride = ctas_per_job * kThreads;
     if constexpr (LT > 0) {
-        if (prune) {
-            const float a = sqrtf(0.5f * theta) * (1.0f - 1.0f / 1024.0f);
-            const uint32_t stride = ctas_per_job * kThreads;
-            uint32_t i = s_local * kThreads + threadIdx.x;
-            uint32_t fn = i < n ? __ldg(P.survf + i) : 0u;
-            for (; i < n; i += stride) {
-                const uint32_t f = fn;
-                if (i + stride < n) fn = __ldg(P.survf + i + stride);
-                estimate_pruned<LT, false>(P, f, theta, a, cnt, nullptr, nullptr, nullptr);
-            }
-            return;
+        const float a = sqrtf(0.5f * theta) * (1.0f - 1.0f / 1024.0f);
+        // the next survivor's frequency is fetched while this one is estimated
+        uint32_t i = s_local * kThreads + threadIdx.x;
+        uint32_t fn = i < n ? __ldg(P.survf + i) : 0u;
+        for (; i < n; i += stride) {
+            const uint32_t f = fn;
+            if (i + stride < n) fn = __ldg(P.survf + i + stride);
+            estimate_pruned<LT, false>(P, f, theta, a, cnt, nullptr, nullptr, nullptr);
         }
+    } else {
+        for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += stride)
+            estimate_record<LT>(P, P.survf[i], true, theta, cnt);
     }
-    for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += ctas_per_job * kThreads)
-        estimate_record<LT>(P, P.survf[i], prune, theta, cnt);
 }
 
 // Pruned-pass estimates with the job's tables staged in shared memory: zhat
@@ -991,6 +970,38 @@ __device__ __forceinline__ unsigned long long surv_key(uint4 r) {
     return ((unsigned long long)r.y << 32) | (uint32_t)(~r.x);  // key desc, then f asc
 }
 
+// Records up to this many are ranked by counting comparisons.
+constexpr uint32_t kRankMax = 1024;
+
+// Fallback pass of one job inside its top-K CTA, taken when fewer than K
+// pruned records reached theta: every candidate (kept in >= T loops) is
+// counted, estimated and recorded (kNCand, kNRec2).  A single CTA scans all N
+// frequencies, so such a job is slow, but the pass is exact and the common
+// case launches nothing for it.
+__device__ void fallback_pass(const PlanDev &P, uint32_t *s_cnt) {
+    if (threadIdx.x == 0) *s_cnt = 0;
+    __syncthreads();
+    const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
+    uint32_t cand = 0;
+    for (uint32_t base = 0; base < P.N; base += blockDim.x) {
+        const uint32_t f = base + threadIdx.x;
+        bool c = false;
+        if (f < P.N) {
+            uint32_t score = 0;
+            for (uint32_t l = 0; l < P.L; ++l)
+                score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << sN) * f + cv) >> top)) & 1u;
+            c = score >= P.T;
+        }
+        cand += c;
+        if (c) estimate_record<0>(P, f, false, 0.f, P.ctr + kNRec2);
+    }
+    cand = __reduce_add_sync(0xFFFFFFFFu, cand);
+    if ((threadIdx.x & 31) == 0 && cand) atomicAdd(s_cnt, cand);
+    __syncthreads();
+    if (threadIdx.x == 0) P.ctr[kNCand] = *s_cnt;
+    __syncthreads();
+}
+
 // One CTA per job: the k_out = min(K, candidates) recorded estimates of
 // largest magnitude (ties to the lower f), written sorted by f.  Records are
 // those of the pruned pass (candidates with key >= theta) when at least K of
@@ -1003,16 +1014,44 @@ __global__ void __launch_bounds__(kThreads) k_topk(Launch ln, uint32_t cap) {
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local, s_S, s_kout, s_hist[256], s_need, s_cnt;
+    __shared__ int s_fb;
     __shared__ unsigned long long s_prefix, s_pmask;
     enter(ln, P, J, s_local);
+    if (threadIdx.x == 0) s_fb = needs_fallback(P);
+    __syncthreads();
+    if (s_fb) fallback_pass(P, &s_cnt);
     if (threadIdx.x == 0) {
-        const bool fb = needs_fallback(P);
-        s_S = fb ? P.ctr[kNRec2] : P.ctr[kNGe];
-        s_kout = fb ? min(P.K, P.ctr[kNCand]) : P.K;  // without fallback >= K candidates exist
+        s_S = s_fb ? P.ctr[kNRec2] : P.ctr[kNGe];
+        s_kout = s_fb ? min(P.K, P.ctr[kNCand]) : P.K;  // without fallback >= K candidates exist
     }
     __syncthreads();
     const uint32_t S = s_S, kout = s_kout;
     const uint4 *surv = P.surv;
+    if (S <= kRankMax) {
+        // ranks by counting: record i wins when fewer than kout keys exceed
+        // its key (keys are distinct: f breaks ties); winners are then placed
+        // by the number of winning frequencies below theirs
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) tk[i] = surv_key(surv[i]);
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+            const unsigned long long k = tk[i];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < S; ++j) r += tk[j] > k;
+            pay[i] = r < kout ? ~(uint32_t)k : 0xFFFFFFFFu;  // the winner's f, else above every f
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+            const uint32_t f = pay[i];
+            if (f == 0xFFFFFFFFu) continue;
+            uint32_t pos = 0;
+            for (uint32_t j = 0; j < S; ++j) pos += pay[j] < f;
+            const uint4 r = surv[i];
+            J.idx[pos] = (int32_t)f;
+            J.val[pos] = make_float2(__uint_as_float(r.z), __uint_as_float(r.w));
+        }
+        if (threadIdx.x == 0) *J.kout = (int32_t)kout;
+        return;
+    }
     if (S <= cap) {
         uint32_t n2 = 1;
         while (n2 < S) n2 <<= 1;
@@ -1116,25 +1155,25 @@ __global__ void k_flags_from_sel(const PlanDev *pd, const int32_t *sel) {
 }
 
 template <int LT, int TAB>
-cudaError_t scan_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, uint32_t fb_ctas,
-                         int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
+cudaError_t scan_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, int32_t *cand_out,
+                         int32_t *ncand_out, cudaStream_t s) {
     auto kern = k_vote_scan<LT, TAB>;
     if (TAB == kTabSmem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<ctas, kThreads, TAB == kTabSmem ? smem : 0, s>>>(ln, mode, fb_ctas, cand_out, ncand_out);
+    kern<<<ctas, kThreads, TAB == kTabSmem ? smem : 0, s>>>(ln, mode, cand_out, ncand_out);
     return cudaGetLastError();
 }
 
 template <int TAB>
-cudaError_t scan_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t L, uint32_t smem, uint32_t fb_ctas,
-                            int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
+cudaError_t scan_dispatch_l(const Launch &ln, uint32_t ctas, int mode, uint32_t L, uint32_t smem, int32_t *cand_out,
+                            int32_t *ncand_out, cudaStream_t s) {
     switch (L) {
-        case 8: return scan_variant<8, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
-        case 12: return scan_variant<12, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
-        case 16: return scan_variant<16, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
-        default: return scan_variant<0, TAB>(ln, ctas, mode, smem, fb_ctas, cand_out, ncand_out, s);
+        case 8: return scan_variant<8, TAB>(ln, ctas, mode, smem, cand_out, ncand_out, s);
+        case 12: return scan_variant<12, TAB>(ln, ctas, mode, smem, cand_out, ncand_out, s);
+        case 16: return scan_variant<16, TAB>(ln, ctas, mode, smem, cand_out, ncand_out, s);
+        default: return scan_variant<0, TAB>(ln, ctas, mode, smem, cand_out, ncand_out, s);
     }
 }
 
@@ -1158,8 +1197,7 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
 }
 
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
-                        uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
-                        cudaStream_t s) {
+                        uint32_t max_flags_bytes, int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
     if (mode == kVotePrune && scan_uses_bits(L_uniform, bits)) {
         switch (L_uniform) {
@@ -1170,17 +1208,15 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
         return cudaGetLastError();
     }
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
-        return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, fb_ctas, cand_out,
-                                         ncand_out, s);
-    return scan_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, fb_ctas, cand_out, ncand_out, s);
+        return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, cand_out, ncand_out, s);
+    return scan_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, cand_out, ncand_out, s);
 }
 
-cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, uint32_t prune_ctas,
-                            uint32_t tab_smem, cudaStream_t s) {
+cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
+                            cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
-    const uint32_t per = mode == kVoteFallback ? kFallbackCtas : prune_ctas;
     const uint32_t ctas = njobs * per;
-    if (mode == kVotePrune && tab_smem && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16)) {
+    if (tab_smem && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16)) {
         auto kern = L_uniform == 8 ? k_estimate_tab<8> : (L_uniform == 12 ? k_estimate_tab<12> : k_estimate_tab<16>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_smem);
         if (e != cudaSuccess) return e;
@@ -1188,10 +1224,10 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t
         return cudaGetLastError();
     }
     switch (L_uniform) {
-        case 8: k_estimate_surv<8><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
-        case 12: k_estimate_surv<12><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
-        case 16: k_estimate_surv<16><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
-        default: k_estimate_surv<0><<<ctas, kThreads, 0, s>>>(ln, mode, per); break;
+        case 8: k_estimate_surv<8><<<ctas, kThreads, 0, s>>>(ln, per); break;
+        case 12: k_estimate_surv<12><<<ctas, kThreads, 0, s>>>(ln, per); break;
+        case 16: k_estimate_surv<16><<<ctas, kThreads, 0, s>>>(ln, per); break;
+        default: k_estimate_surv<0><<<ctas, kThreads, 0, s>>>(ln, per); break;
     }
     return cudaGetLastError();
 }

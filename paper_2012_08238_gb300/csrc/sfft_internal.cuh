@@ -17,7 +17,6 @@ constexpr int kMaxLogN = 30;
 constexpr int kTopkSmemMin = 4096;     // top-K sorts up to max(this, K) records in shared memory
 constexpr int kFlagsSmemBytes = 96 * 1024;
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
-constexpr int kFallbackCtas = 4;        // CTAs per job of the (usually idle) unpruned pass
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
 constexpr int kEstTabCtasPerSm = 3;
@@ -32,14 +31,13 @@ inline uint32_t estimate_tab_bytes(uint64_t N, uint32_t B, uint32_t L) {
 
 // Per-plan counters in device memory (uint32 slots).
 enum Counter : int {
-    kNCand = 0,    // candidates (score >= T), counted by the fallback scan only
+    kNCand = 0,    // candidates (score >= T), counted by the fallback pass only
     kNSurv = 1,    // survivors of the median bound listed by the pruned scan
     kNGe = 2,      // their estimates with key >= theta (records of the pruned pass)
-    kNSurv2 = 3,   // candidates listed by the unpruned fallback scan
     kSelDone = 4,  // loops finished by the FFT/select kernel (last-block pattern)
     kTheta = 5,    // prune threshold theta (float bits)
     kErr = 6,      // device-side error word (0 = none)
-    kNRec2 = 7,    // records written by the unpruned fallback pass
+    kNRec2 = 7,    // records written by the unpruned fallback pass (in the top-K kernel)
     kNumCounters = 16
 };
 
@@ -96,7 +94,7 @@ struct Launch {
     Job one;
 };
 
-enum VoteMode : int { kVotePrune = 0, kVoteFallback = 1, kVoteCandidates = 2 };
+enum VoteMode : int { kVotePrune = 0, kVoteCandidates = 2 };
 
 // ---------------------------------------------------------------- host side
 void set_error(const std::string &msg);
@@ -113,17 +111,17 @@ inline bool scan_uses_bits(uint32_t L_uniform, bool bits) {
 }
 
 // L_uniform: common L of every job (0 when they differ); bits: every job has
-// use_bits (the pruned scan then uses the register table of strong bits);
-// fb_ctas: CTAs per job of a fallback launch (else ignored).
+// use_bits (the pruned scan then uses the register table of strong bits).
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
-                        uint32_t max_flags_bytes, uint32_t fb_ctas, int32_t *cand_out, int32_t *ncand_out,
-                        cudaStream_t s);
-// prune_ctas: CTAs per job of the pruned pass (kFallbackCtas for the
-// fallback pass); ln's prefix array must match.  tab_smem > 0: every job's
-// tables fit that many bytes of shared memory (estimate_tab_bytes) and L is
-// uniform in {8, 12, 16}; the pruned pass then stages them there.
-cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, int mode, uint32_t L_uniform, uint32_t prune_ctas,
-                            uint32_t tab_smem, cudaStream_t s);
+                        uint32_t max_flags_bytes, int32_t *cand_out, int32_t *ncand_out, cudaStream_t s);
+// Pruned-pass estimates, per CTAs per job (ln's prefix array must match).
+// tab_smem > 0: every job's tables fit that many bytes of shared memory
+// (estimate_tab_bytes) and L is uniform in {8, 12, 16}; they are then staged
+// there.
+cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
+                            cudaStream_t s);
+// Top-K per job (one CTA each), running the job's fallback pass first when
+// fewer than K pruned records reached theta.
 cudaError_t launch_topk(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);

@@ -269,6 +269,42 @@ def test_fallback_counts_candidates():
     assert st.fallback == 1 and st.candidates == len(ref["cand"]) == st.recorded
 
 
+@pytest.mark.parametrize("K, n_rec_min", [(8, 1025), (16, 4097)])
+def test_zero_signal_ranks_every_record(K, n_rec_min):
+    # all keys 0 and theta 0: every candidate is recorded; the top K are the
+    # lowest candidate frequencies (ties to the lower f).  K = 8 gives ~2.8 K
+    # records (sorting path), K = 16 ~10.7 K (radix-select path).
+    N, B, L = 1 << 14, 64, 6
+    plan, op = _pair(N, K, B, B * 35, L, 3, c=2, T=3)
+    x = np.zeros(N, np.complex64)
+    ref = oracle.sfft(op, x, intermediates=True)
+    idx, val, k = run_execute(plan, x)
+    st = sfft.sfft_plan_last_stats(plan)
+    assert st.fallback == 0 and st.recorded == len(ref["cand"]) >= n_rec_min
+    assert k == ref["k_out"] == K
+    assert np.array_equal(idx, ref["idx"])
+    assert np.all(val == 0)
+
+
+def test_fallback_with_many_candidates():
+    # four strong coefficients, K = 16: fewer than K estimates reach theta, so
+    # the top-K kernel runs the unpruned pass over ~10 K candidates
+    N, K, B, L = 1 << 14, 16, 64, 6
+    plan, op = _pair(N, K, B, B * 35, L, 5, c=2, T=3)
+    rng = np.random.default_rng(5)
+    x = _sparse(N, [101, 2000, 7777, 12001], [1.0, -0.8j, 0.9, 0.7 + 0.7j])
+    x = (x + 1e-3 * (rng.standard_normal(N) + 1j * rng.standard_normal(N))).astype(np.complex64)
+    ref = oracle.sfft(op, x, intermediates=True)
+    idx, val, k = run_execute(plan, x)
+    st = sfft.sfft_plan_last_stats(plan)
+    assert st.fallback == 1 and st.candidates == len(ref["cand"]) == st.recorded > 4096
+    assert k == ref["k_out"] == K
+    est_of = dict(zip(ref["cand"].tolist(), ref["est"].tolist()))
+    _valid_topk(est_of, set(idx.tolist()), ref["idx"], K)
+    for f in (101, 2000, 7777, 12001):
+        assert f in idx
+
+
 def test_repeat_execute_is_deterministic():
     W = configs.EXACT_N16
     plan = sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, 1)
