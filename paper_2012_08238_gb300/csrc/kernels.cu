@@ -135,6 +135,52 @@ __device__ uint32_t block_kth_largest(const uint32_t *v, uint32_t n, uint32_t k,
     return *s_prefix;
 }
 
+// The k1-th and k2-th largest of n 32-bit keys (1 <= k1, k2 <= n < 65536) in
+// one sequence of four radix passes: two 256-bin histograms per pass, their
+// counts packed into 16-bit halves of one word for a single block scan.
+// Returns the k1-th key (*s_need: keys equal to it within the top k1) and
+// stores the k2-th in *kth2.  hist holds 256 words.  Called by all 256 threads.
+__device__ uint32_t block_kth_largest2(const uint32_t *v, uint32_t n, uint32_t k1, uint32_t k2, uint32_t *hist,
+                                       uint32_t *wsum, uint32_t *s_prefix, uint32_t *s_need, uint32_t *kth2) {
+    __shared__ uint32_t s_prefix2, s_need2;
+    if (threadIdx.x == 0) {
+        *s_prefix = 0;
+        *s_need = k1;
+        s_prefix2 = 0;
+        s_need2 = k2;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 4; ++pass) {
+        const int sh = 24 - 8 * pass;
+        const uint32_t pmask = pass == 0 ? 0u : (0xFFFFFFFFu << (sh + 8));
+        const uint32_t p1 = *s_prefix, need1 = *s_need, p2 = s_prefix2, need2 = s_need2;
+        hist[threadIdx.x] = 0;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
+            const uint32_t u = v[i];
+            const uint32_t add = ((u & pmask) == p1 ? 1u : 0u) | ((u & pmask) == p2 ? 0x10000u : 0u);
+            if (add) atomicAdd(&hist[(u >> sh) & 255u], add);
+        }
+        __syncthreads();
+        const uint32_t c = hist[255 - threadIdx.x];  // thread t scans bins from the top
+        const uint32_t incl = block_incl_scan(c, wsum);
+        const uint32_t excl = incl - c;
+        const uint32_t c1 = c & 0xFFFFu, i1 = incl & 0xFFFFu, e1 = excl & 0xFFFFu;
+        const uint32_t c2 = c >> 16, i2 = incl >> 16, e2 = excl >> 16;
+        if (c1 > 0 && e1 < need1 && need1 <= i1) {
+            *s_prefix = p1 | ((255u - threadIdx.x) << sh);
+            *s_need = need1 - e1;
+        }
+        if (c2 > 0 && e2 < need2 && need2 <= i2) {
+            s_prefix2 = p2 | ((255u - threadIdx.x) << sh);
+            s_need2 = need2 - e2;
+        }
+        __syncthreads();
+    }
+    *kth2 = s_prefix2;
+    return *s_prefix;
+}
+
 // Round-half-up flat-filter hash of frequency f in loop l: bucket h and the
 // offset o from the bucket centre, returned as o + half in [0, N/B).
 __device__ __forceinline__ void hash_freq(const PlanDev &P, uint32_t sigma, uint32_t f, uint32_t &h,
@@ -276,13 +322,21 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
             for (uint32_t k = threadIdx.x; k < B / 2; k += blockDim.x) tw_s[k] = __ldg(P.tw + k);
         const size_t cstride = (size_t)P.L * B;
         for (uint32_t j = threadIdx.x; j < B; j += blockDim.x) {
+            // chunk order, up to 8 chunk loads in flight at once
             float2 acc = make_float2(0.f, 0.f);
             const float2 *src = P.partial + (size_t)l * B + j;
-#pragma unroll 4
-            for (uint32_t c = 0; c < nchunk; ++c) {
-                const float2 v = src[c * cstride];
-                acc.x += v.x;
-                acc.y += v.y;
+            for (uint32_t c0 = 0; c0 < nchunk; c0 += 8) {
+                float2 v[8];
+#pragma unroll
+                for (uint32_t k = 0; k < 8; ++k)
+                    v[k] = c0 + k < nchunk ? __ldcg(src + (c0 + k) * cstride) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (uint32_t k = 0; k < 8; ++k) {
+                    if (c0 + k < nchunk) {
+                        acc.x += v[k].x;
+                        acc.y += v[k].y;
+                    }
+                }
             }
             buf[__brev(j) >> (32 - logB)] = acc;
         }
@@ -330,8 +384,15 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         __syncthreads();
         for (uint32_t s = threadIdx.x; s < P.nsel; s += blockDim.x) frow[~(uint32_t)sm[s]] = 1;
     } else {
-        // kept = energy above the nsel-th largest, plus the lowest-index ties
-        const uint32_t kth = block_kth_largest<false>(en_s, B, P.nsel, s_hist, s_wsum, &s_prefix, &s_need);
+        // kept = energy above the nsel-th largest, plus the lowest-index ties;
+        // also this loop's ceil(K/L)-th largest energy: their minimum over
+        // loops is at most the K-th largest energy of all loops (each loop has
+        // ceil(K/L) values at or above it)
+        const uint32_t kq = (P.K + P.L - 1) / P.L;
+        uint32_t kqv = 0;
+        const uint32_t kth = block_kth_largest2(en_s, B, P.nsel, min(kq, B), s_hist, s_wsum, &s_prefix, &s_need,
+                                                &kqv);
+        if (kq > B) kqv = 0;
         const uint32_t need_eq = s_need;
         const uint32_t per = (B + kThreads - 1) / kThreads;
         const uint32_t k0 = min(B, threadIdx.x * per), k1 = min(B, k0 + per);
@@ -344,11 +405,6 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
             if (e == kth) keep = r++ < need_eq;
             frow[k] = keep ? 1 : 0;
         }
-        // this loop's ceil(K/L)-th largest energy: their minimum over loops is
-        // at most the K-th largest energy of all loops (each loop has
-        // ceil(K/L) values at or above it)
-        const uint32_t kq = (P.K + P.L - 1) / P.L;
-        const uint32_t kqv = kq <= B ? block_kth_largest<false>(en_s, B, kq, s_hist, s_wsum, &s_prefix, &s_need) : 0u;
         if (threadIdx.x == 0) P.loopkth[l] = __uint_as_float(kqv);
     }
 
@@ -380,12 +436,41 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
     // fewer than M strong loops the median estimate is provably below theta
     const float thr = 0.5f * s_theta;
     const float gmul = P.ginv2max * (1.0f + 1.0f / 1024.0f);
-#pragma unroll 4
-    for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-        const float en = __ldcg(P.energy + e);
-        uint16_t f = __ldcg(reinterpret_cast<const unsigned short *>(P.flags) + e) & 1u;
-        if (en * gmul >= thr) f |= 256;
-        P.flags[e] = f;
+    if ((total & 3u) == 0) {
+        // four buckets per thread and step, four steps' loads issued together
+        const float4 *e4 = reinterpret_cast<const float4 *>(P.energy);
+        uint2 *f4 = reinterpret_cast<uint2 *>(P.flags);
+        const uint32_t n4 = total / 4;
+        for (uint32_t b0 = threadIdx.x; b0 < n4; b0 += 4 * kThreads) {
+            float4 en[4];
+            uint2 fl[4];
+#pragma unroll
+            for (uint32_t u = 0; u < 4; ++u) {
+                const uint32_t i = b0 + u * kThreads;
+                if (i < n4) {
+                    en[u] = __ldcg(e4 + i);
+                    fl[u] = __ldcg(f4 + i);
+                }
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < 4; ++u) {
+                const uint32_t i = b0 + u * kThreads;
+                if (i < n4) {
+                    const uint32_t s0 = (fl[u].x & 1u) | (en[u].x * gmul >= thr ? 256u : 0u);
+                    const uint32_t s1 = ((fl[u].x >> 16) & 1u) | (en[u].y * gmul >= thr ? 256u : 0u);
+                    const uint32_t s2 = (fl[u].y & 1u) | (en[u].z * gmul >= thr ? 256u : 0u);
+                    const uint32_t s3 = ((fl[u].y >> 16) & 1u) | (en[u].w * gmul >= thr ? 256u : 0u);
+                    f4[i] = make_uint2(s0 | (s1 << 16), s2 | (s3 << 16));
+                }
+            }
+        }
+    } else {
+        for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+            const float en = __ldcg(P.energy + e);
+            uint16_t f = __ldcg(reinterpret_cast<const unsigned short *>(P.flags) + e) & 1u;
+            if (en * gmul >= thr) f |= 256;
+            P.flags[e] = f;
+        }
     }
     if (P.use_bits) {
         // lane j of loop ll: strong bit of every bucket h = j (mod 32) at bit
