@@ -244,7 +244,8 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(0)) != cudaSuccess) return e;
     if ((e = launch_gather(lg, z.gather, s)) != cudaSuccess) return e;
     if ((e = mark(1)) != cudaSuccess) return e;
-    if ((e = launch_fft_select(ls, z.select, z.max_B, 0, s)) != cudaSuccess) return e;
+    const uint32_t cl = fft_select_cluster_ok(z.L_uniform, z.max_B) ? z.L_uniform : 0u;
+    if ((e = launch_fft_select(ls, z.select, z.max_B, 0, cl, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
     if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.bits, z.max_flags, nullptr, nullptr, s)) !=
         cudaSuccess)
@@ -873,7 +874,7 @@ extern "C" sfft_status sfft_bucketize(sfft_plan *p, const float *x_dev, float *z
     const Launch ln = single(make_job(p, x_dev, nullptr, nullptr, nullptr));
     const Sizes z = plan_sizes(p);
     SFFT_CUDA_TRY(launch_gather(ln, z.gather, s));
-    SFFT_CUDA_TRY(launch_fft_select(ln, z.select, z.max_B, 0, s));
+    SFFT_CUDA_TRY(launch_fft_select(ln, z.select, z.max_B, 0, 0, s));
     SFFT_CUDA_TRY(cudaMemcpyAsync(zhat_dev, p->h.zhat, sizeof(float2) * p->L * p->B, cudaMemcpyDeviceToDevice, s));
     return SFFT_OK;
 }
@@ -886,7 +887,7 @@ extern "C" sfft_status sfft_select(sfft_plan *p, const float *zhat_dev, int32_t 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
     SFFT_CUDA_TRY(cudaMemcpyAsync(p->h.zhat, zhat_dev, sizeof(float2) * p->L * p->B, cudaMemcpyDeviceToDevice, s));
-    SFFT_CUDA_TRY(launch_fft_select(ln, p->h.L, p->h.B, 1, s));
+    SFFT_CUDA_TRY(launch_fft_select(ln, p->h.L, p->h.B, 1, 0, s));
     SFFT_CUDA_TRY(
         cudaMemcpyAsync(sel_dev, p->h.sel, sizeof(int32_t) * p->L * p->nsel, cudaMemcpyDeviceToDevice, s));
     return SFFT_OK;

@@ -10,6 +10,8 @@
 // the median bound) -> k_estimate_tab or k_estimate_surv (a6: estimates,
 // keeps key >= theta) -> k_topk (a7; runs the unpruned fallback pass first
 // when fewer than K estimates reached theta).
+#include <cooperative_groups.h>
+#include <mutex>
 #include <math_constants.h>
 
 #include "sfft_internal.cuh"
@@ -289,6 +291,79 @@ __device__ void bitonic_pairs(unsigned long long *a, uint32_t *pay, uint32_t n, 
     }
 }
 
+// Strong-bit threshold of the vote tables: a loop is "strong" for f when
+// |zhat|^2 * max|1/G~|^2 >= theta/2; with fewer than M strong loops the median
+// estimate is provably below theta.
+__device__ __forceinline__ bool strong_energy(float en, float gmul, float thr) { return en * gmul >= thr; }
+
+// theta = 1/4 of a lower bound of the K-th largest bucket energy over all
+// loops (the minimum over loops of each loop's ceil(K/L)-th largest energy):
+// a guess at a lower bound of the K-th largest estimate.  Exactness never
+// depends on it; a guess that is too high only sends the job to the fallback
+// pass.
+__device__ __forceinline__ float theta_from(float min_kth) {
+    float theta = 0.25f * min_kth;
+    if (!(theta >= 0.f) || isinf(theta)) theta = 0.f;
+    return theta;
+}
+
+// Loop l's packed strong bits for the register-table scan: lane word j holds
+// the bit of every bucket h = j (mod 32) at (sigma^-1 (h >> (log2 B - 5))) mod
+// 32, so that the scan's one rotate puts the bit of f + kN/G (G = B/32) at
+// position k 32/G.  energy(h) returns bucket h's energy.
+template <class E>
+__device__ __forceinline__ uint32_t packed_word(const PlanDev &P, uint32_t l, uint32_t j, float gmul, float thr,
+                                                E energy) {
+    const uint32_t sh = P.logB - 5, si = inv_mod32(P.sigma[l]);
+    uint32_t word = 0;
+#pragma unroll
+    for (uint32_t m = 0; m < 16; ++m) {
+        const uint32_t h = j + 32 * m;
+        if (h < P.B) word |= (uint32_t)strong_energy(energy(h), gmul, thr) << ((si * (h >> sh)) & 31u);
+    }
+    return word;
+}
+
+// Clustered tail of k_fft_select for loop l (all threads of every CTA of the
+// job's cluster): theta from the loops' ceil(K/L)-th energies read through
+// distributed shared memory, then this loop's flags (kept | strong << 8) and
+// packed strong bits.  Cluster rank 0 publishes theta and resets the job's
+// counters.
+__device__ void cluster_tables(const PlanDev &P, uint32_t l, uint32_t kqv, const uint32_t *en_s,
+                               const uint8_t *kept_s, uint16_t *frow) {
+    namespace cg = cooperative_groups;
+    __shared__ float s_kq, s_th;
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x == 0) s_kq = __uint_as_float(kqv);
+    cl.sync();
+    if (threadIdx.x < 32) {
+        float mn = INFINITY;
+        for (uint32_t ll = threadIdx.x; ll < P.L; ll += 32) mn = fminf(mn, *cl.map_shared_rank(&s_kq, ll));
+        for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+        if (threadIdx.x == 0) {
+            const float theta = theta_from(mn);
+            s_th = theta;
+            if (l == 0) {
+                P.ctr[kTheta] = __float_as_uint(theta);
+                P.ctr[kSelDone] = 0;
+                P.ctr[kNCand] = 0;
+                P.ctr[kNSurv] = 0;
+                P.ctr[kNGe] = 0;
+                P.ctr[kNRec2] = 0;
+            }
+        }
+    }
+    cl.sync();  // no CTA leaves while another still reads its s_kq
+    const float thr = 0.5f * s_th;
+    const float gmul = P.ginv2max * (1.0f + 1.0f / 1024.0f);
+    const uint32_t B = P.B;
+    for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
+        frow[k] = (uint16_t)(kept_s[k] | (strong_energy(__uint_as_float(en_s[k]), gmul, thr) ? 256u : 0u));
+    if (P.use_bits && threadIdx.x < 32)
+        P.packed[l * 32 + threadIdx.x] =
+            packed_word(P, l, threadIdx.x, gmul, thr, [&](uint32_t h) { return __uint_as_float(en_s[h]); });
+}
+
 // -------------------------------------------------------------- a2 + a3
 // One CTA per (job, loop): sum the gather partials, B-point radix-2 FFT in
 // shared memory, bucket energies, and the nsel kept buckets (energy
@@ -296,8 +371,14 @@ __device__ void bitonic_pairs(unsigned long long *a, uint32_t *pay, uint32_t n, 
 // prune threshold theta and the kept/strong tables for all loops.
 // select_only: the bucket values are already in P.zhat; the kept buckets are
 // also listed in rank order in P.sel.
-__global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_only) {
-    extern __shared__ unsigned long long sm[];  // B values, B energies, B/2 twiddles (B <= kTwSmemMaxB)
+// clustered: the launch groups each job's L CTAs into one thread-block
+// cluster (every job has this L and B <= kClusterMaxB); then, instead of a
+// last CTA building every loop's tables, each CTA reads the other loops'
+// order statistics from their shared memory, derives theta and builds its
+// own loop's tables.
+__global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int select_only, int clustered) {
+    // B values, B energies, B/2 twiddles (B <= kTwSmemMaxB), B kept bytes (clustered)
+    extern __shared__ unsigned long long sm[];
     float2 *buf = reinterpret_cast<float2 *>(sm);
     uint32_t *en_s;
     const float2 *tw;
@@ -399,11 +480,19 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         uint32_t eq = 0;
         for (uint32_t k = k0; k < k1; ++k) eq += en_s[k] == kth;
         uint32_t r = block_incl_scan(eq, s_wsum) - eq;  // equal keys before k0
+        uint8_t *kept_s = reinterpret_cast<uint8_t *>(tw_s + B / 2);  // clustered only
         for (uint32_t k = k0; k < k1; ++k) {
             const uint32_t e = en_s[k];
             bool keep = e > kth;
             if (e == kth) keep = r++ < need_eq;
-            frow[k] = keep ? 1 : 0;
+            if (clustered)
+                kept_s[k] = keep ? 1 : 0;
+            else
+                frow[k] = keep ? 1 : 0;
+        }
+        if (clustered) {
+            cluster_tables(P, l, kqv, en_s, kept_s, frow);
+            return;
         }
         if (threadIdx.x == 0) P.loopkth[l] = __uint_as_float(kqv);
     }
@@ -425,8 +514,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         for (uint32_t ll = threadIdx.x; ll < P.L; ll += 32) mn = fminf(mn, __ldcg(P.loopkth + ll));
         for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
         if (threadIdx.x == 0) {
-            float theta = select_only ? 0.f : 0.25f * mn;  // single-stage select: no pruning downstream
-            if (!(theta >= 0.f) || isinf(theta)) theta = 0.f;
+            const float theta = select_only ? 0.f : theta_from(mn);  // single-stage select: no pruning downstream
             s_theta = theta;
             P.ctr[kTheta] = __float_as_uint(theta);
         }
@@ -456,10 +544,10 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
             for (uint32_t u = 0; u < 4; ++u) {
                 const uint32_t i = b0 + u * kThreads;
                 if (i < n4) {
-                    const uint32_t s0 = (fl[u].x & 1u) | (en[u].x * gmul >= thr ? 256u : 0u);
-                    const uint32_t s1 = ((fl[u].x >> 16) & 1u) | (en[u].y * gmul >= thr ? 256u : 0u);
-                    const uint32_t s2 = (fl[u].y & 1u) | (en[u].z * gmul >= thr ? 256u : 0u);
-                    const uint32_t s3 = ((fl[u].y >> 16) & 1u) | (en[u].w * gmul >= thr ? 256u : 0u);
+                    const uint32_t s0 = (fl[u].x & 1u) | (strong_energy(en[u].x, gmul, thr) ? 256u : 0u);
+                    const uint32_t s1 = ((fl[u].x >> 16) & 1u) | (strong_energy(en[u].y, gmul, thr) ? 256u : 0u);
+                    const uint32_t s2 = (fl[u].y & 1u) | (strong_energy(en[u].z, gmul, thr) ? 256u : 0u);
+                    const uint32_t s3 = ((fl[u].y >> 16) & 1u) | (strong_energy(en[u].w, gmul, thr) ? 256u : 0u);
                     f4[i] = make_uint2(s0 | (s1 << 16), s2 | (s3 << 16));
                 }
             }
@@ -468,26 +556,15 @@ __global__ void __launch_bounds__(kThreads) k_fft_select(Launch ln, int select_o
         for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
             const float en = __ldcg(P.energy + e);
             uint16_t f = __ldcg(reinterpret_cast<const unsigned short *>(P.flags) + e) & 1u;
-            if (en * gmul >= thr) f |= 256;
+            if (strong_energy(en, gmul, thr)) f |= 256;
             P.flags[e] = f;
         }
     }
     if (P.use_bits) {
-        // lane j of loop ll: strong bit of every bucket h = j (mod 32) at bit
-        // (sigma^-1 * (h >> (log2 B - 5))) mod 32, so that the scan's one
-        // rotate puts the bit of f + kN/G (G = B/32) at position k * 32/G
-        const uint32_t sh = P.logB - 5;
         for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
-            const uint32_t ll = idx >> 5, j = idx & 31;
-            const uint32_t si = inv_mod32(P.sigma[ll]);
+            const uint32_t ll = idx >> 5;
             const float *er = P.energy + (size_t)ll * B;
-            uint32_t word = 0;
-#pragma unroll
-            for (uint32_t m = 0; m < 16; ++m) {
-                const uint32_t h = j + 32 * m;
-                if (h < B) word |= (uint32_t)(__ldcg(er + h) * gmul >= thr) << ((si * (h >> sh)) & 31u);
-            }
-            P.packed[idx] = word;
+            P.packed[idx] = packed_word(P, ll, idx & 31, gmul, thr, [&](uint32_t h) { return __ldcg(er + h); });
         }
     }
     if (threadIdx.x == 0) {
@@ -1271,14 +1348,66 @@ cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s)
 }
 
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
-                              cudaStream_t s) {
+                              uint32_t cluster_L, cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
     const int smem = (int)(max_B * (sizeof(float2) + sizeof(uint32_t)) +
-                           (max_B <= kTwSmemMaxB ? max_B / 2 * sizeof(float2) : 0));
+                           (max_B <= kTwSmemMaxB ? max_B / 2 * sizeof(float2) : 0) + (cluster_L ? max_B : 0));
     cudaError_t e = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_fft_select<<<total_ctas, kThreads, smem, s>>>(ln, select_only);
-    return cudaGetLastError();
+    if (!cluster_L) {
+        k_fft_select<<<total_ctas, kThreads, smem, s>>>(ln, select_only, 0);
+        return cudaGetLastError();
+    }
+    if (cluster_L > 8) {
+        e = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(total_ctas);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster_L;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fft_select, ln, select_only, 1);
+}
+
+bool fft_select_cluster_ok(uint32_t L, uint32_t max_B) {
+    if (L < 2 || L > 16 || max_B > (uint32_t)kClusterMaxB) return false;
+    static std::mutex mu;
+    static int known[17][2] = {};  // [L][B > 1024]: 0 unknown, 1 yes, 2 no
+    const int bb = max_B > 1024 ? 1 : 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!known[L][bb]) {
+        const uint32_t qB = bb ? (uint32_t)kClusterMaxB : 1024u;
+        const int smem = (int)(qB * (sizeof(float2) + sizeof(uint32_t)) + qB / 2 * sizeof(float2) + qB);
+        bool ok = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+        if (ok && L > 8)
+            ok = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+        int n = 0;
+        if (ok) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(L);
+            cfg.blockDim = dim3(kThreads);
+            cfg.dynamicSmemBytes = (size_t)smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = L;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            ok = cudaOccupancyMaxActiveClusters(&n, k_fft_select, &cfg) == cudaSuccess && n > 0;
+        }
+        cudaGetLastError();  // a refused query leaves no sticky error
+        known[L][bb] = ok ? 1 : 2;
+    }
+    return known[L][bb] == 1;
 }
 
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,

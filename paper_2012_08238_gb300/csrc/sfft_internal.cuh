@@ -16,6 +16,7 @@ constexpr int kMaxK = 16384;
 constexpr int kMaxLogN = 30;
 constexpr int kTopkSmemMin = 4096;     // top-K sorts up to max(this, K) records in shared memory
 constexpr int kFlagsSmemBytes = 96 * 1024;
+constexpr int kClusterMaxB = 4096;     // clustered FFT/select up to this B
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
@@ -102,8 +103,12 @@ sfft_status cuda_fail(cudaError_t e, const char *what);
 
 // Kernel launchers (stream-ordered, no synchronisation).
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
+// cluster_L > 0: every job has L = cluster_L and the job's CTAs form one
+// thread-block cluster (fft_select_cluster_ok(cluster_L, max_B) must hold).
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
-                              cudaStream_t s);
+                              uint32_t cluster_L, cudaStream_t s);
+// Whether clusters of L FFT/select CTAs with B <= max_B can be launched here.
+bool fft_select_cluster_ok(uint32_t L, uint32_t max_B);
 // The pruned scan uses the register table of strong bits when every job has
 // use_bits and they share L in {8, 12, 16}.
 inline bool scan_uses_bits(uint32_t L_uniform, bool bits) {
