@@ -119,14 +119,17 @@ sfft_status check_sizes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, i
 
 constexpr int kNumSms = 152;  // GB300; only shapes the default work split
 constexpr int kScanCtasPerSm = 8;  // resident 256-thread scan CTAs per SM
-constexpr int kScanWaves = 3;
+constexpr int kScanWaves = 1;
 
 // Work split of one plan for the gather and vote kernels.
 void decompose(PlanDev &P) {
     P.tb = std::min<uint32_t>(P.B, 256);
     P.tiles = P.B / P.tb;
     P.rounds = P.w / P.B;
-    uint32_t want = (2 * kNumSms + P.tiles * P.L - 1) / (P.tiles * P.L);
+    // about one CTA per SM per signal (measured best of 76..600 at the
+    // N = 2^20, B = 512, L = 12 workload: longer CTAs amortise the set-up,
+    // fewer chunks leave fewer partials to sum)
+    uint32_t want = (kNumSms + P.tiles * P.L - 1) / (P.tiles * P.L);
     want = std::max<uint32_t>(1, std::min<uint32_t>(want, P.rounds));
     P.rpc = (P.rounds + want - 1) / want;
     P.nchunk = (P.rounds + P.rpc - 1) / P.rpc;
@@ -611,13 +614,13 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         z.est_ctas = std::min<uint32_t>(kEstimateCtas, fit);
         for (int32_t i = 0; i < count; ++i) cnt[(size_t)i * 6 + 5] = z.est_ctas;
     }
-    // pruned scan: up to 4 vote tiles per CTA while the launch keeps at least
+    // pruned scan: up to 8 vote tiles per CTA while the launch keeps at least
     // kScanWaves waves of resident CTAs (fewer CTAs amortise the per-CTA
     // set-up; too few leave a mostly idle last wave)
     {
         uint64_t vt = 0;
         for (int32_t i = 0; i < count; ++i) vt += cnt[(size_t)i * 6 + 2];
-        uint32_t tpc = 4;
+        uint32_t tpc = 8;
         while (tpc > 1 && vt / tpc < (uint64_t)kScanWaves * kNumSms * kScanCtasPerSm) tpc >>= 1;
         for (int32_t i = 0; i < count; ++i) {
             uint32_t &c2 = cnt[(size_t)i * 6 + 2];

@@ -968,9 +968,17 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
 // positions are scaled by sigma^-1 to match) puts member k's bit at position
 // k 32/G in every loop, so carry-save adders over the L rotated words count
 // the strong loops of all 32 positions at once (bit-sliced counters).
-// Frequencies with at least M = ceil(L/2) strong loops are queued per tile in
-// shared memory and appended to the job's survivor list; candidacy is checked
-// when they are estimated.
+// Frequencies with at least M = ceil(L/2) strong loops are queued in shared
+// memory (overflow goes straight to the job's survivor list) and appended to
+// the list when the CTA ends; candidacy is checked when they are estimated.
+// A register copy the compiler cannot recompute (keeps loop constants in
+// registers instead of re-deriving them from shared memory in the hot loop).
+__device__ __forceinline__ uint32_t opaque(uint32_t v) {
+    uint32_t r;
+    asm volatile("mov.b32 %0, %1;" : "=r"(r) : "r"(v));
+    return r;
+}
+
 template <int LT>
 __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     __shared__ PlanDev P;
@@ -984,9 +992,9 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     uint32_t av[LT], pw[LT], si[LT];
 #pragma unroll
     for (int l = 0; l < LT; ++l) {
-        av[l] = P.sigma[l] << (32 - P.logN);
+        av[l] = opaque(P.sigma[l] << (32 - P.logN));
         pw[l] = __ldcg(P.packed + l * 32 + lane);
-        si[l] = inv_mod32(P.sigma[l]);
+        si[l] = opaque(inv_mod32(P.sigma[l]));
     }
     const uint32_t cv = P.half << (32 - P.logN);
     const uint32_t top = 32 - P.logB;
@@ -996,9 +1004,11 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     const uint32_t span = P.N >> lgG;
     const uint32_t members = member_mask(lgG);
     uint32_t per = (span + P.vtiles - 1) / P.vtiles;
-    per = (per + kThreads - 1) / kThreads * kThreads;  // G * per <= kVoteTileF (G <= 16)
+    per = (per + kThreads - 1) / kThreads * kThreads;
     __syncthreads();
 
+    // survivors go to the CTA's queue; once it is full, straight to the job's
+    // list (no barrier until the CTA's last tile)
     for (uint32_t tile = s_local; tile < P.vtiles; tile += J.vctas) {
         const uint32_t f0 = tile * per;
         const uint32_t f1 = min(span, f0 + per);
@@ -1016,24 +1026,28 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
             count_planes<LT, NP>(x, pl);
             uint32_t m = f < f1 ? count_at_least<(LT + 1) / 2, NP>(pl) & members : 0u;
             if (m) {
-                uint32_t q = atomicAdd(&s_qn, (uint32_t)__popc(m));  // < kVoteTileF: one slot per f of the tile
+                const uint32_t n = __popc(m);
+                uint32_t q = atomicAdd(&s_qn, n);
+                uint32_t g = q + n > (uint32_t)kVoteTileF ? atomicAdd(P.ctr + kNSurv, q + n - max(q, (uint32_t)kVoteTileF))
+                                                          : 0u;
                 do {
                     const uint32_t b = __ffs(m) - 1;
                     m &= m - 1;
-                    queue[q++] = f + (b >> gsh) * span;
+                    const uint32_t fs = f + (b >> gsh) * span;
+                    if (q < (uint32_t)kVoteTileF)
+                        queue[q++] = fs;
+                    else
+                        P.survf[g++] = fs;
                 } while (m);
             }
         }
+    }
+    __syncthreads();
+    const uint32_t qn = min(s_qn, (uint32_t)kVoteTileF);
+    if (qn) {
+        if (threadIdx.x == 0) s_base = atomicAdd(P.ctr + kNSurv, qn);
         __syncthreads();
-        const uint32_t qn = s_qn;
-        if (qn) {
-            if (threadIdx.x == 0) s_base = atomicAdd(P.ctr + kNSurv, qn);
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) P.survf[s_base + i] = queue[i];
-            __syncthreads();
-            if (threadIdx.x == 0) s_qn = 0;
-            __syncthreads();
-        }
+        for (uint32_t i = threadIdx.x; i < qn; i += blockDim.x) P.survf[s_base + i] = queue[i];
     }
 }
 
