@@ -33,9 +33,9 @@ from paper_2012_08238_gb300 import configs, replicas, signals  # noqa: E402
 
 METRIC = "spectra/s batched+served vs plain at fixed L1 error; p50/p99 ms; HBM GB/s"
 
-# kernels of one batched step: gather, FFT/select, vote scan, estimate, top-K
-# (the top-K kernel runs a job's fallback pass itself when one is needed)
-LAUNCHES_PER_STEP = 5
+# kernels of one batched step: gather, FFT/select, vote scan, estimate (whose
+# last CTA per job takes the top K, running the fallback pass when needed)
+LAUNCHES_PER_STEP = 4
 
 # DRAM bytes per spectrum of the two kernels that can dominate, from one ncu
 # capture each (dram__bytes_read.sum + dram__bytes_write.sum, 8-signal case,

@@ -158,8 +158,9 @@ sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_de
 /* Measurement form of sfft_execute_batch: enqueues `steps` back-to-back runs
    of the batch on `stream` (no graph) with CUDA events recorded on that
    stream around each of its six stages (gather-fold, FFT+select, vote scan,
-   survivor estimate, fallback, top-K; the fallback pass runs inside the
-   top-K kernel, so the fifth stage is empty), waits for the last
+   survivor estimate, fallback, top-K; the top-K and any fallback pass run
+   in the last estimate CTA of each job, so the fourth stage holds them and
+   the last two are empty), waits for the last
    one, and returns the device time from the first event to the last
    (*total_ms) and the summed time of each stage over all steps
    (stage_ms[6]).  Errors as for sfft_execute_batch. */

@@ -236,12 +236,13 @@ Sizes plan_sizes(const sfft_plan *p) {
     return z;
 }
 
-// gather -> FFT/select -> scan -> estimate -> top-K (which runs a job's
-// fallback pass itself when needed), all stream-ordered.  With ev
-// (kStages + 1 events) the events bracket the stages: gather, FFT/select,
-// scan, estimate, fallback (empty: folded into top-K), top-K.
+// gather -> FFT/select -> scan -> estimate (whose last CTA per job takes the
+// top K, running the job's fallback pass first when needed), all
+// stream-ordered.  With ev (kStages + 1 events) the events bracket the
+// stages: gather, FFT/select, scan, estimate + top-K, fallback (empty),
+// top-K (empty).
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
-                            const Launch &lk, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+                            const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
@@ -254,10 +255,9 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
         cudaSuccess)
         return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_estimate(le, z.jobs, z.L_uniform, z.est_ctas, z.est_smem, s)) != cudaSuccess) return e;
+    if ((e = launch_estimate(le, z.jobs, z.L_uniform, z.est_ctas, z.est_smem, z.max_K, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
-    if ((e = launch_topk(lk, z.jobs, z.max_K, s)) != cudaSuccess) return e;
     return mark(6);
 }
 
@@ -540,7 +540,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
         return SFFT_EINVAL;
     }
     const Launch ln = single(make_job(p, x_dev, idx_dev, val_dev, k_out_dev));
-    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
 }
 
@@ -669,7 +669,7 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         ln[k].njobs = count;
         memset(&ln[k].one, 0, sizeof(Job));
     }
-    return launch_pipeline(ln[0], ln[1], ln[2], ln[5], ln[3], b.z, s, ev);
+    return launch_pipeline(ln[0], ln[1], ln[2], ln[5], b.z, s, ev);
 }
 
 sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,

@@ -8,8 +8,8 @@
 // Pipeline per job: k_gather (a1) -> k_fft_select (a2, a3; its last CTA also
 // builds the vote tables) -> k_scan_bits or k_vote_scan (a4, a5: survivors of
 // the median bound) -> k_estimate_tab or k_estimate_surv (a6: estimates,
-// keeps key >= theta) -> k_topk (a7; runs the unpruned fallback pass first
-// when fewer than K estimates reached theta).
+// keeps key >= theta; the job's last CTA then takes the top K, a7, running
+// the unpruned fallback pass first when fewer than K estimates reached theta).
 #include <cooperative_groups.h>
 #include <mutex>
 #include <math_constants.h>
@@ -74,7 +74,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // True when the pruned pass could not certify the top K: fewer than K
 // candidates reached theta.  The fallback pass then records (and counts)
 // every candidate.
-__device__ __forceinline__ bool needs_fallback(const PlanDev &P) { return P.ctr[kNGe] < P.K; }
+__device__ __forceinline__ bool needs_fallback(const PlanDev &P) { return __ldcg(P.ctr + kNGe) < P.K; }
 
 // Inclusive sum over a 256-thread block (warp shuffles + 8 warp totals).
 __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *wsum) {
@@ -350,6 +350,7 @@ __device__ void cluster_tables(const PlanDev &P, uint32_t l, uint32_t kqv, const
                 P.ctr[kNSurv] = 0;
                 P.ctr[kNGe] = 0;
                 P.ctr[kNRec2] = 0;
+                P.ctr[kEstDone] = 0;
             }
         }
     }
@@ -573,6 +574,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
         P.ctr[kNSurv] = 0;
         P.ctr[kNGe] = 0;
         P.ctr[kNRec2] = 0;
+        P.ctr[kEstDone] = 0;
     }
 }
 
@@ -1052,11 +1054,191 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
 }
 
 // ------------------------------------------------------------------ a6
+
+// ------------------------------------------------------------------ a7
+__device__ __forceinline__ unsigned long long surv_key(uint4 r) {
+    return ((unsigned long long)r.y << 32) | (uint32_t)(~r.x);  // key desc, then f asc
+}
+
+// Records up to this many are ranked by counting comparisons.
+constexpr uint32_t kRankMax = 1024;
+
+// Fallback pass of one job inside its top-K CTA, taken when fewer than K
+// pruned records reached theta: every candidate (kept in >= T loops) is
+// counted, estimated and recorded (kNCand, kNRec2).  A single CTA scans all N
+// frequencies, so such a job is slow, but the pass is exact and the common
+// case launches nothing for it.
+__device__ void fallback_pass(const PlanDev &P, uint32_t *s_cnt) {
+    if (threadIdx.x == 0) *s_cnt = 0;
+    __syncthreads();
+    const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
+    uint32_t cand = 0;
+    for (uint32_t base = 0; base < P.N; base += blockDim.x) {
+        const uint32_t f = base + threadIdx.x;
+        bool c = false;
+        if (f < P.N) {
+            uint32_t score = 0;
+            for (uint32_t l = 0; l < P.L; ++l)
+                score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << sN) * f + cv) >> top)) & 1u;
+            c = score >= P.T;
+        }
+        cand += c;
+        if (c) estimate_record<0>(P, f, false, 0.f, P.ctr + kNRec2);
+    }
+    cand = __reduce_add_sync(0xFFFFFFFFu, cand);
+    if ((threadIdx.x & 31) == 0 && cand) atomicAdd(s_cnt, cand);
+    __syncthreads();
+    if (threadIdx.x == 0) P.ctr[kNCand] = *s_cnt;
+    __syncthreads();
+}
+
+// Top-K of one job: the k_out = min(K, candidates) recorded estimates of
+// largest magnitude (ties to the lower f), written sorted by f.  Records are
+// those of the pruned pass (candidates with key >= theta) when at least K of
+// them exist; otherwise those of the fallback pass (every candidate).  Pruned
+// candidates have key < theta, so either set contains the top K.
+// Run by all threads of the job's last estimate CTA (the other CTAs' records
+// are visible: they fenced before taking their ticket).  tk: shared memory for
+// cap keys + cap payloads (cap a power of two >= max(kRankMax, K)).
+__device__ void topk_job(const PlanDev &P, const Job &J, unsigned long long *tk, uint32_t cap) {
+    uint32_t *pay = reinterpret_cast<uint32_t *>(tk + cap);
+    __shared__ uint32_t s_S, s_kout, s_hist[256], s_need, s_cnt;
+    __shared__ int s_fb;
+    __shared__ unsigned long long s_prefix, s_pmask;
+    if (threadIdx.x == 0) s_fb = needs_fallback(P);
+    __syncthreads();
+    if (s_fb) fallback_pass(P, &s_cnt);
+    if (threadIdx.x == 0) {
+        s_S = __ldcg(P.ctr + (s_fb ? kNRec2 : kNGe));
+        s_kout = s_fb ? min(P.K, __ldcg(P.ctr + kNCand)) : P.K;  // without fallback >= K candidates exist
+    }
+    __syncthreads();
+    const uint32_t S = s_S, kout = s_kout;
+    const uint4 *surv = P.surv;
+    if (S <= kRankMax) {
+        // ranks by counting: record i wins when fewer than kout keys exceed
+        // its key (keys are distinct: f breaks ties); winners are then placed
+        // by the number of winning frequencies below theirs
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) tk[i] = surv_key(__ldcg(surv + i));
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+            const unsigned long long k = tk[i];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < S; ++j) r += tk[j] > k;
+            pay[i] = r < kout ? ~(uint32_t)k : 0xFFFFFFFFu;  // the winner's f, else above every f
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+            const uint32_t f = pay[i];
+            if (f == 0xFFFFFFFFu) continue;
+            uint32_t pos = 0;
+            for (uint32_t j = 0; j < S; ++j) pos += pay[j] < f;
+            const uint4 r = __ldcg(surv + i);
+            J.idx[pos] = (int32_t)f;
+            J.val[pos] = make_float2(__uint_as_float(r.z), __uint_as_float(r.w));
+        }
+        if (threadIdx.x == 0) *J.kout = (int32_t)kout;
+        return;
+    }
+    if (S <= cap) {
+        uint32_t n2 = 1;
+        while (n2 < S) n2 <<= 1;
+        for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+            if (i < S) {
+                tk[i] = surv_key(__ldcg(surv + i));
+                pay[i] = i;
+            } else {
+                tk[i] = 0ull;  // ranks below every real entry (~f > 0)
+                pay[i] = 0xFFFFFFFFu;
+            }
+        }
+        __syncthreads();
+        bitonic_pairs(tk, pay, n2, false);
+    } else {
+        // rare path (the unpruned fallback over many candidates): exact radix
+        // select of the kout-th largest key, 8 bits per pass
+        if (threadIdx.x == 0) {
+            s_prefix = 0ull;
+            s_pmask = 0ull;
+            s_need = kout;
+        }
+        for (int pass = 0; pass < 8; ++pass) {
+            const int sh = 56 - 8 * pass;
+            for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
+            __syncthreads();
+            const unsigned long long pre = s_prefix, pm = s_pmask;
+            for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+                const unsigned long long k = surv_key(__ldcg(surv + i));
+                if ((k & pm) == pre) atomicAdd(&s_hist[(k >> sh) & 255u], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && s_need > 0) {
+                uint32_t need = s_need, cum = 0;
+                int d = 255;
+                for (; d > 0; --d) {
+                    if (cum + s_hist[d] >= need) break;
+                    cum += s_hist[d];
+                }
+                s_need = need - cum;
+                s_prefix = pre | ((unsigned long long)d << sh);
+                s_pmask = pm | (255ull << sh);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const unsigned long long kth = s_prefix;
+        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+            const unsigned long long k = surv_key(__ldcg(surv + i));
+            if (kout > 0 && k >= kth) {
+                const uint32_t pos = atomicAdd(&s_cnt, 1u);
+                if (pos < cap) {
+                    tk[pos] = k;
+                    pay[pos] = i;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // winners are tk[0..kout): re-key by frequency and sort ascending
+    uint32_t n2k = 1;
+    while (n2k < kout) n2k <<= 1;
+    for (uint32_t i = threadIdx.x; i < n2k; i += blockDim.x) {
+        if (i < kout) tk[i] = (unsigned long long)(~(uint32_t)tk[i]);
+        else tk[i] = ~0ull;
+    }
+    __syncthreads();
+    if (kout > 1) bitonic_pairs(tk, pay, n2k, true);
+    for (uint32_t s = threadIdx.x; s < kout; s += blockDim.x) {
+        const uint4 r = __ldcg(surv + pay[s]);
+        J.idx[s] = (int32_t)r.x;
+        J.val[s] = make_float2(__uint_as_float(r.z), __uint_as_float(r.w));
+    }
+    if (threadIdx.x == 0) *J.kout = (int32_t)kout;
+}
+
+// True in every thread of the job's last CTA of this launch to finish (each
+// CTA fences its records first); that CTA also re-arms the ticket.
+__device__ bool last_of_job(const PlanDev &P, uint32_t ctas_per_job) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_last = atomicAdd(P.ctr + kEstDone, 1u) == ctas_per_job - 1;
+        if (s_last) atomicExch(P.ctr + kEstDone, 0u);
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
 // Pruned-pass median estimates of the job's survivors, ctas_per_job CTAs per
 // job: candidates whose key reaches theta are recorded as {f, key bits, re
-// bits, im bits}.
+// bits, im bits}.  The job's last CTA to finish (atomic ticket after a fence)
+// then takes the job's top K (a7).
 template <int LT>
-__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t ctas_per_job) {
+__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t ctas_per_job, uint32_t cap) {
+    extern __shared__ unsigned long long est_topk[];  // top-K buffer of the job's last CTA
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
@@ -1079,21 +1261,12 @@ __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t 
         for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += stride)
             estimate_record<LT>(P, P.survf[i], true, theta, cnt);
     }
+    if (last_of_job(P, ctas_per_job)) topk_job(P, J, est_topk, cap);
 }
 
-// Pruned-pass estimates with the job's tables staged in shared memory: zhat
-// (L B complex), 1/G~ (N/B complex) and the kept flags as bits.  A few CTAs
-// per job, each over a strided share of the survivors, so every lookup is a
-// shared-memory load.
 template <int LT>
-__global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t ctas_per_job) {
-    extern __shared__ float4 est_tab[];
-    __shared__ PlanDev P;
-    __shared__ Job J;
-    __shared__ uint32_t s_local;
-    enter(ln, P, J, s_local);
-    const uint32_t n = P.ctr[kNSurv];
-    if (s_local * kThreads >= n) return;  // nothing for this CTA (uniform)
+__device__ void estimate_tab_part(const PlanDev &P, uint32_t s_local, uint32_t ctas_per_job, uint32_t n,
+                                  float4 *est_tab) {
     const uint32_t LB = LT * P.B, NB = P.N >> P.logB;
     float2 *zs = reinterpret_cast<float2 *>(est_tab);
     float2 *gs = zs + LB;
@@ -1141,169 +1314,22 @@ __global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t c
     }
 }
 
-// ------------------------------------------------------------------ a7
-__device__ __forceinline__ unsigned long long surv_key(uint4 r) {
-    return ((unsigned long long)r.y << 32) | (uint32_t)(~r.x);  // key desc, then f asc
-}
-
-// Records up to this many are ranked by counting comparisons.
-constexpr uint32_t kRankMax = 1024;
-
-// Fallback pass of one job inside its top-K CTA, taken when fewer than K
-// pruned records reached theta: every candidate (kept in >= T loops) is
-// counted, estimated and recorded (kNCand, kNRec2).  A single CTA scans all N
-// frequencies, so such a job is slow, but the pass is exact and the common
-// case launches nothing for it.
-__device__ void fallback_pass(const PlanDev &P, uint32_t *s_cnt) {
-    if (threadIdx.x == 0) *s_cnt = 0;
-    __syncthreads();
-    const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
-    uint32_t cand = 0;
-    for (uint32_t base = 0; base < P.N; base += blockDim.x) {
-        const uint32_t f = base + threadIdx.x;
-        bool c = false;
-        if (f < P.N) {
-            uint32_t score = 0;
-            for (uint32_t l = 0; l < P.L; ++l)
-                score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << sN) * f + cv) >> top)) & 1u;
-            c = score >= P.T;
-        }
-        cand += c;
-        if (c) estimate_record<0>(P, f, false, 0.f, P.ctr + kNRec2);
-    }
-    cand = __reduce_add_sync(0xFFFFFFFFu, cand);
-    if ((threadIdx.x & 31) == 0 && cand) atomicAdd(s_cnt, cand);
-    __syncthreads();
-    if (threadIdx.x == 0) P.ctr[kNCand] = *s_cnt;
-    __syncthreads();
-}
-
-// One CTA per job: the k_out = min(K, candidates) recorded estimates of
-// largest magnitude (ties to the lower f), written sorted by f.  Records are
-// those of the pruned pass (candidates with key >= theta) when at least K of
-// them exist; otherwise those of the fallback pass (every candidate).  Pruned
-// candidates have key < theta, so either set contains the top K.
-// cap: shared-memory entries (a power of two >= every job's K).
-__global__ void __launch_bounds__(kThreads) k_topk(Launch ln, uint32_t cap) {
-    extern __shared__ unsigned long long tk[];  // cap keys + cap payloads
-    uint32_t *pay = reinterpret_cast<uint32_t *>(tk + cap);
+// Pruned-pass estimates with the job's tables staged in shared memory: zhat
+// (L B complex), 1/G~ (N/B complex) and the kept flags as bits.  A few CTAs
+// per job, each over a strided share of the survivors, so every lookup is a
+// shared-memory load.
+template <int LT>
+__global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t ctas_per_job, uint32_t cap) {
+    extern __shared__ float4 est_tab[];  // the job's tables, then the last CTA's top-K buffer
     __shared__ PlanDev P;
     __shared__ Job J;
-    __shared__ uint32_t s_local, s_S, s_kout, s_hist[256], s_need, s_cnt;
-    __shared__ int s_fb;
-    __shared__ unsigned long long s_prefix, s_pmask;
+    __shared__ uint32_t s_local;
     enter(ln, P, J, s_local);
-    if (threadIdx.x == 0) s_fb = needs_fallback(P);
-    __syncthreads();
-    if (s_fb) fallback_pass(P, &s_cnt);
-    if (threadIdx.x == 0) {
-        s_S = s_fb ? P.ctr[kNRec2] : P.ctr[kNGe];
-        s_kout = s_fb ? min(P.K, P.ctr[kNCand]) : P.K;  // without fallback >= K candidates exist
-    }
-    __syncthreads();
-    const uint32_t S = s_S, kout = s_kout;
-    const uint4 *surv = P.surv;
-    if (S <= kRankMax) {
-        // ranks by counting: record i wins when fewer than kout keys exceed
-        // its key (keys are distinct: f breaks ties); winners are then placed
-        // by the number of winning frequencies below theirs
-        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) tk[i] = surv_key(surv[i]);
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
-            const unsigned long long k = tk[i];
-            uint32_t r = 0;
-            for (uint32_t j = 0; j < S; ++j) r += tk[j] > k;
-            pay[i] = r < kout ? ~(uint32_t)k : 0xFFFFFFFFu;  // the winner's f, else above every f
-        }
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
-            const uint32_t f = pay[i];
-            if (f == 0xFFFFFFFFu) continue;
-            uint32_t pos = 0;
-            for (uint32_t j = 0; j < S; ++j) pos += pay[j] < f;
-            const uint4 r = surv[i];
-            J.idx[pos] = (int32_t)f;
-            J.val[pos] = make_float2(__uint_as_float(r.z), __uint_as_float(r.w));
-        }
-        if (threadIdx.x == 0) *J.kout = (int32_t)kout;
-        return;
-    }
-    if (S <= cap) {
-        uint32_t n2 = 1;
-        while (n2 < S) n2 <<= 1;
-        for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
-            if (i < S) {
-                tk[i] = surv_key(surv[i]);
-                pay[i] = i;
-            } else {
-                tk[i] = 0ull;  // ranks below every real entry (~f > 0)
-                pay[i] = 0xFFFFFFFFu;
-            }
-        }
-        __syncthreads();
-        bitonic_pairs(tk, pay, n2, false);
-    } else {
-        // rare path (the unpruned fallback over many candidates): exact radix
-        // select of the kout-th largest key, 8 bits per pass
-        if (threadIdx.x == 0) {
-            s_prefix = 0ull;
-            s_pmask = 0ull;
-            s_need = kout;
-        }
-        for (int pass = 0; pass < 8; ++pass) {
-            const int sh = 56 - 8 * pass;
-            for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
-            __syncthreads();
-            const unsigned long long pre = s_prefix, pm = s_pmask;
-            for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
-                const unsigned long long k = surv_key(surv[i]);
-                if ((k & pm) == pre) atomicAdd(&s_hist[(k >> sh) & 255u], 1u);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0 && s_need > 0) {
-                uint32_t need = s_need, cum = 0;
-                int d = 255;
-                for (; d > 0; --d) {
-                    if (cum + s_hist[d] >= need) break;
-                    cum += s_hist[d];
-                }
-                s_need = need - cum;
-                s_prefix = pre | ((unsigned long long)d << sh);
-                s_pmask = pm | (255ull << sh);
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) s_cnt = 0;
-        __syncthreads();
-        const unsigned long long kth = s_prefix;
-        for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
-            const unsigned long long k = surv_key(surv[i]);
-            if (kout > 0 && k >= kth) {
-                const uint32_t pos = atomicAdd(&s_cnt, 1u);
-                if (pos < cap) {
-                    tk[pos] = k;
-                    pay[pos] = i;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // winners are tk[0..kout): re-key by frequency and sort ascending
-    uint32_t n2k = 1;
-    while (n2k < kout) n2k <<= 1;
-    for (uint32_t i = threadIdx.x; i < n2k; i += blockDim.x) {
-        if (i < kout) tk[i] = (unsigned long long)(~(uint32_t)tk[i]);
-        else tk[i] = ~0ull;
-    }
-    __syncthreads();
-    if (kout > 1) bitonic_pairs(tk, pay, n2k, true);
-    for (uint32_t s = threadIdx.x; s < kout; s += blockDim.x) {
-        const uint4 r = surv[pay[s]];
-        J.idx[s] = (int32_t)r.x;
-        J.val[s] = make_float2(__uint_as_float(r.z), __uint_as_float(r.w));
-    }
-    if (threadIdx.x == 0) *J.kout = (int32_t)kout;
+    const uint32_t n = P.ctr[kNSurv];
+    if (s_local * kThreads < n) estimate_tab_part<LT>(P, s_local, ctas_per_job, n, est_tab);
+    if (last_of_job(P, ctas_per_job)) topk_job(P, J, reinterpret_cast<unsigned long long *>(est_tab), cap);
 }
+
 
 // Stage kernels for the single-step entry points.
 template <int LT>
@@ -1441,35 +1467,30 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
 }
 
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
-                            cudaStream_t s) {
+                            uint32_t max_K, cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
     const uint32_t ctas = njobs * per;
+    uint32_t cap = kRankMax;
+    while (cap < max_K) cap <<= 1;  // the top-K buffer holds the K winners (and up to kRankMax records)
+    const uint32_t topk_smem = cap * (uint32_t)(sizeof(unsigned long long) + sizeof(uint32_t));
     if (tab_smem && (L_uniform == 8 || L_uniform == 12 || L_uniform == 16)) {
         auto kern = L_uniform == 8 ? k_estimate_tab<8> : (L_uniform == 12 ? k_estimate_tab<12> : k_estimate_tab<16>);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_smem);
+        const uint32_t smem = max(tab_smem, topk_smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<ctas, kThreads, tab_smem, s>>>(ln, per);
+        kern<<<ctas, kThreads, smem, s>>>(ln, per, cap);
         return cudaGetLastError();
     }
-    switch (L_uniform) {
-        case 8: k_estimate_surv<8><<<ctas, kThreads, 0, s>>>(ln, per); break;
-        case 12: k_estimate_surv<12><<<ctas, kThreads, 0, s>>>(ln, per); break;
-        case 16: k_estimate_surv<16><<<ctas, kThreads, 0, s>>>(ln, per); break;
-        default: k_estimate_surv<0><<<ctas, kThreads, 0, s>>>(ln, per); break;
-    }
+    auto kern = L_uniform == 8    ? k_estimate_surv<8>
+                : L_uniform == 12 ? k_estimate_surv<12>
+                : L_uniform == 16 ? k_estimate_surv<16>
+                                  : k_estimate_surv<0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)topk_smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ctas, kThreads, topk_smem, s>>>(ln, per, cap);
     return cudaGetLastError();
 }
 
-cudaError_t launch_topk(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s) {
-    if (njobs == 0) return cudaSuccess;
-    uint32_t cap = kTopkSmemMin;
-    while (cap < max_K) cap <<= 1;  // the radix path compacts K winners into the buffer
-    const int smem = (int)(cap * (sizeof(unsigned long long) + sizeof(uint32_t)));
-    cudaError_t e = cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_topk<<<njobs, kThreads, smem, s>>>(ln, cap);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s) {

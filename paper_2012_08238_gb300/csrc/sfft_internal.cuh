@@ -14,7 +14,6 @@ constexpr int kMaxL = 32;
 constexpr int kMaxB = 16384;
 constexpr int kMaxK = 16384;
 constexpr int kMaxLogN = 30;
-constexpr int kTopkSmemMin = 4096;     // top-K sorts up to max(this, K) records in shared memory
 constexpr int kFlagsSmemBytes = 96 * 1024;
 constexpr int kClusterMaxB = 4096;     // clustered FFT/select up to this B
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
@@ -38,7 +37,8 @@ enum Counter : int {
     kSelDone = 4,  // loops finished by the FFT/select kernel (last-block pattern)
     kTheta = 5,    // prune threshold theta (float bits)
     kErr = 6,      // device-side error word (0 = none)
-    kNRec2 = 7,    // records written by the unpruned fallback pass (in the top-K kernel)
+    kNRec2 = 7,    // records written by the unpruned fallback pass (in the top-K step)
+    kEstDone = 8,  // estimate CTAs of the job finished (last-CTA ticket for the top-K step)
     kNumCounters = 16
 };
 
@@ -119,15 +119,13 @@ inline bool scan_uses_bits(uint32_t L_uniform, bool bits) {
 // use_bits (the pruned scan then uses the register table of strong bits).
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
                         uint32_t max_flags_bytes, int32_t *cand_out, int32_t *ncand_out, cudaStream_t s);
-// Pruned-pass estimates, per CTAs per job (ln's prefix array must match).
-// tab_smem > 0: every job's tables fit that many bytes of shared memory
-// (estimate_tab_bytes) and L is uniform in {8, 12, 16}; they are then staged
-// there.
+// Pruned-pass estimates, per CTAs per job (ln's prefix array must match); the
+// job's last CTA to finish then takes the job's top K (running the fallback
+// pass first when fewer than K pruned records reached theta).  tab_smem > 0:
+// every job's tables fit that many bytes of shared memory (estimate_tab_bytes)
+// and L is uniform in {8, 12, 16}; they are then staged there.
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
-                            cudaStream_t s);
-// Top-K per job (one CTA each), running the job's fallback pass first when
-// fewer than K pruned records reached theta.
-cudaError_t launch_topk(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s);
+                            uint32_t max_K, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);
 cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *sel, cudaStream_t s);
