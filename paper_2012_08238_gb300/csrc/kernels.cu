@@ -683,8 +683,8 @@ __device__ __forceinline__ bool is_candidate(const PlanDev &P, uint32_t f) {
 
 // Pruned-pass estimate of survivor f with L = LT, appended to the records at
 // *cnt when f is a candidate whose key reaches theta.  One hash word per loop
-// feeds the kept-flag, bucket and gain loads, all issued before any is used.
-// Before the sort, f is dropped when neither median component can reach
+// feeds the bucket and gain loads, all issued before any is used.  Before the
+// candidacy test and the sort, f is dropped when neither median component can reach
 // a = sqrt(theta/2) (1 - 2^-10) in magnitude: a median >= a needs at least
 // M = ceil(L/2) values >= a, one <= -a as many <= -a, and with both medians
 // inside (-a, a) the computed key stays below theta.  Kept records are
@@ -719,7 +719,6 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
     const uint32_t B = P.B;
     float2 z[LT], g[LT];
     uint32_t ph[LT];
-    uint32_t kept = 0;
 #pragma unroll
     for (int l = 0; l < LT; ++l) {
         const uint32_t t = (P.sigma[l] << sN) * f + cv;
@@ -728,20 +727,17 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
         if constexpr (SM) {
             const uint32_t zb = (uint32_t)__cvta_generic_to_shared(zt);
             const uint32_t gb = (uint32_t)__cvta_generic_to_shared(gt);
-            const uint32_t kb = (uint32_t)__cvta_generic_to_shared(kt);
-            kept += (lds_u32(kb + 4 * ((l * B + h) >> 5)) >> (h & 31u)) & 1u;
             z[l] = lds_f2(zb + 8 * (l * B + h));
             g[l] = lds_f2(gb + 8 * opos);
         } else {
-            kept += __ldg(P.flags + l * B + h) & 1u;
             z[l] = __ldg(P.zhat + l * B + h);
             g[l] = __ldg(P.ginv + opos);
         }
         ph[l] = (P.tau[l] << sN) * f;
     }
-    bool keep = kept >= P.T;
+    bool keep = true;
     float re[LT], im[LT];
-    if (keep) {
+    {
         uint32_t rp = 0, rn = 0, ip = 0, in = 0;
 #pragma unroll
         for (int l = 0; l < LT; ++l) {
@@ -755,6 +751,19 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
         }
         constexpr uint32_t M = (LT + 1) / 2;
         keep = rp >= M || rn >= M || ip >= M || in >= M;
+    }
+    if (keep) {
+        // candidacy (kept in >= T loops), only for the few that pass
+        uint32_t kept = 0;
+#pragma unroll
+        for (int l = 0; l < LT; ++l) {
+            const uint32_t h = ((P.sigma[l] << sN) * f + cv) >> top;
+            if constexpr (SM)
+                kept += (lds_u32((uint32_t)__cvta_generic_to_shared(kt) + 4 * ((l * B + h) >> 5)) >> (h & 31u)) & 1u;
+            else
+                kept += __ldg(P.flags + l * B + h) & 1u;
+        }
+        keep = kept >= P.T;
     }
     float2 v = make_float2(0.f, 0.f);
     float key = 0.f;
