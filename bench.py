@@ -37,13 +37,11 @@ METRIC = "spectra/s batched+served vs plain at fixed L1 error; p50/p99 ms; HBM G
 # last CTA per job takes the top K, running the fallback pass when needed)
 LAUNCHES_PER_STEP = 4
 
-# DRAM bytes per spectrum of the two kernels that can dominate, from one ncu
-# capture each (dram__bytes_read.sum + dram__bytes_write.sum, 8-signal case,
-# scaled per spectrum); the summaries are under profiles/.
-NCU_TRAFFIC_PER_SPECTRUM = {
-    "k_vote_scan": 36_096 / 8,
-    "k_gather": (66_689_024 + 2_041_600) / 8,
-}
+# DRAM bytes per spectrum of the gather kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the 64-signal launch, divided by
+# 64); the capture's summary is under profiles/.  None when the kernel changed
+# after the capture.
+NCU_GATHER_TRAFFIC_PER_SPECTRUM = (537_337_856 + 22_532_352) / 64
 UNIT = "spectra/s"
 WORKLOAD = configs.GENERAL_N20
 
@@ -316,38 +314,42 @@ def run_ours(args):
     h2d = S * W.N * 8
     d2h = S * (W.K * 12 + 4)
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel (the gather: HBM-bound)
     hbm_peak, sm_max_mhz, peak_kind = _peaks()
     per_launch = {k: v / args.steps for k, v in stage_ms.items()}
-    dominant = max(per_launch, key=per_launch.get)
     distinct = S * 8 * info.samples_touched  # algorithmic bytes: distinct samples read
     bucket_ms = per_launch["gather_fold"]
     gather_gbs = distinct / (bucket_ms / 1e3) / 1e9
     sector_bytes = S * W.L * W.window * 32
-    # vote scan: N*L table lookups per spectrum, at least 4 integer lane-ops
-    # each (hash multiply-add, bucket shift, bit extraction, accumulate);
-    # peak = one lane-op per lane per clock on 152 SMs x 128 lanes
-    scan_ops = S * W.N * W.L * 4
-    alu_peak = 152 * 128 * sm_max_mhz * 1e6
-    scan_rate = scan_ops / (per_launch["vote_scan"] / 1e3)
-    gather_roof = {"kernel": "k_gather",
-                   "achieved": gather_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gather_gbs / hbm_peak,
-                   "sector_gbs": sector_bytes / (bucket_ms / 1e3) / 1e9,
-                   "sector_efficiency": distinct / sector_bytes, "peak_source": peak_kind,
-                   "traffic": S * NCU_TRAFFIC_PER_SPECTRUM["k_gather"]}
-    if dominant == "vote_scan":
-        roofline = {"kernel": "k_vote_scan (vote scan)", "bound": "alu",
-                    "achieved": scan_rate / 1e12, "peak": alu_peak / 1e12, "unit": "T int lane-ops/s",
-                    "frac": scan_rate / alu_peak, "traffic": S * NCU_TRAFFIC_PER_SPECTRUM["k_vote_scan"],
-                    "per_unit": f"4 x N x L = {4 * W.N * W.L} lane-ops per spectrum",
-                    "peak_source": f"152 SMs x 128 lanes x {sm_max_mhz:.0f} MHz (derived, recipe unit counts)"}
-    else:
-        roofline = {"kernel": gather_roof["kernel"], "bound": "hbm", "achieved": gather_gbs,
-                    "peak": hbm_peak, "unit": "GB/s", "frac": gather_gbs / hbm_peak,
-                    "traffic": S * NCU_TRAFFIC_PER_SPECTRUM["k_gather"],
-                    "per_unit": f"8 B x {info.samples_touched} distinct samples per spectrum",
-                    "peak_source": peak_kind}
+    traffic = None if NCU_GATHER_TRAFFIC_PER_SPECTRUM is None else S * NCU_GATHER_TRAFFIC_PER_SPECTRUM
+    roofline = {"kernel": "k_gather", "bound": "hbm", "achieved": gather_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gather_gbs / hbm_peak, "traffic": traffic,
+                "per_unit": f"8 B x {info.samples_touched} distinct samples per spectrum",
+                "peak_source": peak_kind,
+                "sector_gbs": sector_bytes / (bucket_ms / 1e3) / 1e9,
+                "sector_efficiency": distinct / sector_bytes}
+    if traffic is not None:
+        # physical DRAM bytes of the launch over its event-timed duration
+        roofline["dram_gbs"] = traffic / (bucket_ms / 1e3) / 1e9
+        roofline["dram_frac"] = roofline["dram_gbs"] / hbm_peak
+    # vote scan: N x L table lookups per spectrum (integer ALU work)
+    roofline_scan = {"kernel": "k_scan_bits", "bound": "alu",
+                     "lookups_per_s": S * W.N * W.L / (per_launch["vote_scan"] / 1e3),
+                     "per_unit": f"N x L = {W.N * W.L} bucket lookups per spectrum"}
 
+    # ---- context: a dense FFT of the same batch (cuFFT through torch.fft)
+    xb = torch.stack(xs)
+    torch.fft.fft(xb)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        torch.fft.fft(xb)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dense_ms = e0.elapsed_time(e1) / args.steps
+    dense = {"value": S / (dense_ms / 1e3), "unit": UNIT, "ms_per_step": dense_ms,
+             "what": f"dense complex64 FFT of the same {S} signals (cuFFT via torch.fft), context only"}
+    del xb
 
     # ---- CPU baseline: the oracle on a bounded sample, host cores
     cpu = None
@@ -374,7 +376,7 @@ def run_ours(args):
         "plain_value": plain_value, "graph_value": graph_value, "served": served,
         "stage_ms_per_step": per_launch, "stage_share": {k: v / sum(per_launch.values()) for k, v in per_launch.items()},
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
-        "roofline": roofline, "roofline_gather": gather_roof,
+        "roofline": roofline, "roofline_scan": roofline_scan, "dense_fft_context": dense,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
