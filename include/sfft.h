@@ -170,8 +170,11 @@ sfft_status sfft_execute_batch_timed(sfft_plan *const *plans, const float *const
                                      float *total_ms, float *stage_ms, void *stream);
 
 /* Batch with HOST buffers: copies each x_host[i] (complex64[N_i]) into a
-   device buffer owned by plans[i], runs the batch, copies idx/val/k_out back
-   to x's host arrays (k_out_host int32[count]) and synchronises the stream. */
+   device buffer owned by plans[i] (on an internal copy stream, in up to 8
+   chunks of jobs; each chunk's batch runs on `stream` once its copies have
+   landed, beside the next chunk's copies), copies idx/val/k_out back to the
+   host arrays (k_out_host int32[count]) with one device-to-host copy, and
+   synchronises the stream.  Pinned host memory gives the full link rate. */
 sfft_status sfft_execute_batch_host(sfft_plan *const *plans, const float *const *x_host,
                                     int32_t *const *idx_host, float *const *val_host,
                                     int32_t *k_out_host, int32_t count, void *stream);

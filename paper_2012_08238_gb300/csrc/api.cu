@@ -118,6 +118,7 @@ sfft_status check_sizes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, i
 }
 
 constexpr int kNumSms = 152;  // GB300; only shapes the default work split
+constexpr int kHostChunks = 8;  // host-buffer batches: copies of chunk c+1 overlap chunk c's batch
 constexpr int kScanCtasPerSm = 8;  // resident 256-thread scan CTAs per SM
 constexpr int kScanWaves = 1;
 
@@ -544,6 +545,12 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
     return SFFT_OK;
 }
 
+// Device staging of a plan's host-buffer calls: x, then idx, val and k_out.
+static size_t stage_bytes(const sfft_plan *p) {
+    return align256(sizeof(float2) * p->N) + align256(sizeof(int32_t) * p->K) + align256(sizeof(float2) * p->K) +
+           256;
+}
+
 extern "C" sfft_status sfft_execute_host(sfft_plan *p, const float *x_host, int32_t *idx_host, float *val_host,
                                          int32_t *k_out_host, void *stream) {
     if (!p || !x_host || !idx_host || !val_host || !k_out_host) {
@@ -552,7 +559,7 @@ extern "C" sfft_status sfft_execute_host(sfft_plan *p, const float *x_host, int3
     }
     const size_t xb = align256(sizeof(float2) * p->N), ib = align256(sizeof(int32_t) * p->K),
                  vb = align256(sizeof(float2) * p->K);
-    if (!p->stage) SFFT_CUDA_TRY(cudaMalloc(&p->stage, xb + ib + vb + 256));
+    if (!p->stage) SFFT_CUDA_TRY(cudaMalloc(&p->stage, stage_bytes(p)));
     char *b = static_cast<char *>(p->stage);
     float *x = reinterpret_cast<float *>(b);
     int32_t *idx = reinterpret_cast<int32_t *>(b + xb);
@@ -819,6 +826,51 @@ extern "C" sfft_status sfft_execute_batch_timed(sfft_plan *const *plans, const f
     return SFFT_OK;
 }
 
+namespace {
+
+// Per-thread resources of the host-buffer batch call: a copy stream and one
+// event per chunk (for the calling thread's current device), the contiguous
+// device output region and its pinned host image.
+struct HostBatchRes {
+    int device = -1;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t fork = nullptr, chunk[kHostChunks] = {};
+    void *out_dev = nullptr, *out_host = nullptr;
+    size_t out_cap = 0;
+};
+
+cudaError_t host_batch_res(HostBatchRes &r, int device, size_t out_bytes) {
+    cudaError_t e = cudaSuccess;
+    if (r.device != device) {
+        // resources of another device are left to process teardown
+        r = HostBatchRes();
+        e = cudaStreamCreateWithFlags(&r.copy, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming);
+        for (int i = 0; i < kHostChunks && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&r.chunk[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        r.device = device;
+    }
+    if (r.out_cap < out_bytes) {
+        if (r.out_dev) cudaFree(r.out_dev);
+        if (r.out_host) cudaFreeHost(r.out_host);
+        r.out_dev = r.out_host = nullptr;
+        r.out_cap = 0;
+        const size_t cap = std::max<size_t>(out_bytes, 64 * 1024);
+        if ((e = cudaMalloc(&r.out_dev, cap)) != cudaSuccess) return e;
+        if ((e = cudaMallocHost(&r.out_host, cap)) != cudaSuccess) return e;
+        r.out_cap = cap;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// Host buffers in, host buffers out.  The inputs go to the plans' device
+// staging buffers on a copy stream in up to kHostChunks chunks of jobs; each
+// chunk's batch runs on `stream` as soon as its copies land (the next chunk's
+// copies continue meanwhile); every job's outputs go to one contiguous
+// device region read back by a single copy.
 extern "C" sfft_status sfft_execute_batch_host(sfft_plan *const *plans, const float *const *x_host,
                                                int32_t *const *idx_host, float *const *val_host,
                                                int32_t *k_out_host, int32_t count, void *stream) {
@@ -826,44 +878,59 @@ extern "C" sfft_status sfft_execute_batch_host(sfft_plan *const *plans, const fl
                                       (const void *const *)val_host, k_out_host, count);
     if (st != SFFT_OK || count == 0) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int device = 0;
+    SFFT_CUDA_TRY(cudaGetDevice(&device));
+    // output layout: per job idx int32[K] and val complex64[K], then k_out[count]
+    std::vector<size_t> oi(count), ov(count);
+    size_t out = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        oi[i] = out;
+        out += align256(sizeof(int32_t) * plans[i]->K);
+        ov[i] = out;
+        out += align256(sizeof(float2) * plans[i]->K);
+    }
+    const size_t ok = out;
+    out += sizeof(int32_t) * count;
+    static thread_local HostBatchRes res;
+    SFFT_CUDA_TRY(host_batch_res(res, device, out));
+    char *od = static_cast<char *>(res.out_dev);
     std::vector<const float *> xd(count);
     std::vector<int32_t *> id(count);
     std::vector<float *> vd(count);
-    int32_t *kd = nullptr;
     for (int32_t i = 0; i < count; ++i) {
         sfft_plan *p = plans[i];
-        const size_t xb = align256(sizeof(float2) * p->N), ib = align256(sizeof(int32_t) * p->K),
-                     vb = align256(sizeof(float2) * p->K);
-        if (!p->stage) SFFT_CUDA_TRY(cudaMalloc(&p->stage, xb + ib + vb + 256));
-        char *b = static_cast<char *>(p->stage);
-        xd[i] = reinterpret_cast<const float *>(b);
-        id[i] = reinterpret_cast<int32_t *>(b + xb);
-        vd[i] = reinterpret_cast<float *>(b + xb + ib);
-        SFFT_CUDA_TRY(cudaMemcpyAsync(b, x_host[i], sizeof(float2) * p->N, cudaMemcpyHostToDevice, s));
+        if (!p->stage) SFFT_CUDA_TRY(cudaMalloc(&p->stage, stage_bytes(p)));  // x first
+        xd[i] = static_cast<const float *>(p->stage);
+        id[i] = reinterpret_cast<int32_t *>(od + oi[i]);
+        vd[i] = reinterpret_cast<float *>(od + ov[i]);
     }
-    // k_out of the batch lands in the first plan's staging tail, one int per job
-    {
-        std::lock_guard<std::mutex> lk(g_batch_mu);
-        static thread_local void *kbuf = nullptr;
-        static thread_local int32_t kcap = 0;
-        if (kcap < count) {
-            if (kbuf) cudaFree(kbuf);
-            kbuf = nullptr;
-            kcap = 0;
-            SFFT_CUDA_TRY(cudaMalloc(&kbuf, sizeof(int32_t) * count));
-            kcap = count;
-        }
-        kd = static_cast<int32_t *>(kbuf);
+    int32_t *kd = reinterpret_cast<int32_t *>(od + ok);
+    const int chunks = std::min<int>(kHostChunks, count);
+    // the copy stream follows the caller's earlier work
+    SFFT_CUDA_TRY(cudaEventRecord(res.fork, s));
+    SFFT_CUDA_TRY(cudaStreamWaitEvent(res.copy, res.fork, 0));
+    for (int c = 0; c < chunks; ++c) {
+        const int32_t f0 = (int32_t)((int64_t)count * c / chunks), f1 = (int32_t)((int64_t)count * (c + 1) / chunks);
+        for (int32_t i = f0; i < f1; ++i)
+            SFFT_CUDA_TRY(cudaMemcpyAsync(const_cast<float *>(xd[i]), x_host[i], sizeof(float2) * plans[i]->N,
+                                          cudaMemcpyHostToDevice, res.copy));
+        SFFT_CUDA_TRY(cudaEventRecord(res.chunk[c], res.copy));
     }
-    st = sfft_execute_batch(plans, xd.data(), id.data(), vd.data(), kd, count, stream);
-    if (st != SFFT_OK) return st;
-    SFFT_CUDA_TRY(cudaMemcpyAsync(k_out_host, kd, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
-    for (int32_t i = 0; i < count; ++i) {
-        const sfft_plan *p = plans[i];
-        SFFT_CUDA_TRY(cudaMemcpyAsync(idx_host[i], id[i], sizeof(int32_t) * p->K, cudaMemcpyDeviceToHost, s));
-        SFFT_CUDA_TRY(cudaMemcpyAsync(val_host[i], vd[i], sizeof(float2) * p->K, cudaMemcpyDeviceToHost, s));
+    for (int c = 0; c < chunks; ++c) {
+        const int32_t f0 = (int32_t)((int64_t)count * c / chunks), f1 = (int32_t)((int64_t)count * (c + 1) / chunks);
+        SFFT_CUDA_TRY(cudaStreamWaitEvent(s, res.chunk[c], 0));
+        st = sfft_execute_batch(plans + f0, xd.data() + f0, id.data() + f0, vd.data() + f0, kd + f0, f1 - f0,
+                                stream);
+        if (st != SFFT_OK) return st;
     }
+    SFFT_CUDA_TRY(cudaMemcpyAsync(res.out_host, od, out, cudaMemcpyDeviceToHost, s));
     SFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    const char *oh = static_cast<const char *>(res.out_host);
+    memcpy(k_out_host, oh + ok, sizeof(int32_t) * count);
+    for (int32_t i = 0; i < count; ++i) {
+        memcpy(idx_host[i], oh + oi[i], sizeof(int32_t) * plans[i]->K);
+        memcpy(val_host[i], oh + ov[i], sizeof(float2) * plans[i]->K);
+    }
     return SFFT_OK;
 }
 

@@ -982,14 +982,6 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
 // Frequencies with at least M = ceil(L/2) strong loops are queued in shared
 // memory (overflow goes straight to the job's survivor list) and appended to
 // the list when the CTA ends; candidacy is checked when they are estimated.
-// A register copy the compiler cannot recompute (keeps loop constants in
-// registers instead of re-deriving them from shared memory in the hot loop).
-__device__ __forceinline__ uint32_t opaque(uint32_t v) {
-    uint32_t r;
-    asm volatile("mov.b32 %0, %1;" : "=r"(r) : "r"(v));
-    return r;
-}
-
 template <int LT>
 __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     __shared__ PlanDev P;
@@ -1000,12 +992,17 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     if (threadIdx.x == 0) s_qn = 0;
 
     const uint32_t lane = threadIdx.x & 31;
-    uint32_t av[LT], pw[LT], si[LT];
+    // per loop: sigma << (32 - log2 N), the lane's table word, and sigma^-1
+    // mod 32 packed six 5-bit fields to a word (fewer live registers)
+    constexpr int NSW = (LT + 5) / 6;
+    uint32_t av[LT], pw[LT], sip[NSW];
+#pragma unroll
+    for (int k = 0; k < NSW; ++k) sip[k] = 0;
 #pragma unroll
     for (int l = 0; l < LT; ++l) {
-        av[l] = opaque(P.sigma[l] << (32 - P.logN));
+        av[l] = P.sigma[l] << (32 - P.logN);
         pw[l] = __ldcg(P.packed + l * 32 + lane);
-        si[l] = opaque(inv_mod32(P.sigma[l]));
+        sip[l / 6] |= (inv_mod32(P.sigma[l]) & 31u) << (5 * (l % 6));
     }
     const uint32_t cv = P.half << (32 - P.logN);
     const uint32_t top = 32 - P.logB;
@@ -1030,7 +1027,8 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
             for (int l = 0; l < LT; ++l) {
                 const uint32_t t = av[l] * f + cv;
                 const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> top);  // lane = bucket mod 32
-                x[l] = __funnelshift_r(w, w, (t >> 27) * si[l]);
+                const uint32_t si = (sip[l / 6] >> (5 * (l % 6))) & 31u;
+                x[l] = __funnelshift_r(w, w, (t >> 27) * si);
             }
             constexpr int NP = bit_length(LT);
             uint32_t pl[NP];
