@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the flat-window voting sparse FFT (test infrastructure).
+"""FP64 CPU oracle for the flat-window voting sparse FFT and its phase-encoding
+iterative variant (test infrastructure).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The library path never does: it shares
@@ -75,6 +76,13 @@ def _bind(lib):
             _i64,
             [_i64, _i64, _i64, _i64, _int, _int, _int, _u64, _p, _p, _p, _p, _p, _p, _p,
              _p, _p, _p],
+        ),
+        "oracle_filter_gain_full": (None, [_i64, _i64, _p, _p]),
+        "oracle_pe_subtract": (None, [_i64, _i64, _i64, _i64, _p, _i64, _p, _p, _p]),
+        "oracle_pe_locate": (_i64, [_i64, _i64, _i64, _i64, _p, _p, _p, ctypes.c_double, _p, _p, _p]),
+        "oracle_sfft_pe": (
+            _i64,
+            [_i64, _i64, _i64, _i64, _int, ctypes.c_double, _u64, _p, _p, _p, _p, _p, _p, _p],
         ),
     }
     for name, (res, args) in sig.items():
@@ -293,3 +301,57 @@ def sfft(plan: Plan, x, intermediates: bool = False):
         n = int(ncand[0])
         out.update(zhat=zhat, sel=sel, cand=cand[:n].copy(), est=est[:n].copy())
     return out
+
+
+# ------------------------------------------------ sFFT3.0-style variant
+def filter_gain_full(N: int, w: int, g: np.ndarray) -> np.ndarray:
+    """G~(nu) for every offset nu in [0, N) (one length-N FFT of the padded window)."""
+    out = np.zeros(N, np.complex128)
+    _load().oracle_filter_gain_full(N, w, _ptr(np.ascontiguousarray(g, np.float64)), _ptr(out))
+    return out
+
+
+def pe_subtract(N, B, sigma, tau, Gfull, fidx, fval, zhat):
+    """Iterative framework: remove known coefficients from one loop's bucket values (in place)."""
+    fidx = np.ascontiguousarray(fidx, np.int32)
+    fval = _c128(fval)
+    assert zhat.dtype == np.complex128 and zhat.flags["C_CONTIGUOUS"]
+    _load().oracle_pe_subtract(N, B, int(sigma), int(tau), _ptr(Gfull), len(fidx), _ptr(fidx), _ptr(fval),
+                               _ptr(zhat))
+    return zhat
+
+
+def pe_locate(N, B, sigma, tau, Gfull, zhat0, zhat1, thr):
+    """Phase-encoding location of the lone coefficients of one loop: (f, value, active buckets)."""
+    f = np.zeros(B, np.int32)
+    v = np.zeros(B, np.complex128)
+    active = np.zeros(1, np.int64)
+    n = _load().oracle_pe_locate(N, B, int(sigma), int(tau), _ptr(Gfull), _ptr(_c128(zhat0)),
+                                 _ptr(_c128(zhat1)), float(thr), _ptr(f), _ptr(v), _ptr(active))
+    return f[:n].copy(), v[:n].copy(), int(active[0])
+
+
+class PlanPE:
+    """Taps and the full gain table for one (N, B, w) of the phase-encoding variant."""
+
+    def __init__(self, N, K, B, w, R, seed, eta=1e-6):
+        self.N, self.K, self.B, self.w, self.R, self.seed, self.eta = N, K, B, w, R, seed, eta
+        self.g = window_taps(N, B, w)
+        self.Gfull = filter_gain_full(N, w, self.g)
+        self.sigma, self.tau, self.sigma_inv = loop_params(N, R, seed)
+
+
+def sfft_pe(plan: PlanPE, x):
+    """Whole sFFT3.0-style pipeline.  Returns dict(idx, val, k_out, iters, nfound)."""
+    x = _c128(x)
+    assert x.shape == (plan.N,)
+    idx = np.zeros(plan.K, np.int32)
+    val = np.zeros(plan.K, np.complex128)
+    iters = np.zeros(1, np.int32)
+    nfound = np.zeros(1, np.int64)
+    kout = _load().oracle_sfft_pe(plan.N, plan.K, plan.B, plan.w, plan.R, plan.eta, plan.seed, _ptr(plan.g),
+                                  _ptr(plan.Gfull), _ptr(x), _ptr(idx), _ptr(val), _ptr(iters), _ptr(nfound))
+    if kout < 0:
+        raise ValueError("invalid sfft_pe parameters")
+    return {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout), "iters": int(iters[0]),
+            "nfound": int(nfound[0])}

@@ -387,3 +387,169 @@ int64_t oracle_sfft(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, in
     free(sinv);
     return kout;
 }
+
+/* ==================================================================
+ * sFFT3.0-style location: phase encoding ("Phase encoding method") inside
+ * the iterative framework ("The iterative framework"; Table 1, sFFT3.0:
+ * flat filter, phase encoding, energy estimation, iteration, exactly sparse).
+ * ================================================================== */
+
+/* Textbook iterative radix-2 FFT (decimation in time), in place:
+   a[k] <- sum_n a[n] exp(s 2 pi i n k / n_len), s = +1 or -1. */
+static void fft_radix2(int64_t n, double complex *a, int s)
+{
+    for (int64_t i = 1, j = 0; i < n; ++i) { /* bit reversal */
+        int64_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            double complex t = a[i];
+            a[i] = a[j];
+            a[j] = t;
+        }
+    }
+    for (int64_t len = 2; len <= n; len <<= 1) {
+        for (int64_t i = 0; i < n; i += len) {
+            for (int64_t k = 0; k < len / 2; ++k) {
+                double ang = (double)s * 2.0 * M_PI * (double)k / (double)len;
+                double complex wk = cos(ang) + I * sin(ang);
+                double complex u = a[i + k], v = a[i + k + len / 2] * wk;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+        }
+    }
+}
+
+void oracle_filter_gain_full(int64_t N, int64_t w, const double *g, double *Gfull)
+{
+    double complex *a = (double complex *)calloc((size_t)N, sizeof(double complex));
+    for (int64_t q = 0; q < w; ++q) a[mod_pos(q - w / 2, N)] += g[q]; /* g(m) at index m mod N */
+    fft_radix2(N, a, +1);
+    for (int64_t v = 0; v < N; ++v) {
+        Gfull[2 * v] = creal(a[v]);
+        Gfull[2 * v + 1] = cimag(a[v]);
+    }
+    free(a);
+}
+
+void oracle_pe_subtract(int64_t N, int64_t B, int64_t sigma, int64_t tau, const double *Gfull, int64_t nf,
+                        const int32_t *fidx, const double *fval, double *zhat)
+{
+    int64_t NB = N / B;
+    for (int64_t c = 0; c < nf; ++c) {
+        int64_t f = fidx[c];
+        double complex v = fval[2 * c] + I * fval[2 * c + 1];
+        double complex vt = v * unit_root(tau * f, N); /* x^_f exp(+2 pi i tau f / N) */
+        int64_t p = mod_pos(sigma * f, N);
+        for (int64_t k = 0; k < B; ++k) {
+            int64_t nu = mod_pos(p - k * NB, N);
+            double complex G = Gfull[2 * nu] + I * Gfull[2 * nu + 1];
+            double complex d = vt * G;
+            zhat[2 * k] -= creal(d);
+            zhat[2 * k + 1] -= cimag(d);
+        }
+    }
+}
+
+int64_t oracle_pe_locate(int64_t N, int64_t B, int64_t sigma, int64_t tau, const double *Gfull,
+                         const double *zhat0, const double *zhat1, double thr, int32_t *f_out,
+                         double *v_out, int64_t *active_out)
+{
+    int64_t n = 0, active = 0;
+    for (int64_t k = 0; k < B; ++k) {
+        double complex z0 = zhat0[2 * k] + I * zhat0[2 * k + 1];
+        double complex z1 = zhat1[2 * k] + I * zhat1[2 * k + 1];
+        double e = creal(z0) * creal(z0) + cimag(z0) * cimag(z0);
+        if (!(e >= thr) || e == 0.0) continue;
+        ++active;
+        /* a lone coefficient at f turns by exp(+2 pi i f / N) per unit shift */
+        double complex r = z1 * conj(z0);
+        double phi = atan2(cimag(r), creal(r));
+        int64_t f = mod_pos(llround(phi * (double)N / (2.0 * M_PI)), N);
+        int64_t h, o;
+        oracle_hash(N, B, sigma, f, &h, &o);
+        if (h != k) continue; /* not a lone coefficient of this bucket */
+        double complex G = Gfull[2 * mod_pos(o, N)] + I * Gfull[2 * mod_pos(o, N) + 1];
+        double complex v = z0 * unit_root(-tau * f, N) / G;
+        f_out[n] = (int32_t)f;
+        v_out[2 * n] = creal(v);
+        v_out[2 * n + 1] = cimag(v);
+        ++n;
+    }
+    *active_out = active;
+    return n;
+}
+
+int64_t oracle_sfft_pe(int64_t N, int64_t K, int64_t B, int64_t w, int R, double eta, uint64_t seed,
+                       const double *g, const double *Gfull, const double *x, int32_t *idx, double *val,
+                       int *iters_out, int64_t *nfound_out)
+{
+    if (!is_pow2(N) || N < 2 || !is_pow2(B) || B > N || w < B || w % B || R < 1 || K < 0) return -1;
+    int64_t *sigma = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    int64_t *tau = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    int64_t *sinv = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    oracle_loop_params(N, R, seed, sigma, tau, sinv);
+    double *found = (double *)calloc(2 * (size_t)N, sizeof(double)); /* accumulated values */
+    char *seen = (char *)calloc((size_t)N, 1);
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    double *lval = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    int64_t nf = 0;
+    double *z0 = (double *)malloc(sizeof(double) * 2 * (size_t)B);
+    double *z1 = (double *)malloc(sizeof(double) * 2 * (size_t)B);
+    int32_t *nfi = (int32_t *)malloc(sizeof(int32_t) * (size_t)B);
+    double *nfv = (double *)malloc(sizeof(double) * 2 * (size_t)B);
+    double thr = 0.0;
+    int iters = 0;
+    for (int r = 0; r < R; ++r) {
+        int64_t t0 = tau[r], t1 = mod_pos(tau[r] + 1, N);
+        oracle_bucketize(N, B, w, 1, &sigma[r], &t0, g, x, NULL, z0); /* shift tau_r */
+        oracle_bucketize(N, B, w, 1, &sigma[r], &t1, g, x, NULL, z1); /* shift tau_r + 1 */
+        for (int64_t c = 0; c < nf; ++c) {
+            lval[2 * c] = found[2 * list[c]];
+            lval[2 * c + 1] = found[2 * list[c] + 1];
+        }
+        oracle_pe_subtract(N, B, sigma[r], t0, Gfull, nf, list, lval, z0);
+        oracle_pe_subtract(N, B, sigma[r], t1, Gfull, nf, list, lval, z1);
+        if (r == 0) {
+            double emax = 0.0;
+            for (int64_t k = 0; k < B; ++k) {
+                double e = z0[2 * k] * z0[2 * k] + z0[2 * k + 1] * z0[2 * k + 1];
+                if (e > emax) emax = e;
+            }
+            thr = eta * emax;
+        }
+        int64_t active = 0;
+        int64_t n = oracle_pe_locate(N, B, sigma[r], t0, Gfull, z0, z1, thr, nfi, nfv, &active);
+        iters = r + 1;
+        if (active == 0) break;
+        for (int64_t c = 0; c < n; ++c) {
+            int64_t f = nfi[c];
+            found[2 * f] += nfv[2 * c];
+            found[2 * f + 1] += nfv[2 * c + 1];
+            if (!seen[f]) {
+                seen[f] = 1;
+                list[nf++] = (int32_t)f;
+            }
+        }
+    }
+    for (int64_t c = 0; c < nf; ++c) {
+        lval[2 * c] = found[2 * list[c]];
+        lval[2 * c + 1] = found[2 * list[c] + 1];
+    }
+    int64_t kout = oracle_topk(nf, list, lval, K, idx, val);
+    if (iters_out) *iters_out = iters;
+    if (nfound_out) *nfound_out = nf;
+    free(sigma);
+    free(tau);
+    free(sinv);
+    free(found);
+    free(seen);
+    free(list);
+    free(lval);
+    free(z0);
+    free(z1);
+    free(nfi);
+    free(nfv);
+    return kout;
+}

@@ -1,5 +1,6 @@
 /*
- * FP64 CPU oracle for the flat-window voting sparse FFT (sFFT1.0-style).
+ * FP64 CPU oracle for the flat-window voting sparse FFT (sFFT1.0-style) and
+ * its phase-encoding, iterative variant (sFFT3.0-style).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may include, link or
  * call this code: only the tests, the package smoke check and the benchmark's
@@ -105,6 +106,43 @@ int64_t oracle_sfft(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, in
                     uint64_t seed, const double *g, const double *Gt, const double *x,
                     int32_t *idx, double *val, double *zhat_out, int32_t *sel_out,
                     int32_t *cand_out, double *est_out, int64_t *ncand_out);
+
+/* ---- sFFT3.0-style phase-encoding location, iterative framework ---- */
+
+/* G~(nu) for every offset nu in [0, N) (nu and nu - N name the same offset):
+   Gfull[nu] = sum_m g(m) exp(+2 pi i m nu / N), one length-N radix-2 FFT of
+   the zero-padded window. */
+void oracle_filter_gain_full(int64_t N, int64_t w, const double *g, double *Gfull);
+
+/* The iterative framework's subtraction: removes from the B bucket values of
+   one bucketization (sigma, tau) the contributions of nf known coefficients
+   (fidx, fval complex), by the exact identity
+   zhat[k] = sum_f x^_f exp(+2 pi i tau f / N) G~(sigma f - k N/B). */
+void oracle_pe_subtract(int64_t N, int64_t B, int64_t sigma, int64_t tau, const double *Gfull, int64_t nf,
+                        const int32_t *fidx, const double *fval, double *zhat);
+
+/* Phase-encoding location ("Phase encoding method"): for every bucket k with
+   |zhat0[k]|^2 >= thr (and > 0) -- counted in *active_out -- the time shift
+   by one sample turns a lone coefficient f by exp(+2 pi i f / N), so
+   f = round(arg(zhat1[k] conj(zhat0[k])) N / 2 pi) mod N; f is kept when it
+   hashes back to bucket k, valued zhat0[k] exp(-2 pi i tau f / N) / G~(o).
+   Writes the kept (f, value) pairs and returns their number. */
+int64_t oracle_pe_locate(int64_t N, int64_t B, int64_t sigma, int64_t tau, const double *Gfull,
+                         const double *zhat0, const double *zhat1, double thr, int32_t *f_out,
+                         double *v_out, int64_t *active_out);
+
+/* Whole sFFT3.0-style pipeline for one exactly sparse signal.  Iteration r
+   uses loop parameters r (oracle_loop_params(N, R, seed)) and bucketizes the
+   signal at shifts tau_r and tau_r + 1; the coefficients found so far are
+   subtracted from both; the located (f, value) pairs are added to the found
+   set (values of a frequency found again accumulate).  The threshold is eta
+   times the largest bucket energy of iteration 0; the loop stops after R
+   iterations or when no bucket reaches it.  Output: the K found coefficients
+   of largest magnitude (ties to the lower f), sorted by f.  Returns k_out, or
+   -1 on invalid parameters. */
+int64_t oracle_sfft_pe(int64_t N, int64_t K, int64_t B, int64_t w, int R, double eta, uint64_t seed,
+                       const double *g, const double *Gfull, const double *x, int32_t *idx, double *val,
+                       int *iters_out, int64_t *nfound_out);
 
 #ifdef __cplusplus
 }

@@ -11,6 +11,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_pe_pins as pe_pins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "sfft_oracle.c")
@@ -34,6 +35,13 @@ MUTANTS = [
     ("sigma parity", "int64_t s = 2 * (int64_t)(out[0] % (uint64_t)(N / 2)) + 1;",
      "int64_t s = (int64_t)(out[0] % (uint64_t)N) | 1;"),
     ("threshold off by one", "if (sc[f] >= T) cand[n++]", "if (sc[f] > T) cand[n++]"),
+    # phase-encoding, iterative variant
+    ("pe phase sign", "double phi = atan2(cimag(r), creal(r));", "double phi = -atan2(cimag(r), creal(r));"),
+    ("pe backward shift", "t1 = mod_pos(tau[r] + 1, N);", "t1 = mod_pos(tau[r] - 1, N);"),
+    ("pe subtraction turn", "unit_root(tau * f, N); /* x^_f", "unit_root(-tau * f, N); /* x^_f"),
+    ("pe gain offset reversed", "int64_t nu = mod_pos(p - k * NB, N);", "int64_t nu = mod_pos(k * NB - p, N);"),
+    ("pe no hash check", "if (h != k) continue; /* not a lone", "if (0) continue; /* not a lone"),
+    ("pe estimate without gain", "unit_root(-tau * f, N) / G;", "unit_root(-tau * f, N);"),
 ]
 
 PIN_CHECKS = [
@@ -52,6 +60,13 @@ PIN_CHECKS = [
     pins.test_median_combination,
     pins.test_topk_brute_force,
     pins.test_exact_recovery_noiseless,
+    lambda: pe_pins.test_gain_full_against_numpy_fft(1 << 12, 16),
+    lambda: pe_pins.test_unit_shift_turns_lone_coefficient(1 << 12, 32, 777),
+    lambda: pe_pins.test_subtraction_removes_known_coefficients(1 << 12, 32, 6),
+    pe_pins.test_locate_finds_lone_coefficients,
+    lambda: pe_pins.test_exact_recovery_noiseless(1 << 12, 5, 32, range(6)),
+    pe_pins.test_one_sparse_is_exact_and_stops,
+    pe_pins.test_iterations_resolve_a_collision,
 ]
 
 
