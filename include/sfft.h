@@ -70,8 +70,22 @@ typedef struct {
     int32_t c;         /* buckets kept per loop = min(c*K, B); 0 -> 2 ("2K large buckets") */
     int32_t T;         /* vote threshold; 0 -> ceil(L/2) */
     int32_t precision; /* 0 -> FP32 B-point FFT (the only precision in this build) */
-    int32_t reserved;  /* must be 0 */
+    int32_t method;    /* SFFT_METHOD_VOTING (0, default) or SFFT_METHOD_PHASE */
 } sfft_opts;
+
+/* Location methods.
+   SFFT_METHOD_VOTING: L loops of flat-window bucketization, top-2K buckets,
+     voting, median estimate ("Method of probability and statistics", sFFT1.0).
+   SFFT_METHOD_PHASE: iterative framework with phase-encoding location
+     ("Phase encoding method", "The iterative framework"; Table 1, sFFT3.0):
+     up to L iterations, each bucketizing the signal at shifts tau and tau+1
+     under a new permutation, subtracting the coefficients found so far, and
+     reading every bucket above 1e-6 of iteration 0's largest bucket energy as
+     a lone coefficient at f = arg(zhat' / zhat) N / 2 pi (kept when f hashes
+     back to the bucket), valued by energy concentration.  For exactly sparse
+     signals (Table 2: robustness "none"); c and T are ignored. */
+#define SFFT_METHOD_VOTING 0
+#define SFFT_METHOD_PHASE 1
 
 /* Read-only description of a plan (host struct filled by sfft_plan_get_info). */
 typedef struct {
@@ -81,6 +95,7 @@ typedef struct {
     int64_t samples_touched;     /* distinct sample indices read per execute (Table 2) */
     int64_t candidate_capacity;  /* min(N, (L-T+1)*nsel*N/B): bound on the candidate set */
     size_t device_bytes;         /* device memory held by the plan */
+    int32_t method;              /* SFFT_METHOD_* */
 } sfft_plan_info;
 
 /* ------------------------------------------------------------------ plans */
@@ -117,7 +132,9 @@ typedef struct {
     int64_t estimated;   /* frequencies the median bound could not exclude */
     int64_t recorded;    /* estimates kept for the top-K (candidates, key >= theta) */
     int32_t fallback;    /* 1 if the unpruned pass ran (fewer than K recorded) */
-    float theta;         /* prune threshold: 1/4 of the K-th largest bucket energy */
+    float theta;         /* prune threshold: 1/4 of the K-th largest bucket energy
+                            (phase encoding: the bucket-energy threshold) */
+    int32_t iterations;  /* phase encoding: iterations run; voting: L */
 } sfft_exec_stats;
 
 sfft_status sfft_plan_last_stats(const sfft_plan *plan, sfft_exec_stats *stats);

@@ -130,7 +130,9 @@ void decompose(PlanDev &P) {
     // about one CTA per SM per signal (measured best of 76..600 at the
     // N = 2^20, B = 512, L = 12 workload: longer CTAs amortise the set-up,
     // fewer chunks leave fewer partials to sum)
-    uint32_t want = (kNumSms + P.tiles * P.L - 1) / (P.tiles * P.L);
+    // (phase encoding gathers one loop per launch)
+    const uint32_t loops = P.method == kMethodPhase ? 1u : P.L;
+    uint32_t want = (kNumSms + P.tiles * loops - 1) / (P.tiles * loops);
     want = std::max<uint32_t>(1, std::min<uint32_t>(want, P.rounds));
     P.rpc = (P.rounds + want - 1) / want;
     P.nchunk = (P.rounds + P.rpc - 1) / P.rpc;
@@ -139,7 +141,7 @@ void decompose(PlanDev &P) {
 }
 
 struct Layout {
-    size_t plan, taps, tw, ginv, part, zhat, en, lkth, topk, sel, flags, survf, surv, ctr, total;
+    size_t plan, taps, tw, ginv, gext, part, zhat, en, lkth, topk, sel, flags, survf, surv, ctr, total;
 };
 
 Layout layout_of(const PlanDev &P, int64_t cap) {
@@ -150,11 +152,14 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
         off += align256(bytes);
         return at;
     };
-    const size_t L = P.L, B = P.B;
+    const bool phase = P.method == kMethodPhase;
+    // phase encoding keeps the two shifts' partials and bucket values in rows 0 and 1
+    const size_t L = phase ? std::max<uint32_t>(P.L, 2) : P.L, B = P.B;
     o.plan = take(sizeof(PlanDev));
     o.taps = take(sizeof(float) * P.w);
     o.tw = take(sizeof(float2) * (B / 2));
     o.ginv = take(sizeof(float2) * (P.N / B));
+    o.gext = take(phase ? sizeof(float2) * 3 * (P.N / B) : 0);
     o.part = take(sizeof(float2) * P.nchunk * L * B);
     o.zhat = take(sizeof(float2) * L * B);
     o.en = take(sizeof(float) * L * B);
@@ -171,7 +176,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
 
 // Sizes and work split of a plan, without touching the device.
 void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
-                   int64_t *cap) {
+                   int64_t *cap, uint32_t method) {
     memset(&P, 0, sizeof(P));
     const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     P.N = (uint32_t)N;
@@ -189,18 +194,23 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.nsel = (uint32_t)nsel;
     P.T = (uint32_t)T;
     P.M = (uint32_t)((L + 1) / 2);
+    P.method = method;
     decompose(P);
     *cap = std::min<int64_t>(N, (int64_t)(L - T + 1) * nsel * (N / B));
+    // phase encoding: each iteration adds at most B found coefficients
+    if (method == kMethodPhase) *cap = std::min<int64_t>(N, (int64_t)L * B);
     P.cap = (uint32_t)*cap;
 }
 
 }  // namespace
 
-size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T) {
+size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
+                         int32_t method) {
+    if (method == SFFT_METHOD_PHASE) c = T = 1;
     if (check_sizes(N, K, B, w, L, c, T) != SFFT_OK) return 0;
     PlanDev P;
     int64_t cap;
-    fill_plan_dev(P, N, K, B, w, L, c, T, &cap);
+    fill_plan_dev(P, N, K, B, w, L, c, T, &cap, method == SFFT_METHOD_PHASE ? kMethodPhase : kMethodVoting);
     return layout_of(P, cap).total;
 }
 
@@ -220,10 +230,26 @@ struct Sizes {
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0, max_K = 0;
     uint32_t est_ctas = kEstimateCtas, est_smem = 0;  // pruned estimate: CTAs per job, staged table bytes
     bool bits = true;
+    bool phase = false;  // every job uses the phase-encoding method
+    uint32_t max_L = 0;  // phase encoding: iterations to launch
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
     Sizes z;
+    z.max_L = p->h.L;
+    if (p->h.method == kMethodPhase) {
+        // CTAs per job: one iteration's gather, one iteration CTA, one output CTA
+        z.phase = true;
+        z.gather = p->h.tiles * p->h.nchunk;
+        z.select = 1;
+        z.vote = 0;
+        z.jobs = 1;
+        z.max_B = p->h.B;
+        z.max_K = p->h.K;
+        z.L_uniform = p->h.L;
+        z.bits = false;
+        return z;
+    }
     z.gather = p->h.tiles * p->h.L * p->h.nchunk;
     z.select = p->h.L;
     z.vote = p->h.vtiles;
@@ -235,6 +261,23 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.bits = p->h.use_bits != 0;
     z.est_smem = estimate_tab_bytes(p->h.N, p->h.B, p->h.L);
     return z;
+}
+
+// Phase-encoding method: per iteration the gather of both shifts and the
+// per-job iteration, then the per-job output.  With ev: the iterations are
+// bracketed as the first stage, the output as the last.
+cudaError_t launch_phase(const Launch &lg, const Launch &li, const Launch &lf, const Sizes &z, cudaStream_t s,
+                         cudaEvent_t *ev = nullptr) {
+    cudaError_t e;
+    if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+    for (uint32_t r = 0; r < z.max_L; ++r) {
+        if ((e = launch_pe_gather(lg, z.gather, r, s)) != cudaSuccess) return e;
+        if ((e = launch_pe_iterate(li, z.jobs, z.max_B, r, s)) != cudaSuccess) return e;
+    }
+    for (int i = 1; ev && i <= 5; ++i)
+        if ((e = cudaEventRecord(ev[i], s)) != cudaSuccess) return e;
+    if ((e = launch_pe_finish(lf, z.jobs, z.max_K, s)) != cudaSuccess) return e;
+    return ev ? cudaEventRecord(ev[6], s) : cudaSuccess;
 }
 
 // gather -> FFT/select -> scan -> estimate (whose last CTA per job takes the
@@ -367,12 +410,14 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
         set_error("only precision 0 (FP32 FFT) is implemented");
         return SFFT_ENOTIMPL;
     }
-    if (o.reserved != 0) {
-        set_error("sfft_opts.reserved must be 0");
+    if (o.method != SFFT_METHOD_VOTING && o.method != SFFT_METHOD_PHASE) {
+        set_error("sfft_opts.method must be SFFT_METHOD_VOTING or SFFT_METHOD_PHASE");
         return SFFT_EINVAL;
     }
-    const int32_t c = o.c > 0 ? o.c : 2;
-    const int32_t T = o.T > 0 ? o.T : (L + 1) / 2;
+    const bool phase = o.method == SFFT_METHOD_PHASE;
+    // (phase encoding reads no c or T)
+    const int32_t c = phase ? 1 : (o.c > 0 ? o.c : 2);
+    const int32_t T = phase ? 1 : (o.T > 0 ? o.T : (L + 1) / 2);
     sfft_status st = check_sizes(N, K, B, w, L, c, T);
     if (st != SFFT_OK) return st;
 
@@ -394,7 +439,7 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     p->seed = seed;
 
     PlanDev &P = p->h;
-    fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap);
+    fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap, (uint32_t)o.method);
     loop_params_host(N, L, seed, P.sigma, P.tau, p->sigma_inv);
     const Layout lay = layout_of(P, p->cap);
     p->device_bytes = lay.total;
@@ -409,6 +454,7 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     P.taps = reinterpret_cast<float *>(base + lay.taps);
     P.tw = reinterpret_cast<float2 *>(base + lay.tw);
     P.ginv = reinterpret_cast<float2 *>(base + lay.ginv);
+    P.gext = phase ? reinterpret_cast<float2 *>(base + lay.gext) : nullptr;
     P.partial = reinterpret_cast<float2 *>(base + lay.part);
     P.zhat = reinterpret_cast<float2 *>(base + lay.zhat);
     P.energy = reinterpret_cast<float *>(base + lay.en);
@@ -442,15 +488,15 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     if ((e = cudaMemsetAsync(P.ctr, 0, sizeof(uint32_t) * kNumCounters, s)) != cudaSuccess)
         return fail(e, "clear counters");
     if ((e = plan_tables(P.N, P.B, P.w, const_cast<float *>(P.taps), const_cast<float2 *>(P.tw),
-                         const_cast<float2 *>(P.ginv), ginv2, s)) != cudaSuccess)
+                         const_cast<float2 *>(P.ginv), ginv2, const_cast<float2 *>(P.gext), s)) != cudaSuccess)
         return fail(e, "plan tables");
     unsigned long long *d_count = reinterpret_cast<unsigned long long *>(static_cast<char *>(tmp) + bitmap_bytes);
     unsigned long long *d_max = d_count + 1;
     if ((e = plan_max_bits(ginv2, (uint32_t)nb, d_max, s)) != cudaSuccess) return fail(e, "gain max");
     const uint32_t *d_sigma = reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(p->d) + offsetof(PlanDev, sigma));
     const uint32_t *d_tau = reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(p->d) + offsetof(PlanDev, tau));
-    if ((e = plan_samples_touched(P.N, P.w, P.L, d_sigma, d_tau, static_cast<uint32_t *>(tmp), d_count, s)) !=
-        cudaSuccess)
+    if ((e = plan_samples_touched(P.N, P.w, P.L, d_sigma, d_tau, static_cast<uint32_t *>(tmp), d_count,
+                                  phase ? 1 : 0, s)) != cudaSuccess)
         return fail(e, "samples touched");
     unsigned long long host2[2] = {0, 0};
     if ((e = cudaMemcpyAsync(host2, d_count, sizeof(host2), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -498,6 +544,7 @@ extern "C" sfft_status sfft_plan_get_info(const sfft_plan *p, sfft_plan_info *in
     info->samples_touched = p->samples_touched;
     info->candidate_capacity = p->cap;
     info->device_bytes = p->device_bytes;
+    info->method = (int32_t)p->h.method;
     return SFFT_OK;
 }
 
@@ -522,6 +569,17 @@ extern "C" sfft_status sfft_plan_last_stats(const sfft_plan *p, sfft_exec_stats 
     }
     uint32_t c[kNumCounters];
     SFFT_CUDA_TRY(cudaMemcpy(c, p->h.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    if (p->h.method == kMethodPhase) {
+        // found coefficients (kNGe), iterations run, bucket-energy threshold
+        st->candidates = -1;
+        st->estimated = c[kNGe];
+        st->recorded = c[kNGe];
+        st->fallback = 0;
+        memcpy(&st->theta, &c[kTheta], sizeof(float));
+        st->iterations = (int32_t)c[kPeIter];
+        return SFFT_OK;
+    }
+    st->iterations = p->L;
     const bool fb = c[kNGe] < (uint32_t)p->K;
     st->candidates = fb ? (int64_t)c[kNCand] : -1;
     st->estimated = fb ? c[kNCand] : c[kNSurv];  // the fallback pass estimates every candidate
@@ -541,7 +599,10 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
         return SFFT_EINVAL;
     }
     const Launch ln = single(make_job(p, x_dev, idx_dev, val_dev, k_out_dev));
-    SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+    if (p->h.method == kMethodPhase)
+        SFFT_CUDA_TRY(launch_phase(ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+    else
+        SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
 }
 
@@ -612,6 +673,8 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         z.max_flags = std::max(z.max_flags, s.max_flags);
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
         z.est_smem = (i == 0 || z.est_smem) && s.est_smem ? std::max(z.est_smem, s.est_smem) : 0u;
+        z.phase = i == 0 ? s.phase : z.phase;  // one method per batch (callers split mixed lists)
+        z.max_L = std::max(z.max_L, s.max_L);
     }
     // pruned estimate with staged tables: one wave of resident CTAs over the
     // batch (each CTA stages its job's tables once)
@@ -676,6 +739,7 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         ln[k].njobs = count;
         memset(&ln[k].one, 0, sizeof(Job));
     }
+    if (b.z.phase) return launch_phase(ln[0], ln[1], ln[3], b.z, s, ev);
     return launch_pipeline(ln[0], ln[1], ln[2], ln[5], b.z, s, ev);
 }
 
@@ -695,6 +759,10 @@ sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, cons
                 set_error("a plan appears twice in one batch (each plan owns its scratch)");
                 return SFFT_EINVAL;
             }
+        if (plans[i]->h.method != plans[0]->h.method) {
+            set_error("a batch mixes location methods (voting and phase encoding run as separate batches)");
+            return SFFT_EINVAL;
+        }
     }
     return SFFT_OK;
 }

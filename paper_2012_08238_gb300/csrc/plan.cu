@@ -59,6 +59,36 @@ __global__ void k_gain(uint32_t N, uint32_t B, uint32_t w, const double *g64, fl
     }
 }
 
+// G~(nu) itself (FP32) for nu in [-3N/2B, 3N/2B): the gains of a coefficient
+// in its own bucket and both neighbours, used by the phase-encoding
+// subtraction.  One CTA per offset.
+__global__ void k_gain_ext(uint32_t N, uint32_t B, uint32_t w, const double *g64, float2 *gext) {
+    __shared__ double sre[256], sim[256];
+    const uint32_t NB = N / B;
+    const int64_t o = (int64_t)blockIdx.x - (int64_t)(3 * NB / 2);
+    double re = 0.0, im = 0.0;
+    for (uint32_t q = threadIdx.x; q < w; q += blockDim.x) {
+        const int64_t m = (int64_t)q - (int64_t)(w / 2);
+        int64_t r = (m * o) % (int64_t)N;
+        if (r < 0) r += N;
+        double sn, cs;
+        sincospi(2.0 * (double)r / (double)N, &sn, &cs);
+        re += g64[q] * cs;
+        im += g64[q] * sn;
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (uint32_t s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sre[threadIdx.x] += sre[threadIdx.x + s];
+            sim[threadIdx.x] += sim[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gext[blockIdx.x] = make_float2((float)sre[0], (float)sim[0]);
+}
+
 __global__ void k_twiddle(uint32_t B, float2 *tw) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < B / 2; k += gridDim.x * blockDim.x) {
         double sn, cs;
@@ -67,14 +97,19 @@ __global__ void k_twiddle(uint32_t B, float2 *tw) {
     }
 }
 
+// pair: also the sample one past each (the phase-encoding shift tau + 1)
 __global__ void k_mark(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma, const uint32_t *tau,
-                       uint32_t *bitmap) {
+                       uint32_t *bitmap, int pair) {
     const uint64_t total = (uint64_t)L * w;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t l = (uint32_t)(t / w), q = (uint32_t)(t % w);
         const uint32_t i = (sigma[l] * (q - w / 2) + tau[l]) & (N - 1);
         atomicOr(bitmap + (i >> 5), 1u << (i & 31));
+        if (pair) {
+            const uint32_t i1 = (i + 1) & (N - 1);
+            atomicOr(bitmap + (i1 >> 5), 1u << (i1 & 31));
+        }
     }
 }
 
@@ -111,7 +146,7 @@ cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, 
 }
 
 cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
-                        double *ginv2, cudaStream_t s) {
+                        double *ginv2, float2 *gext, cudaStream_t s) {
     double *g64 = nullptr;
     cudaError_t e = cudaMallocAsync(&g64, sizeof(double) * w, s);
     if (e != cudaSuccess) return e;
@@ -119,6 +154,7 @@ cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 
     const double sg = (double)B * sqrt((double)logN);
     k_taps<<<(w + 255) / 256, 256, 0, s>>>(N, B, w, sg, g64, taps);
     k_gain<<<N / B, 256, 0, s>>>(N, B, w, g64, ginv, ginv2);
+    if (gext) k_gain_ext<<<3 * (N / B), 256, 0, s>>>(N, B, w, g64, gext);
     k_twiddle<<<(B / 2 + 255) / 256, 256, 0, s>>>(B, tw);
     e = cudaGetLastError();
     cudaError_t e2 = cudaFreeAsync(g64, s);
@@ -126,7 +162,7 @@ cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 
 }
 
 cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
-                                 const uint32_t *tau, uint32_t *bitmap, unsigned long long *count,
+                                 const uint32_t *tau, uint32_t *bitmap, unsigned long long *count, int pair,
                                  cudaStream_t s) {
     const uint32_t nwords = (N + 31) / 32;
     cudaError_t e = cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * nwords, s);
@@ -135,7 +171,7 @@ cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint3
     if (e != cudaSuccess) return e;
     const uint64_t total = (uint64_t)L * w;
     const uint32_t blocks = (uint32_t)std::min<uint64_t>((total + 255) / 256, 65535);
-    k_mark<<<blocks, 256, 0, s>>>(N, w, L, sigma, tau, bitmap);
+    k_mark<<<blocks, 256, 0, s>>>(N, w, L, sigma, tau, bitmap, pair);
     const uint32_t pb = std::min<uint32_t>((nwords + 255) / 256, 65535);
     k_popc<<<pb, 256, 0, s>>>(bitmap, nwords, count);
     return cudaGetLastError();

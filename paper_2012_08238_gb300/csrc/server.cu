@@ -20,7 +20,8 @@
 #include "sfft_internal.cuh"
 
 namespace sfft {
-size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T);
+size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
+                         int32_t method);
 }
 
 namespace {
@@ -31,7 +32,7 @@ int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
 }
 
-using PlanKey = std::tuple<int64_t, int64_t, int32_t, int32_t, int32_t, uint64_t, int32_t, int32_t>;
+using PlanKey = std::tuple<int64_t, int64_t, int32_t, int32_t, int32_t, uint64_t, int32_t, int32_t, int32_t>;
 
 struct Request {
     uint64_t ticket = 0;
@@ -124,7 +125,7 @@ bool acquire_plan(sfft_server *s, Request *r, std::unique_lock<std::mutex> &lk) 
     }
     const sfft_request &q = r->req;
     const size_t need = sfft::plan_device_bytes(q.N, q.K, q.B, q.w, q.L, q.opts.c > 0 ? q.opts.c : 2,
-                                                q.opts.T > 0 ? q.opts.T : (q.L + 1) / 2);
+                                                q.opts.T > 0 ? q.opts.T : (q.L + 1) / 2, q.opts.method);
     while (s->plan_bytes + need > s->budget) {
         auto victim = s->plans.end();
         for (auto it = s->plans.begin(); it != s->plans.end(); ++it)
@@ -168,6 +169,8 @@ void worker_main(sfft_server *s) {
         std::vector<Request *> batch, failed;
         while (!s->queue.empty() && s->in_use + (int32_t)batch.size() < s->max_slots) {
             Request *r = s->queue.front();
+            // one location method per batch; the next batch takes the other
+            if (!batch.empty() && r->req.opts.method != batch[0]->req.opts.method) break;
             if (r->plan == nullptr) {
                 if (!acquire_plan(s, r, lk)) break;  // wait for running batches to free plans
             }
@@ -283,7 +286,7 @@ extern "C" sfft_status sfft_submit(sfft_server *s, const sfft_request *q, uint64
     }
     const int32_t c = q->opts.c > 0 ? q->opts.c : 2;
     const int32_t T = q->opts.T > 0 ? q->opts.T : (q->L + 1) / 2;
-    const size_t need = sfft::plan_device_bytes(q->N, q->K, q->B, q->w, q->L, c, T);
+    const size_t need = sfft::plan_device_bytes(q->N, q->K, q->B, q->w, q->L, c, T, q->opts.method);
     if (need == 0) return SFFT_EINVAL;  // sizes rejected, reason already set
     if (need > s->budget) {
         sfft::set_error("request's plan alone exceeds the server's memory budget");
@@ -292,7 +295,7 @@ extern "C" sfft_status sfft_submit(sfft_server *s, const sfft_request *q, uint64
     Request *r = new (std::nothrow) Request();
     if (!r) return SFFT_ENOMEM;
     r->req = *q;
-    r->key = PlanKey(q->N, q->w, q->K, q->B, q->L, q->seed, c, T);
+    r->key = PlanKey(q->N, q->w, q->K, q->B, q->L, q->seed, c, T, q->opts.method);
     r->t_submit = now_ns();
     {
         std::lock_guard<std::mutex> lk(s->mu);

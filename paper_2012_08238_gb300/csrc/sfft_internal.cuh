@@ -16,6 +16,8 @@ constexpr int kMaxK = 16384;
 constexpr int kMaxLogN = 30;
 constexpr int kFlagsSmemBytes = 96 * 1024;
 constexpr int kClusterMaxB = 4096;     // clustered FFT/select up to this B
+constexpr uint32_t kMethodVoting = 0;  // sFFT1.0-style voting (the default)
+constexpr uint32_t kMethodPhase = 1;   // sFFT3.0-style phase encoding, iterative framework
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
@@ -39,6 +41,8 @@ enum Counter : int {
     kErr = 6,      // device-side error word (0 = none)
     kNRec2 = 7,    // records written by the unpruned fallback pass (in the top-K step)
     kEstDone = 8,  // estimate CTAs of the job finished (last-CTA ticket for the top-K step)
+    kPeDone = 9,   // phase encoding: 1 once an iteration found no bucket above the threshold
+    kPeIter = 10,  // phase encoding: iterations run
     kNumCounters = 16
 };
 
@@ -57,10 +61,12 @@ struct PlanDev {
     uint32_t use_bits;                        // 32 <= B <= 512: strong bits in registers (pruned scan)
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
+    uint32_t method;                          // kMethodVoting or kMethodPhase
     uint32_t sigma[kMaxL], tau[kMaxL];
     const float *taps;     // [w]
     const float2 *tw;      // [B/2] exp(-2 pi i k / B)
     const float2 *ginv;    // [N/B] 1 / G~(o), o + half
+    const float2 *gext;    // phase encoding: [3N/B] G~(nu) for nu + 3N/2B in [0, 3N/B)
     float2 *partial;       // [nchunk][L][B]
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
@@ -126,16 +132,23 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
 // and L is uniform in {8, 12, 16}; they are then staged there.
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
                             uint32_t max_K, cudaStream_t s);
+// Phase-encoding variant: iteration r's gather (CTAs = tiles x chunks per
+// job) and per-job iteration (one CTA per job), then the per-job output.
+cudaError_t launch_pe_gather(const Launch &ln, uint32_t total_ctas, uint32_t r, cudaStream_t s);
+cudaError_t launch_pe_iterate(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t r, cudaStream_t s);
+cudaError_t launch_pe_finish(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);
 cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *sel, cudaStream_t s);
 
 // Plan-time FP64 kernels (plan.cu).
+// gext (phase-encoding plans, else NULL): G~ over three buckets around 0.
 cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
-                        double *ginv2, cudaStream_t s);
+                        double *ginv2, float2 *gext, cudaStream_t s);
 cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, cudaStream_t s);
+// pair: count the samples one past each too (phase encoding's second shift)
 cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
-                                 const uint32_t *tau, uint32_t *bitmap, unsigned long long *count,
+                                 const uint32_t *tau, uint32_t *bitmap, unsigned long long *count, int pair,
                                  cudaStream_t s);
 
 }  // namespace sfft

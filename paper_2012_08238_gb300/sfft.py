@@ -27,18 +27,18 @@ SFFT_OK, SFFT_EINVAL, SFFT_ENOMEM, SFFT_ECUDA, SFFT_EBUSY, SFFT_ETIMEDOUT, SFFT_
 
 
 class sfft_opts(ctypes.Structure):
-    _fields_ = [("c", _i32), ("T", _i32), ("precision", _i32), ("reserved", _i32)]
+    _fields_ = [("c", _i32), ("T", _i32), ("precision", _i32), ("method", _i32)]
 
 
 class sfft_plan_info(ctypes.Structure):
     _fields_ = [("N", _i64), ("w", _i64), ("K", _i32), ("B", _i32), ("L", _i32), ("c", _i32), ("T", _i32),
                 ("nsel", _i32), ("seed", _u64), ("samples_touched", _i64), ("candidate_capacity", _i64),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("method", _i32)]
 
 
 class sfft_exec_stats(ctypes.Structure):
     _fields_ = [("candidates", _i64), ("estimated", _i64), ("recorded", _i64), ("fallback", _i32),
-                ("theta", ctypes.c_float)]
+                ("theta", ctypes.c_float), ("iterations", _i32)]
 
 
 class sfft_request(ctypes.Structure):
@@ -177,8 +177,12 @@ def sfft_plan_create(N, K, B, w, L, seed, opts: sfft_opts | None = None) -> Plan
     return Plan(h.value)
 
 
-def sfft_plan_create_ex(N, K, B, w, L, seed, c=0, T=0, precision=0) -> Plan:
-    return sfft_plan_create(N, K, B, w, L, seed, sfft_opts(c, T, precision, 0))
+SFFT_METHOD_VOTING = 0
+SFFT_METHOD_PHASE = 1
+
+
+def sfft_plan_create_ex(N, K, B, w, L, seed, c=0, T=0, precision=0, method=SFFT_METHOD_VOTING) -> Plan:
+    return sfft_plan_create(N, K, B, w, L, seed, sfft_opts(c, T, precision, method))
 
 
 def sfft_plan_destroy(plan: Plan):
@@ -315,8 +319,8 @@ def sfft_server_destroy(srv: Server):
     srv.destroy()
 
 
-def sfft_submit(srv: Server, N, K, B, w, L, seed, x, idx, val, c=0, T=0) -> int:
-    req = sfft_request(N, w, K, B, L, seed, sfft_opts(c, T, 0, 0), _addr(x), _addr(idx), _addr(val))
+def sfft_submit(srv: Server, N, K, B, w, L, seed, x, idx, val, c=0, T=0, method=0) -> int:
+    req = sfft_request(N, w, K, B, L, seed, sfft_opts(c, T, 0, method), _addr(x), _addr(idx), _addr(val))
     ticket = _u64()
     _check(lib().sfft_submit(srv.handle, ctypes.byref(req), ctypes.byref(ticket)))
     return ticket.value
