@@ -194,6 +194,62 @@ def measure_served(sfft, torch, W, xs, dev, n_req, rate, seed=0):
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99))}
 
 
+def measure_exact(sfft, torch, dev, stream, args, S=256, R=8):
+    """The exactly sparse workload (N = 2^16, K = 10, noiseless, B = 64) through
+    sfft_execute_batch with the phase-encoding method (R iterations at most)
+    and with voting (L = 8): spectra/s on the device, support recall, mean
+    iterations, and the phase-encoding oracle on one host core (context)."""
+    from paper_2012_08238_gb300 import metrics as _m
+
+    W = configs.EXACT_N16
+    w = configs.default_window(W.N, W.B)
+    sigs = [signals.make_signal(W.N, W.K, 10_000 + s) for s in range(S)]
+    xs = [torch.from_numpy(sg.x).to(dev) for sg in sigs]
+    out = {"workload": f"exact_N2^16_K10_B64 (noiseless), {S} signals per step, inputs "
+                       f"{S * W.N * 8 / 2**20:.0f} MiB (> L2)"}
+    for name, method, L in (("phase_encoding", sfft.SFFT_METHOD_PHASE, R), ("voting", sfft.SFFT_METHOD_VOTING, W.L)):
+        plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, w, L, 10_000 + s, method=method) for s in range(S)]
+        idxs = [torch.zeros(W.K, dtype=torch.int32, device=dev) for _ in range(S)]
+        vals = [torch.zeros(W.K, dtype=torch.complex64, device=dev) for _ in range(S)]
+        kout = torch.zeros(S, dtype=torch.int32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+        torch.cuda.synchronize(dev)
+        # device time of `steps` batches enqueued by the library itself
+        total_ms, _ = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, args.steps, stream)
+        ms = total_ms / args.steps
+        # and the rate of the Python-level call (ctypes marshalling of S signals per call)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        call_ms = e0.elapsed_time(e1) / args.steps
+        k = kout.cpu().numpy()
+        miss = sum(_m.errors(sg.xhat, W.K, idxs[i].cpu().numpy()[: k[i]], vals[i].cpu().numpy()[: k[i]])["L0"]
+                   for i, sg in enumerate(sigs))
+        entry = {"value": S / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "python_call_value": S / (call_ms / 1e3),
+                 "support_recall": 1.0 - miss / (W.K * S),
+                 "samples_per_spectrum": plans[0].info.samples_touched, "max_iterations": L}
+        if method == sfft.SFFT_METHOD_PHASE:
+            its = [sfft.sfft_plan_last_stats(p).iterations for p in plans[:16]]
+            entry["iterations_mean_first16"] = float(np.mean(its))
+        out[name] = entry
+        del plans
+    if not args.no_cpu:
+        import oracle as _oracle
+
+        n = 4
+        t0 = time.perf_counter()
+        for s in range(n):
+            _oracle.sfft_pe(_oracle.PlanPE(W.N, W.K, W.B, w, R, 10_000 + s), sigs[s].x)
+        out["oracle_phase_cpu"] = {"value": n / (time.perf_counter() - t0), "unit": UNIT, "cores": 1,
+                                   "sample": f"{n} signals, FP64 oracle incl. its plan tables, one process"}
+    return out
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -351,6 +407,9 @@ def run_ours(args):
              "what": f"dense complex64 FFT of the same {S} signals (cuFFT via torch.fft), context only"}
     del xb
 
+    # ---- exactly sparse workload: phase encoding (iterative) vs voting (context)
+    exact = measure_exact(sfft, torch, dev, stream, args) if rank == 0 else None
+
     # ---- CPU baseline: the oracle on a bounded sample, host cores
     cpu = None
     if pool is not None:
@@ -377,6 +436,7 @@ def run_ours(args):
         "stage_ms_per_step": per_launch, "stage_share": {k: v / sum(per_launch.values()) for k, v in per_launch.items()},
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
         "roofline": roofline, "roofline_scan": roofline_scan, "dense_fft_context": dense,
+        "exactly_sparse": exact,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,

@@ -230,17 +230,19 @@ struct Sizes {
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0, max_K = 0;
     uint32_t est_ctas = kEstimateCtas, est_smem = 0;  // pruned estimate: CTAs per job, staged table bytes
     bool bits = true;
-    bool phase = false;  // every job uses the phase-encoding method
-    uint32_t max_L = 0;  // phase encoding: iterations to launch
+    bool phase = false;    // every job uses the phase-encoding method
+    uint32_t max_L = 0;    // phase encoding: iterations to launch
+    uint32_t max_cap = 0;  // phase encoding: largest found-list capacity
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
     Sizes z;
     z.max_L = p->h.L;
     if (p->h.method == kMethodPhase) {
-        // CTAs per job: one iteration's gather, one iteration CTA, one output CTA
+        // one CTA per job (the select slot of the batch maps)
         z.phase = true;
-        z.gather = p->h.tiles * p->h.nchunk;
+        z.max_cap = p->h.cap;
+        z.gather = 0;
         z.select = 1;
         z.vote = 0;
         z.jobs = 1;
@@ -263,21 +265,15 @@ Sizes plan_sizes(const sfft_plan *p) {
     return z;
 }
 
-// Phase-encoding method: per iteration the gather of both shifts and the
-// per-job iteration, then the per-job output.  With ev: the iterations are
-// bracketed as the first stage, the output as the last.
-cudaError_t launch_phase(const Launch &lg, const Launch &li, const Launch &lf, const Sizes &z, cudaStream_t s,
-                         cudaEvent_t *ev = nullptr) {
+// Phase-encoding method: one launch, one CTA per job over all its iterations.
+// With ev: bracketed as the first stage; the other stages are empty.
+cudaError_t launch_phase(const Launch &lj, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-    for (uint32_t r = 0; r < z.max_L; ++r) {
-        if ((e = launch_pe_gather(lg, z.gather, r, s)) != cudaSuccess) return e;
-        if ((e = launch_pe_iterate(li, z.jobs, z.max_B, r, s)) != cudaSuccess) return e;
-    }
-    for (int i = 1; ev && i <= 5; ++i)
+    if ((e = launch_pe(lj, z.jobs, z.max_B, z.max_K, z.max_cap, s)) != cudaSuccess) return e;
+    for (int i = 1; ev && i <= 6; ++i)
         if ((e = cudaEventRecord(ev[i], s)) != cudaSuccess) return e;
-    if ((e = launch_pe_finish(lf, z.jobs, z.max_K, s)) != cudaSuccess) return e;
-    return ev ? cudaEventRecord(ev[6], s) : cudaSuccess;
+    return cudaSuccess;
 }
 
 // gather -> FFT/select -> scan -> estimate (whose last CTA per job takes the
@@ -600,7 +596,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
     }
     const Launch ln = single(make_job(p, x_dev, idx_dev, val_dev, k_out_dev));
     if (p->h.method == kMethodPhase)
-        SFFT_CUDA_TRY(launch_phase(ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+        SFFT_CUDA_TRY(launch_phase(ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     else
         SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
@@ -675,6 +671,7 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         z.est_smem = (i == 0 || z.est_smem) && s.est_smem ? std::max(z.est_smem, s.est_smem) : 0u;
         z.phase = i == 0 ? s.phase : z.phase;  // one method per batch (callers split mixed lists)
         z.max_L = std::max(z.max_L, s.max_L);
+        z.max_cap = std::max(z.max_cap, s.max_cap);
     }
     // pruned estimate with staged tables: one wave of resident CTAs over the
     // batch (each CTA stages its job's tables once)
@@ -739,7 +736,7 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         ln[k].njobs = count;
         memset(&ln[k].one, 0, sizeof(Job));
     }
-    if (b.z.phase) return launch_phase(ln[0], ln[1], ln[3], b.z, s, ev);
+    if (b.z.phase) return launch_phase(ln[1], b.z, s, ev);
     return launch_pipeline(ln[0], ln[1], ln[2], ln[5], b.z, s, ev);
 }
 

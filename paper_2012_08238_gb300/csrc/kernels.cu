@@ -1357,62 +1357,6 @@ __global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t c
 // coefficients are kept as records {f, 0, re bits, im bits} in P.surv
 // (count in kNGe); values of a frequency found again accumulate.
 
-// rows of the partial-sum and bucket arrays (the two shifts use rows 0 and 1)
-__device__ __forceinline__ uint32_t pe_rows(const PlanDev &P) { return P.L > 2 ? P.L : 2; }
-
-// a1 for both shifts: CTA = (bucket tile, chunk of rounds) of iteration r.
-__global__ void __launch_bounds__(kThreads) k_pe_gather(Launch ln, uint32_t r) {
-    __shared__ PlanDev P;
-    __shared__ Job J;
-    __shared__ uint32_t s_local;
-    __shared__ int s_skip;
-    __shared__ float2 red0[kThreads], red1[kThreads];
-    enter(ln, P, J, s_local);
-    if (threadIdx.x == 0) s_skip = r >= P.L || (r > 0 && __ldcg(P.ctr + kPeDone) != 0);
-    __syncthreads();
-    if (s_skip) return;
-    const uint32_t tile = s_local % P.tiles, chunk = s_local / P.tiles;
-    const uint32_t TB = P.tb, PP = kThreads / TB;
-    const uint32_t jt = threadIdx.x & (TB - 1), s = threadIdx.x / TB;
-    const uint32_t j = tile * TB + jt;
-    const uint32_t r0 = chunk * J.rpc, r1 = min(P.rounds, r0 + J.rpc);
-    const uint32_t sig = P.sigma[r], tau = P.tau[r], mask = P.mask, B = P.B, halfw = P.halfw;
-    const uint32_t jq = (j + halfw) & (B - 1);
-    const float2 *__restrict__ x = J.x;
-    float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
-#pragma unroll 4
-    for (uint32_t rr = r0 + s; rr < r1; rr += PP) {
-        const uint32_t q = rr * B + jq;
-        const uint32_t i = (sig * (q - halfw) + tau) & mask;
-        const float g = __ldg(P.taps + q);
-        const float2 v0 = __ldg(x + i), v1 = __ldg(x + ((i + 1) & mask));
-        a0r = fmaf(g, v0.x, a0r);
-        a0i = fmaf(g, v0.y, a0i);
-        a1r = fmaf(g, v1.x, a1r);
-        a1i = fmaf(g, v1.y, a1i);
-    }
-    const size_t row = (size_t)chunk * pe_rows(P) * B;
-    if (PP == 1) {
-        P.partial[row + j] = make_float2(a0r, a0i);
-        P.partial[row + B + j] = make_float2(a1r, a1i);
-        return;
-    }
-    red0[threadIdx.x] = make_float2(a0r, a0i);
-    red1[threadIdx.x] = make_float2(a1r, a1i);
-    __syncthreads();
-    if (s == 0) {
-        float2 c0 = red0[jt], c1 = red1[jt];
-        for (uint32_t k = 1; k < PP; ++k) {
-            c0.x += red0[jt + k * TB].x;
-            c0.y += red0[jt + k * TB].y;
-            c1.x += red1[jt + k * TB].x;
-            c1.y += red1[jt + k * TB].y;
-        }
-        P.partial[row + j] = c0;
-        P.partial[row + B + j] = c1;
-    }
-}
-
 // Radix-2 FFT of two B-point bit-reversed buffers in shared memory, the same
 // stages as k_fft_select (all threads; ends with a barrier).
 __device__ void fft2_smem(float2 *b0, float2 *b1, uint32_t B, uint32_t logB, const float2 *tw) {
@@ -1440,155 +1384,164 @@ __device__ __forceinline__ float2 turn_pos(uint32_t ph) {
     return make_float2(cs, sn);
 }
 
-// Iteration r of one job (one CTA per job): bucket values of both shifts,
-// subtraction of the found coefficients from their own and both neighbouring
-// buckets (G~ of the plan's three-bucket table; the flat window's gain
-// further out is below its stop-band floor), threshold (iteration 0: 1e-6 of
-// the largest bucket energy), location and estimate of lone coefficients.
-// A job whose iteration finds no bucket above the threshold stops.
-__global__ void __launch_bounds__(kThreads) k_pe_iterate(Launch ln, uint32_t r) {
-    extern __shared__ float2 pe_s[];  // bucket values of both shifts [B] [B], twiddles [B/2]
+// One job per CTA, all iterations: bucket values of both shifts (gathered and
+// folded straight into shared memory), subtraction of the found coefficients
+// from their own and both neighbouring buckets (G~ of the plan's three-bucket
+// table; the flat window's gain further out is below its stop-band floor),
+// threshold (1e-6 of iteration 0's largest bucket energy), location and
+// estimate of lone coefficients; stops after the first iteration with no
+// bucket above the threshold, then writes the K largest found coefficients.
+__global__ void __launch_bounds__(kThreads) k_pe_job(Launch ln, uint32_t cap, uint32_t fcap) {
+    // bucket values of both shifts [B] [B], twiddles [B/2]; then the found
+    // list when it fits fcap entries (else it stays in P.surv), or the top-K
+    // buffer at the end
+    extern __shared__ float2 pe_s[];
     __shared__ PlanDev P;
     __shared__ Job J;
-    __shared__ uint32_t s_local, s_active, s_nprev;
-    __shared__ int s_skip;
+    __shared__ uint32_t s_local, s_active, s_n;
     __shared__ float s_thr, s_wmax[kThreads / 32];
+    __shared__ float2 red0[kThreads], red1[kThreads];
     enter(ln, P, J, s_local);
-    if (threadIdx.x == 0) {
-        s_skip = r >= P.L || (r > 0 && __ldcg(P.ctr + kPeDone) != 0);
-        s_active = 0;
-        if (r == 0 && !s_skip) {
-            P.ctr[kNGe] = 0;
-            P.ctr[kPeDone] = 0;
-        }
-        s_nprev = r == 0 ? 0u : __ldcg(P.ctr + kNGe);
-    }
-    __syncthreads();
-    if (s_skip) return;
-    const uint32_t B = P.B, logB = P.logB, rows = pe_rows(P);
+    const uint32_t B = P.B, logB = P.logB, N = P.N, NB = N >> logB;
     float2 *b0 = pe_s, *b1 = pe_s + B, *tw = pe_s + 2 * B;
     for (uint32_t k = threadIdx.x; k < B / 2; k += blockDim.x) tw[k] = __ldg(P.tw + k);
-    const size_t cstride = (size_t)rows * B;
-    for (uint32_t j = threadIdx.x; j < B; j += blockDim.x) {
-        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-        for (uint32_t c = 0; c < J.nchunk; ++c) {
-            const float2 v0 = __ldcg(P.partial + c * cstride + j), v1 = __ldcg(P.partial + c * cstride + B + j);
-            a0.x += v0.x;
-            a0.y += v0.y;
-            a1.x += v1.x;
-            a1.y += v1.y;
-        }
-        const uint32_t br = __brev(j) >> (32 - logB);
-        b0[br] = a0;
-        b1[br] = a1;
-    }
-    __syncthreads();
-    fft2_smem(b0, b1, B, logB, tw);
-
+    if (threadIdx.x == 0) s_n = 0;
+    const uint32_t TB = P.tb, PP = kThreads / TB;
+    const uint32_t jt = threadIdx.x & (TB - 1), sidx = threadIdx.x / TB;
     const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
-    const uint32_t sig = P.sigma[r], tau = P.tau[r], N = P.N, NB = N >> logB;
-    const uint32_t nprev = s_nprev;
-    // subtraction, bucket by bucket over the found list (a fixed order)
-    for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
-        float2 z0 = b0[k], z1 = b1[k];
-        for (uint32_t e = 0; e < nprev; ++e) {
-            const uint4 rec = __ldcg(P.surv + e);
-            const uint32_t f = rec.x;
-            const uint32_t h = ((sig << sN) * f + cv) >> top;
-            const uint32_t d = (k - h) & (B - 1);
-            if (d != 0 && d != 1 && d != B - 1) continue;
-            // nu = (sigma f mod N) - k N/B, wrapped into [-N/2, N/2)
-            const int32_t nu = (int32_t)((((sig * f) & P.mask) - k * NB + N / 2) & P.mask) - (int32_t)(N / 2);
-            const float2 G = __ldg(P.gext + (nu + (int32_t)(3 * NB / 2)));
-            const float2 c0 = cmul(cmul(make_float2(__uint_as_float(rec.z), __uint_as_float(rec.w)),
-                                        turn_pos((tau << sN) * f)),
-                                   G);
-            const float2 c1 = cmul(c0, turn_pos((1u << sN) * f));
-            z0.x -= c0.x;
-            z0.y -= c0.y;
-            z1.x -= c1.x;
-            z1.y -= c1.y;
+    const float2 *__restrict__ x = J.x;
+    uint4 *F = P.cap <= fcap ? reinterpret_cast<uint4 *>(pe_s + 2 * B + B / 2 + (B & 1)) : P.surv;
+    uint32_t iters = 0;
+    for (uint32_t r = 0; r < P.L; ++r) {
+        const uint32_t sig = P.sigma[r], tau = P.tau[r];
+        // a1 for both shifts, bucket tile by bucket tile
+        for (uint32_t tile = 0; tile < P.tiles; ++tile) {
+            const uint32_t j = tile * TB + jt, jq = (j + P.halfw) & (B - 1);
+            float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
+#pragma unroll 8
+            for (uint32_t rr = sidx; rr < P.rounds; rr += PP) {
+                const uint32_t q = rr * B + jq;
+                const uint32_t i = (sig * (q - P.halfw) + tau) & P.mask;
+                const float g = __ldg(P.taps + q);
+                const float2 v0 = __ldg(x + i), v1 = __ldg(x + ((i + 1) & P.mask));
+                a0r = fmaf(g, v0.x, a0r);
+                a0i = fmaf(g, v0.y, a0i);
+                a1r = fmaf(g, v1.x, a1r);
+                a1i = fmaf(g, v1.y, a1i);
+            }
+            red0[threadIdx.x] = make_float2(a0r, a0i);
+            red1[threadIdx.x] = make_float2(a1r, a1i);
+            __syncthreads();
+            if (sidx == 0) {
+                float2 c0 = red0[jt], c1 = red1[jt];
+                for (uint32_t k = 1; k < PP; ++k) {
+                    c0.x += red0[jt + k * TB].x;
+                    c0.y += red0[jt + k * TB].y;
+                    c1.x += red1[jt + k * TB].x;
+                    c1.y += red1[jt + k * TB].y;
+                }
+                const uint32_t br = __brev(j) >> (32 - logB);
+                b0[br] = c0;
+                b1[br] = c1;
+            }
+            __syncthreads();
         }
-        b0[k] = z0;
-        b1[k] = z1;
-    }
-    __syncthreads();
-    if (r == 0) {
-        float m = 0.f;
-        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) m = fmaxf(m, b0[k].x * b0[k].x + b0[k].y * b0[k].y);
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-        if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = m;
+        fft2_smem(b0, b1, B, logB, tw);
+        const uint32_t nprev = s_n;
+        // subtraction, bucket by bucket over the found list (a fixed order)
+        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
+            float2 z0 = b0[k], z1 = b1[k];
+            for (uint32_t e = 0; e < nprev; ++e) {
+                const uint4 rec = F[e];
+                const uint32_t f = rec.x;
+                const uint32_t h = ((sig << sN) * f + cv) >> top;
+                const uint32_t d = (k - h) & (B - 1);
+                if (d != 0 && d != 1 && d != B - 1) continue;
+                // nu = (sigma f mod N) - k N/B, wrapped into [-N/2, N/2)
+                const int32_t nu = (int32_t)((((sig * f) & P.mask) - k * NB + N / 2) & P.mask) - (int32_t)(N / 2);
+                const float2 G = __ldg(P.gext + (nu + (int32_t)(3 * NB / 2)));
+                const float2 c0 = cmul(cmul(make_float2(__uint_as_float(rec.z), __uint_as_float(rec.w)),
+                                            turn_pos((tau << sN) * f)),
+                                       G);
+                const float2 c1 = cmul(c0, turn_pos((1u << sN) * f));
+                z0.x -= c0.x;
+                z0.y -= c0.y;
+                z1.x -= c1.x;
+                z1.y -= c1.y;
+            }
+            b0[k] = z0;
+            b1[k] = z1;
+        }
+        if (threadIdx.x == 0) s_active = 0;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float mm = 0.f;
-            for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2) mm = fmaxf(mm, s_wmax[w2]);
-            s_thr = 1e-6f * mm;
-            P.ctr[kTheta] = __float_as_uint(s_thr);
+        if (r == 0) {
+            float m = 0.f;
+            for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
+                m = fmaxf(m, b0[k].x * b0[k].x + b0[k].y * b0[k].y);
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+            if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = m;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float mm = 0.f;
+                for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2) mm = fmaxf(mm, s_wmax[w2]);
+                s_thr = 1e-6f * mm;
+            }
+            __syncthreads();
         }
-    } else if (threadIdx.x == 0) {
-        s_thr = __uint_as_float(__ldcg(P.ctr + kTheta));
-    }
-    __syncthreads();
-    const float thr = s_thr;
-    uint32_t active = 0;
-    for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
-        const float2 z0 = b0[k], z1 = b1[k];
-        const float e = z0.x * z0.x + z0.y * z0.y;
-        if (!(e >= thr) || e == 0.f) continue;
-        ++active;
-        // a lone coefficient at f turns by exp(+2 pi i f / N) per unit shift
-        const float2 rt = make_float2(z1.x * z0.x + z1.y * z0.y, z1.y * z0.x - z1.x * z0.y);
-        const double phi = atan2((double)rt.y, (double)rt.x);
-        const long long fl = llrint(phi * (double)N / (2.0 * CUDART_PI));
-        const uint32_t f = (uint32_t)fl & P.mask;
-        const uint32_t t = (sig << sN) * f + cv;
-        if ((t >> top) != k) continue;  // not a lone coefficient of this bucket
-        const uint32_t opos = P.logB < P.logN ? (t << P.logB) >> (P.logB + sN) : 0u;
-        const float2 v = turn_scale(z0, __ldg(P.ginv + opos), (tau << sN) * f);
-        bool merged = false;
-        for (uint32_t e2 = 0; e2 < nprev; ++e2) {
-            const uint4 rec = __ldcg(P.surv + e2);
-            if (rec.x == f) {  // f has one home bucket: one writer per iteration
-                P.surv[e2] = make_uint4(f, 0u, __float_as_uint(__uint_as_float(rec.z) + v.x),
-                                        __float_as_uint(__uint_as_float(rec.w) + v.y));
-                merged = true;
-                break;
+        const float thr = s_thr;
+        uint32_t active = 0;
+        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
+            const float2 z0 = b0[k], z1 = b1[k];
+            const float e = z0.x * z0.x + z0.y * z0.y;
+            if (!(e >= thr) || e == 0.f) continue;
+            ++active;
+            // a lone coefficient at f turns by exp(+2 pi i f / N) per unit shift
+            const float2 rt = make_float2(z1.x * z0.x + z1.y * z0.y, z1.y * z0.x - z1.x * z0.y);
+            const double phi = atan2((double)rt.y, (double)rt.x);
+            const long long fl = llrint(phi * (double)N / (2.0 * CUDART_PI));
+            const uint32_t f = (uint32_t)fl & P.mask;
+            const uint32_t t = (sig << sN) * f + cv;
+            if ((t >> top) != k) continue;  // not a lone coefficient of this bucket
+            const uint32_t opos = P.logB < P.logN ? (t << P.logB) >> (P.logB + sN) : 0u;
+            const float2 v = turn_scale(z0, __ldg(P.ginv + opos), (tau << sN) * f);
+            bool merged = false;
+            for (uint32_t e2 = 0; e2 < nprev; ++e2) {
+                const uint4 rec = F[e2];
+                if (rec.x == f) {  // f has one home bucket: one writer per iteration
+                    F[e2] = make_uint4(f, 0u, __float_as_uint(__uint_as_float(rec.z) + v.x),
+                                            __float_as_uint(__uint_as_float(rec.w) + v.y));
+                    merged = true;
+                    break;
+                }
+            }
+            if (!merged) {
+                const uint32_t pos = atomicAdd(&s_n, 1u);  // < cap: at most B per iteration
+                F[pos] = make_uint4(f, 0u, __float_as_uint(v.x), __float_as_uint(v.y));
             }
         }
-        if (!merged) {
-            const uint32_t pos = atomicAdd(P.ctr + kNGe, 1u);  // < L*B: at most B per iteration
-            P.surv[pos] = make_uint4(f, 0u, __float_as_uint(v.x), __float_as_uint(v.y));
-        }
+        active = __reduce_add_sync(0xFFFFFFFFu, active);
+        if ((threadIdx.x & 31) == 0 && active) atomicAdd(&s_active, active);
+        __threadfence_block();
+        __syncthreads();
+        iters = r + 1;
+        if (s_active == 0) break;  // uniform
     }
-    active = __reduce_add_sync(0xFFFFFFFFu, active);
-    if ((threadIdx.x & 31) == 0 && active) atomicAdd(&s_active, active);
-    __syncthreads();
+    const uint32_t S = s_n;
     if (threadIdx.x == 0) {
-        P.ctr[kPeIter] = r + 1;
-        if (s_active == 0) P.ctr[kPeDone] = 1;
+        P.ctr[kNGe] = S;
+        P.ctr[kPeIter] = iters;
+        P.ctr[kTheta] = __float_as_uint(s_thr);
     }
-}
-
-// Output of the phase-encoding variant (one CTA per job): the K found
-// coefficients of largest |value| (ties to the lower f), sorted by f.
-__global__ void __launch_bounds__(kThreads) k_pe_finish(Launch ln, uint32_t cap) {
-    extern __shared__ unsigned long long pe_tk[];
-    __shared__ PlanDev P;
-    __shared__ Job J;
-    __shared__ uint32_t s_local, s_S;
-    enter(ln, P, J, s_local);
-    if (threadIdx.x == 0) s_S = __ldcg(P.ctr + kNGe);
-    __syncthreads();
-    const uint32_t S = s_S;
     for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
-        uint4 rec = __ldcg(P.surv + i);
+        uint4 rec = F[i];
         const float re = __uint_as_float(rec.z), im = __uint_as_float(rec.w);
         rec.y = __float_as_uint(re * re + im * im);
         P.surv[i] = rec;
     }
     __threadfence_block();
     __syncthreads();
-    rank_records(P, J, pe_tk, cap, S, min(S, P.K));
+    unsigned long long *tk = reinterpret_cast<unsigned long long *>(pe_s + 2 * B + B / 2 + (B & 1));
+    rank_records(P, J, tk, cap, S, min(S, P.K));
 }
 
 // Stage kernels for the single-step entry points.
@@ -1752,29 +1705,19 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform
 }
 
 
-cudaError_t launch_pe_gather(const Launch &ln, uint32_t total_ctas, uint32_t r, cudaStream_t s) {
-    if (total_ctas == 0) return cudaSuccess;
-    k_pe_gather<<<total_ctas, kThreads, 0, s>>>(ln, r);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pe_iterate(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t r, cudaStream_t s) {
-    if (njobs == 0) return cudaSuccess;
-    const int smem = (int)(sizeof(float2) * (2 * max_B + max_B / 2));
-    cudaError_t e = cudaFuncSetAttribute(k_pe_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_pe_iterate<<<njobs, kThreads, smem, s>>>(ln, r);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pe_finish(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s) {
+cudaError_t launch_pe(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t max_K, uint32_t max_cap,
+                      cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
     uint32_t cap = kRankMax;
     while (cap < max_K) cap <<= 1;
-    const int smem = (int)(cap * (sizeof(unsigned long long) + sizeof(uint32_t)));
-    cudaError_t e = cudaFuncSetAttribute(k_pe_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const size_t tables = (sizeof(float2) * (2 * max_B + max_B / 2 + 1) + 15) & ~(size_t)15;
+    const size_t rank = cap * (sizeof(unsigned long long) + sizeof(uint32_t));
+    // found list in shared memory when every job's fits kPeSmemFound entries
+    const uint32_t fcap = max_cap <= kPeSmemFound ? max_cap : 0u;
+    const int smem = (int)(tables + std::max<size_t>(rank, sizeof(uint4) * fcap));
+    cudaError_t e = cudaFuncSetAttribute(k_pe_job, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_pe_finish<<<njobs, kThreads, smem, s>>>(ln, cap);
+    k_pe_job<<<njobs, kThreads, smem, s>>>(ln, cap, fcap);
     return cudaGetLastError();
 }
 

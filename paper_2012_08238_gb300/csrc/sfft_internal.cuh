@@ -18,6 +18,7 @@ constexpr int kFlagsSmemBytes = 96 * 1024;
 constexpr int kClusterMaxB = 4096;     // clustered FFT/select up to this B
 constexpr uint32_t kMethodVoting = 0;  // sFFT1.0-style voting (the default)
 constexpr uint32_t kMethodPhase = 1;   // sFFT3.0-style phase encoding, iterative framework
+constexpr uint32_t kPeSmemFound = 2048;  // phase encoding: found lists up to this size live in shared memory
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
@@ -41,7 +42,6 @@ enum Counter : int {
     kErr = 6,      // device-side error word (0 = none)
     kNRec2 = 7,    // records written by the unpruned fallback pass (in the top-K step)
     kEstDone = 8,  // estimate CTAs of the job finished (last-CTA ticket for the top-K step)
-    kPeDone = 9,   // phase encoding: 1 once an iteration found no bucket above the threshold
     kPeIter = 10,  // phase encoding: iterations run
     kNumCounters = 16
 };
@@ -132,11 +132,12 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
 // and L is uniform in {8, 12, 16}; they are then staged there.
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
                             uint32_t max_K, cudaStream_t s);
-// Phase-encoding variant: iteration r's gather (CTAs = tiles x chunks per
-// job) and per-job iteration (one CTA per job), then the per-job output.
-cudaError_t launch_pe_gather(const Launch &ln, uint32_t total_ctas, uint32_t r, cudaStream_t s);
-cudaError_t launch_pe_iterate(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t r, cudaStream_t s);
-cudaError_t launch_pe_finish(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s);
+// Phase-encoding variant: one CTA per job runs all its iterations and writes
+// its top K.
+// max_cap: the largest found-list capacity of the jobs (lists of at most
+// kPeSmemFound entries stay in shared memory).
+cudaError_t launch_pe(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t max_K, uint32_t max_cap,
+                      cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);
 cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *sel, cudaStream_t s);
