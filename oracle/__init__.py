@@ -80,6 +80,11 @@ def _bind(lib):
         "oracle_filter_gain_full": (None, [_i64, _i64, _p, _p]),
         "oracle_pe_subtract": (None, [_i64, _i64, _i64, _i64, _p, _i64, _p, _p, _p]),
         "oracle_pe_locate": (_i64, [_i64, _i64, _i64, _i64, _p, _p, _p, ctypes.c_double, _p, _p, _p]),
+        "oracle_comb": (_i64, [_i64, _i64, _int, _p, _i64, _p, _p, _p]),
+        "oracle_sfft2": (
+            _i64,
+            [_i64, _i64, _i64, _i64, _int, _int, _int, _i64, _int, _u64, _p, _p, _p, _p, _p, _p, _p],
+        ),
         "oracle_sfft_pe": (
             _i64,
             [_i64, _i64, _i64, _i64, _int, ctypes.c_double, _u64, _p, _p, _p, _p, _p, _p, _p],
@@ -355,3 +360,28 @@ def sfft_pe(plan: PlanPE, x):
         raise ValueError("invalid sfft_pe parameters")
     return {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout), "iters": int(iters[0]),
             "nfound": int(nfound[0])}
+
+
+# ----------------------------------------------- sFFT2.0-style pre-filter
+def comb(N: int, Bc: int, tau_c, nkeep: int, x):
+    """Spike-train pre-filter: (kept mask [Bc] bool, energies [Bc])."""
+    tau_c = np.ascontiguousarray(tau_c, np.int64)
+    kept = np.zeros(Bc, np.uint8)
+    E = np.zeros(Bc, np.float64)
+    _load().oracle_comb(N, Bc, len(tau_c), _ptr(tau_c), nkeep, _ptr(_c128(x)), _ptr(kept), _ptr(E))
+    return kept.astype(bool), E
+
+
+def sfft2(plan: Plan, x, Bc: int, C: int = 2):
+    """Voting pipeline behind the spike-train pre-filter.  Returns dict(idx, val, k_out, kept, ncand)."""
+    x = _c128(x)
+    idx = np.zeros(plan.K, np.int32)
+    val = np.zeros(plan.K, np.complex128)
+    kept = np.zeros(Bc, np.uint8)
+    ncand = np.zeros(1, np.int64)
+    kout = _load().oracle_sfft2(plan.N, plan.K, plan.B, plan.w, plan.L, plan.c, plan.T, Bc, C, plan.seed,
+                                _ptr(plan.g), _ptr(plan.Gt), _ptr(x), _ptr(idx), _ptr(val), _ptr(kept), _ptr(ncand))
+    if kout < 0:
+        raise ValueError("invalid sfft2 parameters")
+    return {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout), "kept": kept.astype(bool),
+            "ncand": int(ncand[0])}

@@ -553,3 +553,94 @@ int64_t oracle_sfft_pe(int64_t N, int64_t K, int64_t B, int64_t w, int R, double
     free(nfv);
     return kout;
 }
+
+/* ==================================================================
+ * sFFT2.0-style spike-train pre-filter (Eq. 10 subsampling, Eq. 15 spike
+ * train, Eq. 16 bucket composition; Table 1 sFFT2.0: spike train + flat
+ * filters, statistics, energy, voting).
+ * ================================================================== */
+
+int64_t oracle_comb(int64_t N, int64_t Bc, int C, const int64_t *tau_c, int64_t nkeep, const double *x,
+                    uint8_t *kept, double *E)
+{
+    int64_t stride = N / Bc;
+    double complex *w = (double complex *)malloc(sizeof(double complex) * (size_t)Bc);
+    double complex *y = (double complex *)malloc(sizeof(double complex) * (size_t)Bc);
+    for (int64_t i = 0; i < Bc; ++i) E[i] = 0.0;
+    for (int c = 0; c < C; ++c) {
+        /* subsample (Eq. 10) at a shift: one sample per N/Bc */
+        for (int64_t j = 0; j < Bc; ++j) {
+            int64_t n = mod_pos(tau_c[c] + j * stride, N);
+            w[j] = x[2 * n] + I * x[2 * n + 1];
+        }
+        /* Bc-point DFT with 1/Bc: y[i] = sum over f = i (mod Bc) of x^_f e^{+2 pi i tau f / N} (Eq. 16) */
+        for (int64_t i = 0; i < Bc; ++i) {
+            double complex s = 0;
+            for (int64_t j = 0; j < Bc; ++j) {
+                double a = -2.0 * M_PI * (double)((i * j) % Bc) / (double)Bc;
+                s += w[j] * (cos(a) + I * sin(a));
+            }
+            y[i] = s / (double)Bc;
+        }
+        for (int64_t i = 0; i < Bc; ++i) E[i] += creal(y[i]) * creal(y[i]) + cimag(y[i]) * cimag(y[i]);
+    }
+    /* kept classes: the nkeep largest energies (key rounded to binary32), ties to the lower class */
+    int32_t *sel = (int32_t *)malloc(sizeof(int32_t) * (size_t)Bc);
+    double *Ez = (double *)malloc(sizeof(double) * 2 * (size_t)Bc); /* as |z|^2 with z = sqrt(E) */
+    for (int64_t i = 0; i < Bc; ++i) {
+        Ez[2 * i] = sqrt(E[i]);
+        Ez[2 * i + 1] = 0.0;
+    }
+    int64_t n = oracle_select(Bc, nkeep, Ez, sel);
+    memset(kept, 0, (size_t)Bc);
+    for (int64_t s = 0; s < n; ++s) kept[sel[s]] = 1;
+    free(sel);
+    free(Ez);
+    free(w);
+    free(y);
+    return n;
+}
+
+int64_t oracle_sfft2(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T, int64_t Bc, int C,
+                     uint64_t seed, const double *g, const double *Gt, const double *x, int32_t *idx, double *val,
+                     uint8_t *kept_out, int64_t *ncand_out)
+{
+    if (!is_pow2(N) || N < 2 || !is_pow2(B) || B > N || w < B || w % B || L < 1 || c < 1 || T < 1 || T > L ||
+        !is_pow2(Bc) || Bc > N || C < 1)
+        return -1;
+    int64_t *sigma = (int64_t *)malloc(sizeof(int64_t) * (size_t)(L + C));
+    int64_t *tau = (int64_t *)malloc(sizeof(int64_t) * (size_t)(L + C));
+    int64_t *sinv = (int64_t *)malloc(sizeof(int64_t) * (size_t)(L + C));
+    oracle_loop_params(N, L + C, seed, sigma, tau, sinv); /* loops 0..L-1 vote; L..L+C-1 give the comb shifts */
+
+    uint8_t *kept = kept_out ? kept_out : (uint8_t *)malloc((size_t)Bc);
+    double *E = (double *)malloc(sizeof(double) * (size_t)Bc);
+    oracle_comb(N, Bc, C, tau + L, (int64_t)c * K < Bc ? (int64_t)c * K : Bc, x, kept, E);
+
+    double *zhat = (double *)malloc(sizeof(double) * 2 * (size_t)(L * B));
+    oracle_bucketize(N, B, w, L, sigma, tau, g, x, NULL, zhat);
+    int64_t cK = (int64_t)c * K;
+    int64_t nsel = cK < B ? cK : B;
+    int32_t *sel = (int32_t *)malloc(sizeof(int32_t) * (size_t)(L * nsel));
+    for (int l = 0; l < L; ++l) oracle_select(B, cK, zhat + 2 * l * B, sel + l * nsel);
+    int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int64_t nc = oracle_vote(N, B, L, nsel, T, sinv, sel, NULL, cand);
+    /* only frequencies of kept residue classes stay candidates */
+    int64_t ncand = 0;
+    for (int64_t q = 0; q < nc; ++q)
+        if (kept[mod_pos(cand[q], Bc)]) cand[ncand++] = cand[q];
+    double *est = (double *)malloc(sizeof(double) * 2 * (size_t)(ncand ? ncand : 1));
+    oracle_estimate(N, B, L, sigma, tau, Gt, zhat, ncand, cand, est, NULL);
+    int64_t kout = oracle_topk(ncand, cand, est, K, idx, val);
+    if (ncand_out) *ncand_out = ncand;
+    if (!kept_out) free(kept);
+    free(E);
+    free(zhat);
+    free(sel);
+    free(cand);
+    free(est);
+    free(sigma);
+    free(tau);
+    free(sinv);
+    return kout;
+}

@@ -144,6 +144,27 @@ int64_t oracle_sfft_pe(int64_t N, int64_t K, int64_t B, int64_t w, int R, double
                        const double *g, const double *Gfull, const double *x, int32_t *idx, double *val,
                        int *iters_out, int64_t *nfound_out);
 
+/* ---- sFFT2.0-style spike-train pre-filter ---- */
+
+/* Residue classes kept by the spike-train filter.  Comb c samples the signal
+   at x[(tau_c[c] + j N/Bc) mod N], j < Bc (Eq. 10 at a shift); its Bc-point
+   DFT with 1/Bc gives y_c[i] = sum over f = i (mod Bc) of x^_f e^{+2 pi i tau_c f/N}
+   (Eq. 16); E[i] = sum_c |y_c[i]|^2.  kept[i] = 1 for the nkeep classes of
+   largest E (key rounded to binary32, ties to the lower class).  Returns the
+   number kept. */
+int64_t oracle_comb(int64_t N, int64_t Bc, int C, const int64_t *tau_c, int64_t nkeep, const double *x,
+                    uint8_t *kept, double *E);
+
+/* Voting pipeline behind the spike-train pre-filter (sFFT2.0-style): loop
+   parameters 0..L-1 vote as in oracle_sfft; loops L..L+C-1 give the comb
+   shifts; min(cK, Bc) residue classes are kept; a frequency is a candidate
+   when its score reaches T and its class f mod Bc is kept.  Estimate and
+   top-K as in oracle_sfft.  kept_out (Bc bytes) may be NULL.  Returns k_out,
+   or -1 on invalid parameters. */
+int64_t oracle_sfft2(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T, int64_t Bc, int C,
+                     uint64_t seed, const double *g, const double *Gt, const double *x, int32_t *idx, double *val,
+                     uint8_t *kept_out, int64_t *ncand_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_comb_pins as comb_pins
 import test_oracle_pe_pins as pe_pins
 import test_oracle_pins as pins
 
@@ -42,6 +43,12 @@ MUTANTS = [
     ("pe gain offset reversed", "int64_t nu = mod_pos(p - k * NB, N);", "int64_t nu = mod_pos(k * NB - p, N);"),
     ("pe no hash check", "if (h != k) continue; /* not a lone", "if (0) continue; /* not a lone"),
     ("pe estimate without gain", "unit_root(-tau * f, N) / G;", "unit_root(-tau * f, N);"),
+    # spike-train pre-filter
+    ("comb dft sign", "double a = -2.0 * M_PI * (double)((i * j) % Bc) / (double)Bc;",
+     "double a = 2.0 * M_PI * (double)((i * j) % Bc) / (double)Bc;"),
+    ("comb stride", "int64_t n = mod_pos(tau_c[c] + j * stride, N);", "int64_t n = mod_pos(tau_c[c] + j, N);"),
+    ("comb filter off", "if (kept[mod_pos(cand[q], Bc)]) cand[ncand++] = cand[q];", "cand[ncand++] = cand[q];"),
+    ("comb shifts from the voting loops", "tau + L, (int64_t)c * K", "tau, (int64_t)c * K"),
 ]
 
 PIN_CHECKS = [
@@ -67,6 +74,10 @@ PIN_CHECKS = [
     lambda: pe_pins.test_exact_recovery_noiseless(1 << 12, 5, 32, range(6)),
     pe_pins.test_one_sparse_is_exact_and_stops,
     pe_pins.test_iterations_resolve_a_collision,
+    lambda: comb_pins.test_comb_energy_closed_form(1 << 12, 64, 7),
+    comb_pins.test_comb_keeps_largest_classes_with_ties,
+    lambda: comb_pins.test_filtered_candidates_are_voting_candidates_in_kept_classes(0),
+    lambda: comb_pins.test_exact_recovery_noiseless(1 << 16, 10, 64, 8, 256),
 ]
 
 
