@@ -70,7 +70,9 @@ typedef struct {
     int32_t c;         /* buckets kept per loop = min(c*K, B); 0 -> 2 ("2K large buckets") */
     int32_t T;         /* vote threshold; 0 -> ceil(L/2) */
     int32_t precision; /* 0 -> FP32 B-point FFT (the only precision in this build) */
-    int32_t method;    /* SFFT_METHOD_VOTING (0, default) or SFFT_METHOD_PHASE */
+    int32_t method;    /* SFFT_METHOD_VOTING (0, default), SFFT_METHOD_PHASE or SFFT_METHOD_COMB */
+    int32_t comb;      /* SFFT_METHOD_COMB: residue classes Bc (power of two); 0 -> default
+                          min(2^ceil(log2(16 c K)), 8192, N, 32 N / B for 32 <= B <= 512) */
 } sfft_opts;
 
 /* Location methods.
@@ -86,6 +88,12 @@ typedef struct {
      signals (Table 2: robustness "none"); c and T are ignored. */
 #define SFFT_METHOD_VOTING 0
 #define SFFT_METHOD_PHASE 1
+/* SFFT_METHOD_COMB: voting behind the spike-train pre-filter (sFFT2.0-style;
+   Eq. 10, 15-16; Table 1 sFFT2.0): two subsamplings of the signal at stride
+   N/Bc (shifts tau of loops L and L+1) alias it into Bc residue classes;
+   their energies keep the min(cK, Bc) largest classes, and only frequencies
+   of kept classes are voted on, estimated and output (L <= 30). */
+#define SFFT_METHOD_COMB 2
 
 /* Read-only description of a plan (host struct filled by sfft_plan_get_info). */
 typedef struct {

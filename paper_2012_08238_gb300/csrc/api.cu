@@ -137,11 +137,15 @@ void decompose(PlanDev &P) {
     P.rpc = (P.rounds + want - 1) / want;
     P.nchunk = (P.rounds + P.rpc - 1) / P.rpc;
     P.vtiles = (P.N + kVoteTileF - 1) / kVoteTileF;  // each tile's survivors fit the CTA's queue
+    // comb: only the kept classes' N/Bc frequencies each are scanned
+    if (P.method == kMethodComb)
+        P.vtiles = (uint32_t)(((uint64_t)P.ncls * (P.N / P.Bc) + kVoteTileF - 1) / kVoteTileF);
     P.use_bits = (P.B >= 32 && P.B <= 512) ? 1u : 0u;
 }
 
 struct Layout {
-    size_t plan, taps, tw, ginv, gext, part, zhat, en, lkth, topk, sel, flags, survf, surv, ctr, total;
+    size_t plan, taps, tw, ginv, gext, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, survf, surv, ctr,
+        total;
 };
 
 Layout layout_of(const PlanDev &P, int64_t cap) {
@@ -160,6 +164,10 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.tw = take(sizeof(float2) * (B / 2));
     o.ginv = take(sizeof(float2) * (P.N / B));
     o.gext = take(phase ? sizeof(float2) * 3 * (P.N / B) : 0);
+    const bool comb = P.method == kMethodComb;
+    o.ctw = take(comb ? sizeof(float2) * (P.Bc / 2) : 0);
+    o.cls = take(comb ? sizeof(uint32_t) * P.ncls : 0);
+    o.keptc = take(comb ? sizeof(uint32_t) * ((P.Bc + 31) / 32) : 0);
     o.part = take(sizeof(float2) * P.nchunk * L * B);
     o.zhat = take(sizeof(float2) * L * B);
     o.en = take(sizeof(float) * L * B);
@@ -176,7 +184,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
 
 // Sizes and work split of a plan, without touching the device.
 void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
-                   int64_t *cap, uint32_t method) {
+                   int64_t *cap, uint32_t method, uint32_t Bc) {
     memset(&P, 0, sizeof(P));
     const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     P.N = (uint32_t)N;
@@ -195,6 +203,11 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.T = (uint32_t)T;
     P.M = (uint32_t)((L + 1) / 2);
     P.method = method;
+    if (method == kMethodComb) {
+        P.Bc = Bc;
+        P.logBc = ilog2(Bc);
+        P.ncls = (uint32_t)std::min<int64_t>((int64_t)c * K, Bc);
+    }
     decompose(P);
     *cap = std::min<int64_t>(N, (int64_t)(L - T + 1) * nsel * (N / B));
     // phase encoding: each iteration adds at most B found coefficients
@@ -210,7 +223,12 @@ size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, 
     if (check_sizes(N, K, B, w, L, c, T) != SFFT_OK) return 0;
     PlanDev P;
     int64_t cap;
-    fill_plan_dev(P, N, K, B, w, L, c, T, &cap, method == SFFT_METHOD_PHASE ? kMethodPhase : kMethodVoting);
+    // (a comb plan's residue tables are a few KB; sized here at the largest default)
+    fill_plan_dev(P, N, K, B, w, L, c, T, &cap,
+                  method == SFFT_METHOD_PHASE  ? kMethodPhase
+                  : method == SFFT_METHOD_COMB ? kMethodComb
+                                               : kMethodVoting,
+                  (uint32_t)std::min<int64_t>(N, kMaxComb));
     return layout_of(P, cap).total;
 }
 
@@ -233,6 +251,8 @@ struct Sizes {
     bool phase = false;    // every job uses the phase-encoding method
     uint32_t max_L = 0;    // phase encoding: iterations to launch
     uint32_t max_cap = 0;  // phase encoding: largest found-list capacity
+    bool comb = false;     // every job votes behind the spike-train pre-filter
+    uint32_t max_Bc = 0;   // comb: largest number of residue classes
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -252,6 +272,8 @@ Sizes plan_sizes(const sfft_plan *p) {
         z.bits = false;
         return z;
     }
+    z.comb = p->h.method == kMethodComb;
+    z.max_Bc = p->h.Bc;
     z.gather = p->h.tiles * p->h.L * p->h.nchunk;
     z.select = p->h.L;
     z.vote = p->h.vtiles;
@@ -282,7 +304,7 @@ cudaError_t launch_phase(const Launch &lj, const Sizes &z, cudaStream_t s, cudaE
 // stages: gather, FFT/select, scan, estimate + top-K, fallback (empty),
 // top-K (empty).
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
-                            const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+                            const Launch &lj, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
@@ -290,6 +312,8 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(1)) != cudaSuccess) return e;
     const uint32_t cl = fft_select_cluster_ok(z.L_uniform, z.max_B) ? z.L_uniform : 0u;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, cl, s)) != cudaSuccess) return e;
+    // comb plans: the kept residue classes (lj: one CTA per job)
+    if (z.comb && (e = launch_comb(lj, z.jobs, z.max_Bc, s)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
     if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.bits, z.max_flags, nullptr, nullptr, s)) !=
         cudaSuccess)
@@ -406,16 +430,40 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
         set_error("only precision 0 (FP32 FFT) is implemented");
         return SFFT_ENOTIMPL;
     }
-    if (o.method != SFFT_METHOD_VOTING && o.method != SFFT_METHOD_PHASE) {
-        set_error("sfft_opts.method must be SFFT_METHOD_VOTING or SFFT_METHOD_PHASE");
+    if (o.method != SFFT_METHOD_VOTING && o.method != SFFT_METHOD_PHASE && o.method != SFFT_METHOD_COMB) {
+        set_error("sfft_opts.method must be SFFT_METHOD_VOTING, SFFT_METHOD_PHASE or SFFT_METHOD_COMB");
         return SFFT_EINVAL;
     }
     const bool phase = o.method == SFFT_METHOD_PHASE;
+    const bool comb = o.method == SFFT_METHOD_COMB;
+    if (!comb && o.comb != 0) {
+        set_error("sfft_opts.comb applies to SFFT_METHOD_COMB only");
+        return SFFT_EINVAL;
+    }
     // (phase encoding reads no c or T)
     const int32_t c = phase ? 1 : (o.c > 0 ? o.c : 2);
     const int32_t T = phase ? 1 : (o.T > 0 ? o.T : (L + 1) / 2);
     sfft_status st = check_sizes(N, K, B, w, L, c, T);
     if (st != SFFT_OK) return st;
+    uint32_t Bc = 0;
+    if (comb) {
+        // residue classes: a power of two dividing N/G (G = B/32 frequencies per
+        // register-table scan thread must share one class), at most kMaxComb
+        int64_t lim = std::min<int64_t>(N, kMaxComb);
+        if (B >= 32 && B <= 512) lim = std::min<int64_t>(lim, 32 * N / B);
+        int64_t bc = o.comb;
+        if (bc == 0) {
+            bc = 1;
+            while (bc < 16ll * c * K) bc <<= 1;
+            bc = std::min(bc, lim);
+        }
+        if (bc < 2 || (bc & (bc - 1)) || bc > lim || L + (int32_t)kCombShifts > kMaxL) {
+            set_error("SFFT_METHOD_COMB needs comb a power of two in [2, min(N, 8192, 32N/B for 32 <= B <= 512)] "
+                      "and L <= 30");
+            return SFFT_EINVAL;
+        }
+        Bc = (uint32_t)bc;
+    }
 
     sfft_plan *p = new (std::nothrow) sfft_plan();
     if (!p) {
@@ -435,8 +483,9 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     p->seed = seed;
 
     PlanDev &P = p->h;
-    fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap, (uint32_t)o.method);
-    loop_params_host(N, L, seed, P.sigma, P.tau, p->sigma_inv);
+    fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc);
+    // (comb plans: loops L and L+1 give the comb shifts)
+    loop_params_host(N, L + (comb ? (int32_t)kCombShifts : 0), seed, P.sigma, P.tau, p->sigma_inv);
     const Layout lay = layout_of(P, p->cap);
     p->device_bytes = lay.total;
     const size_t off = lay.total;
@@ -451,6 +500,9 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     P.tw = reinterpret_cast<float2 *>(base + lay.tw);
     P.ginv = reinterpret_cast<float2 *>(base + lay.ginv);
     P.gext = phase ? reinterpret_cast<float2 *>(base + lay.gext) : nullptr;
+    P.ctw = comb ? reinterpret_cast<float2 *>(base + lay.ctw) : nullptr;
+    P.cls = comb ? reinterpret_cast<uint32_t *>(base + lay.cls) : nullptr;
+    P.keptc = comb ? reinterpret_cast<uint32_t *>(base + lay.keptc) : nullptr;
     P.partial = reinterpret_cast<float2 *>(base + lay.part);
     P.zhat = reinterpret_cast<float2 *>(base + lay.zhat);
     P.energy = reinterpret_cast<float *>(base + lay.en);
@@ -486,6 +538,8 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     if ((e = plan_tables(P.N, P.B, P.w, const_cast<float *>(P.taps), const_cast<float2 *>(P.tw),
                          const_cast<float2 *>(P.ginv), ginv2, const_cast<float2 *>(P.gext), s)) != cudaSuccess)
         return fail(e, "plan tables");
+    if (comb && (e = plan_twiddles(P.Bc, const_cast<float2 *>(P.ctw), s)) != cudaSuccess)
+        return fail(e, "comb twiddles");
     unsigned long long *d_count = reinterpret_cast<unsigned long long *>(static_cast<char *>(tmp) + bitmap_bytes);
     unsigned long long *d_max = d_count + 1;
     if ((e = plan_max_bits(ginv2, (uint32_t)nb, d_max, s)) != cudaSuccess) return fail(e, "gain max");
@@ -598,7 +652,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
     if (p->h.method == kMethodPhase)
         SFFT_CUDA_TRY(launch_phase(ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     else
-        SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+        SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
 }
 
@@ -672,6 +726,8 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         z.phase = i == 0 ? s.phase : z.phase;  // one method per batch (callers split mixed lists)
         z.max_L = std::max(z.max_L, s.max_L);
         z.max_cap = std::max(z.max_cap, s.max_cap);
+        z.comb = i == 0 ? s.comb : z.comb;
+        z.max_Bc = std::max(z.max_Bc, s.max_Bc);
     }
     // pruned estimate with staged tables: one wave of resident CTAs over the
     // batch (each CTA stages its job's tables once)
@@ -737,7 +793,7 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         memset(&ln[k].one, 0, sizeof(Job));
     }
     if (b.z.phase) return launch_phase(ln[1], b.z, s, ev);
-    return launch_pipeline(ln[0], ln[1], ln[2], ln[5], b.z, s, ev);
+    return launch_pipeline(ln[0], ln[1], ln[2], ln[5], ln[3], b.z, s, ev);
 }
 
 sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,

@@ -911,7 +911,12 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
     const uint32_t top = 32 - P.logB;
     const uint32_t M = P.M, T = P.T, N = P.N;
 
-    uint32_t per = (N + P.vtiles - 1) / P.vtiles;
+    // comb plans (pruned pass) scan only the kept classes: index v -> class
+    // cls[v >> lm], f = class + (v & (2^lm - 1)) Bc with 2^lm = N / Bc
+    const bool comb = P.method == kMethodComb && mode == kVotePrune;
+    const uint32_t lm = comb ? P.logN - P.logBc : 0u;
+    const uint32_t vspan = comb ? P.ncls << lm : N;
+    uint32_t per = (vspan + P.vtiles - 1) / P.vtiles;
     per = (per + kThreads - 1) / kThreads * kThreads;  // <= kVoteTileF
     const uint32_t stride = mode == kVotePrune ? J.vctas : P.vtiles;
 
@@ -927,10 +932,11 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
 
     for (uint32_t tile = s_local; tile < P.vtiles; tile += stride) {
         const uint32_t f0 = tile * per;
-        const uint32_t f1 = min(N, f0 + per);
+        const uint32_t f1 = min(vspan, f0 + per);
         for (uint32_t base = f0; base < f1; base += kThreads) {
-            const uint32_t f = base + threadIdx.x;
-            const bool valid = f < f1;
+            const uint32_t v = base + threadIdx.x;
+            const bool valid = v < f1;
+            const uint32_t f = comb ? (valid ? __ldg(P.cls + (v >> lm)) + ((v & ((1u << lm) - 1)) << P.logBc) : 0u) : v;
             {
                 uint32_t acc = 0;  // score | strong << 8
                 if constexpr (LT > 0) {
@@ -1011,7 +1017,13 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     const uint32_t gsh = 5 - lgG;
     const uint32_t span = P.N >> lgG;
     const uint32_t members = member_mask(lgG);
-    uint32_t per = (span + P.vtiles - 1) / P.vtiles;
+    // comb plans scan only the kept classes: index v -> class cls[v >> lm],
+    // f = class + (v & (2^lm - 1)) Bc with 2^lm = span / Bc (members f + k span
+    // stay in the class: Bc divides span)
+    const bool comb = P.method == kMethodComb;
+    const uint32_t lm = comb ? (P.logN - lgG) - P.logBc : 0u;
+    const uint32_t vspan = comb ? P.ncls << lm : span;
+    uint32_t per = (vspan + P.vtiles - 1) / P.vtiles;
     per = (per + kThreads - 1) / kThreads * kThreads;
     __syncthreads();
 
@@ -1019,9 +1031,11 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     // list (no barrier until the CTA's last tile)
     for (uint32_t tile = s_local; tile < P.vtiles; tile += J.vctas) {
         const uint32_t f0 = tile * per;
-        const uint32_t f1 = min(span, f0 + per);
+        const uint32_t f1 = min(vspan, f0 + per);
         for (uint32_t base = f0; base < f1; base += kThreads) {
-            const uint32_t f = base + threadIdx.x;
+            const uint32_t v = base + threadIdx.x;
+            const bool valid = v < f1;
+            const uint32_t f = comb ? (valid ? __ldg(P.cls + (v >> lm)) + ((v & ((1u << lm) - 1)) << P.logBc) : 0u) : v;
             uint32_t x[LT];
 #pragma unroll
             for (int l = 0; l < LT; ++l) {
@@ -1033,7 +1047,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
             constexpr int NP = bit_length(LT);
             uint32_t pl[NP];
             count_planes<LT, NP>(x, pl);
-            uint32_t m = f < f1 ? count_at_least<(LT + 1) / 2, NP>(pl) & members : 0u;
+            uint32_t m = valid ? count_at_least<(LT + 1) / 2, NP>(pl) & members : 0u;
             if (m) {
                 const uint32_t n = __popc(m);
                 uint32_t q = atomicAdd(&s_qn, n);
@@ -1083,7 +1097,10 @@ __device__ void fallback_pass(const PlanDev &P, uint32_t *s_cnt) {
     for (uint32_t base = 0; base < P.N; base += blockDim.x) {
         const uint32_t f = base + threadIdx.x;
         bool c = false;
-        if (f < P.N) {
+        // comb plans: only frequencies of kept residue classes
+        const bool eligible = P.method != kMethodComb ||
+                              ((__ldg(P.keptc + ((f & (P.Bc - 1)) >> 5)) >> (f & (P.Bc - 1) & 31u)) & 1u);
+        if (f < P.N && eligible) {
             uint32_t score = 0;
             for (uint32_t l = 0; l < P.L; ++l)
                 score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << sN) * f + cv) >> top)) & 1u;
@@ -1348,6 +1365,76 @@ __global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t c
     if (last_of_job(P, ctas_per_job)) topk_job(P, J, reinterpret_cast<unsigned long long *>(est_tab), cap);
 }
 
+
+// ------------------------------------------------- spike-train pre-filter
+// One CTA per job (sFFT2.0-style; Eq. 10, 15-16): kCombShifts subsamplings at
+// stride N/Bc (shifts tau of loops L, L+1), each a Bc-point FFT scaled by
+// 1/Bc, so class i holds the sum over f = i (mod Bc) of x^_f e^{+2 pi i tau f/N};
+// the energies summed over the shifts keep the ncls largest classes (ties to
+// the lower class), listed ascending in P.cls and marked in P.keptc.
+__global__ void __launch_bounds__(kThreads) k_comb(Launch ln) {
+    extern __shared__ float2 cb[];  // spectrum [Bc], then energies [Bc]
+    __shared__ PlanDev P;
+    __shared__ Job J;
+    __shared__ uint32_t s_local, s_hist[256], s_wsum[8], s_prefix, s_need;
+    enter(ln, P, J, s_local);
+    const uint32_t Bc = P.Bc, logBc = P.logBc, stride = P.N >> logBc;
+    float2 *buf = cb;
+    float *en = reinterpret_cast<float *>(cb + Bc);
+    const float scale = 1.0f / (float)Bc;
+    for (uint32_t c = 0; c < kCombShifts; ++c) {
+        const uint32_t tau = P.tau[P.L + c];
+        for (uint32_t j = threadIdx.x; j < Bc; j += blockDim.x)
+            buf[__brev(j) >> (32 - logBc)] = __ldg(J.x + ((tau + j * stride) & P.mask));
+        __syncthreads();
+        for (uint32_t hs = 0; hs < logBc; ++hs) {
+            const uint32_t h = 1u << hs;
+            for (uint32_t bf = threadIdx.x; bf < Bc / 2; bf += blockDim.x) {
+                const uint32_t k = bf & (h - 1);
+                const uint32_t i0 = ((bf >> hs) << (hs + 1)) + k, i1 = i0 + h;
+                const float2 w = __ldg(P.ctw + (k << (logBc - 1 - hs)));
+                const float2 a = buf[i0], t = cmul(w, buf[i1]);
+                buf[i0] = make_float2(a.x + t.x, a.y + t.y);
+                buf[i1] = make_float2(a.x - t.x, a.y - t.y);
+            }
+            __syncthreads();
+        }
+        for (uint32_t i = threadIdx.x; i < Bc; i += blockDim.x) {
+            const float2 y = make_float2(buf[i].x * scale, buf[i].y * scale);
+            const float e = y.x * y.x + y.y * y.y;
+            en[i] = c == 0 ? e : en[i] + e;
+        }
+        __syncthreads();
+    }
+    // kept = energy above the ncls-th largest, plus the lowest-index ties
+    const uint32_t *keys = reinterpret_cast<const uint32_t *>(en);  // non-negative floats: monotone bits
+    const uint32_t kth = block_kth_largest<false>(keys, Bc, P.ncls, s_hist, s_wsum, &s_prefix, &s_need);
+    const uint32_t need_eq = s_need;
+    const uint32_t per = (Bc + kThreads - 1) / kThreads;
+    const uint32_t k0 = min(Bc, threadIdx.x * per), k1 = min(Bc, k0 + per);
+    uint32_t eq = 0;
+    for (uint32_t k = k0; k < k1; ++k) eq += keys[k] == kth;
+    uint32_t r = block_incl_scan(eq, s_wsum) - eq;  // equal keys before k0
+    uint32_t keepmask = 0, nk = 0;  // per <= 32 (Bc <= 8192)
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint32_t e = keys[k];
+        bool keep = e > kth;
+        if (e == kth) keep = r++ < need_eq;
+        keepmask |= (uint32_t)keep << (k - k0);
+        nk += keep;
+    }
+    uint32_t pos = block_incl_scan(nk, s_wsum) - nk;  // kept classes before k0
+    for (uint32_t k = k0; k < k1; ++k)
+        if ((keepmask >> (k - k0)) & 1u) P.cls[pos++] = k;
+    __syncthreads();
+    uint32_t *bm = reinterpret_cast<uint32_t *>(buf);
+    for (uint32_t i = threadIdx.x; i < (Bc + 31) / 32; i += blockDim.x) bm[i] = 0;
+    __syncthreads();
+    for (uint32_t k = k0; k < k1; ++k)
+        if ((keepmask >> (k - k0)) & 1u) atomicOr(&bm[k >> 5], 1u << (k & 31));
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < (Bc + 31) / 32; i += blockDim.x) P.keptc[i] = bm[i];
+}
 
 // ------------------------------------------------------ phase encoding
 // sFFT3.0-style variant: iteration r bucketizes the signal under loop
@@ -1704,6 +1791,15 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform
     return cudaGetLastError();
 }
 
+
+cudaError_t launch_comb(const Launch &ln, uint32_t njobs, uint32_t max_Bc, cudaStream_t s) {
+    if (njobs == 0) return cudaSuccess;
+    const int smem = (int)((sizeof(float2) + sizeof(float)) * max_Bc);
+    cudaError_t e = cudaFuncSetAttribute(k_comb, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_comb<<<njobs, kThreads, smem, s>>>(ln);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pe(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t max_K, uint32_t max_cap,
                       cudaStream_t s) {

@@ -161,6 +161,11 @@ cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 
     return e != cudaSuccess ? e : e2;
 }
 
+cudaError_t plan_twiddles(uint32_t n, float2 *tw, cudaStream_t s) {
+    k_twiddle<<<(n / 2 + 255) / 256, 256, 0, s>>>(n, tw);
+    return cudaGetLastError();
+}
+
 cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
                                  const uint32_t *tau, uint32_t *bitmap, unsigned long long *count, int pair,
                                  cudaStream_t s) {

@@ -19,6 +19,9 @@ constexpr int kClusterMaxB = 4096;     // clustered FFT/select up to this B
 constexpr uint32_t kMethodVoting = 0;  // sFFT1.0-style voting (the default)
 constexpr uint32_t kMethodPhase = 1;   // sFFT3.0-style phase encoding, iterative framework
 constexpr uint32_t kPeSmemFound = 2048;  // phase encoding: found lists up to this size live in shared memory
+constexpr uint32_t kMethodComb = 2;     // voting behind the spike-train pre-filter
+constexpr uint32_t kCombShifts = 2;     // comb subsamplings (shifts tau of loops L, L+1)
+constexpr uint32_t kMaxComb = 8192;     // largest number of residue classes
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
@@ -61,12 +64,16 @@ struct PlanDev {
     uint32_t use_bits;                        // 32 <= B <= 512: strong bits in registers (pruned scan)
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
-    uint32_t method;                          // kMethodVoting or kMethodPhase
+    uint32_t method;                          // kMethodVoting, kMethodPhase or kMethodComb
+    uint32_t Bc, logBc, ncls;                 // comb: residue classes, kept classes
     uint32_t sigma[kMaxL], tau[kMaxL];
     const float *taps;     // [w]
     const float2 *tw;      // [B/2] exp(-2 pi i k / B)
     const float2 *ginv;    // [N/B] 1 / G~(o), o + half
     const float2 *gext;    // phase encoding: [3N/B] G~(nu) for nu + 3N/2B in [0, 3N/B)
+    const float2 *ctw;     // comb: [Bc/2] exp(-2 pi i k / Bc)
+    uint32_t *cls;         // comb: [ncls] kept residue classes, ascending
+    uint32_t *keptc;       // comb: [Bc/32] kept-class bitmap
     float2 *partial;       // [nchunk][L][B]
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
@@ -132,6 +139,9 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
 // and L is uniform in {8, 12, 16}; they are then staged there.
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
                             uint32_t max_K, cudaStream_t s);
+// Spike-train pre-filter of comb plans: one CTA per job (max_Bc: the largest
+// number of residue classes).
+cudaError_t launch_comb(const Launch &ln, uint32_t njobs, uint32_t max_Bc, cudaStream_t s);
 // Phase-encoding variant: one CTA per job runs all its iterations and writes
 // its top K.
 // max_cap: the largest found-list capacity of the jobs (lists of at most
@@ -147,6 +157,8 @@ cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *s
 cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
                         double *ginv2, float2 *gext, cudaStream_t s);
 cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, cudaStream_t s);
+// exp(-2 pi i k / n), k < n/2 (FP64 -> FP32)
+cudaError_t plan_twiddles(uint32_t n, float2 *tw, cudaStream_t s);
 // pair: count the samples one past each too (phase encoding's second shift)
 cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
                                  const uint32_t *tau, uint32_t *bitmap, unsigned long long *count, int pair,
