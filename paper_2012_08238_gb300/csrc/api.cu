@@ -298,22 +298,61 @@ cudaError_t launch_phase(const Launch &lj, const Sizes &z, cudaStream_t s, cudaE
     return cudaSuccess;
 }
 
+// Per-thread side stream of the comb pre-filter (for the thread's current
+// device) with its fork and join events.  The stream has the highest priority
+// so the comb CTAs are placed while the gather's many short CTAs run.
+struct SideRes {
+    int device = -1;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+cudaError_t side_res(SideRes *&out) {
+    thread_local SideRes r;
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (r.device != device) {
+        // resources of another device are left to process teardown
+        r = SideRes();
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&r.s, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        r.device = device;
+    }
+    out = &r;
+    return cudaSuccess;
+}
+
 // gather -> FFT/select -> scan -> estimate (whose last CTA per job takes the
 // top K, running the job's fallback pass first when needed), all
 // stream-ordered.  With ev (kStages + 1 events) the events bracket the
-// stages: gather, FFT/select, scan, estimate + top-K, fallback (empty),
-// top-K (empty).
+// stages: gather, FFT/select (and the wait for the comb kernel of comb
+// plans), scan, estimate + top-K, fallback (empty), top-K (empty).
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
                             const Launch &lj, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
+    // comb plans: the kept residue classes (lj: one CTA per job).  The comb
+    // kernel reads only the signal, so it runs on the side stream beside the
+    // gather and FFT/select and is joined before the scan.
+    SideRes *sr = nullptr;
+    if (z.comb) {
+        if ((e = side_res(sr)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(sr->fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sr->s, sr->fork, 0)) != cudaSuccess) return e;
+        if ((e = launch_comb(lj, z.jobs, z.max_Bc, sr->s)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(sr->join, sr->s)) != cudaSuccess) return e;
+    }
     if ((e = launch_gather(lg, z.gather, s)) != cudaSuccess) return e;
     if ((e = mark(1)) != cudaSuccess) return e;
     const uint32_t cl = fft_select_cluster_ok(z.L_uniform, z.max_B) ? z.L_uniform : 0u;
     if ((e = launch_fft_select(ls, z.select, z.max_B, 0, cl, s)) != cudaSuccess) return e;
-    // comb plans: the kept residue classes (lj: one CTA per job)
-    if (z.comb && (e = launch_comb(lj, z.jobs, z.max_Bc, s)) != cudaSuccess) return e;
+    if (z.comb && (e = cudaStreamWaitEvent(s, sr->join, 0)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
     if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.bits, z.max_flags, nullptr, nullptr, s)) !=
         cudaSuccess)

@@ -20,7 +20,8 @@ namespace sfft {
 
 namespace {
 
-constexpr int kThreads = 256;  // every kernel
+constexpr int kThreads = 256;  // every kernel but the comb
+constexpr int kCombThreads = 1024;
 constexpr uint32_t kTwSmemMaxB = 8192;  // FFT twiddles staged in shared memory up to this B
 
 __device__ __forceinline__ void locate(const Launch &ln, uint32_t bid, Job &job, uint32_t &local) {
@@ -76,8 +77,10 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // every candidate.
 __device__ __forceinline__ bool needs_fallback(const PlanDev &P) { return __ldcg(P.ctr + kNGe) < P.K; }
 
-// Inclusive sum over a 256-thread block (warp shuffles + 8 warp totals).
-__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *wsum) {
+// Inclusive sum over a block of NW warps (warp shuffles + NW warp totals).
+template <int NW>
+__device__ __forceinline__ uint32_t block_incl_scan_n(uint32_t v, uint32_t *wsum) {
+    static_assert(NW >= 1 && NW <= 32, "one warp scans the warp totals");
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -88,13 +91,13 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *wsum) 
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        uint32_t s = lane < 8 ? wsum[lane] : 0u;
+        uint32_t s = lane < (uint32_t)NW ? wsum[lane] : 0u;
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
+        for (int o = 1; o < NW; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
             if (lane >= (uint32_t)o) s += y;
         }
-        if (lane < 8) wsum[lane] = s;
+        if (lane < (uint32_t)NW) wsum[lane] = s;
     }
     __syncthreads();
     const uint32_t r = x + (wid ? wsum[wid - 1] : 0u);
@@ -102,13 +105,20 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *wsum) 
     return r;
 }
 
+// Inclusive sum over a 256-thread block.
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *wsum) {
+    return block_incl_scan_n<kThreads / 32>(v, wsum);
+}
+
 // k-th largest (1 <= k <= n) of n 32-bit keys by four 8-bit radix passes over
 // a 256-bin histogram whose suffix sums come from one block scan per pass.
 // Returns the key; *s_need is how many keys equal to it rank within the top k.
-// Called by all 256 threads.
-template <bool kGlobal>
+// Called by all NT threads of the block (NT a multiple of 256, at most 1024;
+// wsum holds NT / 32 words).
+template <int NT, bool kGlobal>
 __device__ uint32_t block_kth_largest(const uint32_t *v, uint32_t n, uint32_t k, uint32_t *hist, uint32_t *wsum,
                                       uint32_t *s_prefix, uint32_t *s_need) {
+    static_assert(NT % 256 == 0 && NT <= 1024, "256 bins, one per thread of the first 256");
     if (threadIdx.x == 0) {
         *s_prefix = 0;
         *s_need = k;
@@ -118,15 +128,22 @@ __device__ uint32_t block_kth_largest(const uint32_t *v, uint32_t n, uint32_t k,
         const int sh = 24 - 8 * pass;
         const uint32_t pmask = pass == 0 ? 0u : (0xFFFFFFFFu << (sh + 8));
         const uint32_t prefix = *s_prefix, need = *s_need;
-        hist[threadIdx.x] = 0;
+        if (threadIdx.x < 256) hist[threadIdx.x] = 0;
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
-            const uint32_t u = kGlobal ? __ldcg(v + i) : v[i];
-            if ((u & pmask) == prefix) atomicAdd(&hist[(u >> sh) & 255u], 1u);
+        // one atomic per distinct bin and warp (equal exponents are common)
+        for (uint32_t i0 = threadIdx.x & ~31u; i0 < n; i0 += NT) {
+            const uint32_t i = i0 + (threadIdx.x & 31u);
+            uint32_t bin = 256u;  // none
+            if (i < n) {
+                const uint32_t u = kGlobal ? __ldcg(v + i) : v[i];
+                if ((u & pmask) == prefix) bin = (u >> sh) & 255u;
+            }
+            const uint32_t m = __match_any_sync(0xFFFFFFFFu, bin);
+            if (bin < 256u && (threadIdx.x & 31u) == (uint32_t)(__ffs(m) - 1)) atomicAdd(&hist[bin], __popc(m));
         }
         __syncthreads();
-        const uint32_t c = hist[255 - threadIdx.x];  // thread t scans bins from the top
-        const uint32_t incl = block_incl_scan(c, wsum);
+        const uint32_t c = threadIdx.x < 256 ? hist[255 - threadIdx.x] : 0u;  // thread t scans bins from the top
+        const uint32_t incl = block_incl_scan_n<NT / 32>(c, wsum);
         const uint32_t excl = incl - c;
         if (c > 0 && excl < need && need <= incl) {
             *s_prefix = prefix | ((255u - threadIdx.x) << sh);
@@ -1367,73 +1384,164 @@ __global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t c
 
 
 // ------------------------------------------------- spike-train pre-filter
-// One CTA per job (sFFT2.0-style; Eq. 10, 15-16): kCombShifts subsamplings at
-// stride N/Bc (shifts tau of loops L, L+1), each a Bc-point FFT scaled by
-// 1/Bc, so class i holds the sum over f = i (mod Bc) of x^_f e^{+2 pi i tau f/N};
-// the energies summed over the shifts keep the ncls largest classes (ties to
-// the lower class), listed ascending in P.cls and marked in P.keptc.
-__global__ void __launch_bounds__(kThreads) k_comb(Launch ln) {
-    extern __shared__ float2 cb[];  // spectrum [Bc], then energies [Bc]
+// Radix-4 pass over a bit-reversed buffer: the DIT stages hs and hs + 1 of the
+// group at i0 (distance h = 2^hs).  Same twiddles as two radix-2 stages; the
+// second stage's odd pair takes W_{4h}^{k+h} = -i W_{4h}^k.
+__device__ __forceinline__ void r4_pass(float2 *b, uint32_t i0, uint32_t h, float2 w1, float2 w2) {
+    const float2 x0 = b[i0], x1 = b[i0 + h], x2 = b[i0 + 2 * h], x3 = b[i0 + 3 * h];
+    const float2 t1 = cmul(w1, x1), t3 = cmul(w1, x3);
+    const float2 a0 = make_float2(x0.x + t1.x, x0.y + t1.y), a1 = make_float2(x0.x - t1.x, x0.y - t1.y);
+    const float2 a2 = make_float2(x2.x + t3.x, x2.y + t3.y), a3 = make_float2(x2.x - t3.x, x2.y - t3.y);
+    const float2 u2 = cmul(w2, a2), v3 = cmul(w2, a3), u3 = make_float2(v3.y, -v3.x);
+    b[i0] = make_float2(a0.x + u2.x, a0.y + u2.y);
+    b[i0 + 2 * h] = make_float2(a0.x - u2.x, a0.y - u2.y);
+    b[i0 + h] = make_float2(a1.x + u3.x, a1.y + u3.y);
+    b[i0 + 3 * h] = make_float2(a1.x - u3.x, a1.y - u3.y);
+}
+
+// Per-pass twiddles of fft2_smem_r4, contiguous in k so that a warp's
+// lookups hit distinct banks: the radix-4 pass at hs (distance h = 2^hs)
+// takes W_{2h}^k from tws[o + k] and W_{4h}^k from tws[o + h + k], k < h,
+// where o sums 2h over the earlier passes (at most 2B/3 entries in all).
+// tw: exp(-2 pi i k / B), k < B/2.  All threads; ends with a barrier.
+__device__ void r4_twiddles(float2 *tws, uint32_t logB, const float2 *tw) {
+    uint32_t o = 0;
+    for (uint32_t hs = logB & 1; hs + 1 < logB; hs += 2) {
+        const uint32_t h = 1u << hs;
+        for (uint32_t k = threadIdx.x; k < h; k += blockDim.x) {
+            tws[o + k] = __ldg(tw + (k << (logB - 1 - hs)));
+            tws[o + h + k] = __ldg(tw + (k << (logB - 2 - hs)));
+        }
+        o += 2 * h;
+    }
+    __syncthreads();
+}
+
+// Two B-point FFTs of bit-reversed buffers in shared memory (per-pass
+// twiddles from r4_twiddles), two stages per barrier.  All threads; ends with
+// a barrier.
+__device__ void fft2_smem_r4(float2 *b0, float2 *b1, uint32_t B, uint32_t logB, const float2 *tws) {
+    uint32_t hs = 0;
+    if (logB & 1) {  // odd log2 B: one radix-2 stage (h = 1, twiddle 1) first
+        for (uint32_t q = threadIdx.x; q < B / 2; q += blockDim.x) {
+            float2 *b = b0;
+#pragma unroll
+            for (int t = 0; t < 2; ++t, b = b1) {
+                const float2 a = b[2 * q], c = b[2 * q + 1];
+                b[2 * q] = make_float2(a.x + c.x, a.y + c.y);
+                b[2 * q + 1] = make_float2(a.x - c.x, a.y - c.y);
+            }
+        }
+        __syncthreads();
+        hs = 1;
+    }
+    for (uint32_t o = 0; hs + 1 < logB; hs += 2) {
+        const uint32_t h = 1u << hs;
+        for (uint32_t q = threadIdx.x; q < B / 4; q += blockDim.x) {
+            const uint32_t k = q & (h - 1);
+            const uint32_t i0 = ((q >> hs) << (hs + 2)) + k;
+            const float2 w1 = tws[o + k], w2 = tws[o + h + k];
+            r4_pass(b0, i0, h, w1, w2);
+            r4_pass(b1, i0, h, w1, w2);
+        }
+        o += 2 * h;
+        __syncthreads();
+    }
+}
+
+// One CTA per job (sFFT2.0-style; Eq. 10, 15-16): kCombShifts = 2
+// subsamplings at stride N/Bc (shifts tau of loops L, L+1), each a Bc-point
+// FFT scaled by 1/Bc, so class i holds the sum over f = i (mod Bc) of
+// x^_f e^{+2 pi i tau f/N}; the energies summed over the shifts keep the ncls
+// largest classes (ties to the lower class), listed ascending in P.cls and
+// marked in P.keptc.  Shared memory: both spectra, then Bc entries for the
+// per-pass twiddles (whose room takes the energies once the FFTs are done).
+// kCombThreads threads: the job's whole work is one CTA, latency-bound, so
+// it runs with many warps.
+__global__ void __launch_bounds__(kCombThreads) k_comb(Launch ln) {
+    constexpr uint32_t NT = kCombThreads, NW = NT / 32;
+    extern __shared__ float2 cb[];
     __shared__ PlanDev P;
     __shared__ Job J;
-    __shared__ uint32_t s_local, s_hist[256], s_wsum[8], s_prefix, s_need;
+    __shared__ uint32_t s_local, s_hist[256], s_wsum[NW], s_prefix, s_need;
     enter(ln, P, J, s_local);
-    const uint32_t Bc = P.Bc, logBc = P.logBc, stride = P.N >> logBc;
-    float2 *buf = cb;
-    float *en = reinterpret_cast<float *>(cb + Bc);
-    const float scale = 1.0f / (float)Bc;
-    for (uint32_t c = 0; c < kCombShifts; ++c) {
-        const uint32_t tau = P.tau[P.L + c];
-        for (uint32_t j = threadIdx.x; j < Bc; j += blockDim.x)
-            buf[__brev(j) >> (32 - logBc)] = __ldg(J.x + ((tau + j * stride) & P.mask));
-        __syncthreads();
-        for (uint32_t hs = 0; hs < logBc; ++hs) {
-            const uint32_t h = 1u << hs;
-            for (uint32_t bf = threadIdx.x; bf < Bc / 2; bf += blockDim.x) {
-                const uint32_t k = bf & (h - 1);
-                const uint32_t i0 = ((bf >> hs) << (hs + 1)) + k, i1 = i0 + h;
-                const float2 w = __ldg(P.ctw + (k << (logBc - 1 - hs)));
-                const float2 a = buf[i0], t = cmul(w, buf[i1]);
-                buf[i0] = make_float2(a.x + t.x, a.y + t.y);
-                buf[i1] = make_float2(a.x - t.x, a.y - t.y);
+    const uint32_t Bc = P.Bc, logBc = P.logBc, stride = P.N >> logBc, mask = P.mask;
+    const uint32_t tau0 = P.tau[P.L], tau1 = P.tau[P.L + 1];
+    float2 *b0 = cb, *b1 = cb + Bc, *tws = cb + 2 * Bc;
+    // both subsamplings, kU samples of each in flight per thread; consecutive
+    // threads read consecutive samples j (addresses N/Bc apart, spread over
+    // the memory channels) and store them at the bit-reversed positions
+    constexpr int kU = 4;
+    for (uint32_t j0 = threadIdx.x; j0 < Bc; j0 += kU * NT) {
+        float2 v0[kU], v1[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t j = j0 + u * NT;
+            if (j < Bc) {
+                v0[u] = __ldg(J.x + ((tau0 + j * stride) & mask));
+                v1[u] = __ldg(J.x + ((tau1 + j * stride) & mask));
             }
-            __syncthreads();
         }
-        for (uint32_t i = threadIdx.x; i < Bc; i += blockDim.x) {
-            const float2 y = make_float2(buf[i].x * scale, buf[i].y * scale);
-            const float e = y.x * y.x + y.y * y.y;
-            en[i] = c == 0 ? e : en[i] + e;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t j = j0 + u * NT;
+            if (j < Bc) {
+                const uint32_t r = __brev(j) >> (32 - logBc);
+                b0[r] = v0[u];
+                b1[r] = v1[u];
+            }
         }
-        __syncthreads();
     }
+    r4_twiddles(tws, logBc, P.ctw);  // (its barrier also covers the stores above)
+    fft2_smem_r4(b0, b1, Bc, logBc, tws);
+    const float scale = 1.0f / (float)Bc;
+    float *en = reinterpret_cast<float *>(tws);  // Bc floats: the twiddles' room
+    for (uint32_t i = threadIdx.x; i < Bc; i += NT) {
+        const float2 y0 = make_float2(b0[i].x * scale, b0[i].y * scale);
+        const float2 y1 = make_float2(b1[i].x * scale, b1[i].y * scale);
+        en[i] = (y0.x * y0.x + y0.y * y0.y) + (y1.x * y1.x + y1.y * y1.y);
+    }
+    __syncthreads();
     // kept = energy above the ncls-th largest, plus the lowest-index ties
     const uint32_t *keys = reinterpret_cast<const uint32_t *>(en);  // non-negative floats: monotone bits
-    const uint32_t kth = block_kth_largest<false>(keys, Bc, P.ncls, s_hist, s_wsum, &s_prefix, &s_need);
+    const uint32_t kth = block_kth_largest<NT, false>(keys, Bc, P.ncls, s_hist, s_wsum, &s_prefix, &s_need);
     const uint32_t need_eq = s_need;
-    const uint32_t per = (Bc + kThreads - 1) / kThreads;
-    const uint32_t k0 = min(Bc, threadIdx.x * per), k1 = min(Bc, k0 + per);
-    uint32_t eq = 0;
-    for (uint32_t k = k0; k < k1; ++k) eq += keys[k] == kth;
-    uint32_t r = block_incl_scan(eq, s_wsum) - eq;  // equal keys before k0
-    uint32_t keepmask = 0, nk = 0;  // per <= 32 (Bc <= 8192)
-    for (uint32_t k = k0; k < k1; ++k) {
-        const uint32_t e = keys[k];
-        bool keep = e > kth;
-        if (e == kth) keep = r++ < need_eq;
-        keepmask |= (uint32_t)keep << (k - k0);
-        nk += keep;
+    // each warp takes a contiguous range of bitmap words; ballots give the
+    // words, the ties' ranks and the list positions in class order
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t words = (Bc + 31) / 32, wpw = (words + NW - 1) / NW;
+    const uint32_t w0 = min(words, wid * wpw), w1 = min(words, w0 + wpw);
+    uint32_t neq = 0;
+    for (uint32_t wd = w0; wd < w1; ++wd) {
+        const uint32_t k = wd * 32 + lane;
+        neq += __popc(__ballot_sync(0xFFFFFFFFu, k < Bc && keys[k] == kth));
     }
-    uint32_t pos = block_incl_scan(nk, s_wsum) - nk;  // kept classes before k0
-    for (uint32_t k = k0; k < k1; ++k)
-        if ((keepmask >> (k - k0)) & 1u) P.cls[pos++] = k;
-    __syncthreads();
-    uint32_t *bm = reinterpret_cast<uint32_t *>(buf);
-    for (uint32_t i = threadIdx.x; i < (Bc + 31) / 32; i += blockDim.x) bm[i] = 0;
-    __syncthreads();
-    for (uint32_t k = k0; k < k1; ++k)
-        if ((keepmask >> (k - k0)) & 1u) atomicOr(&bm[k >> 5], 1u << (k & 31));
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < (Bc + 31) / 32; i += blockDim.x) P.keptc[i] = bm[i];
+    uint32_t rank = block_incl_scan_n<NW>(lane == 0 ? neq : 0u, s_wsum);  // ties in earlier warps, inclusive
+    rank = __shfl_sync(0xFFFFFFFFu, rank, 0) - neq;
+    uint32_t *bm = reinterpret_cast<uint32_t *>(b0);  // the kept-class bitmap
+    uint32_t nk = 0;
+    for (uint32_t wd = w0; wd < w1; ++wd) {
+        const uint32_t k = wd * 32 + lane;
+        const uint32_t e = k < Bc ? keys[k] : 0u;
+        const bool tie = k < Bc && e == kth;
+        const uint32_t tm = __ballot_sync(0xFFFFFFFFu, tie);
+        const bool keep = (k < Bc && e > kth) || (tie && rank + __popc(tm & lt) < need_eq);
+        const uint32_t km = __ballot_sync(0xFFFFFFFFu, keep);
+        if (lane == 0) {
+            bm[wd] = km;
+            P.keptc[wd] = km;
+        }
+        rank += __popc(tm);
+        nk += __popc(km);
+    }
+    uint32_t pos = block_incl_scan_n<NW>(lane == 0 ? nk : 0u, s_wsum);  // kept classes before this warp
+    pos = __shfl_sync(0xFFFFFFFFu, pos, 0) - nk;
+    for (uint32_t wd = w0; wd < w1; ++wd) {
+        const uint32_t km = bm[wd];  // written by this warp's lane 0 (block_incl_scan's barriers order it)
+        if ((km >> lane) & 1u) P.cls[pos + __popc(km & lt)] = wd * 32 + lane;
+        pos += __popc(km);
+    }
 }
 
 // ------------------------------------------------------ phase encoding
@@ -1794,10 +1902,10 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform
 
 cudaError_t launch_comb(const Launch &ln, uint32_t njobs, uint32_t max_Bc, cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
-    const int smem = (int)((sizeof(float2) + sizeof(float)) * max_Bc);
+    const int smem = (int)(sizeof(float2) * 3 * max_Bc);  // two spectra, per-pass twiddles
     cudaError_t e = cudaFuncSetAttribute(k_comb, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_comb<<<njobs, kThreads, smem, s>>>(ln);
+    k_comb<<<njobs, kCombThreads, smem, s>>>(ln);
     return cudaGetLastError();
 }
 
