@@ -69,12 +69,18 @@ def _bind(lib):
         "oracle_select": (_i64, [_i64, _i64, _p, _p]),
         "oracle_vote": (_i64, [_i64, _i64, _int, _i64, _int, _p, _p, _p, _p]),
         "oracle_estimate": (None, [_i64, _i64, _int, _p, _p, _p, _p, _i64, _p, _p, _p]),
+        "oracle_estimate_ex": (None, [_i64, _i64, _int, _p, _p, _p, _p, _i64, _p, _int, _p, _p]),
         "oracle_topk": (_i64, [_i64, _p, _p, _i64, _p, _p]),
         "oracle_samples_touched": (_i64, [_i64, _i64, _int, _p, _p]),
         "oracle_dft": (None, [_i64, _p, _p]),
         "oracle_sfft": (
             _i64,
             [_i64, _i64, _i64, _i64, _int, _int, _int, _u64, _p, _p, _p, _p, _p, _p, _p,
+             _p, _p, _p],
+        ),
+        "oracle_sfft_ex": (
+            _i64,
+            [_i64, _i64, _i64, _i64, _int, _int, _int, _u64, _p, _p, _p, _int, _p, _p, _p, _p,
              _p, _p, _p],
         ),
         "oracle_filter_gain_full": (None, [_i64, _i64, _p, _p]),
@@ -84,6 +90,10 @@ def _bind(lib):
         "oracle_sfft2": (
             _i64,
             [_i64, _i64, _i64, _i64, _int, _int, _int, _i64, _int, _u64, _p, _p, _p, _p, _p, _p, _p],
+        ),
+        "oracle_sfft2_ex": (
+            _i64,
+            [_i64, _i64, _i64, _i64, _int, _int, _int, _i64, _int, _u64, _p, _p, _p, _int, _p, _p, _p, _p],
         ),
         "oracle_sfft_pe": (
             _i64,
@@ -227,8 +237,12 @@ def vote(N, B, T, sigma_inv, sel):
 
 
 # ------------------------------------------------------------------- a6
-def estimate(N, B, sigma, tau, Gt, zhat, cand):
-    """(median estimates [ncand], per-loop estimates [ncand][L])."""
+MEDIAN, MEAN = 0, 1  # combinations of the per-loop estimates (a6)
+
+
+def estimate(N, B, sigma, tau, Gt, zhat, cand, combine=MEDIAN):
+    """(combined estimates [ncand], per-loop estimates [ncand][L]); combine is
+    MEDIAN (coordinate-wise) or MEAN."""
     sigma = np.ascontiguousarray(sigma, np.int64)
     tau = np.ascontiguousarray(tau, np.int64)
     L = len(sigma)
@@ -237,8 +251,8 @@ def estimate(N, B, sigma, tau, Gt, zhat, cand):
     cand = np.ascontiguousarray(cand, np.int32)
     est = np.zeros(len(cand), np.complex128)
     per = np.zeros((len(cand), L), np.complex128)
-    _load().oracle_estimate(N, B, L, _ptr(sigma), _ptr(tau), _ptr(Gt), _ptr(zhat), len(cand), _ptr(cand),
-                            _ptr(est), _ptr(per))
+    _load().oracle_estimate_ex(N, B, L, _ptr(sigma), _ptr(tau), _ptr(Gt), _ptr(zhat), len(cand), _ptr(cand),
+                               combine, _ptr(est), _ptr(per))
     return est, per
 
 
@@ -271,9 +285,10 @@ def dft(x) -> np.ndarray:
 class Plan:
     """Window taps and gains for one (N, B, w): the oracle's plan-time work."""
 
-    def __init__(self, N, K, B, w, L, seed, c=2, T=None):
+    def __init__(self, N, K, B, w, L, seed, c=2, T=None, estimator=MEDIAN):
         self.N, self.K, self.B, self.w, self.L, self.seed = N, K, B, w, L, seed
         self.c = c
+        self.estimator = estimator  # MEDIAN or MEAN
         self.T = (L + 1) // 2 if T is None else T
         self.g = window_taps(N, B, w)
         self.Gt = filter_gain(N, B, w, self.g)
@@ -296,9 +311,9 @@ def sfft(plan: Plan, x, intermediates: bool = False):
     cand = np.zeros(N, np.int32) if intermediates else None
     est = np.zeros(N, np.complex128) if intermediates else None
     ncand = np.zeros(1, np.int64)
-    kout = _load().oracle_sfft(N, K, B, plan.w, L, plan.c, plan.T, plan.seed, _ptr(plan.g), _ptr(plan.Gt),
-                               _ptr(x), _ptr(idx), _ptr(val), _ptr(zhat), _ptr(sel), _ptr(cand), _ptr(est),
-                               _ptr(ncand))
+    kout = _load().oracle_sfft_ex(N, K, B, plan.w, L, plan.c, plan.T, plan.seed, _ptr(plan.g), _ptr(plan.Gt),
+                                  _ptr(x), plan.estimator, _ptr(idx), _ptr(val), _ptr(zhat), _ptr(sel), _ptr(cand),
+                                  _ptr(est), _ptr(ncand))
     if kout < 0:
         raise ValueError("invalid sfft parameters")
     out = {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout)}
@@ -379,8 +394,9 @@ def sfft2(plan: Plan, x, Bc: int, C: int = 2):
     val = np.zeros(plan.K, np.complex128)
     kept = np.zeros(Bc, np.uint8)
     ncand = np.zeros(1, np.int64)
-    kout = _load().oracle_sfft2(plan.N, plan.K, plan.B, plan.w, plan.L, plan.c, plan.T, Bc, C, plan.seed,
-                                _ptr(plan.g), _ptr(plan.Gt), _ptr(x), _ptr(idx), _ptr(val), _ptr(kept), _ptr(ncand))
+    kout = _load().oracle_sfft2_ex(plan.N, plan.K, plan.B, plan.w, plan.L, plan.c, plan.T, Bc, C, plan.seed,
+                                   _ptr(plan.g), _ptr(plan.Gt), _ptr(x), plan.estimator, _ptr(idx), _ptr(val),
+                                   _ptr(kept), _ptr(ncand))
     if kout < 0:
         raise ValueError("invalid sfft2 parameters")
     return {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout), "kept": kept.astype(bool),

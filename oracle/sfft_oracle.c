@@ -255,9 +255,12 @@ static double median_of(double *v, int n)
     return 0.5 * (v[n / 2 - 1] + v[n / 2]);
 }
 
-void oracle_estimate(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau,
-                     const double *Gt, const double *zhat, int64_t ncand, const int32_t *cand,
-                     double *est, double *per_loop)
+/* combine = ORACLE_MEDIAN: the coordinate-wise median of the L per-loop
+   estimates; ORACLE_MEAN: their average ("the average value of multiple
+   buckets", § "The method of estimating the value"). */
+void oracle_estimate_ex(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau,
+                        const double *Gt, const double *zhat, int64_t ncand, const int32_t *cand,
+                        int combine, double *est, double *per_loop)
 {
     int64_t half = (N / B) / 2;
     double *re = (double *)malloc(sizeof(double) * (size_t)L);
@@ -279,11 +282,28 @@ void oracle_estimate(int64_t N, int64_t B, int L, const int64_t *sigma, const in
                 per_loop[2 * (c * L + l) + 1] = im[l];
             }
         }
-        est[2 * c] = median_of(re, L);
-        est[2 * c + 1] = median_of(im, L);
+        if (combine == ORACLE_MEAN) {
+            double sr = 0.0, si = 0.0;
+            for (int l = 0; l < L; ++l) {
+                sr += re[l];
+                si += im[l];
+            }
+            est[2 * c] = sr / (double)L;
+            est[2 * c + 1] = si / (double)L;
+        } else {
+            est[2 * c] = median_of(re, L);
+            est[2 * c + 1] = median_of(im, L);
+        }
     }
     free(re);
     free(im);
+}
+
+void oracle_estimate(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau,
+                     const double *Gt, const double *zhat, int64_t ncand, const int32_t *cand,
+                     double *est, double *per_loop)
+{
+    oracle_estimate_ex(N, B, L, sigma, tau, Gt, zhat, ncand, cand, ORACLE_MEDIAN, est, per_loop);
 }
 
 /* --------------------------------------------------------- a7: top-K */
@@ -353,6 +373,15 @@ int64_t oracle_sfft(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, in
                     int32_t *idx, double *val, double *zhat_out, int32_t *sel_out,
                     int32_t *cand_out, double *est_out, int64_t *ncand_out)
 {
+    return oracle_sfft_ex(N, K, B, w, L, c, T, seed, g, Gt, x, ORACLE_MEDIAN, idx, val, zhat_out, sel_out,
+                          cand_out, est_out, ncand_out);
+}
+
+int64_t oracle_sfft_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T,
+                       uint64_t seed, const double *g, const double *Gt, const double *x, int combine,
+                       int32_t *idx, double *val, double *zhat_out, int32_t *sel_out,
+                       int32_t *cand_out, double *est_out, int64_t *ncand_out)
+{
     if (!is_pow2(N) || N < 2 || !is_pow2(B) || B > N || w < B || w > N || w % B || L < 1 ||
         K < 1 || c < 1 || T < 1 || T > L)
         return -1;
@@ -373,7 +402,7 @@ int64_t oracle_sfft(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, in
     int64_t ncand = oracle_vote(N, B, L, nsel, T, sinv, sel, NULL, cand);
 
     double *est = est_out ? est_out : (double *)malloc(sizeof(double) * 2 * (size_t)(ncand ? ncand : 1));
-    oracle_estimate(N, B, L, sigma, tau, Gt, zhat, ncand, cand, est, NULL);
+    oracle_estimate_ex(N, B, L, sigma, tau, Gt, zhat, ncand, cand, combine, est, NULL);
 
     int64_t kout = oracle_topk(ncand, cand, est, K, idx, val);
     if (ncand_out) *ncand_out = ncand;
@@ -605,6 +634,14 @@ int64_t oracle_sfft2(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, i
                      uint64_t seed, const double *g, const double *Gt, const double *x, int32_t *idx, double *val,
                      uint8_t *kept_out, int64_t *ncand_out)
 {
+    return oracle_sfft2_ex(N, K, B, w, L, c, T, Bc, C, seed, g, Gt, x, ORACLE_MEDIAN, idx, val, kept_out,
+                           ncand_out);
+}
+
+int64_t oracle_sfft2_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T, int64_t Bc, int C,
+                        uint64_t seed, const double *g, const double *Gt, const double *x, int combine,
+                        int32_t *idx, double *val, uint8_t *kept_out, int64_t *ncand_out)
+{
     if (!is_pow2(N) || N < 2 || !is_pow2(B) || B > N || w < B || w % B || L < 1 || c < 1 || T < 1 || T > L ||
         !is_pow2(Bc) || Bc > N || C < 1)
         return -1;
@@ -630,7 +667,7 @@ int64_t oracle_sfft2(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, i
     for (int64_t q = 0; q < nc; ++q)
         if (kept[mod_pos(cand[q], Bc)]) cand[ncand++] = cand[q];
     double *est = (double *)malloc(sizeof(double) * 2 * (size_t)(ncand ? ncand : 1));
-    oracle_estimate(N, B, L, sigma, tau, Gt, zhat, ncand, cand, est, NULL);
+    oracle_estimate_ex(N, B, L, sigma, tau, Gt, zhat, ncand, cand, combine, est, NULL);
     int64_t kout = oracle_topk(ncand, cand, est, K, idx, val);
     if (ncand_out) *ncand_out = ncand;
     if (!kept_out) free(kept);

@@ -1,6 +1,7 @@
 /*
- * FP64 CPU oracle for the flat-window voting sparse FFT (sFFT1.0-style) and
- * its phase-encoding, iterative variant (sFFT3.0-style).
+ * FP64 CPU oracle for the flat-window voting sparse FFT (sFFT1.0-style), its
+ * phase-encoding, iterative variant (sFFT3.0-style), the spike-train
+ * pre-filter in front of voting (sFFT2.0-style) and the averaging estimator.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may include, link or
  * call this code: only the tests, the package smoke check and the benchmark's
@@ -18,6 +19,7 @@
  *                  worked example (oracle_hash)
  *   "Method of probability and statistics": top-2K buckets + voting
  *   "Energy concentration method": per-loop estimate, combined by median
+ *                  (or by the mean: oracle_estimate_ex)
  *   "Scaling method": random odd sigma
  *   Table 2        sampling complexity (oracle_samples_touched)
  *
@@ -86,6 +88,17 @@ void oracle_estimate(int64_t N, int64_t B, int L, const int64_t *sigma, const in
                      const double *Gt, const double *zhat, int64_t ncand, const int32_t *cand,
                      double *est, double *per_loop);
 
+/* Combinations of the L per-loop estimates: the coordinate-wise median
+   (sFFT1.0's robust choice), or their mean ("the average value of multiple
+   buckets is more accurate", § "The method of estimating the value"). */
+#define ORACLE_MEDIAN 0
+#define ORACLE_MEAN 1
+
+/* oracle_estimate with the combination chosen by combine. */
+void oracle_estimate_ex(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau,
+                        const double *Gt, const double *zhat, int64_t ncand, const int32_t *cand,
+                        int combine, double *est, double *per_loop);
+
 /* Step a7: the K candidates with largest |est|^2 (key rounded to binary32),
    ties to the lower f, returned sorted by f.  Returns min(K, ncand). */
 int64_t oracle_topk(int64_t ncand, const int32_t *cand, const double *est, int64_t K,
@@ -106,6 +119,13 @@ int64_t oracle_sfft(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, in
                     uint64_t seed, const double *g, const double *Gt, const double *x,
                     int32_t *idx, double *val, double *zhat_out, int32_t *sel_out,
                     int32_t *cand_out, double *est_out, int64_t *ncand_out);
+
+/* oracle_sfft with the a6 combination chosen by combine (ORACLE_MEDIAN or
+   ORACLE_MEAN). */
+int64_t oracle_sfft_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T,
+                       uint64_t seed, const double *g, const double *Gt, const double *x, int combine,
+                       int32_t *idx, double *val, double *zhat_out, int32_t *sel_out,
+                       int32_t *cand_out, double *est_out, int64_t *ncand_out);
 
 /* ---- sFFT3.0-style phase-encoding location, iterative framework ---- */
 
@@ -164,6 +184,11 @@ int64_t oracle_comb(int64_t N, int64_t Bc, int C, const int64_t *tau_c, int64_t 
 int64_t oracle_sfft2(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T, int64_t Bc, int C,
                      uint64_t seed, const double *g, const double *Gt, const double *x, int32_t *idx, double *val,
                      uint8_t *kept_out, int64_t *ncand_out);
+
+/* oracle_sfft2 with the a6 combination chosen by combine. */
+int64_t oracle_sfft2_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T, int64_t Bc, int C,
+                        uint64_t seed, const double *g, const double *Gt, const double *x, int combine,
+                        int32_t *idx, double *val, uint8_t *kept_out, int64_t *ncand_out);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_comb_pins as comb_pins
+import test_oracle_mean_pins as mean_pins
 import test_oracle_pe_pins as pe_pins
 import test_oracle_pins as pins
 
@@ -49,6 +50,11 @@ MUTANTS = [
     ("comb stride", "int64_t n = mod_pos(tau_c[c] + j * stride, N);", "int64_t n = mod_pos(tau_c[c] + j, N);"),
     ("comb filter off", "if (kept[mod_pos(cand[q], Bc)]) cand[ncand++] = cand[q];", "cand[ncand++] = cand[q];"),
     ("comb shifts from the voting loops", "tau + L, (int64_t)c * K", "tau, (int64_t)c * K"),
+    # averaging estimator
+    ("mean without 1/L", "est[2 * c] = sr / (double)L;", "est[2 * c] = sr;"),
+    ("mean replaced by the median", "if (combine == ORACLE_MEAN) {", "if (0) {"),
+    ("mean skips loop 0", "for (int l = 0; l < L; ++l) {\n                sr += re[l];",
+     "for (int l = 1; l < L; ++l) {\n                sr += re[l];"),
 ]
 
 PIN_CHECKS = [
@@ -78,6 +84,9 @@ PIN_CHECKS = [
     comb_pins.test_comb_keeps_largest_classes_with_ties,
     lambda: comb_pins.test_filtered_candidates_are_voting_candidates_in_kept_classes(0),
     lambda: comb_pins.test_exact_recovery_noiseless(1 << 16, 10, 64, 8, 256),
+    lambda: mean_pins.test_mean_exact_on_one_sparse(1 << 12, 16, 5, 1234),
+    mean_pins.test_mean_is_linear_and_median_is_not,
+    mean_pins.test_two_coefficients_closed_form,
 ]
 
 
