@@ -73,6 +73,8 @@ typedef struct {
     int32_t method;    /* SFFT_METHOD_VOTING (0, default), SFFT_METHOD_PHASE or SFFT_METHOD_COMB */
     int32_t comb;      /* SFFT_METHOD_COMB: residue classes Bc (power of two); 0 -> default
                           min(2^ceil(log2(16 c K)), 8192, N, 32 N / B for 32 <= B <= 512) */
+    int32_t estimator; /* SFFT_ESTIMATOR_MEDIAN (0, default) or SFFT_ESTIMATOR_MEAN (voting
+                          and comb methods) */
 } sfft_opts;
 
 /* Location methods.
@@ -95,6 +97,17 @@ typedef struct {
    of kept classes are voted on, estimated and output (L <= 30). */
 #define SFFT_METHOD_COMB 2
 
+/* Combination of a candidate's L per-loop estimates (step a6; "The method of
+   estimating the value").  MEDIAN: the coordinate-wise median, robust to
+   collisions in a minority of loops; candidates whose median cannot reach the
+   top K are pruned exactly before they are estimated.  MEAN: the average of
+   the L estimates (the paper's remark that averaging several buckets is more
+   accurate): lower variance under noise, but a collision in one loop biases
+   it by 1/L of the colliding coefficient, and no bound on a mean prunes the
+   candidates, so every candidate is estimated (slower). */
+#define SFFT_ESTIMATOR_MEDIAN 0
+#define SFFT_ESTIMATOR_MEAN 1
+
 /* Read-only description of a plan (host struct filled by sfft_plan_get_info). */
 typedef struct {
     int64_t N, w;
@@ -104,6 +117,7 @@ typedef struct {
     int64_t candidate_capacity;  /* min(N, (L-T+1)*nsel*N/B): bound on the candidate set */
     size_t device_bytes;         /* device memory held by the plan */
     int32_t method;              /* SFFT_METHOD_* */
+    int32_t estimator;           /* SFFT_ESTIMATOR_* */
 } sfft_plan_info;
 
 /* ------------------------------------------------------------------ plans */

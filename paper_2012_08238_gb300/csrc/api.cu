@@ -140,7 +140,8 @@ void decompose(PlanDev &P) {
     // comb: only the kept classes' N/Bc frequencies each are scanned
     if (P.method == kMethodComb)
         P.vtiles = (uint32_t)(((uint64_t)P.ncls * (P.N / P.Bc) + kVoteTileF - 1) / kVoteTileF);
-    P.use_bits = (P.B >= 32 && P.B <= 512) ? 1u : 0u;
+    // (mean: the register table counts kept bits against M, so T must be M)
+    P.use_bits = (P.B >= 32 && P.B <= 512 && (P.estimator == kEstMedian || P.T == P.M)) ? 1u : 0u;
 }
 
 struct Layout {
@@ -184,7 +185,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
 
 // Sizes and work split of a plan, without touching the device.
 void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
-                   int64_t *cap, uint32_t method, uint32_t Bc) {
+                   int64_t *cap, uint32_t method, uint32_t Bc, uint32_t estimator = kEstMedian) {
     memset(&P, 0, sizeof(P));
     const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     P.N = (uint32_t)N;
@@ -203,6 +204,7 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.T = (uint32_t)T;
     P.M = (uint32_t)((L + 1) / 2);
     P.method = method;
+    P.estimator = estimator;
     if (method == kMethodComb) {
         P.Bc = Bc;
         P.logBc = ilog2(Bc);
@@ -479,6 +481,14 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
         set_error("sfft_opts.comb applies to SFFT_METHOD_COMB only");
         return SFFT_EINVAL;
     }
+    if (o.estimator != SFFT_ESTIMATOR_MEDIAN && o.estimator != SFFT_ESTIMATOR_MEAN) {
+        set_error("sfft_opts.estimator must be SFFT_ESTIMATOR_MEDIAN or SFFT_ESTIMATOR_MEAN");
+        return SFFT_EINVAL;
+    }
+    if (phase && o.estimator != SFFT_ESTIMATOR_MEDIAN) {
+        set_error("sfft_opts.estimator applies to the voting and comb methods");
+        return SFFT_EINVAL;
+    }
     // (phase encoding reads no c or T)
     const int32_t c = phase ? 1 : (o.c > 0 ? o.c : 2);
     const int32_t T = phase ? 1 : (o.T > 0 ? o.T : (L + 1) / 2);
@@ -522,7 +532,8 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     p->seed = seed;
 
     PlanDev &P = p->h;
-    fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc);
+    fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc,
+                  o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian);
     // (comb plans: loops L and L+1 give the comb shifts)
     loop_params_host(N, L + (comb ? (int32_t)kCombShifts : 0), seed, P.sigma, P.tau, p->sigma_inv);
     const Layout lay = layout_of(P, p->cap);
@@ -634,6 +645,7 @@ extern "C" sfft_status sfft_plan_get_info(const sfft_plan *p, sfft_plan_info *in
     info->candidate_capacity = p->cap;
     info->device_bytes = p->device_bytes;
     info->method = (int32_t)p->h.method;
+    info->estimator = (int32_t)p->h.estimator;
     return SFFT_OK;
 }
 

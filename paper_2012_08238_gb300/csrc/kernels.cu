@@ -324,19 +324,19 @@ __device__ __forceinline__ float theta_from(float min_kth) {
     return theta;
 }
 
-// Loop l's packed strong bits for the register-table scan: lane word j holds
-// the bit of every bucket h = j (mod 32) at (sigma^-1 (h >> (log2 B - 5))) mod
+// Loop l's packed bits for the register-table scan: lane word j holds the
+// bit of every bucket h = j (mod 32) at (sigma^-1 (h >> (log2 B - 5))) mod
 // 32, so that the scan's one rotate puts the bit of f + kN/G (G = B/32) at
-// position k 32/G.  energy(h) returns bucket h's energy.
-template <class E>
-__device__ __forceinline__ uint32_t packed_word(const PlanDev &P, uint32_t l, uint32_t j, float gmul, float thr,
-                                                E energy) {
+// position k 32/G.  bit(h) is bucket h's bit: strong for the median
+// estimator, kept for the mean.
+template <class Bit>
+__device__ __forceinline__ uint32_t packed_word(const PlanDev &P, uint32_t l, uint32_t j, Bit bit) {
     const uint32_t sh = P.logB - 5, si = inv_mod32(P.sigma[l]);
     uint32_t word = 0;
 #pragma unroll
     for (uint32_t m = 0; m < 16; ++m) {
         const uint32_t h = j + 32 * m;
-        if (h < P.B) word |= (uint32_t)strong_energy(energy(h), gmul, thr) << ((si * (h >> sh)) & 31u);
+        if (h < P.B) word |= (uint32_t)bit(h) << ((si * (h >> sh)) & 31u);
     }
     return word;
 }
@@ -377,9 +377,11 @@ __device__ void cluster_tables(const PlanDev &P, uint32_t l, uint32_t kqv, const
     const uint32_t B = P.B;
     for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
         frow[k] = (uint16_t)(kept_s[k] | (strong_energy(__uint_as_float(en_s[k]), gmul, thr) ? 256u : 0u));
+    const bool mean = P.estimator == kEstMean;
     if (P.use_bits && threadIdx.x < 32)
-        P.packed[l * 32 + threadIdx.x] =
-            packed_word(P, l, threadIdx.x, gmul, thr, [&](uint32_t h) { return __uint_as_float(en_s[h]); });
+        P.packed[l * 32 + threadIdx.x] = packed_word(P, l, threadIdx.x, [&](uint32_t h) {
+            return mean ? kept_s[h] != 0 : strong_energy(__uint_as_float(en_s[h]), gmul, thr);
+        });
 }
 
 // -------------------------------------------------------------- a2 + a3
@@ -579,10 +581,15 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
         }
     }
     if (P.use_bits) {
+        __syncthreads();  // the flags above are complete
+        const bool mean = P.estimator == kEstMean;
         for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
             const uint32_t ll = idx >> 5;
             const float *er = P.energy + (size_t)ll * B;
-            P.packed[idx] = packed_word(P, ll, idx & 31, gmul, thr, [&](uint32_t h) { return __ldcg(er + h); });
+            const unsigned short *fr = reinterpret_cast<const unsigned short *>(P.flags) + (size_t)ll * B;
+            P.packed[idx] = packed_word(P, ll, idx & 31, [&](uint32_t h) {
+                return mean ? (__ldcg(fr + h) & 1u) != 0 : strong_energy(__ldcg(er + h), gmul, thr);
+            });
         }
     }
     if (threadIdx.x == 0) {
@@ -682,6 +689,23 @@ __device__ float2 median_estimate(const PlanDev &P, const float2 *zhat, uint32_t
     }
 }
 
+// The plan's combination of the L per-loop estimates: the coordinate-wise
+// median, or the mean (summed in loop order).
+template <int LT>
+__device__ float2 combined_estimate(const PlanDev &P, const float2 *zhat, uint32_t f) {
+    if (P.estimator == kEstMean) {
+        const uint32_t L = LT > 0 ? (uint32_t)LT : P.L;
+        float sr = 0.f, si = 0.f;
+        for (uint32_t l = 0; l < L; ++l) {
+            const float2 v = loop_estimate(P, zhat, l, f);
+            sr += v.x;
+            si += v.y;
+        }
+        return make_float2(sr / (float)L, si / (float)L);
+    }
+    return median_estimate<LT>(P, zhat, f);
+}
+
 // kept in at least T loops (the candidate test the register-table scan defers)
 template <int LT>
 __device__ __forceinline__ bool is_candidate(const PlanDev &P, uint32_t f) {
@@ -705,7 +729,9 @@ __device__ __forceinline__ bool is_candidate(const PlanDev &P, uint32_t f) {
 // a = sqrt(theta/2) (1 - 2^-10) in magnitude: a median >= a needs at least
 // M = ceil(L/2) values >= a, one <= -a as many <= -a, and with both medians
 // inside (-a, a) the computed key stays below theta.  Kept records are
-// bit-identical to median_estimate's.
+// bit-identical to median_estimate's.  Mean plans: every survivor is a
+// candidate and is estimated by the mean of its L values (summed in loop
+// order, bit-identical to combined_estimate's).
 // 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned).
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -753,6 +779,7 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
         ph[l] = (P.tau[l] << sN) * f;
     }
     bool keep = true;
+    const bool mean = P.estimator == kEstMean;
     float re[LT], im[LT];
     {
         uint32_t rp = 0, rn = 0, ip = 0, in = 0;
@@ -767,10 +794,11 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
             in += v.y <= -a;
         }
         constexpr uint32_t M = (LT + 1) / 2;
-        keep = rp >= M || rn >= M || ip >= M || in >= M;
+        keep = mean || rp >= M || rn >= M || ip >= M || in >= M;
     }
-    if (keep) {
-        // candidacy (kept in >= T loops), only for the few that pass
+    if (keep && !mean) {
+        // candidacy (kept in >= T loops), only for the few that pass (the
+        // mean's survivors are the candidates already)
         uint32_t kept = 0;
 #pragma unroll
         for (int l = 0; l < LT; ++l) {
@@ -785,9 +813,19 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
     float2 v = make_float2(0.f, 0.f);
     float key = 0.f;
     if (keep) {
-        sort_net<LT>(re);
-        sort_net<LT>(im);
-        v = make_float2(median_sorted(re, LT), median_sorted(im, LT));
+        if (mean) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int l = 0; l < LT; ++l) {
+                sr += re[l];
+                si += im[l];
+            }
+            v = make_float2(sr / (float)LT, si / (float)LT);
+        } else {
+            sort_net<LT>(re);
+            sort_net<LT>(im);
+            v = make_float2(median_sorted(re, LT), median_sorted(im, LT));
+        }
         key = v.x * v.x + v.y * v.y;
         keep = key >= theta;
     }
@@ -804,7 +842,7 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
     }
 }
 
-// Median estimate of f, appended to the job's records {f, key bits, re bits,
+// Estimate of f (the plan's combination), appended to the job's records {f, key bits, re bits,
 // im bits} at *cnt when kept: by the pruned pass when f is a candidate whose
 // key reaches theta, by the fallback pass always (f is a listed candidate).
 template <int LT>
@@ -814,7 +852,7 @@ __device__ __forceinline__ void estimate_record(const PlanDev &P, uint32_t f, bo
     float2 v = make_float2(0.f, 0.f);
     float key = 0.f;
     if (keep) {
-        v = median_estimate<LT>(P, P.zhat, f);
+        v = combined_estimate<LT>(P, P.zhat, f);
         key = v.x * v.x + v.y * v.y;
         keep = !prune || key >= theta;
     }
@@ -927,6 +965,7 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
     const uint32_t cv = P.half << (32 - P.logN);
     const uint32_t top = 32 - P.logB;
     const uint32_t M = P.M, T = P.T, N = P.N;
+    const bool mean = P.estimator == kEstMean;
 
     // comb plans (pruned pass) scan only the kept classes: index v -> class
     // cls[v >> lm], f = class + (v & (2^lm - 1)) Bc with 2^lm = N / Bc
@@ -974,7 +1013,7 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
                     }
                     continue;
                 }
-                enqueue(f, cand && (acc >> 8) >= M);
+                enqueue(f, cand && (mean || (acc >> 8) >= M));  // the mean has no strong-loop bound
             }
         }
         if (mode == kVoteCandidates) continue;
@@ -993,7 +1032,8 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
 
 
 // Pruned scan with the register table of strong bits (32 <= B <= 512, L in
-// {8, 12, 16}).
+// {8, 12, 16}).  Mean plans (T = M) pack kept bits instead, so the survivors
+// are exactly the candidates.
 //
 // A thread takes the G = B/32 frequencies f + kN/G.  Their hash words differ
 // by k sigma_l 2^32/G, so their buckets h + k sigma_l 32 share the lane
@@ -1747,7 +1787,7 @@ __global__ void k_estimate_list(const PlanDev *pd, const float2 *zhat, const int
     load_plan(P, pd);
     __syncthreads();
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        est[i] = median_estimate<LT>(P, zhat, (uint32_t)cand[i]);
+        est[i] = combined_estimate<LT>(P, zhat, (uint32_t)cand[i]);
 }
 
 __global__ void k_flags_from_sel(const PlanDev *pd, const int32_t *sel) {

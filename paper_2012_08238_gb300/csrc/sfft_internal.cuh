@@ -22,6 +22,8 @@ constexpr uint32_t kPeSmemFound = 2048;  // phase encoding: found lists up to th
 constexpr uint32_t kMethodComb = 2;     // voting behind the spike-train pre-filter
 constexpr uint32_t kCombShifts = 2;     // comb subsamplings (shifts tau of loops L, L+1)
 constexpr uint32_t kMaxComb = 8192;     // largest number of residue classes
+constexpr uint32_t kEstMedian = 0;      // a6: coordinate-wise median of the per-loop estimates
+constexpr uint32_t kEstMean = 1;        // a6: their mean (every candidate estimated)
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
@@ -61,11 +63,12 @@ struct PlanDev {
     uint32_t nsel, T, M;  // M = ceil(L/2): strong loops needed by the median bound
     uint32_t nchunk, rounds, rpc, tb, tiles;  // gather decomposition
     uint32_t vtiles;                          // vote tiles per job (<= kVoteTileF frequencies each)
-    uint32_t use_bits;                        // 32 <= B <= 512: strong bits in registers (pruned scan)
+    uint32_t use_bits;                        // 32 <= B <= 512 (and T = M for the mean): table bits in registers
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
     uint32_t method;                          // kMethodVoting, kMethodPhase or kMethodComb
     uint32_t Bc, logBc, ncls;                 // comb: residue classes, kept classes
+    uint32_t estimator;                       // kEstMedian or kEstMean
     uint32_t sigma[kMaxL], tau[kMaxL];
     const float *taps;     // [w]
     const float2 *tw;      // [B/2] exp(-2 pi i k / B)
@@ -78,7 +81,7 @@ struct PlanDev {
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
     float *loopkth;        // [L] ceil(K/L)-th largest energy of each loop
-    uint32_t *packed;      // [L][32]: lane j's strong bits (register-table scan)
+    uint32_t *packed;      // [L][32]: lane j's strong bits, kept bits for the mean (register-table scan)
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
     uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
