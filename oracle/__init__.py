@@ -93,8 +93,9 @@ def _bind(lib):
         ),
         "oracle_sfft2_ex": (
             _i64,
-            [_i64, _i64, _i64, _i64, _int, _int, _int, _i64, _int, _u64, _p, _p, _p, _int, _p, _p, _p, _p],
+            [_i64, _i64, _i64, _i64, _int, _int, _int, _i64, _int, _u64, _p, _p, _p, _int, _p, _p, _p, _p, _p],
         ),
+        "oracle_refine": (None, [_i64, _i64, _int, _p, _p, _p, _p, _i64, _p, _int, _int, _p]),
         "oracle_sfft_pe": (
             _i64,
             [_i64, _i64, _i64, _i64, _int, ctypes.c_double, _u64, _p, _p, _p, _p, _p, _p, _p],
@@ -285,10 +286,11 @@ def dft(x) -> np.ndarray:
 class Plan:
     """Window taps and gains for one (N, B, w): the oracle's plan-time work."""
 
-    def __init__(self, N, K, B, w, L, seed, c=2, T=None, estimator=MEDIAN):
+    def __init__(self, N, K, B, w, L, seed, c=2, T=None, estimator=MEDIAN, refine=0):
         self.N, self.K, self.B, self.w, self.L, self.seed = N, K, B, w, L, seed
         self.c = c
         self.estimator = estimator  # MEDIAN or MEAN
+        self.refine = refine        # refinement passes over the found set (0: none)
         self.T = (L + 1) // 2 if T is None else T
         self.g = window_taps(N, B, w)
         self.Gt = filter_gain(N, B, w, self.g)
@@ -317,6 +319,8 @@ def sfft(plan: Plan, x, intermediates: bool = False):
     if kout < 0:
         raise ValueError("invalid sfft parameters")
     out = {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout)}
+    if plan.refine:
+        out["val"] = refine(plan, zhat, out["idx"], out["val"], plan.refine)
     if intermediates:
         n = int(ncand[0])
         out.update(zhat=zhat, sel=sel, cand=cand[:n].copy(), est=est[:n].copy())
@@ -394,10 +398,28 @@ def sfft2(plan: Plan, x, Bc: int, C: int = 2):
     val = np.zeros(plan.K, np.complex128)
     kept = np.zeros(Bc, np.uint8)
     ncand = np.zeros(1, np.int64)
+    zhat = np.zeros((plan.L, plan.B), np.complex128)
     kout = _load().oracle_sfft2_ex(plan.N, plan.K, plan.B, plan.w, plan.L, plan.c, plan.T, Bc, C, plan.seed,
                                    _ptr(plan.g), _ptr(plan.Gt), _ptr(x), plan.estimator, _ptr(idx), _ptr(val),
-                                   _ptr(kept), _ptr(ncand))
+                                   _ptr(kept), _ptr(ncand), _ptr(zhat))
     if kout < 0:
         raise ValueError("invalid sfft2 parameters")
-    return {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout), "kept": kept.astype(bool),
-            "ncand": int(ncand[0])}
+    out = {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout), "kept": kept.astype(bool),
+           "ncand": int(ncand[0])}
+    if plan.refine:
+        out["val"] = refine(plan, zhat, out["idx"], out["val"], plan.refine)
+    return out
+
+
+# ------------------------------------ iterative-framework refinement
+def refine(plan: Plan, zhat, idx, val, passes: int = 1):
+    """Refined values of the found coefficients idx (start: val) after
+    `passes` rounds of subtracting the other found coefficients from each
+    loop's bucket and re-estimating (combined by plan.estimator)."""
+    sigma, tau, _ = loop_params(plan.N, plan.L, plan.seed)
+    Gfull = filter_gain_full(plan.N, plan.w, plan.g)
+    idx = np.ascontiguousarray(idx, np.int32)
+    out = _c128(np.array(val, np.complex128))
+    _load().oracle_refine(plan.N, plan.B, plan.L, _ptr(sigma), _ptr(tau), _ptr(_c128(Gfull)), _ptr(_c128(zhat)),
+                          len(idx), _ptr(idx), plan.estimator, passes, _ptr(out))
+    return out

@@ -635,12 +635,12 @@ int64_t oracle_sfft2(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, i
                      uint8_t *kept_out, int64_t *ncand_out)
 {
     return oracle_sfft2_ex(N, K, B, w, L, c, T, Bc, C, seed, g, Gt, x, ORACLE_MEDIAN, idx, val, kept_out,
-                           ncand_out);
+                           ncand_out, NULL);
 }
 
 int64_t oracle_sfft2_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T, int64_t Bc, int C,
                         uint64_t seed, const double *g, const double *Gt, const double *x, int combine,
-                        int32_t *idx, double *val, uint8_t *kept_out, int64_t *ncand_out)
+                        int32_t *idx, double *val, uint8_t *kept_out, int64_t *ncand_out, double *zhat_out)
 {
     if (!is_pow2(N) || N < 2 || !is_pow2(B) || B > N || w < B || w % B || L < 1 || c < 1 || T < 1 || T > L ||
         !is_pow2(Bc) || Bc > N || C < 1)
@@ -654,7 +654,7 @@ int64_t oracle_sfft2_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c
     double *E = (double *)malloc(sizeof(double) * (size_t)Bc);
     oracle_comb(N, Bc, C, tau + L, (int64_t)c * K < Bc ? (int64_t)c * K : Bc, x, kept, E);
 
-    double *zhat = (double *)malloc(sizeof(double) * 2 * (size_t)(L * B));
+    double *zhat = zhat_out ? zhat_out : (double *)malloc(sizeof(double) * 2 * (size_t)(L * B));
     oracle_bucketize(N, B, w, L, sigma, tau, g, x, NULL, zhat);
     int64_t cK = (int64_t)c * K;
     int64_t nsel = cK < B ? cK : B;
@@ -672,7 +672,7 @@ int64_t oracle_sfft2_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c
     if (ncand_out) *ncand_out = ncand;
     if (!kept_out) free(kept);
     free(E);
-    free(zhat);
+    if (!zhat_out) free(zhat);
     free(sel);
     free(cand);
     free(est);
@@ -680,4 +680,58 @@ int64_t oracle_sfft2_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c
     free(tau);
     free(sinv);
     return kout;
+}
+
+/* ==================================================================
+ * Iterative-framework refinement of a found set (§ "Four algorithmic
+ * frameworks", its iterative framework, applied to the voting output).
+ * ================================================================== */
+
+void oracle_refine(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau, const double *Gfull,
+                   const double *zhat, int64_t n, const int32_t *idx, int combine, int passes, double *val)
+{
+    int64_t NB = N / B;
+    double *cur = (double *)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+    double *re = (double *)malloc(sizeof(double) * (size_t)L);
+    double *im = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int p = 0; p < passes; ++p) {
+        for (int64_t q = 0; q < 2 * n; ++q) cur[q] = val[q];
+        for (int64_t c = 0; c < n; ++c) {
+            int64_t f = idx[c];
+            for (int l = 0; l < L; ++l) {
+                int64_t h, o;
+                oracle_hash(N, B, sigma[l], f, &h, &o);
+                double complex r = zhat[2 * (l * B + h)] + I * zhat[2 * (l * B + h) + 1];
+                /* the other found coefficients' share of this bucket, by the
+                   identity zhat_l[k] = sum_g x^_g e^{+2 pi i tau g / N} G~(sigma g - k N/B) */
+                for (int64_t d = 0; d < n; ++d) {
+                    if (d == c) continue;
+                    int64_t gq = idx[d];
+                    double complex v = cur[2 * d] + I * cur[2 * d + 1];
+                    int64_t nu = mod_pos(sigma[l] * gq - h * NB, N);
+                    double complex G = Gfull[2 * nu] + I * Gfull[2 * nu + 1];
+                    r -= v * unit_root(tau[l] * gq, N) * G;
+                }
+                double complex Gf = Gfull[2 * mod_pos(o, N)] + I * Gfull[2 * mod_pos(o, N) + 1];
+                double complex e = r * conj(unit_root(tau[l] * f, N)) / Gf; /* undo the turn of f */
+                re[l] = creal(e);
+                im[l] = cimag(e);
+            }
+            if (combine == ORACLE_MEDIAN) {
+                val[2 * c] = median_of(re, L);
+                val[2 * c + 1] = median_of(im, L);
+            } else {
+                double sr = 0.0, si = 0.0;
+                for (int l = 0; l < L; ++l) {
+                    sr += re[l];
+                    si += im[l];
+                }
+                val[2 * c] = sr / (double)L;
+                val[2 * c + 1] = si / (double)L;
+            }
+        }
+    }
+    free(cur);
+    free(re);
+    free(im);
 }

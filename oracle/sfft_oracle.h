@@ -1,7 +1,8 @@
 /*
  * FP64 CPU oracle for the flat-window voting sparse FFT (sFFT1.0-style), its
  * phase-encoding, iterative variant (sFFT3.0-style), the spike-train
- * pre-filter in front of voting (sFFT2.0-style) and the averaging estimator.
+ * pre-filter in front of voting (sFFT2.0-style), the averaging estimator and
+ * the iterative-framework refinement of the voting output.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may include, link or
  * call this code: only the tests, the package smoke check and the benchmark's
@@ -188,7 +189,16 @@ int64_t oracle_sfft2(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, i
 /* oracle_sfft2 with the a6 combination chosen by combine. */
 int64_t oracle_sfft2_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c, int T, int64_t Bc, int C,
                         uint64_t seed, const double *g, const double *Gt, const double *x, int combine,
-                        int32_t *idx, double *val, uint8_t *kept_out, int64_t *ncand_out);
+                        int32_t *idx, double *val, uint8_t *kept_out, int64_t *ncand_out, double *zhat_out);
+
+/* Iterative-framework refinement of the n found coefficients idx[] with
+   values val[] (in: the pipeline's estimates; out: refined).  Each of the
+   passes re-estimates every found f in every loop from its bucket
+   zhat_l[h_l(f)] after subtracting the other found coefficients by the exact
+   bucket identity (Gfull: G~ at every offset, oracle_filter_gain_full), using
+   the previous pass's values, and combines the L estimates by combine. */
+void oracle_refine(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau, const double *Gfull,
+                   const double *zhat, int64_t n, const int32_t *idx, int combine, int passes, double *val);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,7 @@ import pytest
 import oracle
 import test_oracle_comb_pins as comb_pins
 import test_oracle_mean_pins as mean_pins
+import test_oracle_refine_pins as refine_pins
 import test_oracle_pe_pins as pe_pins
 import test_oracle_pins as pins
 
@@ -55,6 +56,15 @@ MUTANTS = [
     ("mean replaced by the median", "if (combine == ORACLE_MEAN) {", "if (0) {"),
     ("mean skips loop 0", "for (int l = 0; l < L; ++l) {\n                sr += re[l];",
      "for (int l = 1; l < L; ++l) {\n                sr += re[l];"),
+    # iterative-framework refinement
+    ("refine subtracts itself", "if (d == c) continue;", "if (0) continue;"),
+    ("refine turn sign", "r -= v * unit_root(tau[l] * gq, N) * G;", "r -= v * unit_root(-(tau[l] * gq), N) * G;"),
+    # (G~ is even up to the window's one unpaired edge tap, so a reversed offset
+    # is nearly an equivalent mutant; the gain at the wrong coefficient's offset is not)
+    ("refine gain at f's offset", "int64_t nu = mod_pos(sigma[l] * gq - h * NB, N);",
+     "int64_t nu = mod_pos(o, N);"),
+    ("refine uses the new values", "for (int64_t q = 0; q < 2 * n; ++q) cur[q] = val[q];",
+     "for (int64_t q = 0; q < 0; ++q) cur[q] = val[q];"),
 ]
 
 PIN_CHECKS = [
@@ -87,6 +97,9 @@ PIN_CHECKS = [
     lambda: mean_pins.test_mean_exact_on_one_sparse(1 << 12, 16, 5, 1234),
     mean_pins.test_mean_is_linear_and_median_is_not,
     mean_pins.test_two_coefficients_closed_form,
+    lambda: refine_pins.test_one_pass_from_true_values_is_exact(oracle.MEDIAN),
+    refine_pins.test_passes_remove_the_mean_bias,
+    refine_pins.test_lone_coefficient_unchanged,
 ]
 
 
