@@ -226,8 +226,9 @@ def measure_comb(sfft, torch, dev, stream, args, W, sigs, xs, Bc=4096):
 def measure_mean(sfft, torch, dev, stream, args, W, sigs, xs, snrs=(0.0, 10.0, 20.0, 40.0), per_snr=8):
     """The bench workload's signals with the averaging estimator (the mean of
     the L per-loop estimates; every candidate is estimated): spectra/s timed
-    by the library and the error figures; then the L1 error of both
-    estimators over an SNR sweep (per_snr signals per SNR, context)."""
+    by the library and the error figures, also with two refinement passes;
+    then the L1 error of both estimators, plain and refined, over an SNR
+    sweep (per_snr signals per SNR, context)."""
     from paper_2012_08238_gb300 import metrics as _m
 
     S = len(xs)
@@ -256,13 +257,32 @@ def measure_mean(sfft, torch, dev, stream, args, W, sigs, xs, snrs=(0.0, 10.0, 2
            "stage_ms_per_step": {kk: v / args.steps for kk, v in stage_ms.items()},
            "what": "same signals as the headline; a6 by the mean of the L per-loop estimates"}
     del plans
+    # both estimators with two refinement passes (the iterative framework's subtraction)
+    for key, est in (("refined", sfft.SFFT_ESTIMATOR_MEAN), ("median_refined", sfft.SFFT_ESTIMATOR_MEDIAN)):
+        plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, W.L, s, estimator=est, refine=2)
+                 for s in range(S)]
+        for _ in range(max(3, args.warmup)):
+            sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+        torch.cuda.synchronize(dev)
+        total_ms, stage_ms = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, args.steps, stream)
+        k = kout.cpu().numpy()
+        errs = [_m.errors(sg.xhat, W.K, idxs[i].cpu().numpy()[: k[i]], vals[i].cpu().numpy()[: k[i]])
+                for i, sg in enumerate(sigs)]
+        out[key] = {"value": S * args.steps / (total_ms / 1e3), "unit": UNIT, "ms_per_step": total_ms / args.steps,
+                    "estimator": "mean" if est == sfft.SFFT_ESTIMATOR_MEAN else "median", "passes": 2,
+                    "l1_error": float(np.mean([e["L1"] for e in errs])),
+                    "support_recall": 1.0 - float(np.sum([e["L0"] for e in errs])) / (W.K * S),
+                    "refine_ms_per_step": stage_ms["refine"] / args.steps}
+        del plans
     sweep = []
     for snr in snrs:
         sg = [signals.make_signal(W.N, W.K, 20_000 + s, snr) for s in range(per_snr)]
         xd = [torch.from_numpy(g.x).to(dev) for g in sg]
         row = {"snr_db": snr}
-        for name, est in (("median", sfft.SFFT_ESTIMATOR_MEDIAN), ("mean", sfft.SFFT_ESTIMATOR_MEAN)):
-            pl = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, W.L, 20_000 + s, estimator=est)
+        for name, est, passes in (("median", sfft.SFFT_ESTIMATOR_MEDIAN, 0), ("mean", sfft.SFFT_ESTIMATOR_MEAN, 0),
+                                  ("median_refined", sfft.SFFT_ESTIMATOR_MEDIAN, 2),
+                                  ("mean_refined", sfft.SFFT_ESTIMATOR_MEAN, 2)):
+            pl = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, W.L, 20_000 + s, estimator=est, refine=passes)
                   for s in range(per_snr)]
             ii, vv, ko = run(pl, xd, W.K)
             sfft.sfft_execute_batch(pl, xd, ii, vv, ko, stream)

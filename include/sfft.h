@@ -75,6 +75,8 @@ typedef struct {
                           min(2^ceil(log2(16 c K)), 8192, N, 32 N / B for 32 <= B <= 512) */
     int32_t estimator; /* SFFT_ESTIMATOR_MEDIAN (0, default) or SFFT_ESTIMATOR_MEAN (voting
                           and comb methods) */
+    int32_t refine;    /* iterative-framework refinement passes over the found set, 0..8
+                          (0, default: none; voting and comb methods, K <= 4096) */
 } sfft_opts;
 
 /* Location methods.
@@ -108,6 +110,17 @@ typedef struct {
 #define SFFT_ESTIMATOR_MEDIAN 0
 #define SFFT_ESTIMATOR_MEAN 1
 
+/* sfft_opts.refine > 0: after the top K, the iterative framework's
+   subtraction ("Four algorithmic frameworks") refines the K output values.
+   Each pass re-estimates every found coefficient f in every loop from its
+   bucket after subtracting the other found coefficients that hash to the same
+   or a neighbouring bucket (by the bucket identity with the filter's gain;
+   further out the gain is below the flat window's stop-band floor), using the
+   previous pass's values, and combines the L estimates by the plan's
+   estimator.  The support is not changed.  Removes the collision bias that
+   the mean estimator otherwise carries. */
+#define SFFT_MAX_REFINE 8
+
 /* Read-only description of a plan (host struct filled by sfft_plan_get_info). */
 typedef struct {
     int64_t N, w;
@@ -118,6 +131,7 @@ typedef struct {
     size_t device_bytes;         /* device memory held by the plan */
     int32_t method;              /* SFFT_METHOD_* */
     int32_t estimator;           /* SFFT_ESTIMATOR_* */
+    int32_t refine;              /* refinement passes */
 } sfft_plan_info;
 
 /* ------------------------------------------------------------------ plans */
@@ -197,9 +211,10 @@ sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_de
 /* Measurement form of sfft_execute_batch: enqueues `steps` back-to-back runs
    of the batch on `stream` (no graph) with CUDA events recorded on that
    stream around each of its six stages (gather-fold, FFT+select, vote scan,
-   survivor estimate, fallback, top-K; the top-K and any fallback pass run
-   in the last estimate CTA of each job, so the fourth stage holds them and
-   the last two are empty), waits for the last
+   survivor estimate, fallback, refinement; the top-K and any fallback pass
+   run in the last estimate CTA of each job, so the fourth stage holds them
+   and the fifth is empty; the sixth holds the refinement passes of plans
+   with sfft_opts.refine > 0, else it is empty), waits for the last
    one, and returns the device time from the first event to the last
    (*total_ms) and the summed time of each stage over all steps
    (stage_ms[6]).  Errors as for sfft_execute_batch. */

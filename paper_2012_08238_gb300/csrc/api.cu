@@ -145,7 +145,7 @@ void decompose(PlanDev &P) {
 }
 
 struct Layout {
-    size_t plan, taps, tw, ginv, gext, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, survf, surv, ctr,
+    size_t plan, taps, tw, ginv, gext, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, survf, surv, rscr, ctr,
         total;
 };
 
@@ -164,7 +164,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.taps = take(sizeof(float) * P.w);
     o.tw = take(sizeof(float2) * (B / 2));
     o.ginv = take(sizeof(float2) * (P.N / B));
-    o.gext = take(phase ? sizeof(float2) * 3 * (P.N / B) : 0);
+    o.gext = take(phase || P.refine ? sizeof(float2) * 3 * (P.N / B) : 0);
     const bool comb = P.method == kMethodComb;
     o.ctw = take(comb ? sizeof(float2) * (P.Bc / 2) : 0);
     o.cls = take(comb ? sizeof(uint32_t) * P.ncls : 0);
@@ -178,6 +178,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.flags = take(sizeof(uint16_t) * L * B);
     o.survf = take(sizeof(uint32_t) * (size_t)cap);
     o.surv = take(sizeof(uint4) * (size_t)cap);
+    o.rscr = take(P.refine ? sizeof(float2) * P.K * P.L : 0);
     o.ctr = take(sizeof(uint32_t) * kNumCounters);
     o.total = off;
     return o;
@@ -185,7 +186,8 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
 
 // Sizes and work split of a plan, without touching the device.
 void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
-                   int64_t *cap, uint32_t method, uint32_t Bc, uint32_t estimator = kEstMedian) {
+                   int64_t *cap, uint32_t method, uint32_t Bc, uint32_t estimator = kEstMedian,
+                   uint32_t refine = 0) {
     memset(&P, 0, sizeof(P));
     const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     P.N = (uint32_t)N;
@@ -205,6 +207,7 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.M = (uint32_t)((L + 1) / 2);
     P.method = method;
     P.estimator = estimator;
+    P.refine = refine;
     if (method == kMethodComb) {
         P.Bc = Bc;
         P.logBc = ilog2(Bc);
@@ -255,6 +258,8 @@ struct Sizes {
     uint32_t max_cap = 0;  // phase encoding: largest found-list capacity
     bool comb = false;     // every job votes behind the spike-train pre-filter
     uint32_t max_Bc = 0;   // comb: largest number of residue classes
+    bool refine = false;   // some job refines its output
+    uint32_t max_rK = 0;   // refinement: largest K of the refining jobs
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -286,6 +291,8 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.L_uniform = p->h.L;
     z.bits = p->h.use_bits != 0;
     z.est_smem = estimate_tab_bytes(p->h.N, p->h.B, p->h.L);
+    z.refine = p->h.refine > 0;
+    z.max_rK = z.refine ? p->h.K : 0u;
     return z;
 }
 
@@ -333,7 +340,8 @@ cudaError_t side_res(SideRes *&out) {
 // top K, running the job's fallback pass first when needed), all
 // stream-ordered.  With ev (kStages + 1 events) the events bracket the
 // stages: gather, FFT/select (and the wait for the comb kernel of comb
-// plans), scan, estimate + top-K, fallback (empty), top-K (empty).
+// plans), scan, estimate + top-K, fallback (empty), refinement (empty unless
+// a plan refines).
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
                             const Launch &lj, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
@@ -363,6 +371,8 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = launch_estimate(le, z.jobs, z.L_uniform, z.est_ctas, z.est_smem, z.max_K, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
+    // refining jobs: the iterative framework's subtraction over the found set
+    if (z.refine && (e = launch_refine(lj, z.jobs, z.max_rK, s)) != cudaSuccess) return e;
     return mark(6);
 }
 
@@ -489,6 +499,10 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
         set_error("sfft_opts.estimator applies to the voting and comb methods");
         return SFFT_EINVAL;
     }
+    if (o.refine < 0 || o.refine > SFFT_MAX_REFINE || (o.refine && (phase || K > (int32_t)kRefineMaxK))) {
+        set_error("sfft_opts.refine must be 0..8 passes, for the voting and comb methods with K <= 4096");
+        return SFFT_EINVAL;
+    }
     // (phase encoding reads no c or T)
     const int32_t c = phase ? 1 : (o.c > 0 ? o.c : 2);
     const int32_t T = phase ? 1 : (o.T > 0 ? o.T : (L + 1) / 2);
@@ -533,7 +547,7 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
 
     PlanDev &P = p->h;
     fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc,
-                  o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian);
+                  o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian, (uint32_t)o.refine);
     // (comb plans: loops L and L+1 give the comb shifts)
     loop_params_host(N, L + (comb ? (int32_t)kCombShifts : 0), seed, P.sigma, P.tau, p->sigma_inv);
     const Layout lay = layout_of(P, p->cap);
@@ -549,7 +563,8 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     P.taps = reinterpret_cast<float *>(base + lay.taps);
     P.tw = reinterpret_cast<float2 *>(base + lay.tw);
     P.ginv = reinterpret_cast<float2 *>(base + lay.ginv);
-    P.gext = phase ? reinterpret_cast<float2 *>(base + lay.gext) : nullptr;
+    P.gext = phase || P.refine ? reinterpret_cast<float2 *>(base + lay.gext) : nullptr;
+    P.rscr = P.refine ? reinterpret_cast<float2 *>(base + lay.rscr) : nullptr;
     P.ctw = comb ? reinterpret_cast<float2 *>(base + lay.ctw) : nullptr;
     P.cls = comb ? reinterpret_cast<uint32_t *>(base + lay.cls) : nullptr;
     P.keptc = comb ? reinterpret_cast<uint32_t *>(base + lay.keptc) : nullptr;
@@ -646,6 +661,7 @@ extern "C" sfft_status sfft_plan_get_info(const sfft_plan *p, sfft_plan_info *in
     info->device_bytes = p->device_bytes;
     info->method = (int32_t)p->h.method;
     info->estimator = (int32_t)p->h.estimator;
+    info->refine = (int32_t)p->h.refine;
     return SFFT_OK;
 }
 
@@ -779,6 +795,8 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         z.max_cap = std::max(z.max_cap, s.max_cap);
         z.comb = i == 0 ? s.comb : z.comb;
         z.max_Bc = std::max(z.max_Bc, s.max_Bc);
+        z.refine = z.refine || s.refine;
+        z.max_rK = std::max(z.max_rK, s.max_rK);
     }
     // pruned estimate with staged tables: one wave of resident CTAs over the
     // batch (each CTA stages its job's tables once)

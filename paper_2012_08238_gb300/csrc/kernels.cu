@@ -1311,13 +1311,13 @@ __device__ void rank_records(const PlanDev &P, const Job &J, unsigned long long 
 
 // True in every thread of the job's last CTA of this launch to finish (each
 // CTA fences its records first); that CTA also re-arms the ticket.
-__device__ bool last_of_job(const PlanDev &P, uint32_t ctas_per_job) {
+__device__ bool last_of_job(const PlanDev &P, uint32_t ctas_per_job, int counter = kEstDone) {
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        s_last = atomicAdd(P.ctr + kEstDone, 1u) == ctas_per_job - 1;
-        if (s_last) atomicExch(P.ctr + kEstDone, 0u);
+        s_last = atomicAdd(P.ctr + counter, 1u) == ctas_per_job - 1;
+        if (s_last) atomicExch(P.ctr + counter, 0u);
     }
     __syncthreads();
     if (s_last) __threadfence();
@@ -1804,6 +1804,144 @@ __global__ void k_flags_from_sel(const PlanDev *pd, const int32_t *sel) {
     }
 }
 
+// ------------------------------------------ iterative-framework refinement
+// After the top K ("Four algorithmic frameworks", its iterative framework,
+// applied to the voting output): P.refine passes, each re-estimating every
+// found coefficient f in every loop from its bucket after subtracting the
+// other found coefficients that hash to the same or a neighbouring bucket
+// (their gain from the three-bucket table gext; further out the flat
+// window's gain is below its stop-band floor), with the previous pass's
+// values, then combining the L estimates as the plan does.  One CTA of
+// kRefineThreads per job runs all passes, the (f, l) pairs spread over its
+// threads.  The found set sits in shared memory (previous and current
+// values [K], frequencies [K]), the per-loop estimates of a pass in P.rscr.
+// Neighbours: with n L <= kRefineSortMax the (loop, bucket, index) keys are
+// sorted once (the buckets do not change between passes) and each pair looks
+// its three buckets up by binary search; larger sets compare every other
+// coefficient's bucket.
+constexpr int kRefineThreads = 1024;
+constexpr uint32_t kRefineSortMax = 4096;
+
+__global__ void __launch_bounds__(kRefineThreads) k_refine(Launch ln) {
+    extern __shared__ float2 rq_s[];
+    __shared__ PlanDev P;
+    __shared__ Job J;
+    __shared__ uint32_t s_local;
+    enter(ln, P, J, s_local);
+    if (P.refine == 0) return;  // (uniform over the CTA)
+    const uint32_t K = P.K, L = P.L, B = P.B, N = P.N, NB = N >> P.logB;
+    const uint32_t n = min((uint32_t)max(__ldcg(J.kout), 0), K);
+    const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
+    float2 *cur = rq_s, *nxt = rq_s + K;
+    uint32_t *fi = reinterpret_cast<uint32_t *>(rq_s + 2 * K);
+    unsigned long long *ks = reinterpret_cast<unsigned long long *>(rq_s + 2 * K + (K + 1) / 2);
+    for (uint32_t i = threadIdx.x; i < n; i += kRefineThreads) {
+        fi[i] = (uint32_t)__ldcg(J.idx + i);
+        cur[i] = __ldcg(J.val + i);
+    }
+    __syncthreads();
+    // keys (l << 40 | h << 20 | i), stored complemented so that the
+    // descending sort leaves them ascending: loop l's n keys at [l n, l n + n)
+    const bool sorted = n * L <= kRefineSortMax;
+    if (sorted) {
+        uint32_t np2 = 1;
+        while (np2 < n * L) np2 <<= 1;
+        for (uint32_t j = threadIdx.x; j < np2; j += kRefineThreads) {
+            unsigned long long key = ~0ull;
+            if (j < n * L) {
+                const uint32_t l = j / n, i = j - l * n;
+                const uint32_t h = ((P.sigma[l] << sN) * fi[i] + cv) >> top;
+                key = ((unsigned long long)l << 40) | ((unsigned long long)h << 20) | i;
+            }
+            ks[j] = ~key;
+        }
+        __syncthreads();
+        bitonic_desc(ks, np2);
+    }
+    for (uint32_t pass = 0; pass < P.refine; ++pass) {
+        for (uint32_t w = threadIdx.x; w < n * L; w += kRefineThreads) {
+            const uint32_t i = w / L, l = w - i * L;
+            const uint32_t sig = P.sigma[l], tau = P.tau[l], a = sig << sN;
+            const uint32_t f = fi[i], h = (a * f + cv) >> top;
+            float2 r = __ldcg(P.zhat + (size_t)l * B + h);
+            auto subtract = [&](uint32_t d) {
+                const uint32_t g = fi[d];
+                // nu = (sigma g mod N) - h N/B, wrapped into [-N/2, N/2): within +-3N/2B
+                const int32_t nu =
+                    (int32_t)((((sig * g) & P.mask) - h * NB + N / 2) & P.mask) - (int32_t)(N / 2);
+                const float2 G = __ldg(P.gext + (nu + (int32_t)(3 * NB / 2)));
+                const float2 c = cmul(cmul(cur[d], turn_pos((tau << sN) * g)), G);
+                r.x -= c.x;
+                r.y -= c.y;
+            };
+            if (sorted) {
+                const uint32_t s0 = l * n, s1 = s0 + n;
+                const uint32_t nb = B < 3 ? B : 3;  // buckets h - 1, h, h + 1 (distinct ones)
+                for (uint32_t q = 0; q < nb; ++q) {
+                    const uint32_t b = (B >= 3 ? h + B - 1 + q : h + q) & (B - 1);
+                    uint32_t lo = s0, hi = s1;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if ((uint32_t)((~ks[mid] >> 20) & 0xFFFFFu) < b)
+                            lo = mid + 1;
+                        else
+                            hi = mid;
+                    }
+                    for (uint32_t j = lo; j < s1; ++j) {
+                        const unsigned long long key = ~ks[j];
+                        if ((uint32_t)((key >> 20) & 0xFFFFFu) != b) break;
+                        const uint32_t d = (uint32_t)(key & 0xFFFFFu);
+                        if (d != i) subtract(d);
+                    }
+                }
+            } else {
+                for (uint32_t d = 0; d < n; ++d) {
+                    const uint32_t dd = (((a * fi[d] + cv) >> top) - h) & (B - 1);
+                    if (d != i && (dd == 0 || dd == 1 || dd == B - 1)) subtract(d);
+                }
+            }
+            uint32_t hh, opos;
+            hash_freq(P, sig, f, hh, opos);
+            P.rscr[(size_t)i * L + l] = turn_scale(r, __ldg(P.ginv + opos), (tau << sN) * f);
+        }
+        __syncthreads();  // the pass's (f, l) estimates are written
+        for (uint32_t i = threadIdx.x; i < n; i += kRefineThreads) {
+            const float2 *v = P.rscr + (size_t)i * L;
+            if (P.estimator == kEstMean) {
+                float sr = 0.f, si = 0.f;
+                for (uint32_t l = 0; l < L; ++l) {
+                    const float2 e = __ldcg(v + l);
+                    sr += e.x;
+                    si += e.y;
+                }
+                nxt[i] = make_float2(sr / (float)L, si / (float)L);
+            } else {
+                float re[kMaxL], im[kMaxL];
+                for (uint32_t l = 0; l < L; ++l) {
+                    const float2 e = __ldcg(v + l);
+                    uint32_t a = l, b = l;
+                    while (a > 0 && re[a - 1] > e.x) {
+                        re[a] = re[a - 1];
+                        --a;
+                    }
+                    re[a] = e.x;
+                    while (b > 0 && im[b - 1] > e.y) {
+                        im[b] = im[b - 1];
+                        --b;
+                    }
+                    im[b] = e.y;
+                }
+                nxt[i] = make_float2(median_sorted(re, L), median_sorted(im, L));
+            }
+        }
+        __syncthreads();  // (the next pass reads nxt and rewrites P.rscr)
+        float2 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    for (uint32_t i = threadIdx.x; i < n; i += kRefineThreads) J.val[i] = cur[i];
+}
+
 template <int LT, int TAB>
 cudaError_t scan_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, int32_t *cand_out,
                          int32_t *ncand_out, cudaStream_t s) {
@@ -1962,6 +2100,17 @@ cudaError_t launch_pe(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t
     cudaError_t e = cudaFuncSetAttribute(k_pe_job, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_pe_job<<<njobs, kThreads, smem, s>>>(ln, cap, fcap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s) {
+    if (njobs == 0 || max_K == 0) return cudaSuccess;
+    // values [2][K], frequencies [K] (padded to 8 bytes), sort keys [kRefineSortMax]: <= 113 KB
+    const int smem = (int)((2 * sizeof(float2) + sizeof(uint32_t)) * max_K + 4 +
+                           sizeof(unsigned long long) * kRefineSortMax);
+    cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_refine<<<njobs, kRefineThreads, smem, s>>>(ln);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ constexpr uint32_t kCombShifts = 2;     // comb subsamplings (shifts tau of loop
 constexpr uint32_t kMaxComb = 8192;     // largest number of residue classes
 constexpr uint32_t kEstMedian = 0;      // a6: coordinate-wise median of the per-loop estimates
 constexpr uint32_t kEstMean = 1;        // a6: their mean (every candidate estimated)
+constexpr uint32_t kRefineMaxK = 4096;  // refinement: the found set lives in shared memory
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
@@ -69,11 +70,12 @@ struct PlanDev {
     uint32_t method;                          // kMethodVoting, kMethodPhase or kMethodComb
     uint32_t Bc, logBc, ncls;                 // comb: residue classes, kept classes
     uint32_t estimator;                       // kEstMedian or kEstMean
+    uint32_t refine;                          // refinement passes (0: none)
     uint32_t sigma[kMaxL], tau[kMaxL];
     const float *taps;     // [w]
     const float2 *tw;      // [B/2] exp(-2 pi i k / B)
     const float2 *ginv;    // [N/B] 1 / G~(o), o + half
-    const float2 *gext;    // phase encoding: [3N/B] G~(nu) for nu + 3N/2B in [0, 3N/B)
+    const float2 *gext;    // phase encoding, refinement: [3N/B] G~(nu) for nu + 3N/2B in [0, 3N/B)
     const float2 *ctw;     // comb: [Bc/2] exp(-2 pi i k / Bc)
     uint32_t *cls;         // comb: [ncls] kept residue classes, ascending
     uint32_t *keptc;       // comb: [Bc/32] kept-class bitmap
@@ -86,6 +88,7 @@ struct PlanDev {
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
     uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
     uint4 *surv;           // [cap] records {f, key bits, re bits, im bits}
+    float2 *rscr;          // refinement: [K][L] per-loop estimates of a pass
     uint32_t *ctr;         // [kNumCounters]
 };
 
@@ -151,6 +154,10 @@ cudaError_t launch_comb(const Launch &ln, uint32_t njobs, uint32_t max_Bc, cudaS
 // kPeSmemFound entries stay in shared memory).
 cudaError_t launch_pe(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t max_K, uint32_t max_cap,
                       cudaStream_t s);
+// Iterative-framework refinement of the jobs' outputs: one CTA per job (ln:
+// one per job) runs all the job's passes; jobs with refine = 0 return at
+// once.  max_K: the largest K of the refining jobs (<= kRefineMaxK).
+cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);
 cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *sel, cudaStream_t s);

@@ -28,13 +28,13 @@ SFFT_OK, SFFT_EINVAL, SFFT_ENOMEM, SFFT_ECUDA, SFFT_EBUSY, SFFT_ETIMEDOUT, SFFT_
 
 class sfft_opts(ctypes.Structure):
     _fields_ = [("c", _i32), ("T", _i32), ("precision", _i32), ("method", _i32), ("comb", _i32),
-                ("estimator", _i32)]
+                ("estimator", _i32), ("refine", _i32)]
 
 
 class sfft_plan_info(ctypes.Structure):
     _fields_ = [("N", _i64), ("w", _i64), ("K", _i32), ("B", _i32), ("L", _i32), ("c", _i32), ("T", _i32),
                 ("nsel", _i32), ("seed", _u64), ("samples_touched", _i64), ("candidate_capacity", _i64),
-                ("device_bytes", ctypes.c_size_t), ("method", _i32), ("estimator", _i32)]
+                ("device_bytes", ctypes.c_size_t), ("method", _i32), ("estimator", _i32), ("refine", _i32)]
 
 
 class sfft_exec_stats(ctypes.Structure):
@@ -183,11 +183,12 @@ SFFT_METHOD_PHASE = 1
 SFFT_METHOD_COMB = 2
 SFFT_ESTIMATOR_MEDIAN = 0
 SFFT_ESTIMATOR_MEAN = 1
+SFFT_MAX_REFINE = 8
 
 
 def sfft_plan_create_ex(N, K, B, w, L, seed, c=0, T=0, precision=0, method=SFFT_METHOD_VOTING, comb=0,
-                        estimator=SFFT_ESTIMATOR_MEDIAN) -> Plan:
-    return sfft_plan_create(N, K, B, w, L, seed, sfft_opts(c, T, precision, method, comb, estimator))
+                        estimator=SFFT_ESTIMATOR_MEDIAN, refine=0) -> Plan:
+    return sfft_plan_create(N, K, B, w, L, seed, sfft_opts(c, T, precision, method, comb, estimator, refine))
 
 
 def sfft_plan_destroy(plan: Plan):
@@ -242,7 +243,7 @@ def sfft_execute_batch(plans, xs, idxs, vals, k_out, stream=None):
                                     _addr(k_out), n, _stream(stream)))
 
 
-STAGES = ("gather_fold", "fft_select", "vote_scan", "estimate", "fallback", "topk")
+STAGES = ("gather_fold", "fft_select", "vote_scan", "estimate", "fallback", "refine")
 
 
 def sfft_execute_batch_timed(plans, xs, idxs, vals, k_out, steps, stream=None):
@@ -324,8 +325,9 @@ def sfft_server_destroy(srv: Server):
     srv.destroy()
 
 
-def sfft_submit(srv: Server, N, K, B, w, L, seed, x, idx, val, c=0, T=0, method=0, comb=0, estimator=0) -> int:
-    req = sfft_request(N, w, K, B, L, seed, sfft_opts(c, T, 0, method, comb, estimator), _addr(x), _addr(idx),
+def sfft_submit(srv: Server, N, K, B, w, L, seed, x, idx, val, c=0, T=0, method=0, comb=0, estimator=0,
+                refine=0) -> int:
+    req = sfft_request(N, w, K, B, L, seed, sfft_opts(c, T, 0, method, comb, estimator, refine), _addr(x), _addr(idx),
                        _addr(val))
     ticket = _u64()
     _check(lib().sfft_submit(srv.handle, ctypes.byref(req), ctypes.byref(ticket)))
