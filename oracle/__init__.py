@@ -96,6 +96,15 @@ def _bind(lib):
             [_i64, _i64, _i64, _i64, _int, _int, _int, _i64, _int, _u64, _p, _p, _p, _int, _p, _p, _p, _p, _p],
         ),
         "oracle_refine": (None, [_i64, _i64, _int, _p, _p, _p, _p, _i64, _p, _int, _int, _p]),
+        "oracle_bs_nshifts": (_i64, [_i64, _i64, _int]),
+        "oracle_bs_shifts": (None, [_i64, _i64, _int, _p]),
+        "oracle_bs_locate": (_i64, [_i64, _i64, _int, _i64, _i64, _i64, _p, _p, ctypes.c_double, ctypes.c_double,
+                                    _p, _p, _p]),
+        "oracle_sfft_bs": (
+            _i64,
+            [_i64, _i64, _i64, _i64, _int, _int, ctypes.c_double, ctypes.c_double, _u64, _p, _p, _p, _p, _p, _p,
+             _p],
+        ),
         "oracle_sfft_pe": (
             _i64,
             [_i64, _i64, _i64, _i64, _int, ctypes.c_double, _u64, _p, _p, _p, _p, _p, _p, _p],
@@ -423,3 +432,50 @@ def refine(plan: Plan, zhat, idx, val, passes: int = 1):
     _load().oracle_refine(plan.N, plan.B, plan.L, _ptr(sigma), _ptr(tau), _ptr(_c128(Gfull)), _ptr(_c128(zhat)),
                           len(idx), _ptr(idx), plan.estimator, passes, _ptr(out))
     return out
+
+
+# ------------------------------- sFFT4.0 / MPFFT-style search location
+def bs_shifts(N: int, B: int, b: int) -> np.ndarray:
+    """Shifts of the search's bucketizations: 0, then N / 2^min((j+1) b, log2(N/B))."""
+    n = int(_load().oracle_bs_nshifts(N, B, b))
+    s = np.zeros(n, np.int64)
+    _load().oracle_bs_shifts(N, B, b, _ptr(s))
+    return s
+
+
+def bs_locate(N, B, b, sigma, sigma_inv, tau, Gfull, zhat, thr, rho=0.25):
+    """Located (f [n], values [n], active) from the nshifts bucketizations zhat [nshifts][B]."""
+    zhat = _c128(zhat)
+    f = np.zeros(B, np.int32)
+    v = np.zeros(B, np.complex128)
+    act = np.zeros(1, np.int64)
+    n = _load().oracle_bs_locate(N, B, b, int(sigma), int(sigma_inv), int(tau), _ptr(_c128(Gfull)), _ptr(zhat),
+                                 float(thr), float(rho), _ptr(f), _ptr(v), _ptr(act))
+    return f[:n].copy(), v[:n].copy(), int(act[0])
+
+
+class PlanBS:
+    """Search-location variant: R iterations at most, digits of b bits
+    (1: binary search, 2: multi-scale search with l = 4)."""
+
+    def __init__(self, N, K, B, w, R, seed, b=1, eta=1e-6, rho=0.25):
+        self.N, self.K, self.B, self.w, self.R, self.seed = N, K, B, w, R, seed
+        self.b, self.eta, self.rho = b, eta, rho
+        self.g = window_taps(N, B, w)
+        self.Gfull = filter_gain_full(N, w, self.g)
+
+
+def sfft_bs(plan: PlanBS, x):
+    """Whole search-location pipeline.  Returns dict(idx, val, k_out, iters, nfound)."""
+    x = _c128(x)
+    idx = np.zeros(max(plan.K, 1), np.int32)
+    val = np.zeros(max(plan.K, 1), np.complex128)
+    iters = np.zeros(1, np.int32)
+    nfound = np.zeros(1, np.int64)
+    kout = _load().oracle_sfft_bs(plan.N, plan.K, plan.B, plan.w, plan.R, plan.b, plan.eta, plan.rho, plan.seed,
+                                  _ptr(plan.g), _ptr(plan.Gfull), _ptr(x), _ptr(idx), _ptr(val), _ptr(iters),
+                                  _ptr(nfound))
+    if kout < 0:
+        raise ValueError("invalid sfft_bs parameters")
+    return {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout), "iters": int(iters[0]),
+            "nfound": int(nfound[0])}

@@ -735,3 +735,182 @@ void oracle_refine(int64_t N, int64_t B, int L, const int64_t *sigma, const int6
     free(re);
     free(im);
 }
+
+/* ==================================================================
+ * sFFT4.0 / MPFFT-style location by binary or multi-scale search (§ "The
+ * method of binary search or multi-scale search"; Table 1: flat filter,
+ * binary or multi-scale search, energy estimation, iterative framework).
+ * ================================================================== */
+
+/* The search decodes the low log2(N/B) + 1 bits of f (capped at log2 N):
+   they fix p = sigma f modulo 2N/B, which picks one value in the window of
+   two bucket widths centred on bucket k, so a coefficient that leaks into a
+   neighbouring bucket is located there too and fails the hash-back test.
+   Digit j covers bits [j b, min((j+1) b, bits)); at shift N / 2^m (m = the
+   digit's top bit + 1) a coefficient f turns by exp(2 pi i f / 2^m), which
+   depends on f mod 2^m only. */
+static int64_t bs_bits(int64_t N, int64_t B)
+{
+    int64_t bits = 1, logN = 0;
+    for (int64_t q = N / B; q > 1; q >>= 1) ++bits;
+    for (int64_t q = N; q > 1; q >>= 1) ++logN;
+    return bits < logN ? bits : logN;
+}
+
+static int64_t bs_steps(int64_t N, int64_t B, int b)
+{
+    int64_t J = 0, bits = bs_bits(N, B);
+    for (int64_t lo = 0; lo < bits; lo += b) ++J;
+    return J;
+}
+
+int64_t oracle_bs_nshifts(int64_t N, int64_t B, int b) { return 1 + bs_steps(N, B, b); }
+
+void oracle_bs_shifts(int64_t N, int64_t B, int b, int64_t *s)
+{
+    int64_t bits = bs_bits(N, B);
+    int64_t J = bs_steps(N, B, b);
+    s[0] = 0;
+    for (int64_t j = 0; j < J; ++j) {
+        int64_t m = (j + 1) * b < bits ? (j + 1) * b : bits;
+        s[j + 1] = N >> m;
+    }
+}
+
+int64_t oracle_bs_locate(int64_t N, int64_t B, int b, int64_t sigma, int64_t sigma_inv, int64_t tau,
+                         const double *Gfull, const double *zhat, double thr, double rho, int32_t *f_out,
+                         double *v_out, int64_t *active_out)
+{
+    int64_t NB = N / B, bits = bs_bits(N, B);
+    int64_t W = (int64_t)1 << bits; /* p is decoded modulo W = 2N/B (N when B = 1) */
+    int64_t J = bs_steps(N, B, b);
+    int64_t *s = (int64_t *)malloc(sizeof(int64_t) * (size_t)(J + 1));
+    oracle_bs_shifts(N, B, b, s);
+    int64_t n = 0, active = 0;
+    for (int64_t k = 0; k < B; ++k) {
+        double complex z0 = zhat[2 * k] + I * zhat[2 * k + 1];
+        double e0 = creal(z0) * creal(z0) + cimag(z0) * cimag(z0);
+        if (!(e0 >= thr) || e0 == 0.0) continue;
+        ++active;
+        /* digit by digit: r = f mod 2^lo so far */
+        int64_t r = 0;
+        for (int64_t j = 0; j < J; ++j) {
+            int64_t lo = j * b, m = (j + 1) * b < bits ? (j + 1) * b : bits;
+            double complex zj = zhat[2 * ((j + 1) * B + k)] + I * zhat[2 * ((j + 1) * B + k) + 1];
+            double complex rho_j = zj * conj(z0); /* |z0|^2 exp(2 pi i f / 2^m) for a lone f */
+            int64_t best = 0;
+            double bestv = -INFINITY;
+            for (int64_t d = 0; d < ((int64_t)1 << (m - lo)); ++d) {
+                int64_t cand = r + (d << lo);
+                double v = creal(rho_j * unit_root(-cand * (N >> m), N));
+                if (v > bestv) {
+                    bestv = v;
+                    best = d;
+                }
+            }
+            r += best << lo;
+        }
+        /* p = sigma f mod N: the value with p = sigma r (mod W) in the window
+           [k N/B - W/2, k N/B + W/2) */
+        int64_t pr = mod_pos(sigma * r, W);
+        int64_t lo_p = k * NB - W / 2;
+        int64_t p = lo_p + mod_pos(pr - lo_p, W);
+        int64_t f = mod_pos(sigma_inv * mod_pos(p, N), N);
+        int64_t h, o;
+        oracle_hash(N, B, sigma, f, &h, &o);
+        if (h != k) continue; /* located in a neighbouring bucket: leakage */
+        /* a lone coefficient: every shifted bucket is z0 turned by exp(2 pi i s_j f / N) */
+        double res = 0.0;
+        for (int64_t j = 1; j <= J; ++j) {
+            double complex zj = zhat[2 * (j * B + k)] + I * zhat[2 * (j * B + k) + 1];
+            double complex dlt = zj - z0 * unit_root(s[j] * f, N);
+            res += creal(dlt) * creal(dlt) + cimag(dlt) * cimag(dlt);
+        }
+        if (res > rho * (double)J * e0) continue;
+        double complex G = Gfull[2 * mod_pos(o, N)] + I * Gfull[2 * mod_pos(o, N) + 1];
+        double complex v = z0 * conj(unit_root(tau * f, N)) / G; /* energy estimation */
+        f_out[n] = (int32_t)f;
+        v_out[2 * n] = creal(v);
+        v_out[2 * n + 1] = cimag(v);
+        ++n;
+    }
+    free(s);
+    *active_out = active;
+    return n;
+}
+int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b, double eta, double rho,
+                       uint64_t seed, const double *g, const double *Gfull, const double *x, int32_t *idx,
+                       double *val, int *iters_out, int64_t *nfound_out)
+{
+    if (!is_pow2(N) || N < 2 || !is_pow2(B) || B > N || w < B || w % B || R < 1 || K < 0 || b < 1 || b > 4)
+        return -1;
+    int64_t *sigma = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    int64_t *tau = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    int64_t *sinv = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    oracle_loop_params(N, R, seed, sigma, tau, sinv);
+    int64_t S = oracle_bs_nshifts(N, B, b);
+    int64_t *s = (int64_t *)malloc(sizeof(int64_t) * (size_t)S);
+    oracle_bs_shifts(N, B, b, s);
+    double *found = (double *)calloc(2 * (size_t)N, sizeof(double));
+    char *seen = (char *)calloc((size_t)N, 1);
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    double *lval = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    int64_t nf = 0;
+    double *z = (double *)malloc(sizeof(double) * 2 * (size_t)(S * B));
+    int32_t *nfi = (int32_t *)malloc(sizeof(int32_t) * (size_t)B);
+    double *nfv = (double *)malloc(sizeof(double) * 2 * (size_t)B);
+    double thr = 0.0;
+    int iters = 0;
+    for (int r = 0; r < R; ++r) {
+        for (int64_t c = 0; c < nf; ++c) {
+            lval[2 * c] = found[2 * list[c]];
+            lval[2 * c + 1] = found[2 * list[c] + 1];
+        }
+        /* bucketize at tau_r + s_j, minus the coefficients found so far */
+        for (int64_t j = 0; j < S; ++j) {
+            int64_t tj = mod_pos(tau[r] + s[j], N);
+            oracle_bucketize(N, B, w, 1, &sigma[r], &tj, g, x, NULL, z + 2 * j * B);
+            oracle_pe_subtract(N, B, sigma[r], tj, Gfull, nf, list, lval, z + 2 * j * B);
+        }
+        if (r == 0) {
+            double emax = 0.0;
+            for (int64_t k = 0; k < B; ++k) {
+                double e = z[2 * k] * z[2 * k] + z[2 * k + 1] * z[2 * k + 1];
+                if (e > emax) emax = e;
+            }
+            thr = eta * emax;
+        }
+        int64_t active = 0;
+        int64_t n = oracle_bs_locate(N, B, b, sigma[r], sinv[r], tau[r], Gfull, z, thr, rho, nfi, nfv, &active);
+        iters = r + 1;
+        if (active == 0) break;
+        for (int64_t c = 0; c < n; ++c) {
+            int64_t f = nfi[c];
+            found[2 * f] += nfv[2 * c];
+            found[2 * f + 1] += nfv[2 * c + 1];
+            if (!seen[f]) {
+                seen[f] = 1;
+                list[nf++] = (int32_t)f;
+            }
+        }
+    }
+    for (int64_t c = 0; c < nf; ++c) {
+        lval[2 * c] = found[2 * list[c]];
+        lval[2 * c + 1] = found[2 * list[c] + 1];
+    }
+    int64_t kout = oracle_topk(nf, list, lval, K, idx, val);
+    if (iters_out) *iters_out = iters;
+    if (nfound_out) *nfound_out = nf;
+    free(sigma);
+    free(tau);
+    free(sinv);
+    free(s);
+    free(found);
+    free(seen);
+    free(list);
+    free(lval);
+    free(z);
+    free(nfi);
+    free(nfv);
+    return kout;
+}

@@ -1,8 +1,9 @@
 /*
  * FP64 CPU oracle for the flat-window voting sparse FFT (sFFT1.0-style), its
  * phase-encoding, iterative variant (sFFT3.0-style), the spike-train
- * pre-filter in front of voting (sFFT2.0-style), the averaging estimator and
- * the iterative-framework refinement of the voting output.
+ * pre-filter in front of voting (sFFT2.0-style), the averaging estimator,
+ * the iterative-framework refinement of the voting output, and the location
+ * by binary or multi-scale search (sFFT4.0 / MPFFT-style).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may include, link or
  * call this code: only the tests, the package smoke check and the benchmark's
@@ -199,6 +200,39 @@ int64_t oracle_sfft2_ex(int64_t N, int64_t K, int64_t B, int64_t w, int L, int c
    the previous pass's values, and combines the L estimates by combine. */
 void oracle_refine(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau, const double *Gfull,
                    const double *zhat, int64_t n, const int32_t *idx, int combine, int passes, double *val);
+
+/* ---- sFFT4.0 / MPFFT-style location by binary or multi-scale search ---- */
+
+/* Number of bucketizations per iteration, 1 + ceil(bits / b) with bits =
+   min(log2(N/B) + 1, log2 N), and their shifts s[0] = 0, s[j+1] =
+   N / 2^min((j+1) b, bits): search step j decides digit j (b bits, the last
+   one possibly fewer) of f. */
+int64_t oracle_bs_nshifts(int64_t N, int64_t B, int b);
+void oracle_bs_shifts(int64_t N, int64_t B, int b, int64_t *s);
+
+/* Location in the buckets of one loop (zhat: the nshifts bucketizations,
+   row j at tau + s[j]).  For a bucket with |zhat_0[k]|^2 >= thr, digit j of f
+   is the d whose predicted turn exp(2 pi i (r + d 2^(jb)) s_j / N) best
+   matches zhat_j[k] conj(zhat_0[k]) (largest real part of their product;
+   r: the lower digits).  The bits fix p = sigma f modulo W = 2^bits: p is
+   the one value with p = sigma r (mod W) in [k N/B - W/2, k N/B + W/2) and
+   f = sigma^-1 p.  Kept when f hashes back to bucket k (else the bucket only
+   holds a neighbour's leakage) and sum_j |zhat_j[k] - zhat_0[k]
+   exp(2 pi i s_j f / N)|^2 <= rho (nshifts - 1) |zhat_0[k]|^2 (a lone
+   coefficient), valued zhat_0[k] exp(-2 pi i tau f/N) / G~(o).  Returns the
+   number kept; *active_out = buckets above thr. */
+int64_t oracle_bs_locate(int64_t N, int64_t B, int b, int64_t sigma, int64_t sigma_inv, int64_t tau,
+                         const double *Gfull, const double *zhat, double thr, double rho, int32_t *f_out,
+                         double *v_out, int64_t *active_out);
+
+/* Whole pipeline: as oracle_sfft_pe (iterations r with loop parameters r,
+   subtraction of the found set, threshold eta times the largest bucket
+   energy of iteration 0, accumulation of values found again, top K), with
+   the location by search in radix 2^b (b = 1: binary search; b > 1:
+   multi-scale search) over the shifts tau_r + s[j]. */
+int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b, double eta, double rho,
+                       uint64_t seed, const double *g, const double *Gfull, const double *x, int32_t *idx,
+                       double *val, int *iters_out, int64_t *nfound_out);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,7 @@ import pytest
 import oracle
 import test_oracle_comb_pins as comb_pins
 import test_oracle_mean_pins as mean_pins
+import test_oracle_bs_pins as bs_pins
 import test_oracle_refine_pins as refine_pins
 import test_oracle_pe_pins as pe_pins
 import test_oracle_pins as pins
@@ -65,6 +66,15 @@ MUTANTS = [
      "int64_t nu = mod_pos(o, N);"),
     ("refine uses the new values", "for (int64_t q = 0; q < 2 * n; ++q) cur[q] = val[q];",
      "for (int64_t q = 0; q < 0; ++q) cur[q] = val[q];"),
+    # location by binary or multi-scale search
+    ("bs digit sign", "double v = creal(rho_j * unit_root(-cand * (N >> m), N));",
+     "double v = creal(rho_j * unit_root(cand * (N >> m), N));"),
+    ("bs shift one scale coarser", "s[j + 1] = N >> m;", "s[j + 1] = N >> (m - 1);"),
+    ("bs residue without sigma", "int64_t pr = mod_pos(sigma * r, W);", "int64_t pr = mod_pos(r, W);"),
+    ("bs no hash-back", "if (h != k) continue; /* located in a neighbouring bucket: leakage */",
+     "if (0) continue; /* located in a neighbouring bucket: leakage */"),
+    ("bs no lone-coefficient test", "if (res > rho * (double)J * e0) continue;", "if (0) continue;"),
+    ("bs window not centred", "int64_t lo_p = k * NB - W / 2;", "int64_t lo_p = k * NB;"),
 ]
 
 PIN_CHECKS = [
@@ -100,6 +110,11 @@ PIN_CHECKS = [
     lambda: refine_pins.test_one_pass_from_true_values_is_exact(oracle.MEDIAN),
     refine_pins.test_passes_remove_the_mean_bias,
     refine_pins.test_lone_coefficient_unchanged,
+    lambda: bs_pins.test_shift_schedule(1 << 16, 64, 1, [0] + [(1 << 16) >> m for m in range(1, 12)]),
+    lambda: bs_pins.test_lone_coefficient_located_exactly(1 << 12, 16, 1),
+    bs_pins.test_matches_exhaustive_search_under_noise,
+    bs_pins.test_shared_bucket_rejected,
+    lambda: bs_pins.test_exact_recovery_noiseless(1 << 12, 5, 32, 1),
 ]
 
 
