@@ -297,11 +297,44 @@ def measure_mean(sfft, torch, dev, stream, args, W, sigs, xs, snrs=(0.0, 10.0, 2
     return out
 
 
+def measure_search(sfft, torch, dev, stream, args, W, sigs, xs, R=8):
+    """The bench workload's (noisy) signals located by binary search in the
+    iterative framework (R iterations; phase encoding finds nothing at this
+    noise level): spectra/s timed by the library, the error figures, and the
+    same for phase encoding (context)."""
+    from paper_2012_08238_gb300 import metrics as _m
+
+    S = len(xs)
+    out = {"what": "same signals as the headline (20 dB); iterative framework, R = 8 iterations at most"}
+    for name, method, sb in (("binary_search", sfft.SFFT_METHOD_SEARCH, 1),
+                             ("phase_encoding", sfft.SFFT_METHOD_PHASE, 0)):
+        plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, R, s, method=method, search_bits=sb)
+                 for s in range(S)]
+        idxs = [torch.zeros(W.K, dtype=torch.int32, device=dev) for _ in range(S)]
+        vals = [torch.zeros(W.K, dtype=torch.complex64, device=dev) for _ in range(S)]
+        kout = torch.zeros(S, dtype=torch.int32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+        torch.cuda.synchronize(dev)
+        total_ms, _ = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, args.steps, stream)
+        k = kout.cpu().numpy()
+        errs = [_m.errors(sg.xhat, W.K, idxs[i].cpu().numpy()[: k[i]], vals[i].cpu().numpy()[: k[i]])
+                for i, sg in enumerate(sigs)]
+        out[name] = {"value": S * args.steps / (total_ms / 1e3), "unit": UNIT, "ms_per_step": total_ms / args.steps,
+                     "l1_error": float(np.mean([e["L1"] for e in errs])),
+                     "support_recall": 1.0 - float(np.sum([e["L0"] for e in errs])) / (W.K * S),
+                     "samples_per_spectrum": plans[0].info.samples_touched,
+                     "iterations_first_signal": sfft.sfft_plan_last_stats(plans[0]).iterations}
+        del plans
+    return out
+
+
 def measure_exact(sfft, torch, dev, stream, args, S=256, R=8):
     """The exactly sparse workload (N = 2^16, K = 10, noiseless, B = 64) through
-    sfft_execute_batch with the phase-encoding method (R iterations at most)
-    and with voting (L = 8): spectra/s on the device, support recall, mean
-    iterations, and the phase-encoding oracle on one host core (context)."""
+    sfft_execute_batch with the phase-encoding method and the binary and
+    multi-scale (l = 4) search (R iterations at most), and with voting
+    (L = 8): spectra/s on the device, support recall, mean iterations, and the
+    phase-encoding oracle on one host core (context)."""
     from paper_2012_08238_gb300 import metrics as _m
 
     W = configs.EXACT_N16
@@ -310,8 +343,12 @@ def measure_exact(sfft, torch, dev, stream, args, S=256, R=8):
     xs = [torch.from_numpy(sg.x).to(dev) for sg in sigs]
     out = {"workload": f"exact_N2^16_K10_B64 (noiseless), {S} signals per step, inputs "
                        f"{S * W.N * 8 / 2**20:.0f} MiB (> L2)"}
-    for name, method, L in (("phase_encoding", sfft.SFFT_METHOD_PHASE, R), ("voting", sfft.SFFT_METHOD_VOTING, W.L)):
-        plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, w, L, 10_000 + s, method=method) for s in range(S)]
+    for name, method, L, sb in (("phase_encoding", sfft.SFFT_METHOD_PHASE, R, 0),
+                                ("binary_search", sfft.SFFT_METHOD_SEARCH, R, 1),
+                                ("multiscale_search_l4", sfft.SFFT_METHOD_SEARCH, R, 2),
+                                ("voting", sfft.SFFT_METHOD_VOTING, W.L, 0)):
+        plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, w, L, 10_000 + s, method=method, search_bits=sb)
+                 for s in range(S)]
         idxs = [torch.zeros(W.K, dtype=torch.int32, device=dev) for _ in range(S)]
         vals = [torch.zeros(W.K, dtype=torch.complex64, device=dev) for _ in range(S)]
         kout = torch.zeros(S, dtype=torch.int32, device=dev)
@@ -336,7 +373,7 @@ def measure_exact(sfft, torch, dev, stream, args, S=256, R=8):
         entry = {"value": S / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "python_call_value": S / (call_ms / 1e3),
                  "support_recall": 1.0 - miss / (W.K * S),
                  "samples_per_spectrum": plans[0].info.samples_touched, "max_iterations": L}
-        if method == sfft.SFFT_METHOD_PHASE:
+        if method in (sfft.SFFT_METHOD_PHASE, sfft.SFFT_METHOD_SEARCH):
             its = [sfft.sfft_plan_last_stats(p).iterations for p in plans[:16]]
             entry["iterations_mean_first16"] = float(np.mean(its))
         out[name] = entry
@@ -514,6 +551,7 @@ def run_ours(args):
     exact = measure_exact(sfft, torch, dev, stream, args) if rank == 0 else None
     comb = measure_comb(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
     mean = measure_mean(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
+    search = measure_search(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
 
     # ---- CPU baseline: the oracle on a bounded sample, host cores
     cpu = None
@@ -541,7 +579,7 @@ def run_ours(args):
         "stage_ms_per_step": per_launch, "stage_share": {k: v / sum(per_launch.values()) for k, v in per_launch.items()},
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
         "roofline": roofline, "roofline_scan": roofline_scan, "dense_fft_context": dense,
-        "exactly_sparse": exact, "comb_prefilter": comb, "averaging_estimator": mean,
+        "exactly_sparse": exact, "comb_prefilter": comb, "averaging_estimator": mean, "search_location": search,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,

@@ -70,13 +70,16 @@ typedef struct {
     int32_t c;         /* buckets kept per loop = min(c*K, B); 0 -> 2 ("2K large buckets") */
     int32_t T;         /* vote threshold; 0 -> ceil(L/2) */
     int32_t precision; /* 0 -> FP32 B-point FFT (the only precision in this build) */
-    int32_t method;    /* SFFT_METHOD_VOTING (0, default), SFFT_METHOD_PHASE or SFFT_METHOD_COMB */
+    int32_t method;    /* SFFT_METHOD_VOTING (0, default), SFFT_METHOD_PHASE, SFFT_METHOD_COMB or
+                          SFFT_METHOD_SEARCH */
     int32_t comb;      /* SFFT_METHOD_COMB: residue classes Bc (power of two); 0 -> default
                           min(2^ceil(log2(16 c K)), 8192, N, 32 N / B for 32 <= B <= 512) */
     int32_t estimator; /* SFFT_ESTIMATOR_MEDIAN (0, default) or SFFT_ESTIMATOR_MEAN (voting
                           and comb methods) */
     int32_t refine;    /* iterative-framework refinement passes over the found set, 0..8
                           (0, default: none; voting and comb methods, K <= 4096) */
+    int32_t search_bits; /* SFFT_METHOD_SEARCH: bits per search digit, 1..4; 0 -> 1 (binary
+                            search); b > 1: multi-scale search with l = 2^b */
 } sfft_opts;
 
 /* Location methods.
@@ -98,6 +101,25 @@ typedef struct {
    their energies keep the min(cK, Bc) largest classes, and only frequencies
    of kept classes are voted on, estimated and output (L <= 30). */
 #define SFFT_METHOD_COMB 2
+
+/* SFFT_METHOD_SEARCH: location by binary or multi-scale search (sFFT4.0 /
+   MPFFT-style; "The method of binary search or multi-scale search"; Table 1)
+   in the iterative framework of SFFT_METHOD_PHASE (L = iterations; found
+   coefficients subtracted before each bucketization; threshold 1e-6 of the
+   largest bucket energy of iteration 0; top K of the found set).  Iteration
+   r bucketizes the signal at the shifts tau_r + N / 2^m, m = b, 2b, ..., up
+   to bits = min(log2(N/B) + 1, log2 N) (b = search_bits), besides tau_r: a
+   coefficient f turns by exp(2 pi i f / 2^m) at shift N / 2^m, so each
+   shifted bucket decides one digit of f (the candidate whose predicted turn
+   best matches), a decision with a margin of 1/2^b of a turn; the bits fix
+   sigma f to one value in a window of two buckets around the bucket.  A
+   located f is kept when it hashes back to the bucket and every shifted
+   bucket matches the lone-coefficient prediction within a residual of 1/4
+   of its energy, valued by energy estimation.  More robust to noise than
+   phase encoding (whose one-sample phase must resolve f to 1 of N); needs
+   1 + ceil(bits / b) bucketizations per iteration, whose buffers and the
+   top-K ranks must fit one CTA's shared memory (160 KB). */
+#define SFFT_METHOD_SEARCH 3
 
 /* Combination of a candidate's L per-loop estimates (step a6; "The method of
    estimating the value").  MEDIAN: the coordinate-wise median, robust to

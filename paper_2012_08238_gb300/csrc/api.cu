@@ -122,6 +122,9 @@ constexpr int kHostChunks = 8;  // host-buffer batches: copies of chunk c+1 over
 constexpr int kScanCtasPerSm = 8;  // resident 256-thread scan CTAs per SM
 constexpr int kScanWaves = 1;
 
+// Methods of the iterative framework: one CTA per job runs every iteration.
+inline bool iterative(uint32_t method) { return method == kMethodPhase || method == kMethodSearch; }
+
 // Work split of one plan for the gather and vote kernels.
 void decompose(PlanDev &P) {
     P.tb = std::min<uint32_t>(P.B, 256);
@@ -130,8 +133,8 @@ void decompose(PlanDev &P) {
     // about one CTA per SM per signal (measured best of 76..600 at the
     // N = 2^20, B = 512, L = 12 workload: longer CTAs amortise the set-up,
     // fewer chunks leave fewer partials to sum)
-    // (phase encoding gathers one loop per launch)
-    const uint32_t loops = P.method == kMethodPhase ? 1u : P.L;
+    // (phase encoding and the search gather one loop per launch)
+    const uint32_t loops = iterative(P.method) ? 1u : P.L;
     uint32_t want = (kNumSms + P.tiles * loops - 1) / (P.tiles * loops);
     want = std::max<uint32_t>(1, std::min<uint32_t>(want, P.rounds));
     P.rpc = (P.rounds + want - 1) / want;
@@ -157,7 +160,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
         off += align256(bytes);
         return at;
     };
-    const bool phase = P.method == kMethodPhase;
+    const bool phase = iterative(P.method);
     // phase encoding keeps the two shifts' partials and bucket values in rows 0 and 1
     const size_t L = phase ? std::max<uint32_t>(P.L, 2) : P.L, B = P.B;
     o.plan = take(sizeof(PlanDev));
@@ -187,7 +190,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
 // Sizes and work split of a plan, without touching the device.
 void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
                    int64_t *cap, uint32_t method, uint32_t Bc, uint32_t estimator = kEstMedian,
-                   uint32_t refine = 0) {
+                   uint32_t refine = 0, uint32_t srch_b = 1) {
     memset(&P, 0, sizeof(P));
     const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     P.N = (uint32_t)N;
@@ -208,6 +211,7 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.method = method;
     P.estimator = estimator;
     P.refine = refine;
+    P.srch_b = srch_b;
     if (method == kMethodComb) {
         P.Bc = Bc;
         P.logBc = ilog2(Bc);
@@ -215,8 +219,8 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     }
     decompose(P);
     *cap = std::min<int64_t>(N, (int64_t)(L - T + 1) * nsel * (N / B));
-    // phase encoding: each iteration adds at most B found coefficients
-    if (method == kMethodPhase) *cap = std::min<int64_t>(N, (int64_t)L * B);
+    // phase encoding, search: each iteration adds at most B found coefficients
+    if (iterative(method)) *cap = std::min<int64_t>(N, (int64_t)L * B);
     P.cap = (uint32_t)*cap;
 }
 
@@ -224,15 +228,16 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
 
 size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
                          int32_t method) {
-    if (method == SFFT_METHOD_PHASE) c = T = 1;
+    if (method == SFFT_METHOD_PHASE || method == SFFT_METHOD_SEARCH) c = T = 1;
     if (check_sizes(N, K, B, w, L, c, T) != SFFT_OK) return 0;
     PlanDev P;
     int64_t cap;
     // (a comb plan's residue tables are a few KB; sized here at the largest default)
     fill_plan_dev(P, N, K, B, w, L, c, T, &cap,
-                  method == SFFT_METHOD_PHASE  ? kMethodPhase
-                  : method == SFFT_METHOD_COMB ? kMethodComb
-                                               : kMethodVoting,
+                  method == SFFT_METHOD_PHASE    ? kMethodPhase
+                  : method == SFFT_METHOD_COMB   ? kMethodComb
+                  : method == SFFT_METHOD_SEARCH ? kMethodSearch
+                                                 : kMethodVoting,
                   (uint32_t)std::min<int64_t>(N, kMaxComb));
     return layout_of(P, cap).total;
 }
@@ -258,6 +263,8 @@ struct Sizes {
     uint32_t max_cap = 0;  // phase encoding: largest found-list capacity
     bool comb = false;     // every job votes behind the spike-train pre-filter
     uint32_t max_Bc = 0;   // comb: largest number of residue classes
+    bool search = false;   // every job locates by binary / multi-scale search
+    uint32_t max_nbuf = 0; // search: largest count of bucket buffers
     bool refine = false;   // some job refines its output
     uint32_t max_rK = 0;   // refinement: largest K of the refining jobs
 };
@@ -265,9 +272,11 @@ struct Sizes {
 Sizes plan_sizes(const sfft_plan *p) {
     Sizes z;
     z.max_L = p->h.L;
-    if (p->h.method == kMethodPhase) {
+    if (iterative(p->h.method)) {
         // one CTA per job (the select slot of the batch maps)
         z.phase = true;
+        z.search = p->h.method == kMethodSearch;
+        z.max_nbuf = z.search ? search_nbuf(p->h.logN, p->h.logB, p->h.srch_b) : 0u;
         z.max_cap = p->h.cap;
         z.gather = 0;
         z.select = 1;
@@ -301,7 +310,9 @@ Sizes plan_sizes(const sfft_plan *p) {
 cudaError_t launch_phase(const Launch &lj, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-    if ((e = launch_pe(lj, z.jobs, z.max_B, z.max_K, z.max_cap, s)) != cudaSuccess) return e;
+    if ((e = z.search ? launch_bs(lj, z.jobs, z.max_B, z.max_K, z.max_cap, z.max_nbuf, s)
+                      : launch_pe(lj, z.jobs, z.max_B, z.max_K, z.max_cap, s)) != cudaSuccess)
+        return e;
     for (int i = 1; ev && i <= 6; ++i)
         if ((e = cudaEventRecord(ev[i], s)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -481,12 +492,24 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
         set_error("only precision 0 (FP32 FFT) is implemented");
         return SFFT_ENOTIMPL;
     }
-    if (o.method != SFFT_METHOD_VOTING && o.method != SFFT_METHOD_PHASE && o.method != SFFT_METHOD_COMB) {
-        set_error("sfft_opts.method must be SFFT_METHOD_VOTING, SFFT_METHOD_PHASE or SFFT_METHOD_COMB");
+    if (o.method != SFFT_METHOD_VOTING && o.method != SFFT_METHOD_PHASE && o.method != SFFT_METHOD_COMB &&
+        o.method != SFFT_METHOD_SEARCH) {
+        set_error("sfft_opts.method must be SFFT_METHOD_VOTING, SFFT_METHOD_PHASE, SFFT_METHOD_COMB or "
+                  "SFFT_METHOD_SEARCH");
         return SFFT_EINVAL;
     }
-    const bool phase = o.method == SFFT_METHOD_PHASE;
+    const bool search = o.method == SFFT_METHOD_SEARCH;
+    const bool phase = o.method == SFFT_METHOD_PHASE || search;  // the iterative-framework methods
     const bool comb = o.method == SFFT_METHOD_COMB;
+    if (!search && o.search_bits != 0) {
+        set_error("sfft_opts.search_bits applies to SFFT_METHOD_SEARCH only");
+        return SFFT_EINVAL;
+    }
+    const int32_t sb = search ? (o.search_bits > 0 ? o.search_bits : 1) : 1;
+    if (sb < 1 || sb > 4) {
+        set_error("sfft_opts.search_bits must be 1..4 (1: binary search)");
+        return SFFT_EINVAL;
+    }
     if (!comb && o.comb != 0) {
         set_error("sfft_opts.comb applies to SFFT_METHOD_COMB only");
         return SFFT_EINVAL;
@@ -528,6 +551,21 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
         Bc = (uint32_t)bc;
     }
 
+    if (search) {
+        // one CTA holds the job's bucket buffers and its top-K ranks
+        const uint32_t logN = ilog2(N), logB = ilog2(B);
+        uint64_t rank = 1024;
+        while (rank < (uint64_t)K) rank <<= 1;
+        const uint64_t fcap = std::min<int64_t>(N, (int64_t)L * B);  // found-list capacity
+        const uint64_t tail = std::max<uint64_t>(12ull * rank, fcap <= kPeSmemFound ? 16ull * fcap : 0ull);
+        const uint64_t bytes = 8ull * search_nbuf(logN, logB, (uint32_t)sb) * B + 8ull * (B / 2 + 1) + tail;
+        if (bytes > kSearchSmemMax) {
+            set_error("SFFT_METHOD_SEARCH: the bucket buffers (1 + ceil((log2(N/B) + 1) / search_bits) of B each) "
+                      "and the top-K ranks exceed one CTA's shared memory");
+            return SFFT_EINVAL;
+        }
+    }
+
     sfft_plan *p = new (std::nothrow) sfft_plan();
     if (!p) {
         set_error("host allocation failed");
@@ -547,7 +585,7 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
 
     PlanDev &P = p->h;
     fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc,
-                  o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian, (uint32_t)o.refine);
+                  o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian, (uint32_t)o.refine, (uint32_t)sb);
     // (comb plans: loops L and L+1 give the comb shifts)
     loop_params_host(N, L + (comb ? (int32_t)kCombShifts : 0), seed, P.sigma, P.tau, p->sigma_inv);
     const Layout lay = layout_of(P, p->cap);
@@ -611,7 +649,7 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     const uint32_t *d_sigma = reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(p->d) + offsetof(PlanDev, sigma));
     const uint32_t *d_tau = reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(p->d) + offsetof(PlanDev, tau));
     if ((e = plan_samples_touched(P.N, P.w, P.L, d_sigma, d_tau, static_cast<uint32_t *>(tmp), d_count,
-                                  phase ? 1 : 0, s)) != cudaSuccess)
+                                  phase ? 1 : 0, s, search ? P.srch_b : 0u, P.logB)) != cudaSuccess)
         return fail(e, "samples touched");
     unsigned long long host2[2] = {0, 0};
     if ((e = cudaMemcpyAsync(host2, d_count, sizeof(host2), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -686,7 +724,7 @@ extern "C" sfft_status sfft_plan_last_stats(const sfft_plan *p, sfft_exec_stats 
     }
     uint32_t c[kNumCounters];
     SFFT_CUDA_TRY(cudaMemcpy(c, p->h.ctr, sizeof(c), cudaMemcpyDeviceToHost));
-    if (p->h.method == kMethodPhase) {
+    if (iterative(p->h.method)) {
         // found coefficients (kNGe), iterations run, bucket-energy threshold
         st->candidates = -1;
         st->estimated = c[kNGe];
@@ -716,7 +754,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
         return SFFT_EINVAL;
     }
     const Launch ln = single(make_job(p, x_dev, idx_dev, val_dev, k_out_dev));
-    if (p->h.method == kMethodPhase)
+    if (iterative(p->h.method))
         SFFT_CUDA_TRY(launch_phase(ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     else
         SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
@@ -791,6 +829,8 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
         z.est_smem = (i == 0 || z.est_smem) && s.est_smem ? std::max(z.est_smem, s.est_smem) : 0u;
         z.phase = i == 0 ? s.phase : z.phase;  // one method per batch (callers split mixed lists)
+        z.search = i == 0 ? s.search : z.search;
+        z.max_nbuf = std::max(z.max_nbuf, s.max_nbuf);
         z.max_L = std::max(z.max_L, s.max_L);
         z.max_cap = std::max(z.max_cap, s.max_cap);
         z.comb = i == 0 ? s.comb : z.comb;
@@ -882,7 +922,7 @@ sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, cons
                 return SFFT_EINVAL;
             }
         if (plans[i]->h.method != plans[0]->h.method) {
-            set_error("a batch mixes location methods (voting and phase encoding run as separate batches)");
+            set_error("a batch mixes location methods (each method runs as a separate batch)");
             return SFFT_EINVAL;
         }
     }

@@ -1779,6 +1779,223 @@ __global__ void __launch_bounds__(kThreads) k_pe_job(Launch ln, uint32_t cap, ui
     rank_records(P, J, tk, cap, S, min(S, P.K));
 }
 
+// ------------------------------------- location by binary / multi-scale search
+// sFFT4.0 / MPFFT-style variant ("The method of binary search or multi-scale
+// search"): the iterative framework of k_pe_job, but iteration r bucketizes
+// the signal at the S shifts tau_r + s_j (s_0 = 0, s_{j+1} = N / 2^m_j) and
+// reads each bucket above the threshold digit by digit: a coefficient f
+// turns by exp(2 pi i f / 2^m) at shift N / 2^m, so with the lower digits r
+// known, digit j (b bits) is the d whose predicted turn of f = r + d 2^(jb)
+// best matches z_{j+1} conj(z_0).  The bits = min(log2(N/B) + 1, log2 N)
+// decoded bits fix p = sigma f modulo 2^bits, one value in the window of two
+// bucket widths centred on the bucket; f is kept when it hashes back there
+// and every shifted bucket is z_0 turned by exp(2 pi i s_j f / N) up to a
+// residual of rho (S - 1) |z_0|^2 (a lone coefficient).
+
+// sigma^-1 mod 2^32 for odd sigma (so also mod N): sigma^2 = 1 (mod 8) holds
+// 3 bits, each Newton step doubles them
+__device__ __forceinline__ uint32_t inv_mod_2p32(uint32_t sigma) {
+    uint32_t x = sigma;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x *= 2u - sigma * x;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t bs_bits(const PlanDev &P) {
+    return min(P.logN - P.logB + 1u, P.logN);
+}
+
+// shift of search step j (0 for the base bucketization j = 0)
+__device__ __forceinline__ uint32_t bs_shift(const PlanDev &P, uint32_t j) {
+    if (j == 0) return 0u;
+    return P.N >> min(j * P.srch_b, bs_bits(P));
+}
+
+__global__ void __launch_bounds__(kThreads) k_bs_job(Launch ln, uint32_t cap, uint32_t fcap, uint32_t nbuf) {
+    // nbuf bucket buffers [B] (S rounded up to even), twiddles [B/2]; then
+    // the found list when it fits fcap entries (else it stays in P.surv), or
+    // the top-K buffer at the end
+    extern __shared__ float2 bs_s[];
+    __shared__ PlanDev P;
+    __shared__ Job J;
+    __shared__ uint32_t s_local, s_active, s_n;
+    __shared__ float s_thr, s_wmax[kThreads / 32];
+    __shared__ float2 red0[kThreads], red1[kThreads];
+    enter(ln, P, J, s_local);
+    const uint32_t B = P.B, logB = P.logB, N = P.N, NB = N >> logB;
+    const uint32_t bits = bs_bits(P), W = 1u << bits, b = P.srch_b;
+    const uint32_t S = 1 + (bits + b - 1) / b;  // bucketizations per iteration (<= nbuf)
+    float2 *tw = bs_s + (size_t)nbuf * B;
+    for (uint32_t k = threadIdx.x; k < B / 2; k += blockDim.x) tw[k] = __ldg(P.tw + k);
+    if (threadIdx.x == 0) s_n = 0;
+    const uint32_t TB = P.tb, PP = kThreads / TB;
+    const uint32_t jt = threadIdx.x & (TB - 1), sidx = threadIdx.x / TB;
+    const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
+    const float2 *__restrict__ x = J.x;
+    uint4 *F = P.cap <= fcap ? reinterpret_cast<uint4 *>(tw + B / 2 + (B & 1)) : P.surv;
+    uint32_t iters = 0;
+    for (uint32_t r = 0; r < P.L; ++r) {
+        const uint32_t sig = P.sigma[r], tau = P.tau[r];
+        // a1 at the shifts, two at a time, bucket tile by bucket tile
+        for (uint32_t sh = 0; sh < S; sh += 2) {
+            const uint32_t t0 = (tau + bs_shift(P, sh)) & P.mask;
+            const uint32_t t1 = sh + 1 < S ? (tau + bs_shift(P, sh + 1)) & P.mask : t0;
+            float2 *b0 = bs_s + (size_t)sh * B, *b1 = b0 + B;
+            for (uint32_t tile = 0; tile < P.tiles; ++tile) {
+                const uint32_t j = tile * TB + jt, jq = (j + P.halfw) & (B - 1);
+                float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
+#pragma unroll 4
+                for (uint32_t rr = sidx; rr < P.rounds; rr += PP) {
+                    const uint32_t q = rr * B + jq;
+                    const uint32_t i = sig * (q - P.halfw);
+                    const float g = __ldg(P.taps + q);
+                    const float2 v0 = __ldg(x + ((i + t0) & P.mask)), v1 = __ldg(x + ((i + t1) & P.mask));
+                    a0r = fmaf(g, v0.x, a0r);
+                    a0i = fmaf(g, v0.y, a0i);
+                    a1r = fmaf(g, v1.x, a1r);
+                    a1i = fmaf(g, v1.y, a1i);
+                }
+                red0[threadIdx.x] = make_float2(a0r, a0i);
+                red1[threadIdx.x] = make_float2(a1r, a1i);
+                __syncthreads();
+                if (sidx == 0) {
+                    float2 c0 = red0[jt], c1 = red1[jt];
+                    for (uint32_t k = 1; k < PP; ++k) {
+                        c0.x += red0[jt + k * TB].x;
+                        c0.y += red0[jt + k * TB].y;
+                        c1.x += red1[jt + k * TB].x;
+                        c1.y += red1[jt + k * TB].y;
+                    }
+                    const uint32_t br = __brev(j) >> (32 - logB);
+                    b0[br] = c0;
+                    b1[br] = c1;
+                }
+                __syncthreads();
+            }
+            fft2_smem(b0, b1, B, logB, tw);
+        }
+        const uint32_t nprev = s_n;
+        // subtraction of the found list from every shift's bucket (a fixed order)
+        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
+            for (uint32_t e = 0; e < nprev; ++e) {
+                const uint4 rec = F[e];
+                const uint32_t f = rec.x;
+                const uint32_t h = ((sig << sN) * f + cv) >> top;
+                const uint32_t d = (k - h) & (B - 1);
+                if (d != 0 && d != 1 && d != B - 1) continue;
+                // nu = (sigma f mod N) - k N/B, wrapped into [-N/2, N/2)
+                const int32_t nu = (int32_t)((((sig * f) & P.mask) - k * NB + N / 2) & P.mask) - (int32_t)(N / 2);
+                const float2 G = __ldg(P.gext + (nu + (int32_t)(3 * NB / 2)));
+                const float2 c0 = cmul(cmul(make_float2(__uint_as_float(rec.z), __uint_as_float(rec.w)),
+                                            turn_pos((tau << sN) * f)),
+                                       G);
+                for (uint32_t sh = 0; sh < S; ++sh) {
+                    const float2 c = sh ? cmul(c0, turn_pos((bs_shift(P, sh) * f) << sN)) : c0;
+                    float2 &z = bs_s[(size_t)sh * B + k];
+                    z.x -= c.x;
+                    z.y -= c.y;
+                }
+            }
+        }
+        if (threadIdx.x == 0) s_active = 0;
+        __syncthreads();
+        if (r == 0) {
+            float m = 0.f;
+            for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
+                m = fmaxf(m, bs_s[k].x * bs_s[k].x + bs_s[k].y * bs_s[k].y);
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+            if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = m;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float mm = 0.f;
+                for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2) mm = fmaxf(mm, s_wmax[w2]);
+                s_thr = 1e-6f * mm;
+            }
+            __syncthreads();
+        }
+        const float thr = s_thr;
+        uint32_t active = 0;
+        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
+            const float2 z0 = bs_s[k];
+            const float e0 = z0.x * z0.x + z0.y * z0.y;
+            if (!(e0 >= thr) || e0 == 0.f) continue;
+            ++active;
+            // digits of f, low to high: rb = f mod 2^lo so far
+            uint32_t rb = 0;
+            for (uint32_t j = 0, lo = 0; lo < bits; ++j, lo += b) {
+                const uint32_t m = min(lo + b, bits);
+                const float2 zj = bs_s[(size_t)(j + 1) * B + k];
+                const float2 rj = make_float2(zj.x * z0.x + zj.y * z0.y, zj.y * z0.x - zj.x * z0.y);  // zj conj(z0)
+                uint32_t best = 0;
+                float bestv = -INFINITY;
+                for (uint32_t dd = 0; dd < (1u << (m - lo)); ++dd) {
+                    const uint32_t cand = rb + (dd << lo);
+                    // Re(rj exp(-2 pi i cand / 2^m))
+                    const float2 u = turn_pos(cand << (32 - m));
+                    const float v = rj.x * u.x + rj.y * u.y;
+                    if (v > bestv) {
+                        bestv = v;
+                        best = dd;
+                    }
+                }
+                rb += best << lo;
+            }
+            // p = sigma f (mod N): p = sigma rb (mod W) in [k N/B - W/2, k N/B + W/2)
+            const uint32_t pr = (sig * rb) & (W - 1);
+            const uint32_t lo_p = (k * NB - W / 2) & P.mask;
+            const uint32_t p = (lo_p + ((pr - lo_p) & (W - 1))) & P.mask;
+            const uint32_t f = (inv_mod_2p32(sig) * p) & P.mask;
+            const uint32_t t = (sig << sN) * f + cv;
+            if ((t >> top) != k) continue;  // a neighbour's leakage
+            float res = 0.f;
+            for (uint32_t sh = 1; sh < S; ++sh) {
+                const float2 zj = bs_s[(size_t)sh * B + k];
+                const float2 pz = cmul(z0, turn_pos((bs_shift(P, sh) * f) << sN));
+                res += (zj.x - pz.x) * (zj.x - pz.x) + (zj.y - pz.y) * (zj.y - pz.y);
+            }
+            if (res > kSearchRho * (float)(S - 1) * e0) continue;  // not a lone coefficient
+            const uint32_t opos = P.logB < P.logN ? (t << P.logB) >> (P.logB + sN) : 0u;
+            const float2 v = turn_scale(z0, __ldg(P.ginv + opos), (tau << sN) * f);
+            bool merged = false;
+            for (uint32_t e2 = 0; e2 < nprev; ++e2) {
+                const uint4 rec = F[e2];
+                if (rec.x == f) {  // f has one home bucket: one writer per iteration
+                    F[e2] = make_uint4(f, 0u, __float_as_uint(__uint_as_float(rec.z) + v.x),
+                                       __float_as_uint(__uint_as_float(rec.w) + v.y));
+                    merged = true;
+                    break;
+                }
+            }
+            if (!merged) {
+                const uint32_t pos = atomicAdd(&s_n, 1u);  // < cap: at most B per iteration
+                F[pos] = make_uint4(f, 0u, __float_as_uint(v.x), __float_as_uint(v.y));
+            }
+        }
+        active = __reduce_add_sync(0xFFFFFFFFu, active);
+        if ((threadIdx.x & 31) == 0 && active) atomicAdd(&s_active, active);
+        __threadfence_block();
+        __syncthreads();
+        iters = r + 1;
+        if (s_active == 0) break;  // uniform
+    }
+    const uint32_t Sn = s_n;
+    if (threadIdx.x == 0) {
+        P.ctr[kNGe] = Sn;
+        P.ctr[kPeIter] = iters;
+        P.ctr[kTheta] = __float_as_uint(s_thr);
+    }
+    for (uint32_t i = threadIdx.x; i < Sn; i += blockDim.x) {
+        uint4 rec = F[i];
+        const float re = __uint_as_float(rec.z), im = __uint_as_float(rec.w);
+        rec.y = __float_as_uint(re * re + im * im);
+        P.surv[i] = rec;
+    }
+    __threadfence_block();
+    __syncthreads();
+    unsigned long long *tk = reinterpret_cast<unsigned long long *>(tw + B / 2 + (B & 1));
+    rank_records(P, J, tk, cap, Sn, min(Sn, P.K));
+}
+
 // Stage kernels for the single-step entry points.
 template <int LT>
 __global__ void k_estimate_list(const PlanDev *pd, const float2 *zhat, const int32_t *cand, uint32_t n,
@@ -2111,6 +2328,21 @@ cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, cuda
     cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_refine<<<njobs, kRefineThreads, smem, s>>>(ln);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bs(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t max_K, uint32_t max_cap,
+                      uint32_t max_nbuf, cudaStream_t s) {
+    if (njobs == 0) return cudaSuccess;
+    uint32_t cap = kRankMax;
+    while (cap < max_K) cap <<= 1;
+    const size_t tables = (sizeof(float2) * ((size_t)max_nbuf * max_B + max_B / 2 + 1) + 15) & ~(size_t)15;
+    const size_t rank = cap * (sizeof(unsigned long long) + sizeof(uint32_t));
+    const uint32_t fcap = max_cap <= kPeSmemFound ? max_cap : 0u;
+    const int smem = (int)(tables + std::max<size_t>(rank, sizeof(uint4) * fcap));
+    cudaError_t e = cudaFuncSetAttribute(k_bs_job, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_bs_job<<<njobs, kThreads, smem, s>>>(ln, cap, fcap, max_nbuf);
     return cudaGetLastError();
 }
 

@@ -98,17 +98,26 @@ __global__ void k_twiddle(uint32_t B, float2 *tw) {
 }
 
 // pair: also the sample one past each (the phase-encoding shift tau + 1)
+// Marks the samples the loops read: at shift tau_l (mode 0), also tau_l + 1
+// (mode 1: phase encoding), or at tau_l + s for the nsh shifts s of the
+// search (mode 2: s_0 = 0, s_j = N >> min(j b, bits)).
 __global__ void k_mark(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma, const uint32_t *tau,
-                       uint32_t *bitmap, int pair) {
+                       uint32_t *bitmap, int mode, uint32_t b, uint32_t bits, uint32_t nsh) {
     const uint64_t total = (uint64_t)L * w;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t l = (uint32_t)(t / w), q = (uint32_t)(t % w);
         const uint32_t i = (sigma[l] * (q - w / 2) + tau[l]) & (N - 1);
         atomicOr(bitmap + (i >> 5), 1u << (i & 31));
-        if (pair) {
+        if (mode == 1) {
             const uint32_t i1 = (i + 1) & (N - 1);
             atomicOr(bitmap + (i1 >> 5), 1u << (i1 & 31));
+        } else if (mode == 2) {
+            for (uint32_t j = 1; j < nsh; ++j) {
+                const uint32_t m = j * b < bits ? j * b : bits;
+                const uint32_t ij = (i + (N >> m)) & (N - 1);
+                atomicOr(bitmap + (ij >> 5), 1u << (ij & 31));
+            }
         }
     }
 }
@@ -168,7 +177,7 @@ cudaError_t plan_twiddles(uint32_t n, float2 *tw, cudaStream_t s) {
 
 cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
                                  const uint32_t *tau, uint32_t *bitmap, unsigned long long *count, int pair,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, uint32_t search_b, uint32_t logB) {
     const uint32_t nwords = (N + 31) / 32;
     cudaError_t e = cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * nwords, s);
     if (e != cudaSuccess) return e;
@@ -176,7 +185,13 @@ cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint3
     if (e != cudaSuccess) return e;
     const uint64_t total = (uint64_t)L * w;
     const uint32_t blocks = (uint32_t)std::min<uint64_t>((total + 255) / 256, 65535);
-    k_mark<<<blocks, 256, 0, s>>>(N, w, L, sigma, tau, bitmap, pair);
+    uint32_t logN = 0, bits = 0, nsh = 1;
+    while ((1u << logN) < N) ++logN;
+    if (search_b) {
+        bits = logN - logB + 1 < logN ? logN - logB + 1 : logN;
+        nsh = 1 + (bits + search_b - 1) / search_b;
+    }
+    k_mark<<<blocks, 256, 0, s>>>(N, w, L, sigma, tau, bitmap, search_b ? 2 : (pair ? 1 : 0), search_b, bits, nsh);
     const uint32_t pb = std::min<uint32_t>((nwords + 255) / 256, 65535);
     k_popc<<<pb, 256, 0, s>>>(bitmap, nwords, count);
     return cudaGetLastError();

@@ -34,7 +34,7 @@ int64_t now_ns() {
 
 using PlanKey =
     std::tuple<int64_t, int64_t, int32_t, int32_t, int32_t, uint64_t, int32_t, int32_t, int32_t, int32_t, int32_t,
-               int32_t>;
+               int32_t, int32_t>;
 
 struct Request {
     uint64_t ticket = 0;
@@ -298,7 +298,7 @@ extern "C" sfft_status sfft_submit(sfft_server *s, const sfft_request *q, uint64
     if (!r) return SFFT_ENOMEM;
     r->req = *q;
     r->key = PlanKey(q->N, q->w, q->K, q->B, q->L, q->seed, c, T, q->opts.method, q->opts.comb, q->opts.estimator,
-                     q->opts.refine);
+                     q->opts.refine, q->opts.search_bits);
     r->t_submit = now_ns();
     {
         std::lock_guard<std::mutex> lk(s->mu);

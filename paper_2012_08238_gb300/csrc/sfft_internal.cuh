@@ -20,6 +20,9 @@ constexpr uint32_t kMethodVoting = 0;  // sFFT1.0-style voting (the default)
 constexpr uint32_t kMethodPhase = 1;   // sFFT3.0-style phase encoding, iterative framework
 constexpr uint32_t kPeSmemFound = 2048;  // phase encoding: found lists up to this size live in shared memory
 constexpr uint32_t kMethodComb = 2;     // voting behind the spike-train pre-filter
+constexpr uint32_t kMethodSearch = 3;   // sFFT4.0 / MPFFT-style location by binary or multi-scale search
+constexpr float kSearchRho = 0.25f;     // search: residual bound of a lone coefficient (relative)
+constexpr uint32_t kSearchSmemMax = 160 * 1024;  // search: bucket buffers of one job in shared memory
 constexpr uint32_t kCombShifts = 2;     // comb subsamplings (shifts tau of loops L, L+1)
 constexpr uint32_t kMaxComb = 8192;     // largest number of residue classes
 constexpr uint32_t kEstMedian = 0;      // a6: coordinate-wise median of the per-loop estimates
@@ -67,7 +70,8 @@ struct PlanDev {
     uint32_t use_bits;                        // 32 <= B <= 512 (and T = M for the mean): table bits in registers
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
-    uint32_t method;                          // kMethodVoting, kMethodPhase or kMethodComb
+    uint32_t method;                          // kMethodVoting, kMethodPhase, kMethodComb or kMethodSearch
+    uint32_t srch_b;                          // search: bits per digit (1: binary search)
     uint32_t Bc, logBc, ncls;                 // comb: residue classes, kept classes
     uint32_t estimator;                       // kEstMedian or kEstMean
     uint32_t refine;                          // refinement passes (0: none)
@@ -154,6 +158,16 @@ cudaError_t launch_comb(const Launch &ln, uint32_t njobs, uint32_t max_Bc, cudaS
 // kPeSmemFound entries stay in shared memory).
 cudaError_t launch_pe(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t max_K, uint32_t max_cap,
                       cudaStream_t s);
+// Search-location variant: one CTA per job runs all its iterations (max_nbuf:
+// the largest count of bucket buffers, 1 + ceil(bits / b) rounded up to even).
+cudaError_t launch_bs(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t max_K, uint32_t max_cap,
+                      uint32_t max_nbuf, cudaStream_t s);
+// Bucket buffers of a search plan: 1 + ceil(min(log2(N/B) + 1, log2 N) / b), rounded up to even.
+inline uint32_t search_nbuf(uint32_t logN, uint32_t logB, uint32_t b) {
+    const uint32_t bits = logN - logB + 1 < logN ? logN - logB + 1 : logN;
+    const uint32_t S = 1 + (bits + b - 1) / b;
+    return (S + 1) & ~1u;
+}
 // Iterative-framework refinement of the jobs' outputs: one CTA per job (ln:
 // one per job) runs all the job's passes; jobs with refine = 0 return at
 // once.  max_K: the largest K of the refining jobs (<= kRefineMaxK).
@@ -169,10 +183,12 @@ cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 
 cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, cudaStream_t s);
 // exp(-2 pi i k / n), k < n/2 (FP64 -> FP32)
 cudaError_t plan_twiddles(uint32_t n, float2 *tw, cudaStream_t s);
-// pair: count the samples one past each too (phase encoding's second shift)
+// pair: count the samples one past each too (phase encoding's second shift);
+// search_b > 0 (search plans with B = 2^logB buckets): the samples at every
+// search shift instead
 cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
                                  const uint32_t *tau, uint32_t *bitmap, unsigned long long *count, int pair,
-                                 cudaStream_t s);
+                                 cudaStream_t s, uint32_t search_b = 0, uint32_t logB = 0);
 
 }  // namespace sfft
 

@@ -28,7 +28,7 @@ SFFT_OK, SFFT_EINVAL, SFFT_ENOMEM, SFFT_ECUDA, SFFT_EBUSY, SFFT_ETIMEDOUT, SFFT_
 
 class sfft_opts(ctypes.Structure):
     _fields_ = [("c", _i32), ("T", _i32), ("precision", _i32), ("method", _i32), ("comb", _i32),
-                ("estimator", _i32), ("refine", _i32)]
+                ("estimator", _i32), ("refine", _i32), ("search_bits", _i32)]
 
 
 class sfft_plan_info(ctypes.Structure):
@@ -181,14 +181,16 @@ def sfft_plan_create(N, K, B, w, L, seed, opts: sfft_opts | None = None) -> Plan
 SFFT_METHOD_VOTING = 0
 SFFT_METHOD_PHASE = 1
 SFFT_METHOD_COMB = 2
+SFFT_METHOD_SEARCH = 3
 SFFT_ESTIMATOR_MEDIAN = 0
 SFFT_ESTIMATOR_MEAN = 1
 SFFT_MAX_REFINE = 8
 
 
 def sfft_plan_create_ex(N, K, B, w, L, seed, c=0, T=0, precision=0, method=SFFT_METHOD_VOTING, comb=0,
-                        estimator=SFFT_ESTIMATOR_MEDIAN, refine=0) -> Plan:
-    return sfft_plan_create(N, K, B, w, L, seed, sfft_opts(c, T, precision, method, comb, estimator, refine))
+                        estimator=SFFT_ESTIMATOR_MEDIAN, refine=0, search_bits=0) -> Plan:
+    return sfft_plan_create(N, K, B, w, L, seed,
+                            sfft_opts(c, T, precision, method, comb, estimator, refine, search_bits))
 
 
 def sfft_plan_destroy(plan: Plan):
@@ -326,8 +328,9 @@ def sfft_server_destroy(srv: Server):
 
 
 def sfft_submit(srv: Server, N, K, B, w, L, seed, x, idx, val, c=0, T=0, method=0, comb=0, estimator=0,
-                refine=0) -> int:
-    req = sfft_request(N, w, K, B, L, seed, sfft_opts(c, T, 0, method, comb, estimator, refine), _addr(x), _addr(idx),
+                refine=0, search_bits=0) -> int:
+    req = sfft_request(N, w, K, B, L, seed, sfft_opts(c, T, 0, method, comb, estimator, refine, search_bits),
+                       _addr(x), _addr(idx),
                        _addr(val))
     ticket = _u64()
     _check(lib().sfft_submit(srv.handle, ctypes.byref(req), ctypes.byref(ticket)))
