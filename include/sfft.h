@@ -105,8 +105,10 @@ typedef struct {
 /* SFFT_METHOD_SEARCH: location by binary or multi-scale search (sFFT4.0 /
    MPFFT-style; "The method of binary search or multi-scale search"; Table 1)
    in the iterative framework of SFFT_METHOD_PHASE (L = iterations; found
-   coefficients subtracted before each bucketization; threshold 1e-6 of the
-   largest bucket energy of iteration 0; top K of the found set).  Iteration
+   coefficients subtracted before each bucketization; top K of the found
+   set; threshold: the larger of 1e-6 of the largest and 20 times the median
+   bucket energy of iteration 0, so that a noisy signal stops once nothing
+   above its noise floor remains).  Iteration
    r bucketizes the signal at the shifts tau_r + N / 2^m, m = b, 2b, ..., up
    to bits = min(log2(N/B) + 1, log2 N) (b = search_bits), besides tau_r: a
    coefficient f turns by exp(2 pi i f / 2^m) at shift N / 2^m, so each

@@ -102,8 +102,8 @@ def _bind(lib):
                                     _p, _p, _p]),
         "oracle_sfft_bs": (
             _i64,
-            [_i64, _i64, _i64, _i64, _int, _int, ctypes.c_double, ctypes.c_double, _u64, _p, _p, _p, _p, _p, _p,
-             _p],
+            [_i64, _i64, _i64, _i64, _int, _int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _u64, _p, _p,
+             _p, _p, _p, _p, _p],
         ),
         "oracle_sfft_pe": (
             _i64,
@@ -458,9 +458,9 @@ class PlanBS:
     """Search-location variant: R iterations at most, digits of b bits
     (1: binary search, 2: multi-scale search with l = 4)."""
 
-    def __init__(self, N, K, B, w, R, seed, b=1, eta=1e-6, rho=0.25):
+    def __init__(self, N, K, B, w, R, seed, b=1, eta=1e-6, kappa=20.0, rho=0.25):
         self.N, self.K, self.B, self.w, self.R, self.seed = N, K, B, w, R, seed
-        self.b, self.eta, self.rho = b, eta, rho
+        self.b, self.eta, self.kappa, self.rho = b, eta, kappa, rho
         self.g = window_taps(N, B, w)
         self.Gfull = filter_gain_full(N, w, self.g)
 
@@ -472,7 +472,8 @@ def sfft_bs(plan: PlanBS, x):
     val = np.zeros(max(plan.K, 1), np.complex128)
     iters = np.zeros(1, np.int32)
     nfound = np.zeros(1, np.int64)
-    kout = _load().oracle_sfft_bs(plan.N, plan.K, plan.B, plan.w, plan.R, plan.b, plan.eta, plan.rho, plan.seed,
+    kout = _load().oracle_sfft_bs(plan.N, plan.K, plan.B, plan.w, plan.R, plan.b, plan.eta, plan.kappa, plan.rho,
+                                  plan.seed,
                                   _ptr(plan.g), _ptr(plan.Gfull), _ptr(x), _ptr(idx), _ptr(val), _ptr(iters),
                                   _ptr(nfound))
     if kout < 0:

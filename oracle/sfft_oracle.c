@@ -838,9 +838,15 @@ int64_t oracle_bs_locate(int64_t N, int64_t B, int b, int64_t sigma, int64_t sig
     *active_out = active;
     return n;
 }
-int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b, double eta, double rho,
-                       uint64_t seed, const double *g, const double *Gfull, const double *x, int32_t *idx,
-                       double *val, int *iters_out, int64_t *nfound_out)
+static int flt_desc(const void *a, const void *b)
+{
+    float x = *(const float *)a, y = *(const float *)b;
+    return (x < y) - (x > y);
+}
+
+int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b, double eta, double kappa,
+                       double rho, uint64_t seed, const double *g, const double *Gfull, const double *x,
+                       int32_t *idx, double *val, int *iters_out, int64_t *nfound_out)
 {
     if (!is_pow2(N) || N < 2 || !is_pow2(B) || B > N || w < B || w % B || R < 1 || K < 0 || b < 1 || b > 4)
         return -1;
@@ -873,12 +879,21 @@ int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b,
             oracle_pe_subtract(N, B, sigma[r], tj, Gfull, nf, list, lval, z + 2 * j * B);
         }
         if (r == 0) {
+            /* eta of the largest bucket energy, and at least kappa times the
+               median one (the noise floor of a noisy signal; leakage-level
+               for an exactly sparse one) */
             double emax = 0.0;
+            float *ek = (float *)malloc(sizeof(float) * (size_t)B);
             for (int64_t k = 0; k < B; ++k) {
                 double e = z[2 * k] * z[2 * k] + z[2 * k + 1] * z[2 * k + 1];
                 if (e > emax) emax = e;
+                ek[k] = (float)e;
             }
+            qsort(ek, (size_t)B, sizeof(float), flt_desc);
+            double emed = (double)ek[(B + 1) / 2 - 1]; /* the ceil(B/2)-th largest, as binary32 */
+            free(ek);
             thr = eta * emax;
+            if (kappa * emed > thr) thr = kappa * emed;
         }
         int64_t active = 0;
         int64_t n = oracle_bs_locate(N, B, b, sigma[r], sinv[r], tau[r], Gfull, z, thr, rho, nfi, nfv, &active);

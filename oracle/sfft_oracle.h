@@ -226,13 +226,14 @@ int64_t oracle_bs_locate(int64_t N, int64_t B, int b, int64_t sigma, int64_t sig
                          double *v_out, int64_t *active_out);
 
 /* Whole pipeline: as oracle_sfft_pe (iterations r with loop parameters r,
-   subtraction of the found set, threshold eta times the largest bucket
-   energy of iteration 0, accumulation of values found again, top K), with
-   the location by search in radix 2^b (b = 1: binary search; b > 1:
-   multi-scale search) over the shifts tau_r + s[j]. */
-int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b, double eta, double rho,
-                       uint64_t seed, const double *g, const double *Gfull, const double *x, int32_t *idx,
-                       double *val, int *iters_out, int64_t *nfound_out);
+   subtraction of the found set, accumulation of values found again, top K),
+   with the location by search in radix 2^b (b = 1: binary search; b > 1:
+   multi-scale search) over the shifts tau_r + s[j].  Threshold: the larger
+   of eta times the largest and kappa times the median (the ceil(B/2)-th
+   largest, as binary32) bucket energy of iteration 0. */
+int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b, double eta, double kappa,
+                       double rho, uint64_t seed, const double *g, const double *Gfull, const double *x,
+                       int32_t *idx, double *val, int *iters_out, int64_t *nfound_out);
 
 #ifdef __cplusplus
 }

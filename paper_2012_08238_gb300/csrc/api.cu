@@ -557,7 +557,8 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
         uint64_t rank = 1024;
         while (rank < (uint64_t)K) rank <<= 1;
         const uint64_t fcap = std::min<int64_t>(N, (int64_t)L * B);  // found-list capacity
-        const uint64_t tail = std::max<uint64_t>(12ull * rank, fcap <= kPeSmemFound ? 16ull * fcap : 0ull);
+        const uint64_t tail = std::max<uint64_t>(std::max<uint64_t>(12ull * rank, fcap <= kPeSmemFound ? 16ull * fcap : 0ull),
+                                                 4ull * B);
         const uint64_t bytes = 8ull * search_nbuf(logN, logB, (uint32_t)sb) * B + 8ull * (B / 2 + 1) + tail;
         if (bytes > kSearchSmemMax) {
             set_error("SFFT_METHOD_SEARCH: the bucket buffers (1 + ceil((log2(N/B) + 1) / search_bits) of B each) "

@@ -1786,7 +1786,9 @@ __global__ void __launch_bounds__(kThreads) k_pe_job(Launch ln, uint32_t cap, ui
 // reads each bucket above the threshold digit by digit: a coefficient f
 // turns by exp(2 pi i f / 2^m) at shift N / 2^m, so with the lower digits r
 // known, digit j (b bits) is the d whose predicted turn of f = r + d 2^(jb)
-// best matches z_{j+1} conj(z_0).  The bits = min(log2(N/B) + 1, log2 N)
+// best matches z_{j+1} conj(z_0) (threshold: the larger of 1e-6 of the
+// largest and kSearchKappa times the median bucket energy of iteration 0).
+// The bits = min(log2(N/B) + 1, log2 N)
 // decoded bits fix p = sigma f modulo 2^bits, one value in the window of two
 // bucket widths centred on the bucket; f is kept when it hashes back there
 // and every shifted bucket is z_0 turned by exp(2 pi i s_j f / N) up to a
@@ -1821,6 +1823,7 @@ __global__ void __launch_bounds__(kThreads) k_bs_job(Launch ln, uint32_t cap, ui
     __shared__ uint32_t s_local, s_active, s_n;
     __shared__ float s_thr, s_wmax[kThreads / 32];
     __shared__ float2 red0[kThreads], red1[kThreads];
+    __shared__ uint32_t s_hist[256], s_wsum[kThreads / 32], s_prefix, s_need;
     enter(ln, P, J, s_local);
     const uint32_t B = P.B, logB = P.logB, N = P.N, NB = N >> logB;
     const uint32_t bits = bs_bits(P), W = 1u << bits, b = P.srch_b;
@@ -1900,16 +1903,26 @@ __global__ void __launch_bounds__(kThreads) k_bs_job(Launch ln, uint32_t cap, ui
         if (threadIdx.x == 0) s_active = 0;
         __syncthreads();
         if (r == 0) {
+            // 1e-6 of the largest bucket energy, and at least kSearchKappa times
+            // the median one (the ceil(B/2)-th largest: the noise floor of a
+            // noisy signal); the energies' bits go through the tail area (the
+            // found list is still empty, the top-K buffer not yet in use)
+            uint32_t *ek = reinterpret_cast<uint32_t *>(tw + B / 2 + (B & 1));
             float m = 0.f;
-            for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
-                m = fmaxf(m, bs_s[k].x * bs_s[k].x + bs_s[k].y * bs_s[k].y);
+            for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
+                const float e = bs_s[k].x * bs_s[k].x + bs_s[k].y * bs_s[k].y;
+                m = fmaxf(m, e);
+                ek[k] = __float_as_uint(e);
+            }
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
             if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = m;
             __syncthreads();
+            const float emed = __uint_as_float(
+                block_kth_largest<kThreads, false>(ek, B, (B + 1) / 2, s_hist, s_wsum, &s_prefix, &s_need));
             if (threadIdx.x == 0) {
                 float mm = 0.f;
                 for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2) mm = fmaxf(mm, s_wmax[w2]);
-                s_thr = 1e-6f * mm;
+                s_thr = fmaxf(1e-6f * mm, kSearchKappa * emed);
             }
             __syncthreads();
         }
@@ -2339,7 +2352,9 @@ cudaError_t launch_bs(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t
     const size_t tables = (sizeof(float2) * ((size_t)max_nbuf * max_B + max_B / 2 + 1) + 15) & ~(size_t)15;
     const size_t rank = cap * (sizeof(unsigned long long) + sizeof(uint32_t));
     const uint32_t fcap = max_cap <= kPeSmemFound ? max_cap : 0u;
-    const int smem = (int)(tables + std::max<size_t>(rank, sizeof(uint4) * fcap));
+    // tail: the top-K ranks or the found list, and the energies' bits of the threshold
+    const size_t tail = std::max<size_t>(std::max<size_t>(rank, sizeof(uint4) * fcap), sizeof(uint32_t) * max_B);
+    const int smem = (int)(tables + tail);
     cudaError_t e = cudaFuncSetAttribute(k_bs_job, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_bs_job<<<njobs, kThreads, smem, s>>>(ln, cap, fcap, max_nbuf);

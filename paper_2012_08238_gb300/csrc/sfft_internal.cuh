@@ -22,6 +22,7 @@ constexpr uint32_t kPeSmemFound = 2048;  // phase encoding: found lists up to th
 constexpr uint32_t kMethodComb = 2;     // voting behind the spike-train pre-filter
 constexpr uint32_t kMethodSearch = 3;   // sFFT4.0 / MPFFT-style location by binary or multi-scale search
 constexpr float kSearchRho = 0.25f;     // search: residual bound of a lone coefficient (relative)
+constexpr float kSearchKappa = 20.0f;   // search: threshold at least this many median bucket energies
 constexpr uint32_t kSearchSmemMax = 160 * 1024;  // search: bucket buffers of one job in shared memory
 constexpr uint32_t kCombShifts = 2;     // comb subsamplings (shifts tau of loops L, L+1)
 constexpr uint32_t kMaxComb = 8192;     // largest number of residue classes

@@ -119,3 +119,22 @@ def test_recovers_where_phase_encoding_fails():
     pe = oracle.sfft_pe(oracle.PlanPE(N, K, B, w, 8, 3), sig.x)
     assert len(np.intersect1d(bs["idx"], sig.freqs)) == K
     assert len(np.intersect1d(pe["idx"], sig.freqs)) < K // 2
+
+
+def test_pure_noise_stops_after_one_iteration():
+    # the threshold's noise-floor term (20 times the median bucket energy): no
+    # bucket of white noise reaches it, so nothing is located and the loop stops
+    N, B = 1 << 14, 64
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    out = oracle.sfft_bs(oracle.PlanBS(N, 8, B, configs.default_window(N, B), 8, 1), x)
+    assert out["iters"] == 1 and out["nfound"] == 0
+
+
+def test_noisy_signal_stops_early():
+    # 20 dB: the planted support is found within a few iterations, then
+    # nothing above the noise floor remains
+    N, K, B = 1 << 16, 10, 64
+    sig = signals.make_signal(N, K, 4, 20.0)
+    out = oracle.sfft_bs(oracle.PlanBS(N, K, B, configs.default_window(N, B), 8, 4), sig.x)
+    assert out["iters"] < 8 and len(np.intersect1d(out["idx"], sig.freqs)) == K

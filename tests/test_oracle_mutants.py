@@ -75,6 +75,7 @@ MUTANTS = [
      "if (0) continue; /* located in a neighbouring bucket: leakage */"),
     ("bs no lone-coefficient test", "if (res > rho * (double)J * e0) continue;", "if (0) continue;"),
     ("bs window not centred", "int64_t lo_p = k * NB - W / 2;", "int64_t lo_p = k * NB;"),
+    ("bs threshold without the noise floor", "if (kappa * emed > thr) thr = kappa * emed;", "(void)emed;"),
 ]
 
 PIN_CHECKS = [
@@ -115,6 +116,7 @@ PIN_CHECKS = [
     bs_pins.test_matches_exhaustive_search_under_noise,
     bs_pins.test_shared_bucket_rejected,
     lambda: bs_pins.test_exact_recovery_noiseless(1 << 12, 5, 32, 1),
+    bs_pins.test_pure_noise_stops_after_one_iteration,
 ]
 
 
