@@ -43,6 +43,15 @@ LAUNCHES_PER_STEP = 4
 # after the capture.
 NCU_GATHER_TRAFFIC_PER_SPECTRUM = (537_337_856 + 22_532_352) / 64
 UNIT = "spectra/s"
+
+# plan options of the variants a --profile run may take (the headline is "voting")
+PROFILE_VARIANTS = {
+    "voting": {},
+    "comb": {"method": 2, "comb": 4096},
+    "median_refine": {"refine": 2},
+    "mean_refine": {"estimator": 1, "refine": 2},
+    "search": {"method": 3, "L": 8},
+}
 WORKLOAD = configs.GENERAL_N20
 
 
@@ -423,7 +432,10 @@ def run_ours(args):
     S = args.signals
     seeds = replicas.shard(rank, world, S)
     sigs = [signals.make_signal(W.N, W.K, s, W.snr_db) for s in seeds]
-    plans = [sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, s) for s in seeds]
+    # (profiler runs may take a variant's plans; the bench line is always the voting path)
+    vopts = dict(PROFILE_VARIANTS[args.variant])
+    L = vopts.pop("L", W.L)
+    plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, L, s, **vopts) for s in seeds]
     info = plans[0].info
     dev = torch.device("cuda", local)
     xs = [torch.from_numpy(sg.x).to(dev) for sg in sigs]
@@ -636,11 +648,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--served-requests", type=int, default=4096, help="requests per serving run")
     ap.add_argument("--served-rate", type=float, default=20000.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--variant", default="voting", choices=sorted(PROFILE_VARIANTS),
+                    help="plans of this variant (--profile runs only; the bench line is the voting path)")
     ap.add_argument("--profile", action="store_true",
                     help="profiler runs: only the warm-up and timed steps (no context runs, no CPU baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.variant != "voting" and not args.profile:
+        ap.error("--variant is for --profile runs; the bench line measures the voting path")
     if args.impl == "reference":
         run_reference(args)
     else:
