@@ -141,6 +141,7 @@ def _oracle_run(seed):
     plan = oracle.Plan.__new__(oracle.Plan)
     plan.N, plan.K, plan.B, plan.w, plan.L, plan.seed = W.N, W.K, W.B, W.window, W.L, seed
     plan.c, plan.T = W.c, W.threshold
+    plan.estimator, plan.refine = oracle.MEDIAN, 0  # the bench line's estimator, no refinement
     plan.g, plan.Gt = _ORACLE_STATE["g"], _ORACLE_STATE["Gt"]
     plan.sigma, plan.tau, plan.sigma_inv = oracle.loop_params(W.N, W.L, seed)
     x = signals.make_signal(W.N, W.K, seed, W.snr_db, keep_xhat=False).x
