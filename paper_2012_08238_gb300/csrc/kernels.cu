@@ -1803,6 +1803,12 @@ __device__ __forceinline__ uint32_t inv_mod_2p32(uint32_t sigma) {
     return x;
 }
 
+// k_bs_job's block: with B >= 256 (one bucket tile of 256 columns) 1024
+// threads, four partitions of the gather rounds per column and many warps
+// for the latency-bound sample loads; smaller B keep 256 threads (several
+// partitions already, more resident CTAs).
+constexpr uint32_t kBsWideB = 256;
+
 __device__ __forceinline__ uint32_t bs_bits(const PlanDev &P) {
     return min(P.logN - P.logB + 1u, P.logN);
 }
@@ -1813,7 +1819,8 @@ __device__ __forceinline__ uint32_t bs_shift(const PlanDev &P, uint32_t j) {
     return P.N >> min(j * P.srch_b, bs_bits(P));
 }
 
-__global__ void __launch_bounds__(kThreads) k_bs_job(Launch ln, uint32_t cap, uint32_t fcap, uint32_t nbuf) {
+template <int kBsThreads>
+__global__ void __launch_bounds__(kBsThreads) k_bs_job(Launch ln, uint32_t cap, uint32_t fcap, uint32_t nbuf) {
     // nbuf bucket buffers [B] (S rounded up to even), twiddles [B/2]; then
     // the found list when it fits fcap entries (else it stays in P.surv), or
     // the top-K buffer at the end
@@ -1821,9 +1828,9 @@ __global__ void __launch_bounds__(kThreads) k_bs_job(Launch ln, uint32_t cap, ui
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local, s_active, s_n;
-    __shared__ float s_thr, s_wmax[kThreads / 32];
-    __shared__ float2 red0[kThreads], red1[kThreads];
-    __shared__ uint32_t s_hist[256], s_wsum[kThreads / 32], s_prefix, s_need;
+    __shared__ float s_thr, s_wmax[kBsThreads / 32];
+    __shared__ float2 red0[kBsThreads], red1[kBsThreads];
+    __shared__ uint32_t s_hist[256], s_wsum[kBsThreads / 32], s_prefix, s_need;
     enter(ln, P, J, s_local);
     const uint32_t B = P.B, logB = P.logB, N = P.N, NB = N >> logB;
     const uint32_t bits = bs_bits(P), W = 1u << bits, b = P.srch_b;
@@ -1831,7 +1838,7 @@ __global__ void __launch_bounds__(kThreads) k_bs_job(Launch ln, uint32_t cap, ui
     float2 *tw = bs_s + (size_t)nbuf * B;
     for (uint32_t k = threadIdx.x; k < B / 2; k += blockDim.x) tw[k] = __ldg(P.tw + k);
     if (threadIdx.x == 0) s_n = 0;
-    const uint32_t TB = P.tb, PP = kThreads / TB;
+    const uint32_t TB = P.tb, PP = kBsThreads / TB;
     const uint32_t jt = threadIdx.x & (TB - 1), sidx = threadIdx.x / TB;
     const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
     const float2 *__restrict__ x = J.x;
@@ -1918,7 +1925,7 @@ __global__ void __launch_bounds__(kThreads) k_bs_job(Launch ln, uint32_t cap, ui
             if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = m;
             __syncthreads();
             const float emed = __uint_as_float(
-                block_kth_largest<kThreads, false>(ek, B, (B + 1) / 2, s_hist, s_wsum, &s_prefix, &s_need));
+                block_kth_largest<kBsThreads, false>(ek, B, (B + 1) / 2, s_hist, s_wsum, &s_prefix, &s_need));
             if (threadIdx.x == 0) {
                 float mm = 0.f;
                 for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2) mm = fmaxf(mm, s_wmax[w2]);
@@ -2355,9 +2362,10 @@ cudaError_t launch_bs(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t
     // tail: the top-K ranks or the found list, and the energies' bits of the threshold
     const size_t tail = std::max<size_t>(std::max<size_t>(rank, sizeof(uint4) * fcap), sizeof(uint32_t) * max_B);
     const int smem = (int)(tables + tail);
-    cudaError_t e = cudaFuncSetAttribute(k_bs_job, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = max_B >= kBsWideB ? k_bs_job<1024> : k_bs_job<256>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_bs_job<<<njobs, kThreads, smem, s>>>(ln, cap, fcap, max_nbuf);
+    kern<<<njobs, max_B >= kBsWideB ? 1024 : 256, smem, s>>>(ln, cap, fcap, max_nbuf);
     return cudaGetLastError();
 }
 
