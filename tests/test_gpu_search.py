@@ -114,3 +114,34 @@ def test_search_option_checks():
         sfft.sfft_plan_create_ex(1 << 24, K, 8192, configs.default_window(1 << 24, 8192), 8, 0, method=SEARCH)
     info = sfft.sfft_plan_create_ex(N, K, B, w, 8, 0, method=SEARCH).info
     assert info.method == SEARCH
+
+
+def test_server_serves_every_method_and_option():
+    # requests of every location method and estimator option through one
+    # server: each equals the same plan executed alone (batches are formed
+    # per method; plans are keyed by every option)
+    srv = sfft.sfft_server_create(2 << 30, 16)
+    N, K, B = 1 << 16, 10, 64
+    w = configs.default_window(N, B)
+    kinds = [dict(), dict(method=sfft.SFFT_METHOD_PHASE), dict(method=sfft.SFFT_METHOD_COMB, comb=256),
+             dict(method=SEARCH), dict(method=SEARCH, search_bits=2), dict(estimator=sfft.SFFT_ESTIMATOR_MEAN),
+             dict(refine=2), dict(estimator=sfft.SFFT_ESTIMATOR_MEAN, refine=1)]
+    reqs, bufs = [], []
+    for i in range(2 * len(kinds)):
+        kind = kinds[i % len(kinds)]
+        sig = signals.make_signal(N, K, 70 + i, 30.0)
+        x = torch.from_numpy(sig.x).cuda()
+        idx = torch.full((K,), -1, dtype=torch.int32, device="cuda")
+        val = torch.zeros(K, dtype=torch.complex64, device="cuda")
+        bufs.append((sig, kind, x, idx, val))
+        reqs.append(sfft.sfft_submit(srv, N, K, B, w, 8, 70 + i, x, idx, val, **kind))
+    for i, (t, (sig, kind, x, idx, val)) in enumerate(zip(reqs, bufs)):
+        res = sfft.sfft_wait(srv, t, 60000)
+        assert res.status == sfft.SFFT_OK
+        torch.cuda.synchronize()
+        plan = sfft.sfft_plan_create_ex(N, K, B, w, 8, 70 + i, **kind)
+        ri, rv, rk = run_execute(plan, sig.x)
+        assert res.k_out == rk
+        assert np.array_equal(idx.cpu().numpy()[:rk], ri)
+        assert rel_l2(val.cpu().numpy()[:rk], rv) <= 1e-5
+    srv.destroy()
