@@ -227,7 +227,8 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
 }  // namespace
 
 size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
-                         int32_t method) {
+                         const sfft_opts &o) {
+    const int32_t method = o.method;
     if (method == SFFT_METHOD_PHASE || method == SFFT_METHOD_SEARCH) c = T = 1;
     if (check_sizes(N, K, B, w, L, c, T) != SFFT_OK) return 0;
     PlanDev P;
@@ -238,7 +239,9 @@ size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, 
                   : method == SFFT_METHOD_COMB   ? kMethodComb
                   : method == SFFT_METHOD_SEARCH ? kMethodSearch
                                                  : kMethodVoting,
-                  (uint32_t)std::min<int64_t>(N, kMaxComb));
+                  (uint32_t)std::min<int64_t>(N, kMaxComb),
+                  o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian,
+                  (uint32_t)std::max<int32_t>(o.refine, 0), (uint32_t)std::max<int32_t>(o.search_bits, 1));
     return layout_of(P, cap).total;
 }
 

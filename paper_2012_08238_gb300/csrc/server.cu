@@ -21,7 +21,7 @@
 
 namespace sfft {
 size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
-                         int32_t method);
+                         const sfft_opts &o);
 }
 
 namespace {
@@ -127,7 +127,7 @@ bool acquire_plan(sfft_server *s, Request *r, std::unique_lock<std::mutex> &lk) 
     }
     const sfft_request &q = r->req;
     const size_t need = sfft::plan_device_bytes(q.N, q.K, q.B, q.w, q.L, q.opts.c > 0 ? q.opts.c : 2,
-                                                q.opts.T > 0 ? q.opts.T : (q.L + 1) / 2, q.opts.method);
+                                                q.opts.T > 0 ? q.opts.T : (q.L + 1) / 2, q.opts);
     while (s->plan_bytes + need > s->budget) {
         auto victim = s->plans.end();
         for (auto it = s->plans.begin(); it != s->plans.end(); ++it)
@@ -288,7 +288,7 @@ extern "C" sfft_status sfft_submit(sfft_server *s, const sfft_request *q, uint64
     }
     const int32_t c = q->opts.c > 0 ? q->opts.c : 2;
     const int32_t T = q->opts.T > 0 ? q->opts.T : (q->L + 1) / 2;
-    const size_t need = sfft::plan_device_bytes(q->N, q->K, q->B, q->w, q->L, c, T, q->opts.method);
+    const size_t need = sfft::plan_device_bytes(q->N, q->K, q->B, q->w, q->L, c, T, q->opts);
     if (need == 0) return SFFT_EINVAL;  // sizes rejected, reason already set
     if (need > s->budget) {
         sfft::set_error("request's plan alone exceeds the server's memory budget");
