@@ -386,7 +386,7 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     // refining jobs: the iterative framework's subtraction over the found set
-    if (z.refine && (e = launch_refine(lj, z.jobs, z.max_rK, s)) != cudaSuccess) return e;
+    if (z.refine && (e = launch_refine(lj, z.jobs, z.max_rK, z.L_uniform, s)) != cudaSuccess) return e;
     return mark(6);
 }
 

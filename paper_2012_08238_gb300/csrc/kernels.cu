@@ -2052,49 +2052,78 @@ __global__ void k_flags_from_sel(const PlanDev *pd, const int32_t *sel) {
 // kRefineThreads per job runs all passes, the (f, l) pairs spread over its
 // threads.  The found set sits in shared memory (previous and current
 // values [K], frequencies [K]), the per-loop estimates of a pass in P.rscr.
-// Neighbours: with n L <= kRefineSortMax the (loop, bucket, index) keys are
-// sorted once (the buckets do not change between passes) and each pair looks
-// its three buckets up by binary search; larger sets compare every other
-// coefficient's bucket.
+// Neighbours: with L B <= kRefineBinMax and n L <= kRefineSortMax the
+// found coefficients are counting-sorted once into the L B (loop, bucket)
+// bins (the buckets do not change between passes; each bin ordered by index,
+// so the subtraction order is fixed) and a pair reads its three bins
+// directly; otherwise it compares every other coefficient's bucket.  LT = L
+// in {8, 12, 16} combines with sorting networks in registers.
 constexpr int kRefineThreads = 1024;
-constexpr uint32_t kRefineSortMax = 4096;
+constexpr uint32_t kRefineSortMax = 4096;   // (f, l) pairs of the binned lists
+constexpr uint32_t kRefineBinMax = 16384;   // bins: L B
 
+template <int LT>
 __global__ void __launch_bounds__(kRefineThreads) k_refine(Launch ln) {
     extern __shared__ float2 rq_s[];
     __shared__ PlanDev P;
     __shared__ Job J;
-    __shared__ uint32_t s_local;
+    __shared__ uint32_t s_local, s_wsum[kRefineThreads / 32];
     enter(ln, P, J, s_local);
     if (P.refine == 0) return;  // (uniform over the CTA)
-    const uint32_t K = P.K, L = P.L, B = P.B, N = P.N, NB = N >> P.logB;
+    const uint32_t K = P.K, L = LT > 0 ? (uint32_t)LT : P.L, B = P.B, N = P.N, NB = N >> P.logB;
     const uint32_t n = min((uint32_t)max(__ldcg(J.kout), 0), K);
     const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
     float2 *cur = rq_s, *nxt = rq_s + K;
     uint32_t *fi = reinterpret_cast<uint32_t *>(rq_s + 2 * K);
-    unsigned long long *ks = reinterpret_cast<unsigned long long *>(rq_s + 2 * K + (K + 1) / 2);
+    uint32_t *bend = fi + K;                                          // [L B] end of each bin
+    uint16_t *ord = reinterpret_cast<uint16_t *>(bend + kRefineBinMax);  // [n L] indices by bin
     for (uint32_t i = threadIdx.x; i < n; i += kRefineThreads) {
         fi[i] = (uint32_t)__ldcg(J.idx + i);
         cur[i] = __ldcg(J.val + i);
     }
-    __syncthreads();
-    // keys (l << 40 | h << 20 | i), stored complemented so that the
-    // descending sort leaves them ascending: loop l's n keys at [l n, l n + n)
-    const bool sorted = n * L <= kRefineSortMax;
-    if (sorted) {
-        uint32_t np2 = 1;
-        while (np2 < n * L) np2 <<= 1;
-        for (uint32_t j = threadIdx.x; j < np2; j += kRefineThreads) {
-            unsigned long long key = ~0ull;
-            if (j < n * L) {
-                const uint32_t l = j / n, i = j - l * n;
-                const uint32_t h = ((P.sigma[l] << sN) * fi[i] + cv) >> top;
-                key = ((unsigned long long)l << 40) | ((unsigned long long)h << 20) | i;
-            }
-            ks[j] = ~key;
+    const uint32_t nbin = L * B;
+    const bool binned = nbin <= kRefineBinMax && n * L <= kRefineSortMax;
+    if (binned) {
+        for (uint32_t b = threadIdx.x; b < nbin; b += kRefineThreads) bend[b] = 0;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < n * L; j += kRefineThreads) {
+            const uint32_t l = j / n, i = j - l * n;
+            atomicAdd(&bend[l * B + (((P.sigma[l] << sN) * fi[i] + cv) >> top)], 1u);
         }
         __syncthreads();
-        bitonic_desc(ks, np2);
+        // exclusive starts: each thread scans a contiguous run of bins
+        const uint32_t per = (nbin + kRefineThreads - 1) / kRefineThreads;
+        const uint32_t b0 = min(nbin, threadIdx.x * per), b1 = min(nbin, b0 + per);
+        uint32_t run = 0;
+        for (uint32_t b = b0; b < b1; ++b) run += bend[b];
+        uint32_t st = block_incl_scan_n<kRefineThreads / 32>(run, s_wsum) - run;
+        for (uint32_t b = b0; b < b1; ++b) {
+            const uint32_t c = bend[b];
+            bend[b] = st;  // start, advanced to the end by the scatter below
+            st += c;
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < n * L; j += kRefineThreads) {
+            const uint32_t l = j / n, i = j - l * n;
+            const uint32_t b = l * B + (((P.sigma[l] << sN) * fi[i] + cv) >> top);
+            ord[atomicAdd(&bend[b], 1u)] = (uint16_t)i;
+        }
+        __syncthreads();
+        // each bin in index order (bins hold a few entries)
+        for (uint32_t b = threadIdx.x; b < nbin; b += kRefineThreads) {
+            const uint32_t e = bend[b], s0 = b ? bend[b - 1] : 0u;
+            for (uint32_t x = s0 + 1; x < e; ++x) {
+                const uint16_t v = ord[x];
+                uint32_t y = x;
+                while (y > s0 && ord[y - 1] > v) {
+                    ord[y] = ord[y - 1];
+                    --y;
+                }
+                ord[y] = v;
+            }
+        }
     }
+    __syncthreads();
     for (uint32_t pass = 0; pass < P.refine; ++pass) {
         for (uint32_t w = threadIdx.x; w < n * L; w += kRefineThreads) {
             const uint32_t i = w / L, l = w - i * L;
@@ -2111,23 +2140,13 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(Launch ln) {
                 r.x -= c.x;
                 r.y -= c.y;
             };
-            if (sorted) {
-                const uint32_t s0 = l * n, s1 = s0 + n;
+            if (binned) {
                 const uint32_t nb = B < 3 ? B : 3;  // buckets h - 1, h, h + 1 (distinct ones)
                 for (uint32_t q = 0; q < nb; ++q) {
-                    const uint32_t b = (B >= 3 ? h + B - 1 + q : h + q) & (B - 1);
-                    uint32_t lo = s0, hi = s1;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if ((uint32_t)((~ks[mid] >> 20) & 0xFFFFFu) < b)
-                            lo = mid + 1;
-                        else
-                            hi = mid;
-                    }
-                    for (uint32_t j = lo; j < s1; ++j) {
-                        const unsigned long long key = ~ks[j];
-                        if ((uint32_t)((key >> 20) & 0xFFFFFu) != b) break;
-                        const uint32_t d = (uint32_t)(key & 0xFFFFFu);
+                    const uint32_t b = l * B + ((B >= 3 ? h + B - 1 + q : h + q) & (B - 1));
+                    const uint32_t e = bend[b];
+                    for (uint32_t x = b ? bend[b - 1] : 0u; x < e; ++x) {
+                        const uint32_t d = ord[x];
                         if (d != i) subtract(d);
                     }
                 }
@@ -2152,6 +2171,17 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(Launch ln) {
                     si += e.y;
                 }
                 nxt[i] = make_float2(sr / (float)L, si / (float)L);
+            } else if constexpr (LT > 0) {
+                float re[LT], im[LT];
+#pragma unroll
+                for (int l = 0; l < LT; ++l) {
+                    const float2 e = __ldcg(v + l);
+                    re[l] = e.x;
+                    im[l] = e.y;
+                }
+                sort_net<LT>(re);
+                sort_net<LT>(im);
+                nxt[i] = make_float2(median_sorted(re, LT), median_sorted(im, LT));
             } else {
                 float re[kMaxL], im[kMaxL];
                 for (uint32_t l = 0; l < L; ++l) {
@@ -2340,14 +2370,16 @@ cudaError_t launch_pe(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s) {
+cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, uint32_t L_uniform, cudaStream_t s) {
     if (njobs == 0 || max_K == 0) return cudaSuccess;
-    // values [2][K], frequencies [K] (padded to 8 bytes), sort keys [kRefineSortMax]: <= 113 KB
-    const int smem = (int)((2 * sizeof(float2) + sizeof(uint32_t)) * max_K + 4 +
-                           sizeof(unsigned long long) * kRefineSortMax);
-    cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // values [2][K], frequencies [K], bin ends [kRefineBinMax], binned indices [kRefineSortMax]
+    const int smem = (int)((2 * sizeof(float2) + sizeof(uint32_t)) * max_K + sizeof(uint32_t) * kRefineBinMax +
+                           sizeof(uint16_t) * kRefineSortMax);
+    auto kern = L_uniform == 8 ? k_refine<8> : L_uniform == 12 ? k_refine<12> : L_uniform == 16 ? k_refine<16>
+                                                                                                    : k_refine<0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_refine<<<njobs, kRefineThreads, smem, s>>>(ln);
+    kern<<<njobs, kRefineThreads, smem, s>>>(ln);
     return cudaGetLastError();
 }
 

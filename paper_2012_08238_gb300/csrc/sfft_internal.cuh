@@ -171,8 +171,9 @@ inline uint32_t search_nbuf(uint32_t logN, uint32_t logB, uint32_t b) {
 }
 // Iterative-framework refinement of the jobs' outputs: one CTA per job (ln:
 // one per job) runs all the job's passes; jobs with refine = 0 return at
-// once.  max_K: the largest K of the refining jobs (<= kRefineMaxK).
-cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, cudaStream_t s);
+// once.  max_K: the largest K of the refining jobs (<= kRefineMaxK);
+// L_uniform: the jobs' common L (0 when they differ).
+cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, uint32_t L_uniform, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);
 cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *sel, cudaStream_t s);
