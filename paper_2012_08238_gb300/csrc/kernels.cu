@@ -1311,13 +1311,13 @@ __device__ void rank_records(const PlanDev &P, const Job &J, unsigned long long 
 
 // True in every thread of the job's last CTA of this launch to finish (each
 // CTA fences its records first); that CTA also re-arms the ticket.
-__device__ bool last_of_job(const PlanDev &P, uint32_t ctas_per_job, int counter = kEstDone) {
+__device__ bool last_of_job(const PlanDev &P, uint32_t ctas_per_job) {
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        s_last = atomicAdd(P.ctr + counter, 1u) == ctas_per_job - 1;
-        if (s_last) atomicExch(P.ctr + counter, 0u);
+        s_last = atomicAdd(P.ctr + kEstDone, 1u) == ctas_per_job - 1;
+        if (s_last) atomicExch(P.ctr + kEstDone, 0u);
     }
     __syncthreads();
     if (s_last) __threadfence();
