@@ -75,3 +75,62 @@ def test_invalid_options_rejected():
 def test_status_strings():
     assert sfft.status_string(sfft.SFFT_OK) == "ok"
     assert sfft.status_string(sfft.SFFT_EPENDING) == "pending"
+
+
+def _c_layout(tmp_path, structs):
+    """sizeof and offsetof of the header's structs, from gcc."""
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sfft.h"', "int main(void) {"]
+    for name, fields in structs.items():
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'    printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = {}
+    for line in subprocess.check_output([str(exe)]).decode().splitlines():
+        key, val = line.rsplit(" ", 1)
+        out[key] = int(val)
+    return out
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes mirrors must have the header's sizes and field offsets
+    classes = [sfft.sfft_opts, sfft.sfft_plan_info, sfft.sfft_exec_stats, sfft.sfft_request, sfft.sfft_result]
+    structs = {c.__name__: [f[0] for f in c._fields_] for c in classes}
+    c = _c_layout(tmp_path, structs)
+    for cls in classes:
+        name = cls.__name__
+        assert ctypes.sizeof(cls) == c[f"{name} size"], name
+        for f in structs[name]:
+            assert getattr(cls, f).offset == c[f"{name}.{f}"], f"{name}.{f}"
+
+
+@pytest.mark.parametrize("kw", [
+    dict(method=4),                                    # no such method
+    dict(estimator=2),                                 # no such estimator
+    dict(refine=9),                                    # at most 8 passes
+    dict(refine=-1),
+    dict(method=sfft.SFFT_METHOD_PHASE, refine=1),     # refinement is for voting / comb
+    dict(method=sfft.SFFT_METHOD_PHASE, estimator=sfft.SFFT_ESTIMATOR_MEAN),
+    dict(method=sfft.SFFT_METHOD_SEARCH, estimator=sfft.SFFT_ESTIMATOR_MEAN),
+    dict(search_bits=1),                               # search_bits is for the search method
+    dict(method=sfft.SFFT_METHOD_SEARCH, search_bits=5),
+    dict(comb=256),                                    # comb is for the comb method
+    dict(method=sfft.SFFT_METHOD_COMB, comb=1000),     # not a power of two
+])
+def test_invalid_variant_options_rejected(kw):
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_plan_create_ex(1 << 16, 10, 64, 2368, 8, 0, **kw)
+    assert ei.value.status == sfft.SFFT_EINVAL
+
+
+def test_refinement_and_search_size_limits_rejected():
+    with pytest.raises(sfft.SfftError):  # refinement keeps the found set in shared memory: K <= 4096
+        sfft.sfft_plan_create_ex(1 << 20, 5000, 8192, 8192 * 41, 8, 0, refine=1)
+    with pytest.raises(sfft.SfftError):  # the search's bucket buffers must fit one CTA
+        sfft.sfft_plan_create_ex(1 << 24, 8, 8192, 8192 * 45, 8, 0, method=sfft.SFFT_METHOD_SEARCH)
