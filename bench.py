@@ -44,13 +44,14 @@ LAUNCHES_PER_STEP = 4
 NCU_GATHER_TRAFFIC_PER_SPECTRUM = (537_337_856 + 22_532_352) / 64
 UNIT = "spectra/s"
 
-# plan options of the variants a --profile run may take (the headline is "voting")
+# plan options of the variants a --profile run may take (the headline is
+# "voting"); strings name the binding's constants
 PROFILE_VARIANTS = {
     "voting": {},
-    "comb": {"method": 2, "comb": 4096},
+    "comb": {"method": "SFFT_METHOD_COMB", "comb": 4096},
     "median_refine": {"refine": 2},
-    "mean_refine": {"estimator": 1, "refine": 2},
-    "search": {"method": 3, "L": 8},
+    "mean_refine": {"estimator": "SFFT_ESTIMATOR_MEAN", "refine": 2},
+    "search": {"method": "SFFT_METHOD_SEARCH", "L": 8},
 }
 WORKLOAD = configs.GENERAL_N20
 
@@ -434,7 +435,7 @@ def run_ours(args):
     seeds = replicas.shard(rank, world, S)
     sigs = [signals.make_signal(W.N, W.K, s, W.snr_db) for s in seeds]
     # (profiler runs may take a variant's plans; the bench line is always the voting path)
-    vopts = dict(PROFILE_VARIANTS[args.variant])
+    vopts = {k: getattr(sfft, v) if isinstance(v, str) else v for k, v in PROFILE_VARIANTS[args.variant].items()}
     L = vopts.pop("L", W.L)
     plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, L, s, **vopts) for s in seeds]
     info = plans[0].info
