@@ -477,6 +477,24 @@ extern "C" sfft_status sfft_loop_params(int64_t N, int32_t L, uint64_t seed, uin
     return SFFT_OK;
 }
 
+extern "C" sfft_status sfft_suggest_params(int64_t N, int32_t K, double snr_db, int32_t *B, int64_t *w,
+                                           int32_t *L) {
+    if (!is_pow2(N) || N < 2 || N > (1ll << kMaxLogN) || K < 1 || K > N || !B || !w || !L) {
+        set_error("N must be a power of two in [2, 2^30], K in [1, N], outputs non-NULL");
+        return SFFT_EINVAL;
+    }
+    int64_t b = 64;
+    while (b < 4ll * K) b <<= 1;
+    b = std::min<int64_t>(b, std::min<int64_t>(4096, N / 64));  // B (log2 N + 21) < N
+    b = std::max<int64_t>(2, std::min<int64_t>(b, N));
+    int64_t ww = b * (int64_t)(ilog2((uint64_t)N) + 21);
+    if (ww > N) ww = N / b * b;
+    *B = (int32_t)b;
+    *w = ww;
+    *L = std::isnan(snr_db) ? 8 : 12;
+    return SFFT_OK;
+}
+
 extern "C" sfft_status sfft_plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L,
                                         uint64_t seed) {
     return sfft_plan_create_ex(plan, N, K, B, w, L, seed, nullptr);

@@ -59,6 +59,7 @@ _SIGS = {
     "sfft_plan_get_info": (_i32, [_p, ctypes.POINTER(sfft_plan_info)]),
     "sfft_plan_get_loops": (_i32, [_p, _p, _p, _p]),
     "sfft_loop_params": (_i32, [_i64, _i32, _u64, _p, _p, _p]),
+    "sfft_suggest_params": (_i32, [_i64, _i32, ctypes.c_double, _p, _p, _p]),
     "sfft_plan_last_stats": (_i32, [_p, ctypes.POINTER(sfft_exec_stats)]),
     "sfft_execute": (_i32, [_p, _p, _p, _p, _p, _p]),
     "sfft_execute_host": (_i32, [_p, _p, _p, _p, _p, _p]),
@@ -220,6 +221,14 @@ def sfft_loop_params(N, L, seed):
     s, t, si = (ctypes.c_uint32 * L)(), (ctypes.c_uint32 * L)(), (ctypes.c_uint32 * L)()
     _check(lib().sfft_loop_params(N, L, seed, s, t, si))
     return list(s), list(t), list(si)
+
+
+def sfft_suggest_params(N, K, snr_db=None):
+    """(B, w, L) for a signal shape by the library's size-class rule (snr_db None: noiseless)."""
+    B, w, L = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    snr = float("nan") if snr_db is None else float(snr_db)
+    _check(lib().sfft_suggest_params(N, K, snr, ctypes.byref(B), ctypes.byref(w), ctypes.byref(L)))
+    return B.value, w.value, L.value
 
 
 def sfft_execute(plan: Plan, x, idx, val, k_out, stream=None):

@@ -134,3 +134,28 @@ def test_refinement_and_search_size_limits_rejected():
         sfft.sfft_plan_create_ex(1 << 20, 5000, 8192, 8192 * 41, 8, 0, refine=1)
     with pytest.raises(sfft.SfftError):  # the search's bucket buffers must fit one CTA
         sfft.sfft_plan_create_ex(1 << 24, 8, 8192, 8192 * 45, 8, 0, method=sfft.SFFT_METHOD_SEARCH)
+
+
+@pytest.mark.parametrize("N,K,snr,want", [
+    (1 << 16, 10, None, (64, 64 * 37, 8)),          # the exactly sparse workload
+    (1 << 20, 100, 20.0, (512, 512 * 41, 12)),      # the general workload
+    (1 << 24, 1000, 20.0, (4096, 4096 * 45, 12)),   # the precision sweep
+    (1 << 14, 1000, 0.0, (256, 256 * 35, 12)),      # capped at N/64
+    (1 << 22, 5000, 10.0, (4096, 4096 * 43, 12)),   # capped at 4096
+    (1 << 10, 3, None, (16, 16 * 31, 8)),           # small N: N/64
+    (32, 1, None, (2, 32, 8)),                      # tiny N: at least 2, window within N
+])
+def test_suggested_params_follow_the_size_class_rule(N, K, snr, want):
+    B, w, L = sfft.sfft_suggest_params(N, K, snr)
+    assert (B, w, L) == want
+    assert w % B == 0 and w <= N
+
+
+def test_suggested_params_agree_with_the_mixed_batch_rule():
+    # the mixed-size batch test's rule is this entry point's
+    import test_gpu_configs as tc
+
+    for N, K, B, L, seed, snr in tc._mixed_specs(96):
+        assert sfft.sfft_suggest_params(N, K, snr)[:1] == (B,)
+    with pytest.raises(sfft.SfftError):
+        sfft.sfft_suggest_params(1000, 10, 20.0)
