@@ -113,14 +113,15 @@ typedef struct {
    to bits = min(log2(N/B) + 1, log2 N) (b = search_bits), besides tau_r: a
    coefficient f turns by exp(2 pi i f / 2^m) at shift N / 2^m, so each
    shifted bucket decides one digit of f (the candidate whose predicted turn
-   best matches), a decision with a margin of 1/2^b of a turn; the bits fix
+   best matches; candidates lie 1/2^b of a turn apart); the bits fix
    sigma f to one value in a window of two buckets around the bucket.  A
    located f is kept when it hashes back to the bucket and every shifted
    bucket matches the lone-coefficient prediction within a residual of 1/4
    of its energy, valued by energy estimation.  More robust to noise than
    phase encoding (whose one-sample phase must resolve f to 1 of N); needs
    1 + ceil(bits / b) bucketizations per iteration, whose buffers and the
-   top-K ranks must fit one CTA's shared memory (160 KB). */
+   top-K ranks must fit one CTA's shared memory (160 KB); c and T are
+   ignored. */
 #define SFFT_METHOD_SEARCH 3
 
 /* Combination of a candidate's L per-loop estimates (step a6; "The method of
