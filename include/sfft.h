@@ -209,15 +209,16 @@ sfft_status sfft_loop_params(int64_t N, int32_t L, uint64_t seed, uint32_t *sigm
 /* Plan sizes for a signal shape by a fixed size-class rule (host only, no
    GPU needed; not a measuring autotuner):
      B = the smallest power of two >= max(64, 4K) (so the 2K kept buckets
-         are at most half of them), at most min(4096, N/64) (which keeps the
-         window inside the signal) and at least 2;
+         are at most half of them), at most min(16384, N/64) (which keeps the
+         window inside the signal) and at least 2; a cap below 2K is refused
+         (SFFT_EINVAL): the rule plans K <= min(8192, N/128) only;
      w = B (log2 N + 21) (the flat window's width; Eq. 13's Gaussian at
          sigma_g = B sqrt(log2 N) falls below its stop-band floor at its edge),
          lowered to the largest multiple of B <= N;
      L = 8 for a noiseless signal (snr_db NaN: exactly sparse) and 12 else.
    The rule gives the named workloads' B (K = 10: 64; K = 100: 512;
    K = 1000: 4096).  Errors: SFFT_EINVAL (N not a power of two in
-   [2, 2^30], K not in [1, N], NULL outputs). */
+   [2, 2^30], K not in [1, N], K beyond the rule's range, NULL outputs). */
 sfft_status sfft_suggest_params(int64_t N, int32_t K, double snr_db, int32_t *B, int64_t *w, int32_t *L);
 
 /* ---------------------------------------------------------------- execute */

@@ -485,8 +485,15 @@ extern "C" sfft_status sfft_suggest_params(int64_t N, int32_t K, double snr_db, 
     }
     int64_t b = 64;
     while (b < 4ll * K) b <<= 1;
-    b = std::min<int64_t>(b, std::min<int64_t>(4096, N / 64));  // B (log2 N + 21) < N
+    b = std::min<int64_t>(b, std::min<int64_t>(kMaxB, N / 64));  // B (log2 N + 21) < N
     b = std::max<int64_t>(2, std::min<int64_t>(b, N));
+    if (b < 2ll * K) {
+        // the 2K kept buckets would be all of them: no bucket is left empty to
+        // tell the large ones apart, and the flat window needs N/B >= 64
+        set_error("K too large for N: the size-class rule needs B >= 2K with B <= min(16384, N/64), i.e. "
+                  "K <= min(8192, N/128)");
+        return SFFT_EINVAL;
+    }
     int64_t ww = b * (int64_t)(ilog2((uint64_t)N) + 21);
     if (ww > N) ww = N / b * b;
     *B = (int32_t)b;

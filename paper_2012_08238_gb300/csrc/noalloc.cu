@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_noalloc(StaticArgs a) {
 
 std::mutex g_addr_mu;
 void *g_addr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};  // multiprocessor count of each device (shapes the chunk split)
 
 bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -157,16 +158,23 @@ extern "C" sfft_status sfft_bucketize_noalloc(int64_t N, int32_t B, int64_t w, i
         return SFFT_EINVAL;
     }
     void *partial = nullptr;
+    int sms = 0;
     {
-        // once per device, with that device current: the array's device address
+        // once per device, with that device current: the array's device
+        // address and the multiprocessor count (neither query allocates)
         std::lock_guard<std::mutex> lk(g_addr_mu);
         if (!g_addr[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_static_partial);
             if (e != cudaSuccess) return sfft::cuda_fail(e, "cudaGetSymbolAddress(g_static_partial)");
+            int n = 0;
+            e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return sfft::cuda_fail(e, "cudaDeviceGetAttribute(multiprocessors)");
+            g_sms[dev] = n > 0 ? n : 1;
             g_addr[dev] = p;
         }
         partial = g_addr[dev];
+        sms = g_sms[dev];
     }
 
     StaticArgs a;
@@ -184,7 +192,7 @@ extern "C" sfft_status sfft_bucketize_noalloc(int64_t N, int32_t B, int64_t w, i
     a.tb = B < kThreads ? (uint32_t)B : (uint32_t)kThreads;
     a.tiles = a.B / a.tb;
     a.rounds = a.w / a.B;
-    uint32_t want = (2 * 152 + a.tiles * a.L - 1) / (a.tiles * a.L);
+    uint32_t want = (2 * (uint32_t)sms + a.tiles * a.L - 1) / (a.tiles * a.L);
     const uint32_t fit = kStaticPartialEntries / (a.L * a.B);
     want = want < a.rounds ? want : a.rounds;
     want = want < fit ? want : fit;

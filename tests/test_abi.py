@@ -140,9 +140,11 @@ def test_refinement_and_search_size_limits_rejected():
     (1 << 16, 10, None, (64, 64 * 37, 8)),          # the exactly sparse workload
     (1 << 20, 100, 20.0, (512, 512 * 41, 12)),      # the general workload
     (1 << 24, 1000, 20.0, (4096, 4096 * 45, 12)),   # the precision sweep
-    (1 << 14, 1000, 0.0, (256, 256 * 35, 12)),      # capped at N/64
-    (1 << 22, 5000, 10.0, (4096, 4096 * 43, 12)),   # capped at 4096
+    (1 << 14, 100, 0.0, (256, 256 * 35, 12)),       # capped at N/64 (still >= 2K)
+    (1 << 22, 5000, 10.0, (16384, 16384 * 43, 12)),  # capped at 16384
+    (1 << 20, 4096, 10.0, (16384, 16384 * 41, 12)),  # the largest serving K
     (1 << 10, 3, None, (16, 16 * 31, 8)),           # small N: N/64
+    (1 << 11, 16, None, (32, 32 * 32, 8)),          # N/64 = 2K exactly
     (32, 1, None, (2, 32, 8)),                      # tiny N: at least 2, window within N
 ])
 def test_suggested_params_follow_the_size_class_rule(N, K, snr, want):
@@ -159,3 +161,11 @@ def test_suggested_params_agree_with_the_mixed_batch_rule():
         assert sfft.sfft_suggest_params(N, K, snr)[:1] == (B,)
     with pytest.raises(sfft.SfftError):
         sfft.sfft_suggest_params(1000, 10, 20.0)
+
+
+@pytest.mark.parametrize("N,K", [(1 << 14, 1000), (1 << 12, 4096), (1 << 12, 33), (1 << 26, 8193)])
+def test_suggested_params_refuse_K_beyond_the_rule(N, K):
+    # the capped B would be below 2K (K > N/128 or K > 8192)
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_suggest_params(N, K, 20.0)
+    assert ei.value.status == sfft.SFFT_EINVAL and "K too large" in str(ei.value)

@@ -2,9 +2,8 @@
 
 * Mixed batch (the batched shape: N log-uniform over 2^14..2^22, K uniform
   in [10, 1000] with K <= N/256, SNR uniform in [0, 40] dB, one plan per
-  signal with B the smallest power of two >= 4K within [64, min(4096, N/64)]
-  as the size-class rule, so that the window B (log2 N + 21) stays below N,
-  L = 12): the batch gives every signal the answer of its plain execution,
+  signal with B from the library's size-class rule sfft_suggest_params,
+  which keeps the window B (log2 N + 21) below N, L = 12): the batch gives every signal the answer of its plain execution,
   and three small signals match the FP64 oracle.
 * Precision sweep (N = 2^24, K = 1000, B = 4096, L = 12, SNR in
   {-10, 0, 10, 20, 40} dB, two seeds each): properties that hold at any
@@ -25,10 +24,7 @@ torch = pytest.importorskip("torch")
 
 
 def _size_class_B(N, K):
-    B = 64
-    while B < 4 * K:
-        B <<= 1
-    return max(64, min(B, 4096, N // 64))
+    return sfft.sfft_suggest_params(N, K, 20.0)[0]
 
 
 def _mixed_specs(n, seed=0):

@@ -3,8 +3,10 @@
 Noiseless inputs: supports identical to the oracle's and to the planted
 spectrum, values within relative L2 1e-4 of the oracle's, iterations equal
 to the oracle's.  Noisy inputs (the variant's advantage over phase
-encoding): supports agree with the oracle's up to near-tie decisions and
-recover the planted support.  Batches give the plain path's answers.
+encoding): supports agree with the oracle's up to near-tie decisions, values
+on the common support within relative L2 1e-4 of the oracle's (the FP32
+tolerance; measured ~2e-7 on these cases and on the 2^20 workload), and the
+planted support is recovered.  Batches give the plain path's answers.
 """
 import numpy as np
 import pytest
@@ -53,7 +55,7 @@ def test_noisy_matches_oracle(N, K, B, b, snr, seed):
     idx, val, k = run_execute(plan, sig.x)
     common, gi, oi = np.intersect1d(idx, ref["idx"], return_indices=True)
     assert len(common) >= k - 1
-    assert rel_l2(val[gi], ref["val"][oi]) <= 1e-3
+    assert rel_l2(val[gi], ref["val"][oi]) <= 1e-4
     assert len(np.intersect1d(idx, sig.freqs)) == K
 
 
@@ -64,8 +66,12 @@ def test_general_workload_search():
     plan, op = _pair(W.N, W.K, W.B, 8, 0)
     ref = oracle.sfft_bs(op, sig.x)
     idx, val, k = run_execute(plan, sig.x)
-    common = np.intersect1d(idx, ref["idx"])
+    common, gi, oi = np.intersect1d(idx, ref["idx"], return_indices=True)
     assert len(common) >= 0.99 * len(ref["idx"])
+    # element by element on the common support
+    assert rel_l2(val[gi], ref["val"][oi]) <= 1e-4
+    assert np.max(np.abs(val[gi] - ref["val"][oi])) <= 1e-4 * np.max(np.abs(ref["val"]))
+    assert sfft.sfft_plan_last_stats(plan).iterations == ref["iters"]
     e = metrics.errors(sig.xhat, W.K, idx, val)
     assert e["L0"] <= 1
 

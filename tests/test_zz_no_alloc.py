@@ -5,13 +5,15 @@ This entry point serves callers that cannot call cudaMalloc while running
 block is not allowed in their steady state), so they cannot create a plan.
 It keeps its scratch in a static device array shared by all calls.  The test
 calls it through the C ABI and compares it with sfft_bucketize on a plan,
-within the bucket-value tolerance of the parity tests, on two calls in a row;
+within the bucket-value tolerance of the parity tests, on two calls in a row,
+and with the FP64 oracle's bucket values on the small shape;
 it is collected last so that a failure here stops a run only after every
 other test has run, and it holds alone in a fresh process.
 """
 import numpy as np
 import pytest
 
+import oracle
 from gpu_helpers import rel_l2, run_bucketize
 from paper_2012_08238_gb300 import configs, sfft, signals
 
@@ -44,6 +46,16 @@ def test_noalloc_matches_plan_bucketize_on_consecutive_calls():
         z = _noalloc(N, B, w, L, seed, x)
         assert np.isfinite(z).all()
         assert rel_l2(z, refs[i]) <= 1e-5
+
+
+def test_noalloc_matches_oracle_bucket_values():
+    # the same quantity from the FP64 oracle (Eq. 11 fold + Eq. 2 DFT), no plan involved
+    N, B, w, L, seed = 1 << 12, 32, 32 * 33, 5, 4
+    x = signals.make_signal(N, 4, seed, 10.0).x
+    sigma, tau, _ = oracle.loop_params(N, L, seed)
+    _, zo = oracle.bucketize(N, B, w, sigma, tau, oracle.window_taps(N, B, w), x)
+    for _ in range(2):
+        assert rel_l2(_noalloc(N, B, w, L, seed, x), zo) <= 1e-5
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
