@@ -109,6 +109,7 @@ def _bind(lib):
             _i64,
             [_i64, _i64, _i64, _i64, _int, ctypes.c_double, _u64, _p, _p, _p, _p, _p, _p, _p],
         ),
+        "oracle_residual_energy": (None, [_i64, _i64, _int, _p, _p, _p, _p, _i64, _p, _p, _p, _p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -295,11 +296,12 @@ def dft(x) -> np.ndarray:
 class Plan:
     """Window taps and gains for one (N, B, w): the oracle's plan-time work."""
 
-    def __init__(self, N, K, B, w, L, seed, c=2, T=None, estimator=MEDIAN, refine=0):
+    def __init__(self, N, K, B, w, L, seed, c=2, T=None, estimator=MEDIAN, refine=0, residual=False):
         self.N, self.K, self.B, self.w, self.L, self.seed = N, K, B, w, L, seed
         self.c = c
         self.estimator = estimator  # MEDIAN or MEAN
         self.refine = refine        # refinement passes over the found set (0: none)
+        self.residual = residual    # final residual-energy check of the output
         self.T = (L + 1) // 2 if T is None else T
         self.g = window_taps(N, B, w)
         self.Gt = filter_gain(N, B, w, self.g)
@@ -330,6 +332,8 @@ def sfft(plan: Plan, x, intermediates: bool = False):
     out = {"idx": idx[:kout].copy(), "val": val[:kout].copy(), "k_out": int(kout)}
     if plan.refine:
         out["val"] = refine(plan, zhat, out["idx"], out["val"], plan.refine)
+    if getattr(plan, "residual", False):
+        out["residual"] = residual_energy(plan, zhat, out["idx"], out["val"])
     if intermediates:
         n = int(ncand[0])
         out.update(zhat=zhat, sel=sel, cand=cand[:n].copy(), est=est[:n].copy())
@@ -417,6 +421,8 @@ def sfft2(plan: Plan, x, Bc: int, C: int = 2):
            "ncand": int(ncand[0])}
     if plan.refine:
         out["val"] = refine(plan, zhat, out["idx"], out["val"], plan.refine)
+    if getattr(plan, "residual", False):
+        out["residual"] = residual_energy(plan, zhat, out["idx"], out["val"])
     return out
 
 
@@ -432,6 +438,23 @@ def refine(plan: Plan, zhat, idx, val, passes: int = 1):
     _load().oracle_refine(plan.N, plan.B, plan.L, _ptr(sigma), _ptr(tau), _ptr(_c128(Gfull)), _ptr(_c128(zhat)),
                           len(idx), _ptr(idx), plan.estimator, passes, _ptr(out))
     return out
+
+
+# ---------------------------------------- final residual-energy check
+def residual_energy(plan, zhat, idx, val):
+    """(e_res, e_tot): energy of the plan's L loops of bucket values zhat
+    after subtracting the coefficients (idx, val) from every bucket by the
+    exact bucket identity, and their energy before (Eq. 5's error left after
+    recovery, seen through the buckets)."""
+    sigma, tau, _ = loop_params(plan.N, plan.L, plan.seed)
+    Gfull = filter_gain_full(plan.N, plan.w, plan.g)
+    idx = np.ascontiguousarray(idx, np.int32)
+    v = _c128(np.asarray(val, np.complex128))
+    er = np.zeros(1, np.float64)
+    et = np.zeros(1, np.float64)
+    _load().oracle_residual_energy(plan.N, plan.B, plan.L, _ptr(sigma), _ptr(tau), _ptr(_c128(Gfull)),
+                                   _ptr(_c128(zhat)), len(idx), _ptr(idx), _ptr(v), _ptr(er), _ptr(et))
+    return float(er[0]), float(et[0])
 
 
 # ------------------------------- sFFT4.0 / MPFFT-style search location

@@ -929,3 +929,26 @@ int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b,
     free(nfv);
     return kout;
 }
+
+/* ==================================================================
+ * Final residual-energy check (problem statement, Eq. 5: the error left
+ * after recovery).  Energy of every loop's buckets after the recovered
+ * coefficients are subtracted by the exact bucket identity.
+ * ================================================================== */
+
+void oracle_residual_energy(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau,
+                            const double *Gfull, const double *zhat, int64_t n, const int32_t *idx,
+                            const double *val, double *e_res, double *e_tot)
+{
+    double *r = (double *)malloc(sizeof(double) * 2 * (size_t)B);
+    double er = 0.0, et = 0.0;
+    for (int l = 0; l < L; ++l) {
+        for (int64_t k = 0; k < 2 * B; ++k) r[k] = zhat[2 * (int64_t)l * B + k];
+        for (int64_t k = 0; k < B; ++k) et += r[2 * k] * r[2 * k] + r[2 * k + 1] * r[2 * k + 1];
+        oracle_pe_subtract(N, B, sigma[l], tau[l], Gfull, n, idx, val, r);
+        for (int64_t k = 0; k < B; ++k) er += r[2 * k] * r[2 * k] + r[2 * k + 1] * r[2 * k + 1];
+    }
+    free(r);
+    *e_res = er;
+    *e_tot = et;
+}

@@ -2,8 +2,9 @@
  * FP64 CPU oracle for the flat-window voting sparse FFT (sFFT1.0-style), its
  * phase-encoding, iterative variant (sFFT3.0-style), the spike-train
  * pre-filter in front of voting (sFFT2.0-style), the averaging estimator,
- * the iterative-framework refinement of the voting output, and the location
- * by binary or multi-scale search (sFFT4.0 / MPFFT-style).
+ * the iterative-framework refinement of the voting output, the location
+ * by binary or multi-scale search (sFFT4.0 / MPFFT-style), and the final
+ * residual-energy check.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may include, link or
  * call this code: only the tests, the package smoke check and the benchmark's
@@ -234,6 +235,17 @@ int64_t oracle_bs_locate(int64_t N, int64_t B, int b, int64_t sigma, int64_t sig
 int64_t oracle_sfft_bs(int64_t N, int64_t K, int64_t B, int64_t w, int R, int b, double eta, double kappa,
                        double rho, uint64_t seed, const double *g, const double *Gfull, const double *x,
                        int32_t *idx, double *val, int *iters_out, int64_t *nfound_out);
+
+/* ---- final residual-energy check (Eq. 5, problem statement) ---- */
+
+/* Energy left in the L loops' bucket values zhat ([L][B] complex) after the
+   n recovered coefficients (idx, val complex) are subtracted from every
+   bucket of every loop by the exact identity of oracle_pe_subtract:
+   *e_res = sum_l sum_k |zhat_l[k] - sum_f v_f e^{+2 pi i tau_l f / N}
+   G~(sigma_l f - k N/B)|^2; *e_tot = sum_l sum_k |zhat_l[k]|^2. */
+void oracle_residual_energy(int64_t N, int64_t B, int L, const int64_t *sigma, const int64_t *tau,
+                            const double *Gfull, const double *zhat, int64_t n, const int32_t *idx,
+                            const double *val, double *e_res, double *e_tot);
 
 #ifdef __cplusplus
 }

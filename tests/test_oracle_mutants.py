@@ -17,6 +17,7 @@ import test_oracle_bs_pins as bs_pins
 import test_oracle_refine_pins as refine_pins
 import test_oracle_pe_pins as pe_pins
 import test_oracle_pins as pins
+import test_oracle_residual_pins as residual_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "sfft_oracle.c")
 
@@ -76,6 +77,14 @@ MUTANTS = [
     ("bs no lone-coefficient test", "if (res > rho * (double)J * e0) continue;", "if (0) continue;"),
     ("bs window not centred", "int64_t lo_p = k * NB - W / 2;", "int64_t lo_p = k * NB;"),
     ("bs threshold without the noise floor", "if (kappa * emed > thr) thr = kappa * emed;", "(void)emed;"),
+    # final residual-energy check
+    ("residual without subtraction", "oracle_pe_subtract(N, B, sigma[l], tau[l], Gfull, n, idx, val, r);",
+     "(void)val;"),
+    ("residual of loop 0 only", "for (int l = 0; l < L; ++l) {\n        for (int64_t k = 0; k < 2 * B; ++k) r[k]",
+     "for (int l = 0; l < 1; ++l) {\n        for (int64_t k = 0; k < 2 * B; ++k) r[k]"),
+    ("residual energy without the imaginary part",
+     "for (int64_t k = 0; k < B; ++k) er += r[2 * k] * r[2 * k] + r[2 * k + 1] * r[2 * k + 1];",
+     "for (int64_t k = 0; k < B; ++k) er += r[2 * k] * r[2 * k];"),
 ]
 
 PIN_CHECKS = [
@@ -117,6 +126,9 @@ PIN_CHECKS = [
     bs_pins.test_shared_bucket_rejected,
     lambda: bs_pins.test_exact_recovery_noiseless(1 << 12, 5, 32, 1),
     bs_pins.test_pure_noise_stops_after_one_iteration,
+    residual_pins.test_exact_recovery_leaves_nothing,
+    lambda: residual_pins.test_planted_miss_closed_form(3),
+    residual_pins.test_flipped_value_leaves_four_times_the_tone,
 ]
 
 
