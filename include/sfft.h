@@ -80,6 +80,9 @@ typedef struct {
                           (0, default: none; voting and comb methods, K <= 4096) */
     int32_t search_bits; /* SFFT_METHOD_SEARCH: bits per search digit, 1..4; 0 -> 1 (binary
                             search); b > 1: multi-scale search with l = 2^b */
+    int32_t residual;  /* 1: final residual-energy check in FP64 after the output (voting and
+                          comb methods; 4 <= B <= 8192), read with sfft_plan_last_stats;
+                          0 (default): none */
 } sfft_opts;
 
 /* Location methods.
@@ -146,14 +149,28 @@ typedef struct {
    the mean estimator otherwise carries. */
 #define SFFT_MAX_REFINE 8
 
+/* sfft_opts.residual = 1: the final residual-energy check (the error that
+   Eq. 5 bounds, seen through the buckets).  After the output (and any
+   refinement) the k_out recovered coefficients are subtracted in FP64 from
+   the L loops' bucket values by the bucket identity
+       zhat_l[k] = sum_f xhat_f exp(+2 pi i tau_l f / N) G~(sigma_l f - k N/B)
+   (each coefficient from its own and both neighbouring buckets; further out
+   the flat window's gain is below 1e-7 of its passband), and the energy left,
+   sum_l sum_k |residual_l[k]|^2, is reported beside the buckets' energy
+   sum_l sum_k |zhat_l[k]|^2 (sfft_exec_stats).  A small ratio says the output
+   explains the buckets; a planted miss or a wrong value leaves that
+   coefficient's bucket energy. */
+
 /* Read-only description of a plan (host struct filled by sfft_plan_get_info). */
 typedef struct {
     int64_t N, w;
     int32_t K, B, L, c, T, nsel; /* nsel = min(c*K, B) */
     uint64_t seed;
-    int64_t samples_touched;     /* distinct sample indices read per execute (Table 2) */
+    int64_t samples_touched;     /* distinct sample indices read per execute (Table 2; counted
+                                    on the host at the first sfft_plan_get_info of a seed) */
     int64_t candidate_capacity;  /* min(N, (L-T+1)*nsel*N/B): bound on the candidate set */
-    size_t device_bytes;         /* device memory held by the plan */
+    size_t device_bytes;         /* device memory held by the plan itself (its scratch; the
+                                    tables it shares with plans of the same N, B, w are apart) */
     int32_t method;              /* SFFT_METHOD_* */
     int32_t estimator;           /* SFFT_ESTIMATOR_* */
     int32_t refine;              /* refinement passes */
@@ -161,11 +178,13 @@ typedef struct {
 
 /* ------------------------------------------------------------------ plans */
 
-/* Create a plan: validates sizes, derives sigma_l, tau_l (a0), computes the
-   window taps, the gain table and the FFT twiddles on the GPU in FP64 (a0'),
-   and allocates scratch on the current CUDA device.  *plan is NULL on failure.
-   Blocks until the plan-time kernels finish.  Errors: SFFT_EINVAL, SFFT_ENOMEM,
-   SFFT_ECUDA. */
+/* Create a plan: validates sizes, derives sigma_l, tau_l (a0), and allocates
+   scratch on the current CUDA device.  The seed-independent tables (window
+   taps, gain tables, FFT twiddles; a0') are computed on the GPU in FP64 for
+   the first plan of each (device, N, B, w) and shared, reference-counted, by
+   every later plan of that shape (kept for reuse after their last plan goes).
+   *plan is NULL on failure.  Blocks until its set-up (and any table build)
+   has finished.  Errors: SFFT_EINVAL, SFFT_ENOMEM, SFFT_ECUDA. */
 sfft_status sfft_plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t B, int64_t w,
                              int32_t L, uint64_t seed);
 
@@ -176,6 +195,14 @@ sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t K, int32_t 
 /* Release a plan and its device memory (NULL is a no-op).  The caller must
    ensure no enqueued work still uses it. */
 void sfft_plan_destroy(sfft_plan *plan);
+
+/* Re-draw the plan's loop parameters for another seed (a0; the scratch and
+   the shared tables stay): sigma_l, tau_l as sfft_plan_create would draw them
+   for `seed`, uploaded on `stream`, so work enqueued on that stream afterwards
+   uses them (cached batch graphs of the plan stay valid).  The caller must
+   ensure no work of the plan is in flight on another stream.  Errors:
+   SFFT_EINVAL, SFFT_ECUDA. */
+sfft_status sfft_plan_reseed(sfft_plan *plan, uint64_t seed, void *stream);
 
 sfft_status sfft_plan_get_info(const sfft_plan *plan, sfft_plan_info *info);
 
@@ -196,6 +223,9 @@ typedef struct {
     float theta;         /* prune threshold: 1/4 of the K-th largest bucket energy
                             (phase encoding: the bucket-energy threshold) */
     int32_t iterations;  /* phase encoding: iterations run; voting: L */
+    double residual_energy;  /* sfft_opts.residual: energy left in the buckets after
+                                subtracting the output (FP64); else -1 */
+    double bucket_energy;    /* sfft_opts.residual: energy of the buckets (FP64); else -1 */
 } sfft_exec_stats;
 
 sfft_status sfft_plan_last_stats(const sfft_plan *plan, sfft_exec_stats *stats);
@@ -251,10 +281,11 @@ sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *const *x_de
 /* Measurement form of sfft_execute_batch: enqueues `steps` back-to-back runs
    of the batch on `stream` (no graph) with CUDA events recorded on that
    stream around each of its six stages (gather-fold, FFT+select, vote scan,
-   survivor estimate, fallback, refinement; the top-K and any fallback pass
-   run in the last estimate CTA of each job, so the fourth stage holds them
-   and the fifth is empty; the sixth holds the refinement passes of plans
-   with sfft_opts.refine > 0, else it is empty), waits for the last
+   survivor estimate, refinement, residual check; the top-K and any fallback
+   pass run in the last estimate CTA of each job, so the fourth stage holds
+   them; the fifth holds the refinement passes of plans with
+   sfft_opts.refine > 0 and the sixth the residual check of plans with
+   sfft_opts.residual, else they are empty), waits for the last
    one, and returns the device time from the first event to the last
    (*total_ms) and the summed time of each stage over all steps
    (stage_ms[6]).  Errors as for sfft_execute_batch. */
@@ -326,6 +357,8 @@ typedef struct {
     const float *x_dev;    /* complex64[N], device, caller-owned, valid until done */
     int32_t *idx_dev;      /* int32[K], device */
     float *val_dev;        /* complex64[K], device */
+    int32_t count_samples; /* 1: sfft_result.samples_touched is counted (O(L w) host work
+                              on the thread that takes the result); 0: it is -1 */
 } sfft_request;
 
 typedef struct {
@@ -337,8 +370,15 @@ typedef struct {
 
 /* Start a serving loop on the current device: a host thread admits submitted
    requests while their plans fit in hbm_budget_bytes and at most max_slots
-   are in flight, batches whatever is admitted, and launches it while earlier
-   batches still run (continuous batching).  Plans are cached and reused. */
+   are in flight, batches whatever is admitted (one location method per
+   batch), and launches it while earlier batches still run (continuous
+   batching: requests arriving meanwhile join the next batch).  Plans are
+   cached by shape (N, B, w, L, options and, for voting, K rounded up to a
+   power of two) and rebound to each request's own K and seed, so distinct
+   seeds reuse them; a shape without an idle plan is built by a second host
+   thread while admission goes on, and idle plans are evicted least recently
+   used to fit the budget.  max_slots = 1 serves one request at a time (the
+   plain per-signal path through the same machinery). */
 sfft_status sfft_server_create(sfft_server **srv, size_t hbm_budget_bytes, int32_t max_slots);
 
 /* Queue one request; *ticket identifies it.  SFFT_EBUSY if its plan alone

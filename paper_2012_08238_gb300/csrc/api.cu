@@ -18,14 +18,16 @@ struct sfft_plan {
     int device;
     int64_t N, w;
     int32_t K, B, L, c, T, nsel;
+    int32_t K_cap;           // largest K the scratch was sized for (>= K)
     uint64_t seed;
     uint32_t sigma_inv[sfft::kMaxL];
-    int64_t samples_touched;
+    mutable int64_t samples_touched;  // -1 until first asked for (host count)
     int64_t cap;
-    size_t device_bytes;
+    size_t device_bytes;     // this plan's scratch (the shared tables not included)
     sfft::PlanDev h;         // host mirror of the device descriptor
     sfft::PlanDev *d;        // device descriptor
-    void *dmem;              // single allocation holding everything
+    void *dmem;              // single allocation holding the descriptor and the scratch
+    const void *tables;      // shared seed-independent tables (tables_acquire)
     // staging for sfft_execute_host (allocated on first use)
     void *stage;
 };
@@ -148,8 +150,7 @@ void decompose(PlanDev &P) {
 }
 
 struct Layout {
-    size_t plan, taps, tw, ginv, gext, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, survf, surv, rscr, ctr,
-        total;
+    size_t plan, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, survf, surv, rscr, resid, ctr, total;
 };
 
 Layout layout_of(const PlanDev &P, int64_t cap) {
@@ -164,10 +165,6 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     // phase encoding keeps the two shifts' partials and bucket values in rows 0 and 1
     const size_t L = phase ? std::max<uint32_t>(P.L, 2) : P.L, B = P.B;
     o.plan = take(sizeof(PlanDev));
-    o.taps = take(sizeof(float) * P.w);
-    o.tw = take(sizeof(float2) * (B / 2));
-    o.ginv = take(sizeof(float2) * (P.N / B));
-    o.gext = take(phase || P.refine ? sizeof(float2) * 3 * (P.N / B) : 0);
     const bool comb = P.method == kMethodComb;
     o.ctw = take(comb ? sizeof(float2) * (P.Bc / 2) : 0);
     o.cls = take(comb ? sizeof(uint32_t) * P.ncls : 0);
@@ -182,6 +179,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.survf = take(sizeof(uint32_t) * (size_t)cap);
     o.surv = take(sizeof(uint4) * (size_t)cap);
     o.rscr = take(P.refine ? sizeof(float2) * P.K * P.L : 0);
+    o.resid = take(P.residual ? sizeof(double) * 2 * P.L : 0);
     o.ctr = take(sizeof(uint32_t) * kNumCounters);
     o.total = off;
     return o;
@@ -190,7 +188,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
 // Sizes and work split of a plan, without touching the device.
 void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
                    int64_t *cap, uint32_t method, uint32_t Bc, uint32_t estimator = kEstMedian,
-                   uint32_t refine = 0, uint32_t srch_b = 1) {
+                   uint32_t refine = 0, uint32_t srch_b = 1, uint32_t residual = 0) {
     memset(&P, 0, sizeof(P));
     const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     P.N = (uint32_t)N;
@@ -212,6 +210,7 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.estimator = estimator;
     P.refine = refine;
     P.srch_b = srch_b;
+    P.residual = residual;
     if (method == kMethodComb) {
         P.Bc = Bc;
         P.logBc = ilog2(Bc);
@@ -224,7 +223,73 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.cap = (uint32_t)*cap;
 }
 
+// A voting plan's descriptor fields that depend on K (scratch already sized
+// for a K at least this large).
+void set_K(PlanDev &P, int32_t K, int64_t *cap, int32_t c) {
+    P.K = (uint32_t)K;
+    P.Kl = (uint32_t)std::min<int32_t>(K, (int32_t)P.B);
+    P.nsel = (uint32_t)std::min<int64_t>((int64_t)c * K, P.B);
+    *cap = std::min<int64_t>(P.N, (int64_t)(P.L - P.T + 1) * P.nsel * (P.N / P.B));
+    P.cap = (uint32_t)*cap;
+}
+
+// Distinct sample indices the plan's loops read (Table 2's sampling count),
+// counted on the host with an N-bit map: the gather's indices
+// (sigma m + tau) mod N, plus for phase encoding the sample one past each and
+// for the search the samples at every search shift.
+int64_t samples_touched_host(const PlanDev &P) {
+    const uint32_t N = P.N, w = P.w, mask = N - 1;
+    std::vector<uint64_t> bits(((size_t)N + 63) / 64, 0);
+    auto mark = [&](uint32_t i) { bits[i >> 6] |= 1ull << (i & 63); };
+    uint32_t nsh = 1, bb = 0, sbits = 0;
+    if (P.method == kMethodSearch) {
+        bb = P.srch_b;
+        sbits = P.logN - P.logB + 1 < P.logN ? P.logN - P.logB + 1 : P.logN;
+        nsh = 1 + (sbits + bb - 1) / bb;
+    }
+    for (uint32_t l = 0; l < P.L; ++l)
+        for (uint32_t q = 0; q < w; ++q) {
+            const uint32_t i = (P.sigma[l] * (q - w / 2) + P.tau[l]) & mask;
+            mark(i);
+            if (P.method == kMethodPhase) mark((i + 1) & mask);
+            for (uint32_t j = 1; j < nsh; ++j) mark((i + (N >> std::min(j * bb, sbits))) & mask);
+        }
+    int64_t n = 0;
+    for (uint64_t v : bits) n += __builtin_popcountll(v);
+    return n;
+}
+
+// The calling thread's non-blocking stream for plan set-up on the current device.
+cudaError_t setup_stream(cudaStream_t &out) {
+    thread_local int dev = -1;
+    thread_local cudaStream_t st = nullptr;
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (dev != d) {
+        // a stream of another device is left to process teardown
+        st = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        dev = d;
+    }
+    out = st;
+    return cudaSuccess;
+}
+
 }  // namespace
+
+int64_t samples_touched_of(int64_t N, int32_t B, int64_t w, int32_t L, uint64_t seed, const sfft_opts &o) {
+    PlanDev P;
+    int64_t cap;
+    const uint32_t method = o.method == SFFT_METHOD_PHASE    ? kMethodPhase
+                            : o.method == SFFT_METHOD_SEARCH ? kMethodSearch
+                            : o.method == SFFT_METHOD_COMB   ? kMethodComb
+                                                             : kMethodVoting;
+    fill_plan_dev(P, N, 1, B, w, L, 1, 1, &cap, method, method == kMethodComb ? 2u : 0u, kEstMedian, 0,
+                  (uint32_t)std::max<int32_t>(o.search_bits, 1));
+    loop_params_host(N, L, seed, P.sigma, P.tau, nullptr);
+    return samples_touched_host(P);
+}
 
 size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
                          const sfft_opts &o) {
@@ -241,7 +306,8 @@ size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, 
                                                  : kMethodVoting,
                   (uint32_t)std::min<int64_t>(N, kMaxComb),
                   o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian,
-                  (uint32_t)std::max<int32_t>(o.refine, 0), (uint32_t)std::max<int32_t>(o.search_bits, 1));
+                  (uint32_t)std::max<int32_t>(o.refine, 0), (uint32_t)std::max<int32_t>(o.search_bits, 1),
+                  o.residual ? 1u : 0u);
     return layout_of(P, cap).total;
 }
 
@@ -270,6 +336,7 @@ struct Sizes {
     uint32_t max_nbuf = 0; // search: largest count of bucket buffers
     bool refine = false;   // some job refines its output
     uint32_t max_rK = 0;   // refinement: largest K of the refining jobs
+    uint32_t max_resB = 0; // residual check: largest B of the checking jobs (0: none checks)
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -305,6 +372,7 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.est_smem = estimate_tab_bytes(p->h.N, p->h.B, p->h.L);
     z.refine = p->h.refine > 0;
     z.max_rK = z.refine ? p->h.K : 0u;
+    z.max_resB = p->h.residual ? p->h.B : 0u;
     return z;
 }
 
@@ -354,8 +422,8 @@ cudaError_t side_res(SideRes *&out) {
 // top K, running the job's fallback pass first when needed), all
 // stream-ordered.  With ev (kStages + 1 events) the events bracket the
 // stages: gather, FFT/select (and the wait for the comb kernel of comb
-// plans), scan, estimate + top-K, fallback (empty), refinement (empty unless
-// a plan refines).
+// plans), scan, estimate + top-K, refinement (empty unless a plan refines),
+// residual check (empty unless a plan checks).
 cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
                             const Launch &lj, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
@@ -384,9 +452,11 @@ cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv
     if ((e = mark(3)) != cudaSuccess) return e;
     if ((e = launch_estimate(le, z.jobs, z.L_uniform, z.est_ctas, z.est_smem, z.max_K, s)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    if ((e = mark(5)) != cudaSuccess) return e;
     // refining jobs: the iterative framework's subtraction over the found set
     if (z.refine && (e = launch_refine(lj, z.jobs, z.max_rK, z.L_uniform, s)) != cudaSuccess) return e;
+    if ((e = mark(5)) != cudaSuccess) return e;
+    // checking jobs: FP64 energy left after subtracting the final output
+    if (z.max_resB && (e = launch_residual(ls, z.select, z.max_resB, s)) != cudaSuccess) return e;
     return mark(6);
 }
 
@@ -507,8 +577,12 @@ extern "C" sfft_status sfft_plan_create(sfft_plan **plan, int64_t N, int32_t K, 
     return sfft_plan_create_ex(plan, N, K, B, w, L, seed, nullptr);
 }
 
-extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t K, int32_t B, int64_t w,
-                                           int32_t L, uint64_t seed, const sfft_opts *opts) {
+namespace sfft {
+
+// Plan creation with scratch sized for up to K_cap output coefficients (K <=
+// K_cap; the serving loop rebinds cached voting plans to other K and seeds).
+sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, int64_t B, int64_t w, int32_t L,
+                        uint64_t seed, const sfft_opts *opts) {
     if (!plan) {
         set_error("plan pointer is NULL");
         return SFFT_EINVAL;
@@ -550,15 +624,27 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
         set_error("sfft_opts.estimator applies to the voting and comb methods");
         return SFFT_EINVAL;
     }
-    if (o.refine < 0 || o.refine > SFFT_MAX_REFINE || (o.refine && (phase || K > (int32_t)kRefineMaxK))) {
+    if (K_cap < K || (K_cap != K && o.method != SFFT_METHOD_VOTING)) {
+        set_error("plan capacity below K (or a capacity for a method other than voting)");
+        return SFFT_EINVAL;
+    }
+    if (o.refine < 0 || o.refine > SFFT_MAX_REFINE || (o.refine && (phase || K_cap > (int32_t)kRefineMaxK))) {
         set_error("sfft_opts.refine must be 0..8 passes, for the voting and comb methods with K <= 4096");
+        return SFFT_EINVAL;
+    }
+    if (o.residual != 0 && (o.residual != 1 || phase || B < 4 || B > (int32_t)kResidualMaxB)) {
+        set_error("sfft_opts.residual must be 0 or 1, for the voting and comb methods with 4 <= B <= 8192");
         return SFFT_EINVAL;
     }
     // (phase encoding reads no c or T)
     const int32_t c = phase ? 1 : (o.c > 0 ? o.c : 2);
     const int32_t T = phase ? 1 : (o.T > 0 ? o.T : (L + 1) / 2);
-    sfft_status st = check_sizes(N, K, B, w, L, c, T);
+    sfft_status st = check_sizes(N, K_cap, (int32_t)B, w, L, c, T);
     if (st != SFFT_OK) return st;
+    if (K < 1) {
+        set_error("K must lie in [1, min(N, 16384)]");
+        return SFFT_EINVAL;
+    }
     uint32_t Bc = 0;
     if (comb) {
         // residue classes: a power of two dividing N/G (G = B/32 frequencies per
@@ -605,33 +691,48 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     p->N = N;
     p->w = w;
     p->K = K;
-    p->B = B;
+    p->K_cap = K_cap;
+    p->B = (int32_t)B;
     p->L = L;
     p->c = c;
     p->T = T;
-    p->nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     p->seed = seed;
+    p->samples_touched = -1;
 
+    // scratch sized for K_cap, then the descriptor set to K
     PlanDev &P = p->h;
-    fill_plan_dev(P, N, K, B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc,
-                  o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian, (uint32_t)o.refine, (uint32_t)sb);
+    fill_plan_dev(P, N, K_cap, (int32_t)B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc,
+                  o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian, (uint32_t)o.refine, (uint32_t)sb,
+                  (uint32_t)o.residual);
+    const Layout lay = layout_of(P, p->cap);
+    if (K != K_cap) set_K(P, K, &p->cap, c);
+    p->nsel = (int32_t)P.nsel;
     // (comb plans: loops L and L+1 give the comb shifts)
     loop_params_host(N, L + (comb ? (int32_t)kCombShifts : 0), seed, P.sigma, P.tau, p->sigma_inv);
-    const Layout lay = layout_of(P, p->cap);
+
+    TableSet tab;
+    st = tables_acquire(P.N, P.B, P.w, phase || P.refine, P.residual != 0, &p->tables, &tab);
+    if (st != SFFT_OK) {
+        delete p;
+        return st;
+    }
     p->device_bytes = lay.total;
-    const size_t off = lay.total;
-    cudaError_t e = cudaMalloc(&p->dmem, off);
+    cudaError_t e = cudaMalloc(&p->dmem, lay.total);
     if (e != cudaSuccess) {
+        tables_release(p->tables);
         delete p;
         return cuda_fail(e, "cudaMalloc(plan)");
     }
     char *base = static_cast<char *>(p->dmem);
     p->d = reinterpret_cast<PlanDev *>(base + lay.plan);
-    P.taps = reinterpret_cast<float *>(base + lay.taps);
-    P.tw = reinterpret_cast<float2 *>(base + lay.tw);
-    P.ginv = reinterpret_cast<float2 *>(base + lay.ginv);
-    P.gext = phase || P.refine ? reinterpret_cast<float2 *>(base + lay.gext) : nullptr;
+    P.taps = tab.taps;
+    P.tw = tab.tw;
+    P.ginv = tab.ginv;
+    P.gext = tab.gext;
+    P.gext64 = tab.gext64;
+    P.ginv2max = tab.ginv2max;
     P.rscr = P.refine ? reinterpret_cast<float2 *>(base + lay.rscr) : nullptr;
+    P.resid = P.residual ? reinterpret_cast<double *>(base + lay.resid) : nullptr;
     P.ctw = comb ? reinterpret_cast<float2 *>(base + lay.ctw) : nullptr;
     P.cls = comb ? reinterpret_cast<uint32_t *>(base + lay.cls) : nullptr;
     P.keptc = comb ? reinterpret_cast<uint32_t *>(base + lay.keptc) : nullptr;
@@ -646,59 +747,65 @@ extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t 
     P.surv = reinterpret_cast<uint4 *>(base + lay.surv);
     P.ctr = reinterpret_cast<uint32_t *>(base + lay.ctr);
 
-    // plan-time tables on a private stream
-    cudaStream_t s = nullptr;
-    double *ginv2 = nullptr;
-    void *tmp = nullptr;  // bitmap + counters
-    const size_t nb = (size_t)(N / B);
-    const size_t bitmap_bytes = align256(((size_t)N + 31) / 32 * 4);
+    // descriptor, counters and the comb twiddles on the thread's set-up stream
     auto fail = [&](cudaError_t err, const char *what) {
-        if (s) cudaStreamDestroy(s);
-        if (ginv2) cudaFree(ginv2);
-        if (tmp) cudaFree(tmp);
         cudaFree(p->dmem);
+        tables_release(p->tables);
         delete p;
         return cuda_fail(err, what);
     };
-    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
-    if ((e = cudaMalloc(&ginv2, sizeof(double) * nb)) != cudaSuccess) return fail(e, "cudaMalloc(gain)");
-    if ((e = cudaMalloc(&tmp, bitmap_bytes + 256)) != cudaSuccess) return fail(e, "cudaMalloc(bitmap)");
+    cudaStream_t s = nullptr;
+    if ((e = setup_stream(s)) != cudaSuccess) return fail(e, "set-up stream");
     if ((e = cudaMemcpyAsync(p->d, &P, sizeof(PlanDev), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(e, "upload plan");
     if ((e = cudaMemsetAsync(P.ctr, 0, sizeof(uint32_t) * kNumCounters, s)) != cudaSuccess)
         return fail(e, "clear counters");
-    if ((e = plan_tables(P.N, P.B, P.w, const_cast<float *>(P.taps), const_cast<float2 *>(P.tw),
-                         const_cast<float2 *>(P.ginv), ginv2, const_cast<float2 *>(P.gext), s)) != cudaSuccess)
-        return fail(e, "plan tables");
     if (comb && (e = plan_twiddles(P.Bc, const_cast<float2 *>(P.ctw), s)) != cudaSuccess)
         return fail(e, "comb twiddles");
-    unsigned long long *d_count = reinterpret_cast<unsigned long long *>(static_cast<char *>(tmp) + bitmap_bytes);
-    unsigned long long *d_max = d_count + 1;
-    if ((e = plan_max_bits(ginv2, (uint32_t)nb, d_max, s)) != cudaSuccess) return fail(e, "gain max");
-    const uint32_t *d_sigma = reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(p->d) + offsetof(PlanDev, sigma));
-    const uint32_t *d_tau = reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(p->d) + offsetof(PlanDev, tau));
-    if ((e = plan_samples_touched(P.N, P.w, P.L, d_sigma, d_tau, static_cast<uint32_t *>(tmp), d_count,
-                                  phase ? 1 : 0, s, search ? P.srch_b : 0u, P.logB)) != cudaSuccess)
-        return fail(e, "samples touched");
-    unsigned long long host2[2] = {0, 0};
-    if ((e = cudaMemcpyAsync(host2, d_count, sizeof(host2), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return fail(e, "download stats");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "plan kernels");
-    p->samples_touched = (int64_t)host2[0];
-    double gmax;
-    memcpy(&gmax, &host2[1], sizeof(double));
-    float gf = (float)gmax;
-    if ((double)gf < gmax) gf = nextafterf(gf, INFINITY);
-    P.ginv2max = gf;
-    // second upload with the gain bound filled in
-    if ((e = cudaMemcpyAsync(p->d, &P, sizeof(PlanDev), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return fail(e, "upload plan");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "upload plan");
-    cudaStreamDestroy(s);
-    cudaFree(ginv2);
-    cudaFree(tmp);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "plan set-up");
     *plan = p;
     return SFFT_OK;
+}
+
+// Rebinds an idle plan to another seed (new sigma, tau) and, for voting
+// plans, another K <= K_cap: the descriptor is re-uploaded on stream s, so
+// work enqueued on s afterwards sees the new parameters.  A changed K changes
+// launch shapes, so the plan takes a new identity (cached batch graphs of
+// the old one no longer match).
+sfft_status plan_rebind(sfft_plan *p, int32_t K, uint64_t seed, cudaStream_t s) {
+    if (K < 1 || K > p->K_cap || (K != p->K && p->h.method != kMethodVoting)) {
+        set_error("rebind: K beyond the plan's capacity (or K changed on a plan other than voting)");
+        return SFFT_EINVAL;
+    }
+    PlanDev &P = p->h;
+    if (K != p->K) {
+        set_K(P, K, &p->cap, p->c);
+        p->K = K;
+        p->nsel = (int32_t)P.nsel;
+        p->id = g_next_id.fetch_add(1);
+    }
+    const bool comb = P.method == kMethodComb;
+    loop_params_host(p->N, p->L + (comb ? (int32_t)kCombShifts : 0), seed, P.sigma, P.tau, p->sigma_inv);
+    p->seed = seed;
+    p->samples_touched = -1;
+    // (from pageable memory: the descriptor is staged before the call returns)
+    SFFT_CUDA_TRY(cudaMemcpyAsync(p->d, &P, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
+    return SFFT_OK;
+}
+
+}  // namespace sfft
+
+extern "C" sfft_status sfft_plan_create_ex(sfft_plan **plan, int64_t N, int32_t K, int32_t B, int64_t w,
+                                           int32_t L, uint64_t seed, const sfft_opts *opts) {
+    return plan_create(plan, N, K, K, B, w, L, seed, opts);
+}
+
+extern "C" sfft_status sfft_plan_reseed(sfft_plan *p, uint64_t seed, void *stream) {
+    if (!p) {
+        set_error("NULL plan");
+        return SFFT_EINVAL;
+    }
+    return plan_rebind(p, p->K, seed, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" void sfft_plan_destroy(sfft_plan *plan) {
@@ -706,6 +813,7 @@ extern "C" void sfft_plan_destroy(sfft_plan *plan) {
     forget_plan_graphs(plan->id);
     if (plan->stage) cudaFree(plan->stage);
     cudaFree(plan->dmem);
+    tables_release(plan->tables);
     delete plan;
 }
 
@@ -723,6 +831,7 @@ extern "C" sfft_status sfft_plan_get_info(const sfft_plan *p, sfft_plan_info *in
     info->T = p->T;
     info->nsel = p->nsel;
     info->seed = p->seed;
+    if (p->samples_touched < 0) p->samples_touched = samples_touched_host(p->h);
     info->samples_touched = p->samples_touched;
     info->candidate_capacity = p->cap;
     info->device_bytes = p->device_bytes;
@@ -753,6 +862,20 @@ extern "C" sfft_status sfft_plan_last_stats(const sfft_plan *p, sfft_exec_stats 
     }
     uint32_t c[kNumCounters];
     SFFT_CUDA_TRY(cudaMemcpy(c, p->h.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    st->residual_energy = -1.0;
+    st->bucket_energy = -1.0;
+    if (p->h.residual) {
+        // per-loop pairs summed in loop order
+        std::vector<double> r(2 * (size_t)p->L);
+        SFFT_CUDA_TRY(cudaMemcpy(r.data(), p->h.resid, sizeof(double) * r.size(), cudaMemcpyDeviceToHost));
+        double er = 0.0, et = 0.0;
+        for (int32_t l = 0; l < p->L; ++l) {
+            er += r[2 * l];
+            et += r[2 * l + 1];
+        }
+        st->residual_energy = er;
+        st->bucket_energy = et;
+    }
     if (iterative(p->h.method)) {
         // found coefficients (kNGe), iterations run, bucket-energy threshold
         st->candidates = -1;
@@ -866,6 +989,7 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         z.max_Bc = std::max(z.max_Bc, s.max_Bc);
         z.refine = z.refine || s.refine;
         z.max_rK = std::max(z.max_rK, s.max_rK);
+        z.max_resB = std::max(z.max_resB, s.max_resB);
     }
     // pruned estimate with staged tables: one wave of resident CTAs over the
     // batch (each CTA stages its job's tables once)

@@ -1,5 +1,5 @@
-// Plan-time kernels: flat-window taps, window gain table and FFT twiddles in
-// FP64 (step a0'), and the count of distinct samples a plan reads.
+// Plan-time kernels: flat-window taps, window gain tables and FFT twiddles in
+// FP64 (step a0').
 #include <math_constants.h>
 
 #include <algorithm>
@@ -59,10 +59,11 @@ __global__ void k_gain(uint32_t N, uint32_t B, uint32_t w, const double *g64, fl
     }
 }
 
-// G~(nu) itself (FP32) for nu in [-3N/2B, 3N/2B): the gains of a coefficient
-// in its own bucket and both neighbours, used by the phase-encoding
-// subtraction.  One CTA per offset.
-__global__ void k_gain_ext(uint32_t N, uint32_t B, uint32_t w, const double *g64, float2 *gext) {
+// G~(nu) itself for nu in [-3N/2B, 3N/2B): the gains of a coefficient in its
+// own bucket and both neighbours, used by the phase-encoding and refinement
+// subtractions (FP32, gext) and the residual check (FP64, gext64; either may
+// be NULL).  One CTA per offset.
+__global__ void k_gain_ext(uint32_t N, uint32_t B, uint32_t w, const double *g64, float2 *gext, double2 *gext64) {
     __shared__ double sre[256], sim[256];
     const uint32_t NB = N / B;
     const int64_t o = (int64_t)blockIdx.x - (int64_t)(3 * NB / 2);
@@ -86,7 +87,10 @@ __global__ void k_gain_ext(uint32_t N, uint32_t B, uint32_t w, const double *g64
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) gext[blockIdx.x] = make_float2((float)sre[0], (float)sim[0]);
+    if (threadIdx.x == 0) {
+        if (gext) gext[blockIdx.x] = make_float2((float)sre[0], (float)sim[0]);
+        if (gext64) gext64[blockIdx.x] = make_double2(sre[0], sim[0]);
+    }
 }
 
 __global__ void k_twiddle(uint32_t B, float2 *tw) {
@@ -95,39 +99,6 @@ __global__ void k_twiddle(uint32_t B, float2 *tw) {
         sincospi(-2.0 * (double)k / (double)B, &sn, &cs);
         tw[k] = make_float2((float)cs, (float)sn);
     }
-}
-
-// pair: also the sample one past each (the phase-encoding shift tau + 1)
-// Marks the samples the loops read: at shift tau_l (mode 0), also tau_l + 1
-// (mode 1: phase encoding), or at tau_l + s for the nsh shifts s of the
-// search (mode 2: s_0 = 0, s_j = N >> min(j b, bits)).
-__global__ void k_mark(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma, const uint32_t *tau,
-                       uint32_t *bitmap, int mode, uint32_t b, uint32_t bits, uint32_t nsh) {
-    const uint64_t total = (uint64_t)L * w;
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t l = (uint32_t)(t / w), q = (uint32_t)(t % w);
-        const uint32_t i = (sigma[l] * (q - w / 2) + tau[l]) & (N - 1);
-        atomicOr(bitmap + (i >> 5), 1u << (i & 31));
-        if (mode == 1) {
-            const uint32_t i1 = (i + 1) & (N - 1);
-            atomicOr(bitmap + (i1 >> 5), 1u << (i1 & 31));
-        } else if (mode == 2) {
-            for (uint32_t j = 1; j < nsh; ++j) {
-                const uint32_t m = j * b < bits ? j * b : bits;
-                const uint32_t ij = (i + (N >> m)) & (N - 1);
-                atomicOr(bitmap + (ij >> 5), 1u << (ij & 31));
-            }
-        }
-    }
-}
-
-__global__ void k_popc(const uint32_t *bitmap, uint32_t nwords, unsigned long long *count) {
-    unsigned long long c = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x)
-        c += __popc(bitmap[i]);
-    c = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
 // max of non-negative doubles through their (monotone) bit patterns
@@ -155,7 +126,7 @@ cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, 
 }
 
 cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
-                        double *ginv2, float2 *gext, cudaStream_t s) {
+                        double *ginv2, float2 *gext, double2 *gext64, cudaStream_t s) {
     double *g64 = nullptr;
     cudaError_t e = cudaMallocAsync(&g64, sizeof(double) * w, s);
     if (e != cudaSuccess) return e;
@@ -163,7 +134,7 @@ cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 
     const double sg = (double)B * sqrt((double)logN);
     k_taps<<<(w + 255) / 256, 256, 0, s>>>(N, B, w, sg, g64, taps);
     k_gain<<<N / B, 256, 0, s>>>(N, B, w, g64, ginv, ginv2);
-    if (gext) k_gain_ext<<<3 * (N / B), 256, 0, s>>>(N, B, w, g64, gext);
+    if (gext || gext64) k_gain_ext<<<3 * (N / B), 256, 0, s>>>(N, B, w, g64, gext, gext64);
     k_twiddle<<<(B / 2 + 255) / 256, 256, 0, s>>>(B, tw);
     e = cudaGetLastError();
     cudaError_t e2 = cudaFreeAsync(g64, s);
@@ -172,28 +143,6 @@ cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 
 
 cudaError_t plan_twiddles(uint32_t n, float2 *tw, cudaStream_t s) {
     k_twiddle<<<(n / 2 + 255) / 256, 256, 0, s>>>(n, tw);
-    return cudaGetLastError();
-}
-
-cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
-                                 const uint32_t *tau, uint32_t *bitmap, unsigned long long *count, int pair,
-                                 cudaStream_t s, uint32_t search_b, uint32_t logB) {
-    const uint32_t nwords = (N + 31) / 32;
-    cudaError_t e = cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * nwords, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
-    const uint64_t total = (uint64_t)L * w;
-    const uint32_t blocks = (uint32_t)std::min<uint64_t>((total + 255) / 256, 65535);
-    uint32_t logN = 0, bits = 0, nsh = 1;
-    while ((1u << logN) < N) ++logN;
-    if (search_b) {
-        bits = logN - logB + 1 < logN ? logN - logB + 1 : logN;
-        nsh = 1 + (bits + search_b - 1) / search_b;
-    }
-    k_mark<<<blocks, 256, 0, s>>>(N, w, L, sigma, tau, bitmap, search_b ? 2 : (pair ? 1 : 0), search_b, bits, nsh);
-    const uint32_t pb = std::min<uint32_t>((nwords + 255) / 256, 65535);
-    k_popc<<<pb, 256, 0, s>>>(bitmap, nwords, count);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
 constexpr int kEstTabCtasPerSm = 3;
+constexpr uint32_t kResidualMaxB = 8192;  // residual check: a loop's B residuals (FP64) in shared memory
 
 // Shared-memory bytes of a job's staged estimate tables: zhat (L B complex),
 // 1/G~ (N/B complex), kept bits (L B / 8 bytes); 0 when B < 32 (whole bit words).
@@ -76,6 +77,7 @@ struct PlanDev {
     uint32_t Bc, logBc, ncls;                 // comb: residue classes, kept classes
     uint32_t estimator;                       // kEstMedian or kEstMean
     uint32_t refine;                          // refinement passes (0: none)
+    uint32_t residual;                        // final residual-energy check (0: none)
     uint32_t sigma[kMaxL], tau[kMaxL];
     const float *taps;     // [w]
     const float2 *tw;      // [B/2] exp(-2 pi i k / B)
@@ -94,6 +96,8 @@ struct PlanDev {
     uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
     uint4 *surv;           // [cap] records {f, key bits, re bits, im bits}
     float2 *rscr;          // refinement: [K][L] per-loop estimates of a pass
+    const double2 *gext64; // residual check: [3N/B] G~(nu) in FP64, as gext
+    double *resid;         // residual check: [L][2] energy left, bucket energy per loop
     uint32_t *ctr;         // [kNumCounters]
 };
 
@@ -124,6 +128,14 @@ enum VoteMode : int { kVotePrune = 0, kVoteCandidates = 2 };
 // ---------------------------------------------------------------- host side
 void set_error(const std::string &msg);
 sfft_status cuda_fail(cudaError_t e, const char *what);
+// Plan creation with scratch for up to K_cap output coefficients (K <= K_cap;
+// K_cap != K only for the voting method), and the rebinding of an idle plan
+// to another K <= K_cap and seed on stream s (api.cu).
+sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, int64_t B, int64_t w, int32_t L,
+                        uint64_t seed, const sfft_opts *opts);
+sfft_status plan_rebind(sfft_plan *p, int32_t K, uint64_t seed, cudaStream_t s);
+// Distinct samples a plan of these sizes, options and seed reads (host count).
+int64_t samples_touched_of(int64_t N, int32_t B, int64_t w, int32_t L, uint64_t seed, const sfft_opts &o);
 
 // Kernel launchers (stream-ordered, no synchronisation).
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
@@ -174,23 +186,40 @@ inline uint32_t search_nbuf(uint32_t logN, uint32_t logB, uint32_t b) {
 // once.  max_K: the largest K of the refining jobs (<= kRefineMaxK);
 // L_uniform: the jobs' common L (0 when they differ).
 cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, uint32_t L_uniform, cudaStream_t s);
+// Final residual-energy check: one CTA per (job, loop) (ln: the FFT/select
+// prefix, L CTAs per job); jobs without the option return at once.  max_B:
+// the largest B of the checking jobs (<= kResidualMaxB).
+cudaError_t launch_residual(const Launch &ln, uint32_t total_ctas, uint32_t max_B, cudaStream_t s);
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s);
 cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *sel, cudaStream_t s);
 
+// Seed-independent tables of one (device, N, B, w), shared by plans
+// (tables.cu).  gext / gext64 are NULL unless requested.
+struct TableSet {
+    const float *taps;      // [w]
+    const float2 *tw;       // [B/2]
+    const float2 *ginv;     // [N/B]
+    const float2 *gext;     // [3N/B] or NULL
+    const double2 *gext64;  // [3N/B] or NULL
+    float ginv2max;         // max_o |1/G~(o)|^2, rounded up
+    size_t bytes;           // device bytes of the entry
+};
+// The current device's tables of this shape (built and waited for on first
+// use; ext: G~ over three buckets in FP32, ext64: in FP64).  *handle is
+// released by tables_release when the plan goes.
+sfft_status tables_acquire(uint32_t N, uint32_t B, uint32_t w, bool ext, bool ext64, const void **handle,
+                           TableSet *out);
+void tables_release(const void *handle);
+
 // Plan-time FP64 kernels (plan.cu).
 // gext (phase-encoding plans, else NULL): G~ over three buckets around 0.
+// gext64 (residual-checking plans, else NULL): the same three buckets in FP64.
 cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
-                        double *ginv2, float2 *gext, cudaStream_t s);
+                        double *ginv2, float2 *gext, double2 *gext64, cudaStream_t s);
 cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, cudaStream_t s);
 // exp(-2 pi i k / n), k < n/2 (FP64 -> FP32)
 cudaError_t plan_twiddles(uint32_t n, float2 *tw, cudaStream_t s);
-// pair: count the samples one past each too (phase encoding's second shift);
-// search_b > 0 (search plans with B = 2^logB buckets): the samples at every
-// search shift instead
-cudaError_t plan_samples_touched(uint32_t N, uint32_t w, uint32_t L, const uint32_t *sigma,
-                                 const uint32_t *tau, uint32_t *bitmap, unsigned long long *count, int pair,
-                                 cudaStream_t s, uint32_t search_b = 0, uint32_t logB = 0);
 
 }  // namespace sfft
 

@@ -28,7 +28,7 @@ SFFT_OK, SFFT_EINVAL, SFFT_ENOMEM, SFFT_ECUDA, SFFT_EBUSY, SFFT_ETIMEDOUT, SFFT_
 
 class sfft_opts(ctypes.Structure):
     _fields_ = [("c", _i32), ("T", _i32), ("precision", _i32), ("method", _i32), ("comb", _i32),
-                ("estimator", _i32), ("refine", _i32), ("search_bits", _i32)]
+                ("estimator", _i32), ("refine", _i32), ("search_bits", _i32), ("residual", _i32)]
 
 
 class sfft_plan_info(ctypes.Structure):
@@ -39,12 +39,13 @@ class sfft_plan_info(ctypes.Structure):
 
 class sfft_exec_stats(ctypes.Structure):
     _fields_ = [("candidates", _i64), ("estimated", _i64), ("recorded", _i64), ("fallback", _i32),
-                ("theta", ctypes.c_float), ("iterations", _i32)]
+                ("theta", ctypes.c_float), ("iterations", _i32), ("residual_energy", ctypes.c_double),
+                ("bucket_energy", ctypes.c_double)]
 
 
 class sfft_request(ctypes.Structure):
     _fields_ = [("N", _i64), ("w", _i64), ("K", _i32), ("B", _i32), ("L", _i32), ("seed", _u64),
-                ("opts", sfft_opts), ("x_dev", _p), ("idx_dev", _p), ("val_dev", _p)]
+                ("opts", sfft_opts), ("x_dev", _p), ("idx_dev", _p), ("val_dev", _p), ("count_samples", _i32)]
 
 
 class sfft_result(ctypes.Structure):
@@ -56,6 +57,7 @@ _SIGS = {
     "sfft_plan_create_ex": (_i32, [ctypes.POINTER(_p), _i64, _i32, _i32, _i64, _i32, _u64,
                                    ctypes.POINTER(sfft_opts)]),
     "sfft_plan_destroy": (None, [_p]),
+    "sfft_plan_reseed": (_i32, [_p, _u64, _p]),
     "sfft_plan_get_info": (_i32, [_p, ctypes.POINTER(sfft_plan_info)]),
     "sfft_plan_get_loops": (_i32, [_p, _p, _p, _p]),
     "sfft_loop_params": (_i32, [_i64, _i32, _u64, _p, _p, _p]),
@@ -189,13 +191,19 @@ SFFT_MAX_REFINE = 8
 
 
 def sfft_plan_create_ex(N, K, B, w, L, seed, c=0, T=0, precision=0, method=SFFT_METHOD_VOTING, comb=0,
-                        estimator=SFFT_ESTIMATOR_MEDIAN, refine=0, search_bits=0) -> Plan:
+                        estimator=SFFT_ESTIMATOR_MEDIAN, refine=0, search_bits=0, residual=0) -> Plan:
     return sfft_plan_create(N, K, B, w, L, seed,
-                            sfft_opts(c, T, precision, method, comb, estimator, refine, search_bits))
+                            sfft_opts(c, T, precision, method, comb, estimator, refine, search_bits, residual))
 
 
 def sfft_plan_destroy(plan: Plan):
     plan.destroy()
+
+
+def sfft_plan_reseed(plan: Plan, seed: int, stream=None):
+    """New loop parameters for `seed`, uploaded on `stream` (scratch and tables kept)."""
+    _check(lib().sfft_plan_reseed(plan.handle, seed, _stream(stream)))
+    plan._info = None
 
 
 def sfft_plan_get_info(plan: Plan) -> sfft_plan_info:
@@ -254,7 +262,7 @@ def sfft_execute_batch(plans, xs, idxs, vals, k_out, stream=None):
                                     _addr(k_out), n, _stream(stream)))
 
 
-STAGES = ("gather_fold", "fft_select", "vote_scan", "estimate", "fallback", "refine")
+STAGES = ("gather_fold", "fft_select", "vote_scan", "estimate", "refine", "residual")
 
 
 def sfft_execute_batch_timed(plans, xs, idxs, vals, k_out, steps, stream=None):
@@ -337,10 +345,10 @@ def sfft_server_destroy(srv: Server):
 
 
 def sfft_submit(srv: Server, N, K, B, w, L, seed, x, idx, val, c=0, T=0, method=0, comb=0, estimator=0,
-                refine=0, search_bits=0) -> int:
-    req = sfft_request(N, w, K, B, L, seed, sfft_opts(c, T, 0, method, comb, estimator, refine, search_bits),
-                       _addr(x), _addr(idx),
-                       _addr(val))
+                refine=0, search_bits=0, residual=0, count_samples=1) -> int:
+    req = sfft_request(N, w, K, B, L, seed,
+                       sfft_opts(c, T, 0, method, comb, estimator, refine, search_bits, residual),
+                       _addr(x), _addr(idx), _addr(val), int(count_samples))
     ticket = _u64()
     _check(lib().sfft_submit(srv.handle, ctypes.byref(req), ctypes.byref(ticket)))
     return ticket.value

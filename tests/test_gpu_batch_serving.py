@@ -229,3 +229,66 @@ def test_server_destroy_drains_outstanding_work():
     torch.cuda.synchronize()
     for sig, x, idx, val in bufs:
         assert np.array_equal(idx.cpu().numpy(), sig.freqs)
+
+
+# ------------------------------------------------- reseeding and shared tables
+def test_reseeded_plan_equals_a_fresh_plan_also_under_graph_replay():
+    N, K, B, L = 1 << 16, 10, 64, 8
+    w = configs.default_window(N, B)
+    sigs = [signals.make_signal(N, K, s, 20.0) for s in (21, 22)]
+    plans = [sfft.sfft_plan_create(N, K, B, w, L, s) for s in (1, 2)]
+    xs = [torch.from_numpy(g.x).cuda() for g in sigs]
+    idxs = [torch.zeros(K, dtype=torch.int32, device="cuda") for _ in range(2)]
+    vals = [torch.zeros(K, dtype=torch.complex64, device="cuda") for _ in range(2)]
+    kout = torch.zeros(2, dtype=torch.int32, device="cuda")
+    for _ in range(3):  # staging run, capture, replay: the graph now exists
+        sfft.sfft_execute_batch(plans, xs, idxs, vals, kout)
+    for p, s in zip(plans, (21, 22)):
+        sfft.sfft_plan_reseed(p, s)
+    assert plans[0].info.seed == 21
+    assert sfft.sfft_plan_get_loops(plans[0]) == sfft.sfft_loop_params(N, L, 21)
+    sfft.sfft_execute_batch(plans, xs, idxs, vals, kout)  # replays the cached graph
+    got = _collect(idxs, vals, kout)
+    for i, s in enumerate((21, 22)):
+        fresh = sfft.sfft_plan_create(N, K, B, w, L, s)
+        ref = run_execute(fresh, sigs[i].x)
+        assert _identical(ref[:2], got[i])
+        assert plans[i].info.samples_touched == fresh.info.samples_touched
+
+
+def test_plans_sharing_tables_outlive_each_other():
+    N, K, B, L = 1 << 15, 8, 128, 8
+    w = configs.default_window(N, B)
+    sig = signals.make_signal(N, K, 3, 30.0)
+    a = sfft.sfft_plan_create(N, K, B, w, L, 3)
+    ref = run_execute(a, sig.x)
+    b = sfft.sfft_plan_create(N, K, B, w, L, 3)  # same shape: the tables of a
+    a.destroy()
+    assert _identical(ref[:2], run_execute(b, sig.x)[:2])
+    c = sfft.sfft_plan_create(N, K, B, w, L, 3)
+    b.destroy()
+    assert _identical(ref[:2], run_execute(c, sig.x)[:2])
+
+
+def test_server_rebinds_cached_plans_to_each_seed_and_K():
+    # one voting shape (K up to 128 share a plan), 40 requests of distinct seeds and K
+    N, B, L = 1 << 16, 512, 8
+    w = configs.default_window(N, B)
+    srv = sfft.sfft_server_create(2 << 30, 8)
+    Ks = [65 + (37 * i) % 64 for i in range(40)]
+    reqs = [(N, Ks[i], B, w, L, 300 + i, 20.0) for i in range(40)]
+    served = _serve(srv, reqs)
+    for (N_, K, B_, w_, L_, seed, snr), (idx, val, res) in zip(reqs, served):
+        assert res.status == sfft.SFFT_OK and res.k_out == K
+        ref = run_execute(sfft.sfft_plan_create(N, K, B, w, L, seed), signals.make_signal(N, K, seed, snr).x)
+        assert _identical(ref[:2], (idx, val))
+    srv.destroy()
+
+
+def test_one_slot_server_is_the_plain_path():
+    srv = sfft.sfft_server_create(1 << 30, 1)
+    reqs = [(1 << 14, 5, 64, 64 * 35, 6, 900 + i, 20.0) for i in range(6)]
+    for (N, K, B, w, L, seed, snr), (idx, val, res) in zip(reqs, _serve(srv, reqs)):
+        ref = run_execute(sfft.sfft_plan_create(N, K, B, w, L, seed), signals.make_signal(N, K, seed, snr).x)
+        assert res.status == sfft.SFFT_OK and _identical(ref[:2], (idx, val))
+    srv.destroy()
