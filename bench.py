@@ -168,41 +168,184 @@ def time_oracle(pool, seeds) -> float:
     return max(per.values())
 
 
-def measure_served(sfft, torch, W, xs, dev, n_req, rate, seed=0):
-    """Requests through sfft_submit/sfft_wait: a saturation run (all
-    submitted at once) and a Poisson run at `rate` requests/s; latencies are
-    the server's submit-to-completion times."""
-    S = len(xs)
-    srv = sfft.sfft_server_create(16 << 30, 64)
-    idx = torch.zeros((n_req, W.K), dtype=torch.int32, device=dev)
-    val = torch.zeros((n_req, W.K), dtype=torch.complex64, device=dev)
+def _slices(torch, dev, Ks):
+    """One int32 and one complex64 device buffer holding every job's K outputs."""
+    off = np.concatenate([[0], np.cumsum(Ks)]).astype(np.int64)
+    idx_all = torch.zeros(int(off[-1]), dtype=torch.int32, device=dev)
+    val_all = torch.zeros(int(off[-1]), dtype=torch.complex64, device=dev)
+    return ([idx_all[off[i]:off[i + 1]] for i in range(len(Ks))],
+            [val_all[off[i]:off[i + 1]] for i in range(len(Ks))])
 
-    def submit(i):
-        return sfft.sfft_submit(srv, W.N, W.K, W.B, W.window, W.L, i % S, xs[i % S], idx[i], val[i])
 
-    def drain(tickets):
-        return [sfft.sfft_wait(srv, t, 120000).latency_ns for t in tickets]
+def _device_errors(torch, dev, N, K, seed, snr, idx, val):
+    """errors_sparse of one output against its regenerated exact spectrum (on the device)."""
+    from paper_2012_08238_gb300 import metrics as _m
 
-    drain([submit(i) for i in range(min(n_req, 2 * S))])  # plan cache warm-up
+    _, _, _, xhat = signals.make_signal_device(N, K, seed, snr, dev, with_xhat=True)
+    supp = torch.sort(torch.topk(xhat.abs(), K).indices).values
+    idx_t = idx.to(torch.int64)
+    return _m.errors_sparse(K, supp.cpu().numpy(), xhat[supp].cpu().numpy(), idx_t.cpu().numpy(),
+                            val.cpu().numpy(), xhat[idx_t].cpu().numpy())
+
+
+def measure_batched_c3(sfft, torch, dev, stream, args):
+    """The batched workload: 4096 signals of uneven N (2^14..2^22), K and SNR
+    in one sfft_execute_batch (one launch per stage over every signal), plans
+    sized by sfft_suggest_params; spectra/s timed by the library, by graph
+    replay and through the plain per-signal path, with L1 error and support
+    recall per size class."""
+    specs = configs.batched_mix(args.c3_signals)
+    plans, xs, Ks = [], [], []
+    for N, K, snr, seed in specs:
+        B, w, L = sfft.sfft_suggest_params(N, K, snr)
+        plans.append(sfft.sfft_plan_create(N, K, B, w, L, 50_000 + seed))
+        xs.append(signals.make_signal_device(N, K, 50_000 + seed, snr, dev)[0])
+        Ks.append(K)
+    idxs, vals = _slices(torch, dev, Ks)
+    kout = torch.zeros(len(specs), dtype=torch.int32, device=dev)
+    in_bytes = sum(8 * N for N, _, _, _ in specs)
+    for _ in range(max(3, args.warmup)):
+        sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+    torch.cuda.synchronize(dev)
+    steps = max(3, args.steps // 4)
+    total_ms, stage_ms = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, steps, stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)  # cached graph
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    graph_ms = e0.elapsed_time(e1) / steps
+    ks = torch.zeros(1, dtype=torch.int32, device=dev)
+    e0.record(stream)
+    for i in range(len(specs)):
+        sfft.sfft_execute(plans[i], xs[i], idxs[i], vals[i], ks, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = e0.elapsed_time(e1)
+    sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+    torch.cuda.synchronize(dev)
+    k = kout.cpu().numpy()
+    classes = {}
+    for i, (N, K, snr, seed) in enumerate(specs):
+        if i % args.c3_error_stride:
+            continue
+        e = _device_errors(torch, dev, N, K, 50_000 + seed, snr, idxs[i][: k[i]], vals[i][: k[i]])
+        c = classes.setdefault(N.bit_length() - 1, {"signals": 0, "l1": [], "miss": 0, "K": 0})
+        c["signals"] += 1
+        c["l1"].append(e["L1"])
+        c["miss"] += e["L0"]
+        c["K"] += K
+    per_class = {f"2^{n}": {"signals_checked": c["signals"], "l1_error": float(np.mean(c["l1"])),
+                            "support_recall": 1.0 - c["miss"] / c["K"]} for n, c in sorted(classes.items())}
+    S = len(specs)
+    out = {"value": S * steps / (total_ms / 1e3), "unit": UNIT, "ms_per_step": total_ms / steps,
+           "graph_value": S / (graph_ms / 1e3), "plain_value": S / (plain_ms / 1e3),
+           "signals": S, "input_bytes": in_bytes,
+           "l1_error": float(np.mean([x for c in classes.values() for x in c["l1"]])),
+           "support_recall": 1.0 - sum(c["miss"] for c in classes.values()) / sum(c["K"] for c in classes.values()),
+           "per_size_class": per_class,
+           "stage_ms_per_step": {kk: v / steps for kk, v in stage_ms.items()},
+           "what": "4096 signals, N = 2^n with n uniform on 14..22, K uniform on [10, 1000] (<= N/128), SNR "
+                   "uniform on [0, 40] dB, one batch (one launch per stage); B, w, L per signal by "
+                   "sfft_suggest_params; errors over every "
+                   f"{args.c3_error_stride}th signal"}
+    del plans, xs
+    torch.cuda.empty_cache()
+    return out
+
+
+def _serve_stream(sfft, torch, dev, reqs, pool, slots, budget, count=None):
+    """Replays the request stream (arrival s, N, K, snr) through a server with
+    `slots` slots: submits each request at its arrival time, waits for all;
+    returns (latencies ms, wall seconds from the first submission to the last
+    completion, lag of the submitter behind the arrivals in ms, outputs)."""
+    n = len(reqs) if count is None else min(count, len(reqs))
+    Ks = [reqs[i][2] for i in range(n)]
+    idxs, vals = _slices(torch, dev, Ks)
+    srv = sfft.sfft_server_create(budget, slots)
+    # one request of every shape first, so plans and tables exist (not timed)
+    seen, warm = set(), []
+    for i in range(n):
+        t, N, K, snr = reqs[i]
+        B, w, L = sfft.sfft_suggest_params(N, K, snr)
+        if (N, B, K) not in seen:
+            seen.add((N, B, K))
+            x = pool[(N, K)][0][0]
+            warm.append(sfft.sfft_submit(srv, N, K, B, w, L, 1, x, idxs[i], vals[i], count_samples=0))
+    for tk in warm:
+        sfft.sfft_wait(srv, tk, 600000)
+    tickets, lag = [], 0.0
     t0 = time.perf_counter()
-    lat_sat = drain([submit(i) for i in range(n_req)])
-    sat_value = n_req / (time.perf_counter() - t0)
-    gaps = np.random.default_rng(seed).exponential(1.0 / rate, n_req)
-    arrivals = np.cumsum(gaps)
-    tickets = []
-    t0 = time.perf_counter()
-    for i in range(n_req):
-        while time.perf_counter() - t0 < arrivals[i]:
+    for i in range(n):
+        t, N, K, snr = reqs[i]
+        while time.perf_counter() - t0 < t:
             pass
-        tickets.append(submit(i))
-    lat = drain(tickets)
-    span = time.perf_counter() - t0
+        lag = max(lag, time.perf_counter() - t0 - t)
+        B, w, L = sfft.sfft_suggest_params(N, K, snr)
+        sigs = pool[(N, K)]
+        x = sigs[i % len(sigs)][0]
+        tickets.append(sfft.sfft_submit(srv, N, K, B, w, L, 70_000 + i, x, idxs[i], vals[i], count_samples=0))
+    res = [sfft.sfft_wait(srv, tk, 600000) for tk in tickets]
+    wall = time.perf_counter() - t0
     srv.destroy()
-    lat_ms = np.asarray(lat) / 1e6
-    return {"unit": UNIT, "saturated_value": sat_value,
-            "saturated_p50_ms": float(np.percentile(np.asarray(lat_sat) / 1e6, 50)),
-            "offered_per_s": rate, "value": n_req / span, "requests": n_req,
-            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99))}
+    lat = np.asarray([r.latency_ns for r in res]) / 1e6
+    return lat, wall, 1e3 * lag, idxs, vals, res
+
+
+def measure_served_c5(sfft, torch, dev, args):
+    """The serving workload: a Poisson request stream (2000 requests/s, N
+    2^12..2^26, K log-uniform, SNR -10..40 dB, a distinct seed per request)
+    through the continuous-batching server, and the same stream through a
+    one-slot server (the plain per-signal path); p50/p99 latency and
+    spectra/s of both, and the error figures of a sample of requests."""
+    reqs = configs.serving_stream(args.c5_rate, args.c5_seconds)
+    # a pool of device signals per (N, K): requests of one shape cycle through it
+    pool = {}
+    for _, N, K, _ in reqs:
+        if (N, K) not in pool:
+            P = max(2, min(8, (1 << 30) // (8 * N)))
+            snrs = np.random.default_rng(31 * N + K).uniform(-10.0, 40.0, P)  # the stream's SNR range
+            seeds = [90_000 + 97 * j + 13 * N.bit_length() + K for j in range(P)]
+            pool[(N, K)] = [signals.make_signal_device(N, K, sd, float(sn), dev) + (sd, float(sn))
+                            for sd, sn in zip(seeds, snrs)]
+    pool_bytes = sum(8 * N * len(v) for (N, K), v in pool.items())
+    budget = int(args.c5_budget_gb * (1 << 30))
+    lat, wall, lag, idxs, vals, res = _serve_stream(sfft, torch, dev, reqs, pool, 64, budget)
+    n = len(reqs)
+    ok = sum(r.status == sfft.SFFT_OK for r in res)
+    # errors of a sample (every 97th request): its output against its pooled signal's spectrum
+    e1, miss, kk = [], 0, 0
+    for i in range(0, n, 97):
+        t, N, K, snr = reqs[i]
+        sigs = pool[(N, K)]
+        _, _, _, seed, s_snr = sigs[i % len(sigs)]
+        k = res[i].k_out
+        e = _device_errors(torch, dev, N, K, seed, s_snr, idxs[i][:k], vals[i][:k])
+        e1.append(e["L1"])
+        miss += e["L0"]
+        kk += K
+    out = {"value": ok / wall, "unit": UNIT, "requests": n, "ok": ok, "offered_per_s": args.c5_rate,
+           "seconds": args.c5_seconds, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "submit_lag_max_ms": lag, "pool_signals": sum(len(v) for v in pool.values()), "pool_bytes": pool_bytes,
+           "mean_input_bytes": float(np.mean([8 * N for _, N, _, _ in reqs])),
+           "l1_error_sample": float(np.mean(e1)), "support_recall_sample": 1.0 - miss / max(kk, 1),
+           "what": "Poisson arrivals; N = 2^n, n uniform on 12..26; K log-uniform on the powers of two 1..4096 "
+                   "(<= N/128); SNR uniform on [-10, 40] dB; a distinct seed per request; signals from a device "
+                   "pool per (N, K); 64 slots, plans cached by shape and rebound per request"}
+    del idxs, vals
+    # the plain per-signal path: the same stream through a one-slot server
+    lat1, wall1, lag1, idxs, vals, res1 = _serve_stream(sfft, torch, dev, reqs, pool, 1, budget,
+                                                        count=args.c5_plain_requests)
+    n1 = len(res1)
+    out["plain"] = {"value": sum(r.status == sfft.SFFT_OK for r in res1) / wall1, "unit": UNIT, "requests": n1,
+                    "p50_ms": float(np.percentile(lat1, 50)), "p99_ms": float(np.percentile(lat1, 99)),
+                    "submit_lag_max_ms": lag1,
+                    "what": "the first requests of the same stream, one at a time (one-slot server)"}
+    del idxs, vals, pool
+    torch.cuda.empty_cache()
+    return out
 
 
 def measure_comb(sfft, torch, dev, stream, args, W, sigs, xs, Bc=4096):
@@ -505,8 +648,6 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     plain_value = S * reps / (e0.elapsed_time(e1) / 1e3)
 
-    # ---- served: requests through the continuous-batching server
-    served = measure_served(sfft, torch, W, xs, dev, args.served_requests, args.served_rate)
 
     # ---- end to end through the host-buffer batch call (pinned host memory)
     xh = [torch.from_numpy(sg.x).pin_memory() for sg in sigs]
@@ -566,6 +707,8 @@ def run_ours(args):
     comb = measure_comb(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
     mean = measure_mean(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
     search = measure_search(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
+    batched = measure_batched_c3(sfft, torch, dev, stream, args) if rank == 0 and not args.no_c3 else None
+    served = measure_served_c5(sfft, torch, dev, args) if rank == 0 and not args.no_c5 else None
 
     # ---- CPU baseline: the oracle on a bounded sample, host cores
     cpu = None
@@ -589,7 +732,7 @@ def run_ours(args):
                    "l2": f"no flush: inputs {S * W.N * 8 / 2**20:.0f} MiB and touched sectors "
                          f"{sector_bytes / 2**20:.0f} MiB per step exceed the 129 MB L2"},
         "l1_error": l1, "support_recall": recall,
-        "plain_value": plain_value, "graph_value": graph_value, "served": served,
+        "plain_value": plain_value, "graph_value": graph_value, "batched_c3": batched, "served_c5": served,
         "stage_ms_per_step": per_launch, "stage_share": {k: v / sum(per_launch.values()) for k, v in per_launch.items()},
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
         "roofline": roofline, "roofline_scan": roofline_scan, "dense_fft_context": dense,
@@ -648,8 +791,14 @@ def main():
     ap.add_argument("--signals", type=int, default=64, help="signals per step (per GPU)")
     ap.add_argument("--cpu-signals", type=int, default=32, help="oracle sample size for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--served-requests", type=int, default=4096, help="requests per serving run")
-    ap.add_argument("--served-rate", type=float, default=20000.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--c3-signals", type=int, default=4096, help="signals of the batched workload")
+    ap.add_argument("--c3-error-stride", type=int, default=8, help="error figures of every n-th batched signal")
+    ap.add_argument("--no-c3", action="store_true", help="skip the batched workload")
+    ap.add_argument("--c5-rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--c5-seconds", type=float, default=20.0, help="serving: length of the request stream (s)")
+    ap.add_argument("--c5-budget-gb", type=float, default=96.0, help="serving: device memory budget of the plans")
+    ap.add_argument("--c5-plain-requests", type=int, default=4000, help="serving: requests of the one-slot run")
+    ap.add_argument("--no-c5", action="store_true", help="skip the serving workload")
     ap.add_argument("--variant", default="voting", choices=sorted(PROFILE_VARIANTS),
                     help="plans of this variant (--profile runs only; the bench line is the voting path)")
     ap.add_argument("--profile", action="store_true",

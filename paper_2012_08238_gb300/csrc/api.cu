@@ -146,7 +146,10 @@ void decompose(PlanDev &P) {
     if (P.method == kMethodComb)
         P.vtiles = (uint32_t)(((uint64_t)P.ncls * (P.N / P.Bc) + kVoteTileF - 1) / kVoteTileF);
     // (mean: the register table counts kept bits against M, so T must be M)
-    P.use_bits = (P.B >= 32 && P.B <= 512 && (P.estimator == kEstMedian || P.T == P.M)) ? 1u : 0u;
+    P.use_bits = (P.B >= 32 && (P.B <= 512 || (P.B <= 4096 && P.method != kMethodComb)) &&
+                  (P.estimator == kEstMedian || P.T == P.M))
+                     ? 1u
+                     : 0u;
 }
 
 struct Layout {
@@ -173,7 +176,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.zhat = take(sizeof(float2) * L * B);
     o.en = take(sizeof(float) * L * B);
     o.lkth = take(sizeof(float) * L);
-    o.topk = take(sizeof(uint32_t) * L * 32);
+    o.topk = take(sizeof(uint32_t) * L * 32 * (B > 1024 ? B / 1024 : 1));
     o.sel = take(sizeof(int32_t) * L * P.nsel);
     o.flags = take(sizeof(uint16_t) * L * B);
     o.survf = take(sizeof(uint32_t) * (size_t)cap);
@@ -324,6 +327,7 @@ namespace {
 
 struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
+    uint32_t fb = 0;  // fallback-pass CTAs
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0, max_K = 0;
     uint32_t est_ctas = kEstimateCtas, est_smem = 0;  // pruned estimate: CTAs per job, staged table bytes
     bool bits = true;
@@ -362,6 +366,7 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.max_Bc = p->h.Bc;
     z.gather = p->h.tiles * p->h.L * p->h.nchunk;
     z.select = p->h.L;
+    z.fb = fallback_ctas(p->h.N);
     z.vote = p->h.vtiles;
     z.jobs = 1;
     z.max_B = p->h.B;
@@ -418,46 +423,82 @@ cudaError_t side_res(SideRes *&out) {
     return cudaSuccess;
 }
 
+// Jobs of a batch that share every kernel variant (they are contiguous in
+// the batch's job order): their sizes and, per kernel slot, the group's first
+// CTA in the slot's CTA map and its CTA count.
+struct Group {
+    Sizes z;
+    uint32_t cta0[6] = {0, 0, 0, 0, 0, 0}, ctas[6] = {0, 0, 0, 0, 0, 0};
+};
+
 // gather -> FFT/select -> scan -> estimate (whose last CTA per job takes the
 // top K, running the job's fallback pass first when needed), all
-// stream-ordered.  With ev (kStages + 1 events) the events bracket the
-// stages: gather, FFT/select (and the wait for the comb kernel of comb
-// plans), scan, estimate + top-K, refinement (empty unless a plan refines),
-// residual check (empty unless a plan checks).
-cudaError_t launch_pipeline(const Launch &lg, const Launch &ls, const Launch &lv, const Launch &le,
-                            const Launch &lj, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+// stream-ordered.  lk[k] is the launch of kernel slot k (0 gather, 1
+// FFT/select, 2 scan, 3 one CTA per job, 5 estimate); the gather runs over
+// every job at once, the FFT/select, scan and estimate once per group of
+// jobs with common variants.  With ev (kStages + 1 events) the events
+// bracket the stages: gather, FFT/select (and the wait for the comb kernel
+// of comb plans), scan, estimate + top-K, refinement (empty unless a plan
+// refines), residual check (empty unless a plan checks).
+cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vector<Group> &gs, cudaStream_t s,
+                            cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+    auto at = [&](int k, const Group &g) {
+        Launch l = lk[k];
+        l.cta0 = g.cta0[k];
+        return l;
+    };
     if ((e = mark(0)) != cudaSuccess) return e;
-    // comb plans: the kept residue classes (lj: one CTA per job).  The comb
+    // comb plans: the kept residue classes (one CTA per job).  The comb
     // kernel reads only the signal, so it runs on the side stream beside the
     // gather and FFT/select and is joined before the scan.
     SideRes *sr = nullptr;
-    if (z.comb) {
+    if (all.comb) {
         if ((e = side_res(sr)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(sr->fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(sr->s, sr->fork, 0)) != cudaSuccess) return e;
-        if ((e = launch_comb(lj, z.jobs, z.max_Bc, sr->s)) != cudaSuccess) return e;
+        if ((e = launch_comb(lk[3], all.jobs, all.max_Bc, sr->s)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(sr->join, sr->s)) != cudaSuccess) return e;
     }
-    if ((e = launch_gather(lg, z.gather, s)) != cudaSuccess) return e;
+    if ((e = launch_gather(lk[0], all.gather, s)) != cudaSuccess) return e;
     if ((e = mark(1)) != cudaSuccess) return e;
-    const uint32_t cl = fft_select_cluster_ok(z.L_uniform, z.max_B) ? z.L_uniform : 0u;
-    if ((e = launch_fft_select(ls, z.select, z.max_B, 0, cl, s)) != cudaSuccess) return e;
-    if (z.comb && (e = cudaStreamWaitEvent(s, sr->join, 0)) != cudaSuccess) return e;
+    for (const Group &g : gs) {
+        const uint32_t cl = fft_select_cluster_ok(g.z.L_uniform, g.z.max_B) ? g.z.L_uniform : 0u;
+        if ((e = launch_fft_select(at(1, g), g.ctas[1], g.z.max_B, 0, cl, s)) != cudaSuccess) return e;
+    }
+    if (all.comb && (e = cudaStreamWaitEvent(s, sr->join, 0)) != cudaSuccess) return e;
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_vote(lv, z.vote, kVotePrune, z.L_uniform, z.bits, z.max_flags, nullptr, nullptr, s)) !=
-        cudaSuccess)
-        return e;
+    for (const Group &g : gs)
+        if ((e = launch_vote(at(2, g), g.ctas[2], kVotePrune, g.z.L_uniform, g.z.bits, g.z.max_flags, g.z.max_B,
+                             nullptr, nullptr, s)) != cudaSuccess)
+            return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_estimate(le, z.jobs, z.L_uniform, z.est_ctas, z.est_smem, z.max_K, s)) != cudaSuccess) return e;
+    for (const Group &g : gs) {
+        if ((e = launch_estimate(at(5, g), g.z.jobs, g.z.L_uniform, g.z.est_ctas, g.z.est_smem, g.z.max_K, s)) !=
+            cudaSuccess)
+            return e;
+        // jobs whose pruned records could not certify their top K
+        if ((e = launch_fallback(at(4, g), g.ctas[4], g.z.L_uniform, g.z.max_K, s)) != cudaSuccess) return e;
+    }
     if ((e = mark(4)) != cudaSuccess) return e;
     // refining jobs: the iterative framework's subtraction over the found set
-    if (z.refine && (e = launch_refine(lj, z.jobs, z.max_rK, z.L_uniform, s)) != cudaSuccess) return e;
+    if (all.refine && (e = launch_refine(lk[3], all.jobs, all.max_rK, all.L_uniform, s)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     // checking jobs: FP64 energy left after subtracting the final output
-    if (z.max_resB && (e = launch_residual(ls, z.select, z.max_resB, s)) != cudaSuccess) return e;
+    if (all.max_resB && (e = launch_residual(lk[1], all.select, all.max_resB, s)) != cudaSuccess) return e;
     return mark(6);
+}
+
+// One plan's launch: a single group covering its CTAs.
+cudaError_t launch_single(const Launch &ln, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+    Launch lk[6] = {ln, ln, ln, ln, ln, ln};
+    std::vector<Group> gs(1);
+    gs[0].z = z;
+    gs[0].ctas[1] = z.select;
+    gs[0].ctas[2] = z.vote;
+    gs[0].ctas[4] = z.fb;
+    return launch_pipeline(lk, z, gs, s, ev);
 }
 
 Job make_job(const sfft_plan *p, const float *x, int32_t *idx, float *val, int32_t *kout) {
@@ -480,6 +521,7 @@ Launch single(const Job &j) {
     ln.offs = nullptr;
     ln.map = nullptr;
     ln.njobs = 1;
+    ln.cta0 = 0;
     ln.one = j;
     return ln;
 }
@@ -909,7 +951,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
     if (iterative(p->h.method))
         SFFT_CUDA_TRY(launch_phase(ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     else
-        SFFT_CUDA_TRY(launch_pipeline(ln, ln, ln, ln, ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+        SFFT_CUDA_TRY(launch_single(ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
 }
 
@@ -950,68 +992,104 @@ namespace {
 struct BatchLayout {
     std::vector<unsigned char> bytes;  // jobs, then per kernel a CTA prefix and a CTA -> job map
     size_t off_offs[6], off_map[6];
-    Sizes z;
+    Sizes z;                  // the whole batch
+    std::vector<Group> groups;  // runs of jobs with common kernel variants
 };
+
+// Accumulates job sizes s into batch sizes z (first: z is still empty).
+void merge_sizes(Sizes &z, const Sizes &s, bool first) {
+    z.max_B = std::max(z.max_B, s.max_B);
+    z.max_K = std::max(z.max_K, s.max_K);
+    z.bits = (first || z.bits) && s.bits;
+    z.max_flags = std::max(z.max_flags, s.max_flags);
+    if (first) z.L_uniform = s.L_uniform;
+    else if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
+    z.est_smem = (first || z.est_smem) && s.est_smem ? std::max(z.est_smem, s.est_smem) : 0u;
+    z.phase = first ? s.phase : z.phase;  // one method per batch (callers split mixed lists)
+    z.search = first ? s.search : z.search;
+    z.max_nbuf = std::max(z.max_nbuf, s.max_nbuf);
+    z.max_L = std::max(z.max_L, s.max_L);
+    z.max_cap = std::max(z.max_cap, s.max_cap);
+    z.comb = first ? s.comb : z.comb;
+    z.max_Bc = std::max(z.max_Bc, s.max_Bc);
+    z.refine = z.refine || s.refine;
+    z.max_rK = std::max(z.max_rK, s.max_rK);
+    z.max_resB = std::max(z.max_resB, s.max_resB);
+    z.gather += s.gather;
+    z.select += s.select;
+    z.vote += s.vote;
+    z.fb += s.fb;
+    z.jobs += 1;
+}
+
+// Kernel variants a job runs (jobs with equal keys form one group): L, the
+// scan's table kind, the estimate's table kind, a clusterable FFT/select.
+uint32_t variant_key(const Sizes &s) {
+    const uint32_t L = s.L_uniform;
+    // (register-table jobs also by their table words per lane)
+    const uint32_t scan = scan_uses_bits(L, s.bits) ? (s.max_B > 1024 ? s.max_B / 1024 : 0u)
+                                                    : (s.max_flags <= (uint32_t)kFlagsSmemBytes ? 8u : 9u);
+    const uint32_t est = (s.est_smem && (L == 8 || L == 12 || L == 16)) ? 0u : 1u;
+    const uint32_t cl = s.max_B <= (uint32_t)kClusterMaxB ? 0u : 1u;
+    return (L << 8) | (scan << 4) | (est << 2) | cl;
+}
 
 BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t *const *idx,
                         float *const *val, int32_t *kout, int32_t count) {
     BatchLayout b;
-    // CTA counts per job and kernel: gather, select, vote, top-K, fallback, estimate
+    std::vector<Sizes> ps(count);
+    for (int32_t i = 0; i < count; ++i) ps[i] = plan_sizes(plans[i]);
+    // jobs ordered by variant group (the iterative methods: one group, in
+    // the caller's order); each job keeps its own output pointers
+    std::vector<int32_t> order(count);
+    for (int32_t i = 0; i < count; ++i) order[i] = i;
+    if (!ps[0].phase)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t c) { return variant_key(ps[a]) < variant_key(ps[c]); });
+    // CTA counts per job and kernel: gather, select, vote, one per job, fallback, estimate
     std::vector<uint32_t> cnt((size_t)count * 6);
     std::vector<Job> jobs(count);
     Sizes &z = b.z;
-    z.L_uniform = plans[0]->h.L;
-    // gather split: the plan's (short CTAs, many waves; measured faster than
-    // fewer, longer CTAs, whose last wave runs a mostly idle GPU)
-    for (int32_t i = 0; i < count; ++i) {
+    for (int32_t r = 0; r < count; ++r) {
+        const int32_t i = order[r];
         const sfft_plan *p = plans[i];
-        jobs[i] = make_job(p, x[i], idx[i], val[i], kout + i);
-        const Sizes s = plan_sizes(p);
-        uint32_t *c = &cnt[(size_t)i * 6];
+        jobs[r] = make_job(p, x[i], idx[i], val[i], kout + i);
+        const Sizes &s = ps[i];
+        uint32_t *c = &cnt[(size_t)r * 6];
         c[0] = s.gather;
         c[1] = s.select;
         c[2] = s.vote;
         c[3] = 1;
-        c[4] = 0;  // (unused slot)
+        c[4] = s.fb;
         c[5] = kEstimateCtas;
-        z.max_B = std::max(z.max_B, s.max_B);
-        z.max_K = std::max(z.max_K, s.max_K);
-        z.bits = z.bits && s.bits;
-        z.max_flags = std::max(z.max_flags, s.max_flags);
-        if (s.L_uniform != z.L_uniform) z.L_uniform = 0;
-        z.est_smem = (i == 0 || z.est_smem) && s.est_smem ? std::max(z.est_smem, s.est_smem) : 0u;
-        z.phase = i == 0 ? s.phase : z.phase;  // one method per batch (callers split mixed lists)
-        z.search = i == 0 ? s.search : z.search;
-        z.max_nbuf = std::max(z.max_nbuf, s.max_nbuf);
-        z.max_L = std::max(z.max_L, s.max_L);
-        z.max_cap = std::max(z.max_cap, s.max_cap);
-        z.comb = i == 0 ? s.comb : z.comb;
-        z.max_Bc = std::max(z.max_Bc, s.max_Bc);
-        z.refine = z.refine || s.refine;
-        z.max_rK = std::max(z.max_rK, s.max_rK);
-        z.max_resB = std::max(z.max_resB, s.max_resB);
+        merge_sizes(z, s, r == 0);
+        bool start = r == 0;
+        if (r > 0 && !ps[0].phase) start = variant_key(s) != variant_key(ps[order[r - 1]]);
+        if (start) b.groups.push_back(Group());
+        merge_sizes(b.groups.back().z, s, start);
     }
-    // pruned estimate with staged tables: one wave of resident CTAs over the
-    // batch (each CTA stages its job's tables once)
-    if (z.L_uniform != 8 && z.L_uniform != 12 && z.L_uniform != 16) z.est_smem = 0;
-    if (z.est_smem) {
-        const uint32_t fit = std::max<uint32_t>(1, kEstTabCtasPerSm * kNumSms / (uint32_t)count);
-        z.est_ctas = std::min<uint32_t>(kEstimateCtas, fit);
-        for (int32_t i = 0; i < count; ++i) cnt[(size_t)i * 6 + 5] = z.est_ctas;
-    }
-    // pruned scan: up to 8 vote tiles per CTA while the launch keeps at least
-    // kScanWaves waves of resident CTAs (fewer CTAs amortise the per-CTA
-    // set-up; too few leave a mostly idle last wave)
-    {
+    // per group: the pruned scan takes up to 8 vote tiles per CTA while the
+    // launch keeps at least kScanWaves waves of resident CTAs (fewer CTAs
+    // amortise the per-CTA set-up; too few leave a mostly idle last wave);
+    // the estimate launches kEstimateCtas CTAs per job, of which one per
+    // 2048 survivors takes work
+    size_t r0 = 0;
+    for (Group &g : b.groups) {
+        Sizes &gz = g.z;
+        if (gz.L_uniform != 8 && gz.L_uniform != 12 && gz.L_uniform != 16) gz.est_smem = 0;
         uint64_t vt = 0;
-        for (int32_t i = 0; i < count; ++i) vt += cnt[(size_t)i * 6 + 2];
+        for (size_t r = r0; r < r0 + gz.jobs; ++r) vt += cnt[r * 6 + 2];
         uint32_t tpc = 8;
         while (tpc > 1 && vt / tpc < (uint64_t)kScanWaves * kNumSms * kScanCtasPerSm) tpc >>= 1;
-        for (int32_t i = 0; i < count; ++i) {
-            uint32_t &c2 = cnt[(size_t)i * 6 + 2];
+        gz.vote = 0;
+        for (size_t r = r0; r < r0 + gz.jobs; ++r) {
+            cnt[r * 6 + 5] = gz.est_ctas;
+            uint32_t &c2 = cnt[r * 6 + 2];
             c2 = (c2 + tpc - 1) / tpc;
-            jobs[i].vctas = c2;
+            jobs[r].vctas = c2;
+            gz.vote += c2;
         }
+        r0 += gz.jobs;
     }
     uint64_t tot[6] = {0, 0, 0, 0, 0, 0};
     for (int32_t i = 0; i < count; ++i)
@@ -1036,6 +1114,19 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
             for (uint32_t t = 0; t < c; ++t) map[offs[i] + t] = (uint32_t)i;
         }
     }
+    // each group's first CTA and CTA count per kernel
+    {
+        const uint32_t *o[6];
+        for (int k = 0; k < 6; ++k) o[k] = reinterpret_cast<const uint32_t *>(b.bytes.data() + b.off_offs[k]);
+        size_t first = 0;
+        for (Group &g : b.groups) {
+            for (int k = 0; k < 6; ++k) {
+                g.cta0[k] = o[k][first];
+                g.ctas[k] = o[k][first + g.z.jobs] - o[k][first];
+            }
+            first += g.z.jobs;
+        }
+    }
     z.gather = (uint32_t)tot[0];
     z.select = (uint32_t)tot[1];
     z.vote = (uint32_t)tot[2];
@@ -1052,10 +1143,11 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         ln[k].offs = reinterpret_cast<const uint32_t *>(base + b.off_offs[k]);
         ln[k].map = reinterpret_cast<const uint32_t *>(base + b.off_map[k]);
         ln[k].njobs = count;
+        ln[k].cta0 = 0;
         memset(&ln[k].one, 0, sizeof(Job));
     }
     if (b.z.phase) return launch_phase(ln[1], b.z, s, ev);
-    return launch_pipeline(ln[0], ln[1], ln[2], ln[5], ln[3], b.z, s, ev);
+    return launch_pipeline(ln, b.z, b.groups, s, ev);
 }
 
 sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,
@@ -1360,8 +1452,8 @@ extern "C" sfft_status sfft_vote(sfft_plan *p, const int32_t *sel_dev, int32_t *
     const Launch ln = single(make_job(p, nullptr, nullptr, nullptr, nullptr));
     SFFT_CUDA_TRY(cudaMemsetAsync(n_cand_dev, 0, sizeof(int32_t), s));
     SFFT_CUDA_TRY(launch_flags_from_sel(p->d, p->h.L, sel_dev, s));
-    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, cand_dev,
-                              n_cand_dev, s));
+    SFFT_CUDA_TRY(launch_vote(ln, p->h.vtiles, kVoteCandidates, p->h.L, false, p->h.L * p->h.B * 2, p->h.B,
+                              cand_dev, n_cand_dev, s));
     return SFFT_OK;
 }
 

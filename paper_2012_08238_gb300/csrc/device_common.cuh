@@ -42,7 +42,7 @@ __device__ __forceinline__ void enter(const Launch &ln, PlanDev &P, Job &J, uint
     if (threadIdx.x == 0) {
         Job j;
         uint32_t loc;
-        locate(ln, blockIdx.x, j, loc);
+        locate(ln, ln.cta0 + blockIdx.x, j, loc);
         J = j;
         s_local = loc;
     }

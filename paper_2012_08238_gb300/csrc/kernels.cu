@@ -11,6 +11,8 @@
 // keeps key >= theta; the job's last CTA then takes the top K, a7, running
 // the unpruned fallback pass first when fewer than K estimates reached theta).
 #include <cooperative_groups.h>
+
+#include <cstddef>
 #include <mutex>
 #include <math_constants.h>
 
@@ -92,19 +94,21 @@ __device__ __forceinline__ float theta_from(float min_kth) {
     return theta;
 }
 
-// Loop l's packed bits for the register-table scan: lane word j holds the
-// bit of every bucket h = j (mod 32) at (sigma^-1 (h >> (log2 B - 5))) mod
-// 32, so that the scan's one rotate puts the bit of f + kN/G (G = B/32) at
-// position k 32/G.  bit(h) is bucket h's bit: strong for the median
-// estimator, kept for the mean.
+// Words per lane and loop of the register table: B/1024 for B >= 1024, else 1.
+__host__ __device__ __forceinline__ uint32_t table_words(uint32_t logB) { return logB > 10 ? 1u << (logB - 10) : 1u; }
+
+// Loop l's packed bits for the register-table scan: word c of lane j holds
+// the bit of every bucket h = j + 32 m (m = c mod E, E = table_words) at
+// (sigma^-1 (h >> (log2 B - 5))) mod 32, so that the scan's one rotate puts
+// the bit of f + kN/G (G = min(B/32, 32)) at position k 32/G.  bit(h) is
+// bucket h's bit: strong for the median estimator, kept for the mean.
 template <class Bit>
-__device__ __forceinline__ uint32_t packed_word(const PlanDev &P, uint32_t l, uint32_t j, Bit bit) {
-    const uint32_t sh = P.logB - 5, si = inv_mod32(P.sigma[l]);
+__device__ __forceinline__ uint32_t packed_word(const PlanDev &P, uint32_t l, uint32_t c, uint32_t j, Bit bit) {
+    const uint32_t sh = P.logB - 5, si = inv_mod32(P.sigma[l]), E = table_words(P.logB);
     uint32_t word = 0;
-#pragma unroll
-    for (uint32_t m = 0; m < 16; ++m) {
+    for (uint32_t m = c; 32 * m < P.B; m += E) {
         const uint32_t h = j + 32 * m;
-        if (h < P.B) word |= (uint32_t)bit(h) << ((si * (h >> sh)) & 31u);
+        word |= (uint32_t)bit(h) << ((si * (h >> sh)) & 31u);
     }
     return word;
 }
@@ -146,10 +150,12 @@ __device__ void cluster_tables(const PlanDev &P, uint32_t l, uint32_t kqv, const
     for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
         frow[k] = (uint16_t)(kept_s[k] | (strong_energy(__uint_as_float(en_s[k]), gmul, thr) ? 256u : 0u));
     const bool mean = P.estimator == kEstMean;
-    if (P.use_bits && threadIdx.x < 32)
-        P.packed[l * 32 + threadIdx.x] = packed_word(P, l, threadIdx.x, [&](uint32_t h) {
-            return mean ? kept_s[h] != 0 : strong_energy(__uint_as_float(en_s[h]), gmul, thr);
-        });
+    const uint32_t E = table_words(P.logB);
+    if (P.use_bits)
+        for (uint32_t i = threadIdx.x; i < 32 * E; i += blockDim.x)
+            P.packed[(l * E + (i >> 5)) * 32 + (i & 31)] = packed_word(P, l, i >> 5, i & 31, [&](uint32_t h) {
+                return mean ? kept_s[h] != 0 : strong_energy(__uint_as_float(en_s[h]), gmul, thr);
+            });
 }
 
 // -------------------------------------------------------------- a2 + a3
@@ -351,11 +357,12 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
     if (P.use_bits) {
         __syncthreads();  // the flags above are complete
         const bool mean = P.estimator == kEstMean;
-        for (uint32_t idx = threadIdx.x; idx < P.L * 32; idx += blockDim.x) {
-            const uint32_t ll = idx >> 5;
+        const uint32_t E = table_words(P.logB);
+        for (uint32_t idx = threadIdx.x; idx < P.L * E * 32; idx += blockDim.x) {
+            const uint32_t ll = idx / (32 * E), c = (idx >> 5) % E;
             const float *er = P.energy + (size_t)ll * B;
             const unsigned short *fr = reinterpret_cast<const unsigned short *>(P.flags) + (size_t)ll * B;
-            P.packed[idx] = packed_word(P, ll, idx & 31, [&](uint32_t h) {
+            P.packed[idx] = packed_word(P, ll, c, idx & 31, [&](uint32_t h) {
                 return mean ? (__ldcg(fr + h) & 1u) != 0 : strong_energy(__ldcg(er + h), gmul, thr);
             });
         }
@@ -758,21 +765,23 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
 }
 
 
-// Pruned scan with the register table of strong bits (32 <= B <= 512, L in
+// Pruned scan with the register table of strong bits (32 <= B <= 4096, L in
 // {8, 12, 16}).  Mean plans (T = M) pack kept bits instead, so the survivors
 // are exactly the candidates.
 //
-// A thread takes the G = B/32 frequencies f + kN/G.  Their hash words differ
-// by k sigma_l 2^32/G, so their buckets h + k sigma_l 32 share the lane
-// h mod 32 of the packed table, and one warp shuffle fetches the word holding
-// all G strong bits.  A rotate by sigma^-1 (h >> (log2 B - 5)) (the table's
-// positions are scaled by sigma^-1 to match) puts member k's bit at position
-// k 32/G in every loop, so carry-save adders over the L rotated words count
-// the strong loops of all 32 positions at once (bit-sliced counters).
-// Frequencies with at least M = ceil(L/2) strong loops are queued in shared
-// memory (overflow goes straight to the job's survivor list) and appended to
-// the list when the CTA ends; candidacy is checked when they are estimated.
-template <int LT>
+// A thread takes the G = min(B/32, 32) frequencies f + kN/G.  Their hash
+// words differ by k sigma_l 2^32/G, so their buckets h + k sigma_l B/G share
+// the lane h mod 32 of the packed table, and for B >= 1024 also the word
+// c = (h >> 5) mod E of the lane's E = B/1024 words; E warp shuffles (one per
+// word, the thread keeping word c) fetch the word holding all G strong bits.
+// A rotate by sigma^-1 (h >> (log2 B - 5)) (the table's positions are scaled
+// by sigma^-1 to match) puts member k's bit at position k 32/G in every loop,
+// so carry-save adders over the L rotated words count the strong loops of
+// all 32 positions at once (bit-sliced counters).  Frequencies with at least
+// M = ceil(L/2) strong loops are queued in shared memory (overflow goes
+// straight to the job's survivor list) and appended to the list when the CTA
+// ends; candidacy is checked when they are estimated.
+template <int LT, int E>
 __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     __shared__ PlanDev P;
     __shared__ Job J;
@@ -785,19 +794,20 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
     // per loop: sigma << (32 - log2 N), the lane's table word, and sigma^-1
     // mod 32 packed six 5-bit fields to a word (fewer live registers)
     constexpr int NSW = (LT + 5) / 6;
-    uint32_t av[LT], pw[LT], sip[NSW];
+    uint32_t av[LT], pw[LT][E], sip[NSW];
 #pragma unroll
     for (int k = 0; k < NSW; ++k) sip[k] = 0;
 #pragma unroll
     for (int l = 0; l < LT; ++l) {
         av[l] = P.sigma[l] << (32 - P.logN);
-        pw[l] = __ldcg(P.packed + l * 32 + lane);
+#pragma unroll
+        for (int c = 0; c < E; ++c) pw[l][c] = __ldcg(P.packed + (l * E + c) * 32 + lane);
         sip[l / 6] |= (inv_mod32(P.sigma[l]) & 31u) << (5 * (l % 6));
     }
     const uint32_t cv = P.half << (32 - P.logN);
     const uint32_t top = 32 - P.logB;
     // G = 2^lgG frequencies f + k span per thread, member k's counter at bit k << gsh
-    const uint32_t lgG = P.logB - 5;
+    const uint32_t lgG = min(P.logB - 5, 5u);
     const uint32_t gsh = 5 - lgG;
     const uint32_t span = P.N >> lgG;
     const uint32_t members = member_mask(lgG);
@@ -824,7 +834,16 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
 #pragma unroll
             for (int l = 0; l < LT; ++l) {
                 const uint32_t t = av[l] * f + cv;
-                const uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l], t >> top);  // lane = bucket mod 32
+                const uint32_t h = t >> top;
+                uint32_t w = __shfl_sync(0xFFFFFFFFu, pw[l][0], h);  // lane = bucket mod 32
+                if constexpr (E > 1) {
+                    const uint32_t c = (h >> 5) & (E - 1);
+#pragma unroll
+                    for (int cc = 1; cc < E; ++cc) {
+                        const uint32_t v = __shfl_sync(0xFFFFFFFFu, pw[l][cc], h);
+                        w = c == (uint32_t)cc ? v : w;
+                    }
+                }
                 const uint32_t si = (sip[l / 6] >> (5 * (l % 6))) & 31u;
                 x[l] = __funnelshift_r(w, w, (t >> 27) * si);
             }
@@ -861,36 +880,38 @@ __global__ void __launch_bounds__(kThreads) k_scan_bits(Launch ln) {
 // ------------------------------------------------------------------ a6
 
 // ------------------------------------------------------------------ a7
-// Fallback pass of one job inside its top-K CTA, taken when fewer than K
-// pruned records reached theta: every candidate (kept in >= T loops) is
-// counted, estimated and recorded (kNCand, kNRec2).  A single CTA scans all N
-// frequencies, so such a job is slow, but the pass is exact and the common
-// case launches nothing for it.
-__device__ void fallback_pass(const PlanDev &P, uint32_t *s_cnt) {
+// Fallback share of one job, taken when fewer than K pruned records reached
+// theta: every candidate (kept in >= T loops) among the frequencies [f0, f1)
+// is counted (kNCand), estimated and recorded (kNRec2).  Each of the job's
+// fallback CTAs scans one share, so the pass is exact and parallel; jobs that
+// need none launch CTAs that return at once.
+template <int LT>
+__device__ void fallback_share(const PlanDev &P, uint32_t f0, uint32_t f1, uint32_t *s_cnt) {
     if (threadIdx.x == 0) *s_cnt = 0;
     __syncthreads();
     const uint32_t sN = 32 - P.logN, top = 32 - P.logB, cv = P.half << sN;
+    const uint32_t L = LT > 0 ? (uint32_t)LT : P.L;
     uint32_t cand = 0;
-    for (uint32_t base = 0; base < P.N; base += blockDim.x) {
+    for (uint32_t base = f0; base < f1; base += blockDim.x) {
         const uint32_t f = base + threadIdx.x;
         bool c = false;
         // comb plans: only frequencies of kept residue classes
         const bool eligible = P.method != kMethodComb ||
                               ((__ldg(P.keptc + ((f & (P.Bc - 1)) >> 5)) >> (f & (P.Bc - 1) & 31u)) & 1u);
-        if (f < P.N && eligible) {
+        if (f < f1 && eligible) {
             uint32_t score = 0;
-            for (uint32_t l = 0; l < P.L; ++l)
+#pragma unroll
+            for (uint32_t l = 0; l < L; ++l)
                 score += __ldg(P.flags + (size_t)l * P.B + (((P.sigma[l] << sN) * f + cv) >> top)) & 1u;
             c = score >= P.T;
         }
         cand += c;
-        if (c) estimate_record<0>(P, f, false, 0.f, P.ctr + kNRec2);
+        if (c) estimate_record<LT>(P, f, false, 0.f, P.ctr + kNRec2);
     }
     cand = __reduce_add_sync(0xFFFFFFFFu, cand);
     if ((threadIdx.x & 31) == 0 && cand) atomicAdd(s_cnt, cand);
     __syncthreads();
-    if (threadIdx.x == 0) P.ctr[kNCand] = *s_cnt;
-    __syncthreads();
+    if (threadIdx.x == 0 && *s_cnt) atomicAdd(P.ctr + kNCand, *s_cnt);
 }
 
 // Top-K of one job: the k_out = min(K, candidates) recorded estimates of
@@ -898,24 +919,22 @@ __device__ void fallback_pass(const PlanDev &P, uint32_t *s_cnt) {
 // those of the pruned pass (candidates with key >= theta) when at least K of
 // them exist; otherwise those of the fallback pass (every candidate).  Pruned
 // candidates have key < theta, so either set contains the top K.
-// Run by all threads of the job's last estimate CTA (the other CTAs' records
-// are visible: they fenced before taking their ticket).  tk: shared memory for
+// Run by all threads of the job's last CTA (the other CTAs' records are
+// visible: they fenced before taking their ticket).  tk: shared memory for
 // cap keys + cap payloads (cap a power of two >= max(kRankMax, K)).
 __device__ void rank_records(const PlanDev &P, const Job &J, unsigned long long *tk, uint32_t cap, uint32_t S,
                              uint32_t kout);
 
+// The estimate's last CTA of a job: the top K of the pruned records, or, when
+// they cannot certify it, the flag that hands the job to the fallback pass.
 __device__ void topk_job(const PlanDev &P, const Job &J, unsigned long long *tk, uint32_t cap) {
-    __shared__ uint32_t s_S, s_kout, s_cnt;
     __shared__ int s_fb;
-    if (threadIdx.x == 0) s_fb = needs_fallback(P);
-    __syncthreads();
-    if (s_fb) fallback_pass(P, &s_cnt);
     if (threadIdx.x == 0) {
-        s_S = __ldcg(P.ctr + (s_fb ? kNRec2 : kNGe));
-        s_kout = s_fb ? min(P.K, __ldcg(P.ctr + kNCand)) : P.K;  // without fallback >= K candidates exist
+        s_fb = needs_fallback(P);
+        P.ctr[kFbPend] = s_fb ? 1u : 0u;
     }
     __syncthreads();
-    rank_records(P, J, tk, cap, s_S, s_kout);
+    if (!s_fb) rank_records(P, J, tk, cap, __ldcg(P.ctr + kNGe), P.K);  // >= K candidates exist
 }
 
 // True in every thread of the job's last CTA of this launch to finish (each
@@ -933,6 +952,15 @@ __device__ bool last_of_job(const PlanDev &P, uint32_t ctas_per_job) {
     return s_last;
 }
 
+// CTAs of a job's estimate launch that take survivors: one per kEstChunk of
+// them, at most the job's CTAs (the rest only take their ticket), so few
+// survivors are not spread over CTAs that each stage the tables.
+constexpr uint32_t kEstChunk = 2048;
+__device__ __forceinline__ uint32_t est_active(uint32_t n, uint32_t ctas_per_job) {
+    const uint32_t a = (n + kEstChunk - 1) / kEstChunk;
+    return a < 1 ? 1u : (a > ctas_per_job ? ctas_per_job : a);
+}
+
 // Pruned-pass median estimates of the job's survivors, ctas_per_job CTAs per
 // job: candidates whose key reaches theta are recorded as {f, key bits, re
 // bits, im bits}.  The job's last CTA to finish (atomic ticket after a fence)
@@ -947,11 +975,14 @@ __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t 
     const uint32_t n = P.ctr[kNSurv];
     const float theta = __uint_as_float(P.ctr[kTheta]);
     uint32_t *cnt = P.ctr + kNGe;
-    const uint32_t stride = ctas_per_job * kThreads;
+    // CTAs past the job's active count take no survivors (their strides would overlap)
+    const uint32_t active = est_active(n, ctas_per_job);
+    const uint32_t stride = active * kThreads;
+    const uint32_t i0 = s_local < active ? s_local * kThreads + threadIdx.x : n;
     if constexpr (LT > 0) {
         const float a = sqrtf(0.5f * theta) * (1.0f - 1.0f / 1024.0f);
         // the next survivor's frequency is fetched while this one is estimated
-        uint32_t i = s_local * kThreads + threadIdx.x;
+        uint32_t i = i0;
         uint32_t fn = i < n ? __ldg(P.survf + i) : 0u;
         for (; i < n; i += stride) {
             const uint32_t f = fn;
@@ -959,14 +990,13 @@ __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t 
             estimate_pruned<LT, false>(P, f, theta, a, cnt, nullptr, nullptr, nullptr);
         }
     } else {
-        for (uint32_t i = s_local * kThreads + threadIdx.x; i < n; i += stride)
-            estimate_record<LT>(P, P.survf[i], true, theta, cnt);
+        for (uint32_t i = i0; i < n; i += stride) estimate_record<LT>(P, P.survf[i], true, theta, cnt);
     }
     if (last_of_job(P, ctas_per_job)) topk_job(P, J, est_topk, cap);
 }
 
 template <int LT>
-__device__ void estimate_tab_part(const PlanDev &P, uint32_t s_local, uint32_t ctas_per_job, uint32_t n,
+__device__ void estimate_tab_part(const PlanDev &P, uint32_t s_local, uint32_t active, uint32_t n,
                                   float4 *est_tab) {
     const uint32_t LB = LT * P.B, NB = P.N >> P.logB;
     float2 *zs = reinterpret_cast<float2 *>(est_tab);
@@ -1005,7 +1035,7 @@ __device__ void estimate_tab_part(const PlanDev &P, uint32_t s_local, uint32_t c
     const float theta = __uint_as_float(P.ctr[kTheta]);
     const float a = sqrtf(0.5f * theta) * (1.0f - 1.0f / 1024.0f);
     // the next survivor's frequency is fetched while this one is estimated
-    const uint32_t stride = ctas_per_job * kThreads;
+    const uint32_t stride = active * kThreads;
     uint32_t i = s_local * kThreads + threadIdx.x;
     uint32_t fn = i < n ? __ldg(P.survf + i) : 0u;
     for (; i < n; i += stride) {
@@ -1027,10 +1057,55 @@ __global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t c
     __shared__ uint32_t s_local;
     enter(ln, P, J, s_local);
     const uint32_t n = P.ctr[kNSurv];
-    if (s_local * kThreads < n) estimate_tab_part<LT>(P, s_local, ctas_per_job, n, est_tab);
+    // only the CTAs with a share of at least kEstChunk survivors stage the tables
+    const uint32_t active = est_active(n, ctas_per_job);
+    if (s_local < active) estimate_tab_part<LT>(P, s_local, active, n, est_tab);
     if (last_of_job(P, ctas_per_job)) topk_job(P, J, reinterpret_cast<unsigned long long *>(est_tab), cap);
 }
 
+
+// Unpruned fallback pass, fallback_ctas(N) CTAs per job: a CTA of a job with
+// no pending fallback returns after reading one flag; otherwise it records
+// the candidates of its share of the frequencies, and the job's last CTA to
+// finish (atomic ticket after a fence) ranks them (top K of every candidate).
+template <int LT>
+__global__ void __launch_bounds__(kThreads) k_fallback(Launch ln, uint32_t cap) {
+    extern __shared__ unsigned long long fb_topk[];
+    __shared__ PlanDev P;
+    __shared__ Job J;
+    __shared__ uint32_t s_local, s_cnt;
+    __shared__ int s_go, s_last;
+    if (threadIdx.x == 0) {
+        Job j;
+        uint32_t loc;
+        locate(ln, ln.cta0 + blockIdx.x, j, loc);
+        J = j;
+        s_local = loc;
+        // the descriptor's counter pointer, then the job's flag (one load each)
+        const uint32_t *ctr = *reinterpret_cast<uint32_t *const *>(reinterpret_cast<const char *>(j.p) +
+                                                                   offsetof(PlanDev, ctr));
+        s_go = __ldcg(ctr + kFbPend) != 0;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    load_plan(P, J.p);
+    __syncthreads();
+    const uint32_t n = fallback_ctas(P.N);
+    const uint32_t per = ((P.N + n - 1) / n + kThreads - 1) / kThreads * kThreads;
+    const uint32_t f0 = min(P.N, s_local * per), f1 = min(P.N, f0 + per);
+    fallback_share<LT>(P, f0, f1, &s_cnt);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_last = atomicAdd(P.ctr + kFbDone, 1u) == n - 1;
+        if (s_last) atomicExch(P.ctr + kFbDone, 0u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const uint32_t S = __ldcg(P.ctr + kNRec2), kout = min(P.K, __ldcg(P.ctr + kNCand));
+    rank_records(P, J, fb_topk, cap, S, kout);
+}
 
 // Stage kernels for the single-step entry points.
 template <int LT>
@@ -1152,13 +1227,22 @@ bool fft_select_cluster_ok(uint32_t L, uint32_t max_B) {
 }
 
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
-                        uint32_t max_flags_bytes, int32_t *cand_out, int32_t *ncand_out, cudaStream_t s) {
+                        uint32_t max_flags_bytes, uint32_t max_B, int32_t *cand_out, int32_t *ncand_out,
+                        cudaStream_t s) {
     if (total_ctas == 0) return cudaSuccess;
     if (mode == kVotePrune && scan_uses_bits(L_uniform, bits)) {
-        switch (L_uniform) {
-            case 8: k_scan_bits<8><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            case 12: k_scan_bits<12><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            default: k_scan_bits<16><<<total_ctas, kThreads, 0, s>>>(ln); break;
+        // words per lane and loop of the largest B (every job's B in the group is the same class)
+        const uint32_t E = table_words(31 - __builtin_clz(max_B));
+        switch (L_uniform * 8 + E) {
+            case 8 * 8 + 1: k_scan_bits<8, 1><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 8 * 8 + 2: k_scan_bits<8, 2><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 8 * 8 + 4: k_scan_bits<8, 4><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 12 * 8 + 1: k_scan_bits<12, 1><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 12 * 8 + 2: k_scan_bits<12, 2><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 12 * 8 + 4: k_scan_bits<12, 4><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 16 * 8 + 1: k_scan_bits<16, 1><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 16 * 8 + 2: k_scan_bits<16, 2><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            default: k_scan_bits<16, 4><<<total_ctas, kThreads, 0, s>>>(ln); break;
         }
         return cudaGetLastError();
     }
@@ -1192,6 +1276,22 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform
     return cudaGetLastError();
 }
 
+
+cudaError_t launch_fallback(const Launch &ln, uint32_t total_ctas, uint32_t L_uniform, uint32_t max_K,
+                            cudaStream_t s) {
+    if (total_ctas == 0) return cudaSuccess;
+    uint32_t cap = kRankMax;
+    while (cap < max_K) cap <<= 1;
+    const uint32_t smem = cap * (uint32_t)(sizeof(unsigned long long) + sizeof(uint32_t));
+    auto kern = L_uniform == 8    ? k_fallback<8>
+                : L_uniform == 12 ? k_fallback<12>
+                : L_uniform == 16 ? k_fallback<16>
+                                  : k_fallback<0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<total_ctas, kThreads, smem, s>>>(ln, cap);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,
                                  uint32_t n, float2 *est, cudaStream_t s) {

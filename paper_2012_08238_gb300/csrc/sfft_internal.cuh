@@ -32,7 +32,6 @@ constexpr uint32_t kRefineMaxK = 4096;  // refinement: the found set lives in sh
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
-constexpr int kEstTabCtasPerSm = 3;
 constexpr uint32_t kResidualMaxB = 8192;  // residual check: a loop's B residuals (FP64) in shared memory
 
 // Shared-memory bytes of a job's staged estimate tables: zhat (L B complex),
@@ -54,6 +53,8 @@ enum Counter : int {
     kNRec2 = 7,    // records written by the unpruned fallback pass (in the top-K step)
     kEstDone = 8,  // estimate CTAs of the job finished (last-CTA ticket for the top-K step)
     kPeIter = 10,  // phase encoding: iterations run
+    kFbPend = 11,  // 1 when the job's pruned records could not certify the top K (fallback pass due)
+    kFbDone = 12,  // fallback CTAs of the job finished (last-CTA ticket for its top-K step)
     kNumCounters = 16
 };
 
@@ -69,7 +70,7 @@ struct PlanDev {
     uint32_t nsel, T, M;  // M = ceil(L/2): strong loops needed by the median bound
     uint32_t nchunk, rounds, rpc, tb, tiles;  // gather decomposition
     uint32_t vtiles;                          // vote tiles per job (<= kVoteTileF frequencies each)
-    uint32_t use_bits;                        // 32 <= B <= 512 (and T = M for the mean): table bits in registers
+    uint32_t use_bits;                        // register-table scan (32 <= B <= 4096, B <= 512 for comb; T = M for the mean)
     uint32_t cap;                             // candidate capacity
     float ginv2max;                           // max_o |1/G~(o)|^2 (rounded up)
     uint32_t method;                          // kMethodVoting, kMethodPhase, kMethodComb or kMethodSearch
@@ -90,7 +91,8 @@ struct PlanDev {
     float2 *zhat;          // [L][B]
     float *energy;         // [L][B]
     float *loopkth;        // [L] ceil(K/L)-th largest energy of each loop
-    uint32_t *packed;      // [L][32]: lane j's strong bits, kept bits for the mean (register-table scan)
+    uint32_t *packed;      // [L][E][32]: lane j's strong bits, kept bits for the mean (register-table scan;
+                           // E = B/1024 words per lane for B >= 1024, else 1)
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
     uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
@@ -120,6 +122,7 @@ struct Launch {
     const uint32_t *offs;   // [njobs + 1] CTA prefix for this kernel (batch only)
     const uint32_t *map;    // [total CTAs] job of each CTA (batch only)
     int njobs;
+    uint32_t cta0;          // batch: CTA of the map that this launch's block 0 is (a group's first)
     Job one;
 };
 
@@ -153,8 +156,11 @@ inline bool scan_uses_bits(uint32_t L_uniform, bool bits) {
 
 // L_uniform: common L of every job (0 when they differ); bits: every job has
 // use_bits (the pruned scan then uses the register table of strong bits).
+// max_B: the largest B of the jobs (register-table jobs of one launch share
+// its number of table words per lane, B/1024 for B >= 1024).
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
-                        uint32_t max_flags_bytes, int32_t *cand_out, int32_t *ncand_out, cudaStream_t s);
+                        uint32_t max_flags_bytes, uint32_t max_B, int32_t *cand_out, int32_t *ncand_out,
+                        cudaStream_t s);
 // Pruned-pass estimates, per CTAs per job (ln's prefix array must match); the
 // job's last CTA to finish then takes the job's top K (running the fallback
 // pass first when fewer than K pruned records reached theta).  tab_smem > 0:
@@ -162,6 +168,18 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
 // and L is uniform in {8, 12, 16}; they are then staged there.
 cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
                             uint32_t max_K, cudaStream_t s);
+// Unpruned fallback pass of the jobs whose pruned records could not certify
+// the top K (the estimate's last CTA flags them): fb_ctas(N) CTAs per job
+// (ln's prefix array must match), each scanning a share of the frequencies
+// and recording every candidate; the job's last one takes the top K.  CTAs
+// of jobs without a pending fallback return at once.
+cudaError_t launch_fallback(const Launch &ln, uint32_t total_ctas, uint32_t L_uniform, uint32_t max_K,
+                            cudaStream_t s);
+// CTAs per job of the fallback pass: one per 2^16 frequencies, 1..64.
+__host__ __device__ inline uint32_t fallback_ctas(uint32_t N) {
+    const uint32_t c = (N + 65535u) >> 16;
+    return c < 1 ? 1u : (c > 64 ? 64u : c);
+}
 // Spike-train pre-filter of comb plans: one CTA per job (max_Bc: the largest
 // number of residue classes).
 cudaError_t launch_comb(const Launch &ln, uint32_t njobs, uint32_t max_Bc, cudaStream_t s);

@@ -54,3 +54,31 @@ def errors(xhat: np.ndarray, K: int, idx: np.ndarray, val: np.ndarray) -> dict:
         "L2_rel": l2 / y_norm if y_norm > 0 else float("nan"),
         "C": err_full / best if best > 0 else float("inf"),
     }
+
+
+def errors_sparse(K: int, supp: np.ndarray, xhat_supp: np.ndarray, idx: np.ndarray, val: np.ndarray,
+                  xhat_idx: np.ndarray) -> dict:
+    """L0, false positives, L1, L2 and L2_rel of errors() from the exact
+    spectrum's values on the two supports only: supp = the best K-term
+    support with values xhat_supp, and xhat_idx = the exact values at the
+    recovered frequencies idx.  For spectra too large to hold on the host
+    (C, which needs every bin, is not computed)."""
+    supp = np.asarray(supp, np.int64)
+    idx = np.asarray(idx, np.int64)
+    union = np.union1d(supp, idx)
+    exact = np.zeros(len(union), np.complex128)
+    exact[np.searchsorted(union, idx)] = np.asarray(xhat_idx, np.complex128)
+    exact[np.searchsorted(union, supp)] = np.asarray(xhat_supp, np.complex128)
+    rec = np.zeros(len(union), np.complex128)
+    rec[np.searchsorted(union, idx)] = np.asarray(val, np.complex128)
+    diff = rec - exact
+    y_norm = float(np.linalg.norm(np.asarray(xhat_supp, np.complex128)))
+    l2 = float(np.linalg.norm(diff))
+    return {
+        "L0": int(len(np.setdiff1d(supp, idx))),
+        "false_pos": int(len(np.setdiff1d(idx, supp))),
+        "L1": float(np.sum(np.abs(diff)) / K),
+        "L2": l2,
+        "L2_rel": l2 / y_norm if y_norm > 0 else float("nan"),
+    }
+

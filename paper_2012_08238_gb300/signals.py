@@ -56,3 +56,34 @@ def make_signal(N: int, K: int, seed: int, snr_db: float | None = None,
     return Signal(x=x, freqs=freqs, coefs=coefs, xhat=xhat if keep_xhat else None,
                   N=N, K=K, snr_db=snr_db)
 
+
+def make_signal_device(N: int, K: int, seed: int, snr_db: float | None, device, with_xhat: bool = False):
+    """The same recipe generated on a CUDA device with torch, for workloads
+    too large to synthesise on the host (thousands of signals, N up to 2^26).
+
+    Frequencies and phases come from the same numpy streams as make_signal;
+    the noise bins come from torch's own counter-based generator on the
+    device, seeded by `seed`, so the spectrum is reproducible but its noise
+    differs from make_signal's.  Returns (x, freqs, coefs[, xhat]) with x and
+    xhat complex64 device tensors.
+    """
+    import torch
+
+    if N < 2 or N & (N - 1):
+        raise ValueError("N must be a power of two")
+    if not 1 <= K <= N:
+        raise ValueError("K must lie in [1, N]")
+    freqs = np.sort(_rng(seed, _FREQ).choice(N, size=K, replace=False).astype(np.int64))
+    coefs = np.exp(1j * _rng(seed, _PHASE).uniform(0.0, 2.0 * np.pi, size=K))
+    if snr_db is not None:
+        g = torch.Generator(device=device)
+        g.manual_seed((seed * 2654435761 + _NOISE) & (2**63 - 1))
+        var = K * 10.0 ** (-snr_db / 10.0) / N
+        xhat = torch.randn(N, dtype=torch.complex64, device=device, generator=g) * float(np.sqrt(var))
+    else:
+        xhat = torch.zeros(N, dtype=torch.complex64, device=device)
+    fi = torch.from_numpy(freqs).to(device)
+    xhat[fi] += torch.from_numpy(coefs.astype(np.complex64)).to(device)
+    x = torch.fft.ifft(xhat) * N
+    return (x, freqs, coefs, xhat) if with_xhat else (x, freqs, coefs)
+

@@ -49,6 +49,9 @@ SHAPES = [
     (1 << 13, 8, 64, 64 * 34, 16, 7, 2, None, "noisy"),           # L = 16 specialisation
     (1 << 13, 8, 64, 64 * 34, 7, 8, 2, 7, "noisy"),               # T = L, generic L
     (1 << 13, 8, 64, 64 * 34, 32, 9, 3, 10, "noisy"),             # L = 32, c = 3
+    (1 << 16, 200, 1024, 1024 * 37, 12, 10, 2, None, "noisy"),    # register-table scan, 1 word per lane
+    (1 << 17, 300, 2048, 2048 * 38, 8, 11, 2, None, "noisy"),     # register-table scan, 2 words per lane
+    (1 << 18, 500, 4096, 4096 * 39, 16, 12, 2, None, "exact"),    # register-table scan, 4 words per lane
 ]
 
 

@@ -99,3 +99,25 @@ def test_pin_catches_planted_mistake(tmp_path, name, old, new):
     with pytest.raises(AssertionError):
         _check(mod)
     assert os.path.exists(SRC)
+
+
+def test_sparse_form_equals_the_full_definition():
+    # the hand case, then random spectra with misses and false positives
+    xhat, idx, val = _case()
+    supp = metrics.best_k_support(xhat, 3)
+    e = metrics.errors_sparse(3, supp, xhat[supp], idx, val, xhat[idx])
+    for k in ("L0", "false_pos", "L1", "L2", "L2_rel"):
+        assert e[k] == pytest.approx(EXPECTED[k], rel=1e-6, abs=1e-7), k
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        N, K = 256, int(rng.integers(1, 20))
+        xh = (rng.standard_normal(N) + 1j * rng.standard_normal(N)) * 0.01
+        xh[rng.choice(N, K, replace=False)] += np.exp(2j * np.pi * rng.uniform(size=K))
+        idx = np.sort(rng.choice(N, int(rng.integers(0, K + 1)), replace=False))
+        val = xh[idx] + 0.05 * (rng.standard_normal(len(idx)) + 1j * rng.standard_normal(len(idx)))
+        full = metrics.errors(xh, K, idx, val)
+        supp = metrics.best_k_support(xh, K)
+        sp = metrics.errors_sparse(K, supp, xh[supp], idx, val, xh[idx])
+        for k in sp:
+            assert sp[k] == pytest.approx(full[k], rel=1e-12, abs=1e-15), k
+
