@@ -69,7 +69,8 @@ typedef struct sfft_server sfft_server;
 typedef struct {
     int32_t c;         /* buckets kept per loop = min(c*K, B); 0 -> 2 ("2K large buckets") */
     int32_t T;         /* vote threshold; 0 -> ceil(L/2) */
-    int32_t precision; /* 0 -> FP32 B-point FFT (the only precision in this build) */
+    int32_t precision; /* B-point transform (a2): 0 -> FP32 radix-2 FFT; 1 -> split-BF16 DFT on the
+                          tensor cores (voting and comb methods, 64 <= B <= 1024; see below) */
     int32_t method;    /* SFFT_METHOD_VOTING (0, default), SFFT_METHOD_PHASE, SFFT_METHOD_COMB or
                           SFFT_METHOD_SEARCH */
     int32_t comb;      /* SFFT_METHOD_COMB: residue classes Bc (power of two); 0 -> default
@@ -149,6 +150,15 @@ typedef struct {
    the mean estimator otherwise carries. */
 #define SFFT_MAX_REFINE 8
 
+/* sfft_opts.precision = 1: the B-point DFT of step a2 (Eq. 2) as a matrix
+   product on the tensor cores.  Every (signal, loop) row of bucket sums z
+   (interleaved re, im) is multiplied by the real 2B x 2B DFT matrix W
+   (cos / sin of 2 pi j k / B); z and W are split into BF16 hi and lo parts and
+   zhat = z_hi W_hi + z_lo W_hi + z_hi W_lo with FP32 accumulation (the
+   dropped z_lo W_lo is ~2^-16 of the result): relative error ~1e-5, within
+   the 1e-3 tolerance stated for it.  The rows of a batch that share B form
+   one GEMM.  The W table (16 B^2 bytes) is built once per device and B. */
+
 /* sfft_opts.residual = 1: the final residual-energy check (the error that
    Eq. 5 bounds, seen through the buckets).  After the output (and any
    refinement) the k_out recovered coefficients are subtracted in FP64 from
@@ -226,6 +236,8 @@ typedef struct {
     double residual_energy;  /* sfft_opts.residual: energy left in the buckets after
                                 subtracting the output (FP64); else -1 */
     double bucket_energy;    /* sfft_opts.residual: energy of the buckets (FP64); else -1 */
+    int32_t device_error;    /* 0, or the code of a bounded device-side wait that gave up
+                                (tensor-core DFT: 1 operand load, 2 accumulator) */
 } sfft_exec_stats;
 
 sfft_status sfft_plan_last_stats(const sfft_plan *plan, sfft_exec_stats *stats);
@@ -236,8 +248,11 @@ sfft_status sfft_plan_last_stats(const sfft_plan *plan, sfft_exec_stats *stats);
 sfft_status sfft_loop_params(int64_t N, int32_t L, uint64_t seed, uint32_t *sigma, uint32_t *tau,
                              uint32_t *sigma_inv);
 
-/* Plan sizes for a signal shape by a fixed size-class rule (host only, no
-   GPU needed; not a measuring autotuner):
+/* Plan sizes for a signal shape (host only, no GPU needed).  When a loaded
+   tuning cache (sfft_tuning_load) has a class covering (log2 N, K, SNR), its
+   measured choice is used: B = the smallest power of two >= B_per_K K
+   (bounded as below), w = B (log2 N + w_extra), its L.  Otherwise the fixed
+   size-class rule:
      B = the smallest power of two >= max(64, 4K) (so the 2K kept buckets
          are at most half of them), at most min(16384, N/64) (which keeps the
          window inside the signal) and at least 2; a cap below 2K is refused
@@ -250,6 +265,21 @@ sfft_status sfft_loop_params(int64_t N, int32_t L, uint64_t seed, uint32_t *sigm
    K = 1000: 4096).  Errors: SFFT_EINVAL (N not a power of two in
    [2, 2^30], K not in [1, N], K beyond the rule's range, NULL outputs). */
 sfft_status sfft_suggest_params(int64_t N, int32_t K, double snr_db, int32_t *B, int64_t *w, int32_t *L);
+
+/* Load the autotuner's cache (JSON written by paper_2012_08238_gb300/tune.py,
+   which measures per size class the fastest B/K ratio, window width and L
+   whose L1 error and support recall match the fixed rule's):
+     {"version": 1, "classes": [{"logN": n, "K_lo": a, "K_hi": b, "snr_lo": s0,
+       "snr_hi": s1, "B_per_K": r, "w_extra": e, "L": l, ...}, ...]}
+   A class covers N = 2^n, a <= K <= b and s0 <= SNR < s1 (snr_lo null: the
+   noiseless class).  Replaces any loaded classes (process-wide; host only).
+   Errors: SFFT_EINVAL (unreadable file, malformed JSON, values out of range;
+   the previously loaded classes stay). */
+sfft_status sfft_tuning_load(const char *path);
+/* Forget the loaded classes (the fixed rule applies again). */
+void sfft_tuning_clear(void);
+/* Number of loaded classes. */
+int32_t sfft_tuning_classes(void);
 
 /* ---------------------------------------------------------------- execute */
 

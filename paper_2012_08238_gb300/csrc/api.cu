@@ -28,6 +28,7 @@ struct sfft_plan {
     sfft::PlanDev *d;        // device descriptor
     void *dmem;              // single allocation holding the descriptor and the scratch
     const void *tables;      // shared seed-independent tables (tables_acquire)
+    void *dft;               // precision 1: scratch of the tensor-core DFT of this plan's L rows
     // staging for sfft_execute_host (allocated on first use)
     void *stage;
 };
@@ -153,7 +154,7 @@ void decompose(PlanDev &P) {
 }
 
 struct Layout {
-    size_t plan, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, survf, surv, rscr, resid, ctr, total;
+    size_t plan, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, survf, surv, rscr, resid, dft, ctr, total;
 };
 
 Layout layout_of(const PlanDev &P, int64_t cap) {
@@ -179,10 +180,14 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.topk = take(sizeof(uint32_t) * L * 32 * (B > 1024 ? B / 1024 : 1));
     o.sel = take(sizeof(int32_t) * L * P.nsel);
     o.flags = take(sizeof(uint16_t) * L * B);
-    o.survf = take(sizeof(uint32_t) * (size_t)cap);
+    // the register-table scan lists survivors of the median bound before their
+    // candidacy is checked: each frequency at most once, up to N of them; the
+    // other scans list candidates only (at most cap)
+    o.survf = take(sizeof(uint32_t) * (P.use_bits ? (size_t)P.N : (size_t)cap));
     o.surv = take(sizeof(uint4) * (size_t)cap);
     o.rscr = take(P.refine ? sizeof(float2) * P.K * P.L : 0);
     o.resid = take(P.residual ? sizeof(double) * 2 * P.L : 0);
+    o.dft = take(P.precision ? dft_scratch_bytes(P.L, P.B) + 256 : 0);  // (+ its error word)
     o.ctr = take(sizeof(uint32_t) * kNumCounters);
     o.total = off;
     return o;
@@ -191,7 +196,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
 // Sizes and work split of a plan, without touching the device.
 void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
                    int64_t *cap, uint32_t method, uint32_t Bc, uint32_t estimator = kEstMedian,
-                   uint32_t refine = 0, uint32_t srch_b = 1, uint32_t residual = 0) {
+                   uint32_t refine = 0, uint32_t srch_b = 1, uint32_t residual = 0, uint32_t precision = 0) {
     memset(&P, 0, sizeof(P));
     const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     P.N = (uint32_t)N;
@@ -214,6 +219,7 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.refine = refine;
     P.srch_b = srch_b;
     P.residual = residual;
+    P.precision = precision;
     if (method == kMethodComb) {
         P.Bc = Bc;
         P.logBc = ilog2(Bc);
@@ -310,7 +316,7 @@ size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, 
                   (uint32_t)std::min<int64_t>(N, kMaxComb),
                   o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian,
                   (uint32_t)std::max<int32_t>(o.refine, 0), (uint32_t)std::max<int32_t>(o.search_bits, 1),
-                  o.residual ? 1u : 0u);
+                  o.residual ? 1u : 0u, o.precision ? 1u : 0u);
     return layout_of(P, cap).total;
 }
 
@@ -341,6 +347,7 @@ struct Sizes {
     bool refine = false;   // some job refines its output
     uint32_t max_rK = 0;   // refinement: largest K of the refining jobs
     uint32_t max_resB = 0; // residual check: largest B of the checking jobs (0: none checks)
+    uint32_t dft_B = 0;    // split-BF16 tensor-core DFT of B buckets (0: the FP32 FFT)
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -378,6 +385,7 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.refine = p->h.refine > 0;
     z.max_rK = z.refine ? p->h.K : 0u;
     z.max_resB = p->h.residual ? p->h.B : 0u;
+    z.dft_B = p->h.precision ? p->h.B : 0u;
     return z;
 }
 
@@ -440,8 +448,8 @@ struct Group {
 // bracket the stages: gather, FFT/select (and the wait for the comb kernel
 // of comb plans), scan, estimate + top-K, refinement (empty unless a plan
 // refines), residual check (empty unless a plan checks).
-cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vector<Group> &gs, cudaStream_t s,
-                            cudaEvent_t *ev = nullptr) {
+cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vector<Group> &gs, void *dft_scratch,
+                            cudaStream_t s, cudaEvent_t *ev = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     auto at = [&](int k, const Group &g) {
@@ -465,6 +473,18 @@ cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vecto
     if ((e = mark(1)) != cudaSuccess) return e;
     for (const Group &g : gs) {
         const uint32_t cl = fft_select_cluster_ok(g.z.L_uniform, g.z.max_B) ? g.z.L_uniform : 0u;
+        if (g.z.dft_B) {
+            // split-BF16 tensor-core DFT of the group's rows, then select on its partial planes
+            const uint32_t rows = g.ctas[1], Bd = g.z.dft_B;
+            uint32_t *err = reinterpret_cast<uint32_t *>(static_cast<char *>(dft_scratch) + dft_scratch_bytes(rows, Bd));
+            if ((e = cudaMemsetAsync(err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+            if ((e = launch_dft(at(1, g), rows, Bd, dft_scratch, err, s)) != cudaSuccess) return e;
+            const uint32_t mpad = (rows + kDftRowTile - 1) / kDftRowTile * kDftRowTile;
+            if ((e = launch_fft_select(at(1, g), rows, Bd, 0, cl, s, dft_partials(dft_scratch, rows, Bd), mpad, err)) !=
+                cudaSuccess)
+                return e;
+            continue;
+        }
         if ((e = launch_fft_select(at(1, g), g.ctas[1], g.z.max_B, 0, cl, s)) != cudaSuccess) return e;
     }
     if (all.comb && (e = cudaStreamWaitEvent(s, sr->join, 0)) != cudaSuccess) return e;
@@ -490,15 +510,16 @@ cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vecto
     return mark(6);
 }
 
-// One plan's launch: a single group covering its CTAs.
-cudaError_t launch_single(const Launch &ln, const Sizes &z, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+// One plan's launch: a single group covering its CTAs (dft: the plan's own
+// tensor-core DFT scratch, precision 1).
+cudaError_t launch_single(const Launch &ln, const Sizes &z, void *dft, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     Launch lk[6] = {ln, ln, ln, ln, ln, ln};
     std::vector<Group> gs(1);
     gs[0].z = z;
     gs[0].ctas[1] = z.select;
     gs[0].ctas[2] = z.vote;
     gs[0].ctas[4] = z.fb;
-    return launch_pipeline(lk, z, gs, s, ev);
+    return launch_pipeline(lk, z, gs, dft, s, ev);
 }
 
 Job make_job(const sfft_plan *p, const float *x, int32_t *idx, float *val, int32_t *kout) {
@@ -595,8 +616,12 @@ extern "C" sfft_status sfft_suggest_params(int64_t N, int32_t K, double snr_db, 
         set_error("N must be a power of two in [2, 2^30], K in [1, N], outputs non-NULL");
         return SFFT_EINVAL;
     }
+    // a loaded tuning class for this shape overrides the rule's ratios
+    int64_t bpk = 4, wex = 21;
+    int32_t Lt = 0;
+    const bool tuned = tuning_lookup((int)ilog2((uint64_t)N), K, snr_db, &bpk, &wex, &Lt);
     int64_t b = 64;
-    while (b < 4ll * K) b <<= 1;
+    while (b < bpk * K) b <<= 1;
     b = std::min<int64_t>(b, std::min<int64_t>(kMaxB, N / 64));  // B (log2 N + 21) < N
     b = std::max<int64_t>(2, std::min<int64_t>(b, N));
     if (b < 2ll * K) {
@@ -606,11 +631,11 @@ extern "C" sfft_status sfft_suggest_params(int64_t N, int32_t K, double snr_db, 
                   "K <= min(8192, N/128)");
         return SFFT_EINVAL;
     }
-    int64_t ww = b * (int64_t)(ilog2((uint64_t)N) + 21);
+    int64_t ww = b * (int64_t)(ilog2((uint64_t)N) + wex);
     if (ww > N) ww = N / b * b;
     *B = (int32_t)b;
     *w = ww;
-    *L = std::isnan(snr_db) ? 8 : 12;
+    *L = tuned ? Lt : (std::isnan(snr_db) ? 8 : 12);
     return SFFT_OK;
 }
 
@@ -632,9 +657,9 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     *plan = nullptr;
     sfft_opts o = {};
     if (opts) o = *opts;
-    if (o.precision != 0) {
-        set_error("only precision 0 (FP32 FFT) is implemented");
-        return SFFT_ENOTIMPL;
+    if (o.precision != 0 && o.precision != 1) {
+        set_error("sfft_opts.precision must be 0 (FP32 FFT) or 1 (split-BF16 tensor-core DFT)");
+        return SFFT_EINVAL;
     }
     if (o.method != SFFT_METHOD_VOTING && o.method != SFFT_METHOD_PHASE && o.method != SFFT_METHOD_COMB &&
         o.method != SFFT_METHOD_SEARCH) {
@@ -672,6 +697,11 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     }
     if (o.refine < 0 || o.refine > SFFT_MAX_REFINE || (o.refine && (phase || K_cap > (int32_t)kRefineMaxK))) {
         set_error("sfft_opts.refine must be 0..8 passes, for the voting and comb methods with K <= 4096");
+        return SFFT_EINVAL;
+    }
+    if (o.precision == 1 && (phase || B < 64 || B > (int64_t)kDftMaxB)) {
+        set_error("sfft_opts.precision 1 (split-BF16 tensor-core DFT) is for the voting and comb methods with "
+                  "64 <= B <= 1024");
         return SFFT_EINVAL;
     }
     if (o.residual != 0 && (o.residual != 1 || phase || B < 4 || B > (int32_t)kResidualMaxB)) {
@@ -745,13 +775,17 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     PlanDev &P = p->h;
     fill_plan_dev(P, N, K_cap, (int32_t)B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc,
                   o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian, (uint32_t)o.refine, (uint32_t)sb,
-                  (uint32_t)o.residual);
+                  (uint32_t)o.residual, (uint32_t)o.precision);
     const Layout lay = layout_of(P, p->cap);
     if (K != K_cap) set_K(P, K, &p->cap, c);
     p->nsel = (int32_t)P.nsel;
     // (comb plans: loops L and L+1 give the comb shifts)
     loop_params_host(N, L + (comb ? (int32_t)kCombShifts : 0), seed, P.sigma, P.tau, p->sigma_inv);
 
+    if (P.precision && (st = dft_table_prepare(P.B)) != SFFT_OK) {
+        delete p;
+        return st;
+    }
     TableSet tab;
     st = tables_acquire(P.N, P.B, P.w, phase || P.refine, P.residual != 0, &p->tables, &tab);
     if (st != SFFT_OK) {
@@ -775,6 +809,7 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     P.ginv2max = tab.ginv2max;
     P.rscr = P.refine ? reinterpret_cast<float2 *>(base + lay.rscr) : nullptr;
     P.resid = P.residual ? reinterpret_cast<double *>(base + lay.resid) : nullptr;
+    p->dft = P.precision ? static_cast<void *>(base + lay.dft) : nullptr;
     P.ctw = comb ? reinterpret_cast<float2 *>(base + lay.ctw) : nullptr;
     P.cls = comb ? reinterpret_cast<uint32_t *>(base + lay.cls) : nullptr;
     P.keptc = comb ? reinterpret_cast<uint32_t *>(base + lay.keptc) : nullptr;
@@ -906,6 +941,7 @@ extern "C" sfft_status sfft_plan_last_stats(const sfft_plan *p, sfft_exec_stats 
     SFFT_CUDA_TRY(cudaMemcpy(c, p->h.ctr, sizeof(c), cudaMemcpyDeviceToHost));
     st->residual_energy = -1.0;
     st->bucket_energy = -1.0;
+    st->device_error = (int32_t)c[kErr];
     if (p->h.residual) {
         // per-loop pairs summed in loop order
         std::vector<double> r(2 * (size_t)p->L);
@@ -951,7 +987,7 @@ extern "C" sfft_status sfft_execute(sfft_plan *p, const float *x_dev, int32_t *i
     if (iterative(p->h.method))
         SFFT_CUDA_TRY(launch_phase(ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
     else
-        SFFT_CUDA_TRY(launch_single(ln, plan_sizes(p), static_cast<cudaStream_t>(stream)));
+        SFFT_CUDA_TRY(launch_single(ln, plan_sizes(p), p->dft, static_cast<cudaStream_t>(stream)));
     return SFFT_OK;
 }
 
@@ -994,6 +1030,9 @@ struct BatchLayout {
     size_t off_offs[6], off_map[6];
     Sizes z;                  // the whole batch
     std::vector<Group> groups;  // runs of jobs with common kernel variants
+    size_t dft_bytes = 0;     // tensor-core DFT scratch after the bytes (largest group; groups run in turn)
+    // device bytes of the batch buffer: the bytes (copied), then the DFT scratch (not copied)
+    size_t dev_bytes() const { return align256(bytes.size()) + dft_bytes; }
 };
 
 // Accumulates job sizes s into batch sizes z (first: z is still empty).
@@ -1015,6 +1054,7 @@ void merge_sizes(Sizes &z, const Sizes &s, bool first) {
     z.refine = z.refine || s.refine;
     z.max_rK = std::max(z.max_rK, s.max_rK);
     z.max_resB = std::max(z.max_resB, s.max_resB);
+    z.dft_B = std::max(z.dft_B, s.dft_B);
     z.gather += s.gather;
     z.select += s.select;
     z.vote += s.vote;
@@ -1031,7 +1071,8 @@ uint32_t variant_key(const Sizes &s) {
                                                     : (s.max_flags <= (uint32_t)kFlagsSmemBytes ? 8u : 9u);
     const uint32_t est = (s.est_smem && (L == 8 || L == 12 || L == 16)) ? 0u : 1u;
     const uint32_t cl = s.max_B <= (uint32_t)kClusterMaxB ? 0u : 1u;
-    return (L << 8) | (scan << 4) | (est << 2) | cl;
+    const uint32_t dft = s.dft_B ? ilog2(s.dft_B) : 0u;  // tensor-core DFT groups share B
+    return (dft << 16) | (L << 8) | (scan << 4) | (est << 2) | cl;
 }
 
 BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t *const *idx,
@@ -1127,6 +1168,8 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
             first += g.z.jobs;
         }
     }
+    for (const Group &g : b.groups)
+        if (g.z.dft_B) b.dft_bytes = std::max(b.dft_bytes, dft_scratch_bytes(g.ctas[1], g.z.dft_B) + 256);
     z.gather = (uint32_t)tot[0];
     z.select = (uint32_t)tot[1];
     z.vote = (uint32_t)tot[2];
@@ -1147,7 +1190,8 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         memset(&ln[k].one, 0, sizeof(Job));
     }
     if (b.z.phase) return launch_phase(ln[1], b.z, s, ev);
-    return launch_pipeline(ln, b.z, b.groups, s, ev);
+    void *dft = b.dft_bytes ? static_cast<void *>(const_cast<char *>(base) + align256(b.bytes.size())) : nullptr;
+    return launch_pipeline(ln, b.z, b.groups, dft, s, ev);
 }
 
 sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,
@@ -1205,7 +1249,7 @@ extern "C" sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *
         GraphEntry &ge = *it;
         if (!ge.exec) {
             // second sighting: keep a persistent job buffer and capture the pipeline
-            cudaError_t e = cudaMalloc(&ge.dev, b.bytes.size());
+            cudaError_t e = cudaMalloc(&ge.dev, b.dev_bytes());
             if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch graph)");
             SFFT_CUDA_TRY(cudaMemcpy(ge.dev, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice));
             cudaStream_t cap = nullptr;
@@ -1242,12 +1286,12 @@ extern "C" sfft_status sfft_execute_batch(sfft_plan *const *plans, const float *
     Slot &sl = g_slots[g_next_slot];
     g_next_slot = (g_next_slot + 1) % 4;
     if (sl.done) SFFT_CUDA_TRY(cudaEventSynchronize(sl.done));
-    if (sl.device != device || sl.cap < b.bytes.size()) {
+    if (sl.device != device || sl.cap < b.dev_bytes()) {
         if (sl.host) cudaFreeHost(sl.host);
         if (sl.dev) cudaFree(sl.dev);
         if (sl.done) cudaEventDestroy(sl.done);
         sl = Slot();
-        const size_t cap = std::max<size_t>(b.bytes.size(), 64 * 1024);
+        const size_t cap = std::max<size_t>(b.dev_bytes(), 64 * 1024);
         SFFT_CUDA_TRY(cudaMallocHost(&sl.host, cap));
         SFFT_CUDA_TRY(cudaMalloc(&sl.dev, cap));
         SFFT_CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
@@ -1275,7 +1319,7 @@ extern "C" sfft_status sfft_execute_batch_timed(sfft_plan *const *plans, const f
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     BatchLayout b = build_batch(plans, x_dev, idx_dev, val_dev, k_out_dev, count);
     void *dev = nullptr;
-    SFFT_CUDA_TRY(cudaMalloc(&dev, b.bytes.size()));
+    SFFT_CUDA_TRY(cudaMalloc(&dev, b.dev_bytes()));
     constexpr int kStages = 6;
     std::vector<cudaEvent_t> ev((size_t)steps * (kStages + 1), nullptr);
     cudaError_t e = cudaMemcpy(dev, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice);
@@ -1419,7 +1463,17 @@ extern "C" sfft_status sfft_bucketize(sfft_plan *p, const float *x_dev, float *z
     const Launch ln = single(make_job(p, x_dev, nullptr, nullptr, nullptr));
     const Sizes z = plan_sizes(p);
     SFFT_CUDA_TRY(launch_gather(ln, z.gather, s));
-    SFFT_CUDA_TRY(launch_fft_select(ln, z.select, z.max_B, 0, 0, s));
+    if (z.dft_B) {
+        // the plan's tensor-core DFT, as in the pipeline
+        uint32_t *err = reinterpret_cast<uint32_t *>(static_cast<char *>(p->dft) + dft_scratch_bytes(z.select, z.dft_B));
+        SFFT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+        SFFT_CUDA_TRY(launch_dft(ln, z.select, z.dft_B, p->dft, err, s));
+        const uint32_t mpad = (z.select + kDftRowTile - 1) / kDftRowTile * kDftRowTile;
+        SFFT_CUDA_TRY(launch_fft_select(ln, z.select, z.max_B, 0, 0, s, dft_partials(p->dft, z.select, z.dft_B), mpad,
+                                        err));
+    } else {
+        SFFT_CUDA_TRY(launch_fft_select(ln, z.select, z.max_B, 0, 0, s));
+    }
     SFFT_CUDA_TRY(cudaMemcpyAsync(zhat_dev, p->h.zhat, sizeof(float2) * p->L * p->B, cudaMemcpyDeviceToDevice, s));
     return SFFT_OK;
 }

@@ -170,7 +170,12 @@ __device__ void cluster_tables(const PlanDev &P, uint32_t l, uint32_t kqv, const
 // last CTA building every loop's tables, each CTA reads the other loops'
 // order statistics from their shared memory, derives theta and builds its
 // own loop's tables.
-__global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int select_only, int clustered) {
+// dftC (precision 1): the bucket values come from the tensor-core DFT's three
+// FP32 partial planes C[3][dft_mpad][B] (complex), row blockIdx.x, summed in
+// product order instead of the gather partials and the radix-2 FFT.
+__global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int select_only, int clustered,
+                                                            const float2 *dftC, uint32_t dft_mpad,
+                                                            const uint32_t *dft_err) {
     // B values, B energies, B/2 twiddles (B <= kTwSmemMaxB), B kept bytes (clustered)
     extern __shared__ unsigned long long sm[];
     float2 *buf = reinterpret_cast<float2 *>(sm);
@@ -191,7 +196,19 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
     float2 *zrow = P.zhat + (size_t)l * B;
     float *erow = P.energy + (size_t)l * B;
     uint16_t *frow = P.flags + (size_t)l * B;
-    if (!select_only) {
+    if (!select_only && dftC) {
+        const size_t plane = (size_t)dft_mpad * B;
+        const float2 *c0 = dftC + (size_t)blockIdx.x * B;
+        for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
+            const float2 a = __ldcg(c0 + k), b = __ldcg(c0 + plane + k), c = __ldcg(c0 + 2 * plane + k);
+            const float2 z = make_float2((a.x + b.x) + c.x, (a.y + b.y) + c.y);
+            const float e = z.x * z.x + z.y * z.y;
+            zrow[k] = z;
+            erow[k] = e;
+            en_s[k] = __float_as_uint(e);
+        }
+        if (threadIdx.x == 0 && *dft_err) P.ctr[kErr] = *dft_err;  // a tensor-core wait gave up
+    } else if (!select_only) {
         const uint32_t nchunk = J.nchunk;
         if (tw_s)
             for (uint32_t k = threadIdx.x; k < B / 2; k += blockDim.x) tw_s[k] = __ldg(P.tw + k);
@@ -1164,14 +1181,16 @@ cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s)
 }
 
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
-                              uint32_t cluster_L, cudaStream_t s) {
+                              uint32_t cluster_L, cudaStream_t s, const float *dftC, uint32_t dft_mpad,
+                              const uint32_t *dft_err) {
     if (total_ctas == 0) return cudaSuccess;
     const int smem = (int)(max_B * (sizeof(float2) + sizeof(uint32_t)) +
                            (max_B <= kTwSmemMaxB ? max_B / 2 * sizeof(float2) : 0) + (cluster_L ? max_B : 0));
     cudaError_t e = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (!cluster_L) {
-        k_fft_select<<<total_ctas, kThreads, smem, s>>>(ln, select_only, 0);
+        k_fft_select<<<total_ctas, kThreads, smem, s>>>(ln, select_only, 0, reinterpret_cast<const float2 *>(dftC),
+                                                        dft_mpad, dft_err);
         return cudaGetLastError();
     }
     if (cluster_L > 8) {
@@ -1190,7 +1209,8 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_fft_select, ln, select_only, 1);
+    return cudaLaunchKernelEx(&cfg, k_fft_select, ln, select_only, 1, reinterpret_cast<const float2 *>(dftC),
+                              dft_mpad, dft_err);
 }
 
 bool fft_select_cluster_ok(uint32_t L, uint32_t max_B) {

@@ -33,6 +33,8 @@ constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor
 constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
 constexpr uint32_t kResidualMaxB = 8192;  // residual check: a loop's B residuals (FP64) in shared memory
+constexpr uint32_t kDftMaxB = 1024;       // split-BF16 tensor-core DFT: B in [64, 1024]
+constexpr uint32_t kDftRowTile = 128;     // its GEMM's row tile (rows padded to a multiple)
 
 // Shared-memory bytes of a job's staged estimate tables: zhat (L B complex),
 // 1/G~ (N/B complex), kept bits (L B / 8 bytes); 0 when B < 32 (whole bit words).
@@ -79,6 +81,8 @@ struct PlanDev {
     uint32_t estimator;                       // kEstMedian or kEstMean
     uint32_t refine;                          // refinement passes (0: none)
     uint32_t residual;                        // final residual-energy check (0: none)
+    uint32_t precision;                       // 0: FP32 radix-2 FFT; 1: split-BF16 tensor-core DFT
+    uint32_t pad0;
     uint32_t sigma[kMaxL], tau[kMaxL];
     const float *taps;     // [w]
     const float2 *tw;      // [B/2] exp(-2 pi i k / B)
@@ -95,7 +99,7 @@ struct PlanDev {
                            // E = B/1024 words per lane for B >= 1024, else 1)
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
-    uint32_t *survf;       // [cap] frequencies to estimate (survivors, or all candidates)
+    uint32_t *survf;       // [N] with use_bits (survivors of the median bound), else [cap] (candidates)
     uint4 *surv;           // [cap] records {f, key bits, re bits, im bits}
     float2 *rscr;          // refinement: [K][L] per-loop estimates of a pass
     const double2 *gext64; // residual check: [3N/B] G~(nu) in FP64, as gext
@@ -137,6 +141,9 @@ sfft_status cuda_fail(cudaError_t e, const char *what);
 sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, int64_t B, int64_t w, int32_t L,
                         uint64_t seed, const sfft_opts *opts);
 sfft_status plan_rebind(sfft_plan *p, int32_t K, uint64_t seed, cudaStream_t s);
+// The loaded tuning class of a signal shape (tuning.cu): B = pow2 >= B_per_K K,
+// w = B (log2 N + w_extra), L.  False when no class covers it.
+bool tuning_lookup(int logN, int64_t K, double snr_db, int64_t *B_per_K, int64_t *w_extra, int32_t *L);
 // Distinct samples a plan of these sizes, options and seed reads (host count).
 int64_t samples_touched_of(int64_t N, int32_t B, int64_t w, int32_t L, uint64_t seed, const sfft_opts &o);
 
@@ -144,8 +151,19 @@ int64_t samples_touched_of(int64_t N, int32_t B, int64_t w, int32_t L, uint64_t 
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
 // cluster_L > 0: every job has L = cluster_L and the job's CTAs form one
 // thread-block cluster (fft_select_cluster_ok(cluster_L, max_B) must hold).
+// dftC != NULL: the bucket values are the tensor-core DFT's partial planes
+// (dft_partials) instead of gather partials + FFT; dft_err its error word.
 cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t max_B, int select_only,
-                              uint32_t cluster_L, cudaStream_t s);
+                              uint32_t cluster_L, cudaStream_t s, const float *dftC = nullptr, uint32_t dft_mpad = 0,
+                              const uint32_t *dft_err = nullptr);
+// Split-BF16 tensor-core DFT (dft_tc.cu): scratch bytes for `rows` rows of B
+// buckets; the W table of B (built once per device, at plan creation);
+// the DFT of a group's rows (ln: the FFT/select prefix, one CTA per row) into
+// the scratch's partial planes, waits bounded (error word *err).
+size_t dft_scratch_bytes(uint32_t rows, uint32_t B);
+sfft_status dft_table_prepare(uint32_t B);
+cudaError_t launch_dft(const Launch &ln, uint32_t rows, uint32_t B, void *scratch, uint32_t *err, cudaStream_t s);
+const float *dft_partials(void *scratch, uint32_t rows, uint32_t B);
 // Whether clusters of L FFT/select CTAs with B <= max_B can be launched here.
 bool fft_select_cluster_ok(uint32_t L, uint32_t max_B);
 // The pruned scan uses the register table of strong bits when every job has

@@ -40,7 +40,7 @@ class sfft_plan_info(ctypes.Structure):
 class sfft_exec_stats(ctypes.Structure):
     _fields_ = [("candidates", _i64), ("estimated", _i64), ("recorded", _i64), ("fallback", _i32),
                 ("theta", ctypes.c_float), ("iterations", _i32), ("residual_energy", ctypes.c_double),
-                ("bucket_energy", ctypes.c_double)]
+                ("bucket_energy", ctypes.c_double), ("device_error", _i32)]
 
 
 class sfft_request(ctypes.Structure):
@@ -62,6 +62,9 @@ _SIGS = {
     "sfft_plan_get_loops": (_i32, [_p, _p, _p, _p]),
     "sfft_loop_params": (_i32, [_i64, _i32, _u64, _p, _p, _p]),
     "sfft_suggest_params": (_i32, [_i64, _i32, ctypes.c_double, _p, _p, _p]),
+    "sfft_tuning_load": (_i32, [ctypes.c_char_p]),
+    "sfft_tuning_clear": (None, []),
+    "sfft_tuning_classes": (_i32, []),
     "sfft_plan_last_stats": (_i32, [_p, ctypes.POINTER(sfft_exec_stats)]),
     "sfft_execute": (_i32, [_p, _p, _p, _p, _p, _p]),
     "sfft_execute_host": (_i32, [_p, _p, _p, _p, _p, _p]),
@@ -237,6 +240,19 @@ def sfft_suggest_params(N, K, snr_db=None):
     snr = float("nan") if snr_db is None else float(snr_db)
     _check(lib().sfft_suggest_params(N, K, snr, ctypes.byref(B), ctypes.byref(w), ctypes.byref(L)))
     return B.value, w.value, L.value
+
+
+def sfft_tuning_load(path: str):
+    """Load the autotuner's JSON cache of per-size-class plan sizes."""
+    _check(lib().sfft_tuning_load(str(path).encode()))
+
+
+def sfft_tuning_clear():
+    lib().sfft_tuning_clear()
+
+
+def sfft_tuning_classes() -> int:
+    return int(lib().sfft_tuning_classes())
 
 
 def sfft_execute(plan: Plan, x, idx, val, k_out, stream=None):

@@ -67,9 +67,12 @@ def test_invalid_options_rejected():
     with pytest.raises(sfft.SfftError) as ei:
         sfft.sfft_plan_create_ex(1 << 16, 10, 64, 2368, 8, 0, c=1, T=9)
     assert ei.value.status == sfft.SFFT_EINVAL
-    with pytest.raises(sfft.SfftError) as ei:
-        sfft.sfft_plan_create_ex(1 << 16, 10, 64, 2368, 8, 0, precision=1)
-    assert ei.value.status == sfft.SFFT_ENOTIMPL
+    for bad in (dict(precision=2), dict(precision=1, B=32), dict(precision=1, method=sfft.SFFT_METHOD_SEARCH)):
+        kw = dict(bad)
+        B = kw.pop("B", 64)
+        with pytest.raises(sfft.SfftError) as ei:  # refused before any device call
+            sfft.sfft_plan_create_ex(1 << 16, 10, B, B * 37, 8, 0, **kw)
+        assert ei.value.status == sfft.SFFT_EINVAL
 
 
 def test_status_strings():
@@ -169,3 +172,39 @@ def test_suggested_params_refuse_K_beyond_the_rule(N, K):
     with pytest.raises(sfft.SfftError) as ei:
         sfft.sfft_suggest_params(N, K, 20.0)
     assert ei.value.status == sfft.SFFT_EINVAL and "K too large" in str(ei.value)
+
+
+def test_tuning_cache_overrides_the_rule_for_its_classes(tmp_path):
+    import json
+
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({"version": 1, "device": "test", "classes": [
+        {"logN": 20, "K_lo": 50, "K_hi": 200, "snr_lo": 10.0, "snr_hi": 30.0, "B_per_K": 16, "w_extra": 15, "L": 8,
+         "spectra_per_s": 1.0},
+        {"logN": 16, "K_lo": 1, "K_hi": 20, "snr_lo": None, "snr_hi": None, "B_per_K": 32, "w_extra": 21, "L": 12}]}))
+    try:
+        sfft.sfft_tuning_load(path)
+        assert sfft.sfft_tuning_classes() == 2
+        assert sfft.sfft_suggest_params(1 << 20, 100, 20.0) == (2048, 2048 * 35, 8)  # 16 K -> 2048
+        assert sfft.sfft_suggest_params(1 << 20, 100, 5.0) == (512, 512 * 41, 12)    # SNR outside: the rule
+        assert sfft.sfft_suggest_params(1 << 16, 10, None) == (512, 512 * 37, 12)    # the noiseless class
+        assert sfft.sfft_suggest_params(1 << 16, 10, 20.0) == (64, 64 * 37, 12)      # noisy: the rule
+        assert sfft.sfft_suggest_params(1 << 20, 1000, 20.0)[0] == 4096              # K outside the class
+    finally:
+        sfft.sfft_tuning_clear()
+    assert sfft.sfft_tuning_classes() == 0
+    assert sfft.sfft_suggest_params(1 << 20, 100, 20.0) == (512, 512 * 41, 12)
+
+
+@pytest.mark.parametrize("text", ['{"version": 2, "classes": []}', '{"classes": [', '[1, 2]',
+                                  '{"version": 1, "classes": [{"logN": 20}]}',
+                                  '{"version": 1, "classes": [{"logN": 20, "K_lo": 5, "K_hi": 1, "B_per_K": 4, '
+                                  '"w_extra": 21, "L": 12}]}'])
+def test_tuning_cache_rejects_malformed_files(tmp_path, text):
+    path = tmp_path / "bad.json"
+    path.write_text(text)
+    with pytest.raises(sfft.SfftError) as ei:
+        sfft.sfft_tuning_load(path)
+    assert ei.value.status == sfft.SFFT_EINVAL and "tuning cache" in str(ei.value)
+    with pytest.raises(sfft.SfftError):
+        sfft.sfft_tuning_load(tmp_path / "missing.json")

@@ -326,3 +326,23 @@ def test_plan_info_and_sampling_count():
     assert info.nsel == 200 and info.T == 6
     s, t, si = sfft.sfft_plan_get_loops(plan)
     assert s == list(op.sigma) and t == list(op.tau) and si == list(op.sigma_inv)
+
+
+@pytest.mark.parametrize("snr", [-8.0, 0.0])
+def test_survivors_beyond_the_candidate_bound(snr):
+    # K = 1 with B = 64: the candidate bound (L-T+1) nsel N/B = 640 is below N = 4096,
+    # and at low SNR nearly every frequency passes the median bound of the register-table
+    # scan (its survivor list must hold up to N); the output still matches the oracle
+    N, K, B, L, seed = 1 << 12, 1, 64, 8, 21
+    w = 64 * 33
+    plan, op = _pair(N, K, B, w, L, seed)
+    assert plan.info.candidate_capacity < N
+    sig = signals.make_signal(N, K, seed, snr)
+    ref = oracle.sfft(op, sig.x)
+    idx, val, k = run_execute(plan, sig.x)
+    st = sfft.sfft_plan_last_stats(plan)
+    assert k == ref["k_out"]
+    if st.fallback == 0:
+        assert st.estimated > plan.info.candidate_capacity or snr > -5
+    assert np.array_equal(idx, ref["idx"])
+    assert rel_l2(val, ref["val"]) <= 1e-4
