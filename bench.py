@@ -34,8 +34,9 @@ from paper_2012_08238_gb300 import configs, replicas, signals  # noqa: E402
 METRIC = "spectra/s batched+served vs plain at fixed L1 error; p50/p99 ms; HBM GB/s"
 
 # kernels of one batched step: gather, FFT/select, vote scan, estimate (whose
-# last CTA per job takes the top K, running the fallback pass when needed)
-LAUNCHES_PER_STEP = 4
+# last CTA per job takes the top K) and the fallback pass (whose CTAs return
+# at once unless a job's pruned records could not certify its top K)
+LAUNCHES_PER_STEP = 5
 
 # DRAM bytes per spectrum of the gather kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the 64-signal launch, divided by
@@ -52,6 +53,7 @@ PROFILE_VARIANTS = {
     "median_refine": {"refine": 2},
     "mean_refine": {"estimator": "SFFT_ESTIMATOR_MEAN", "refine": 2},
     "search": {"method": "SFFT_METHOD_SEARCH", "L": 8},
+    "split_bf16": {"precision": 1},
 }
 WORKLOAD = configs.GENERAL_N20
 
@@ -149,6 +151,18 @@ def _oracle_run(seed):
     t0 = time.perf_counter()
     out = oracle.sfft(plan, x)
     return os.getpid(), time.perf_counter() - t0, out["k_out"]
+
+
+def _oracle_signal_job(job):
+    """The oracle on one signal it synthesises itself (N, K, B, w, L, plan seed,
+    signal seed, SNR): returns (idx, val, seconds)."""
+    import oracle
+
+    N, K, B, w, L, pseed, sseed, snr = job
+    x = signals.make_signal(N, K, sseed, snr, keep_xhat=False).x
+    t0 = time.perf_counter()
+    out = oracle.sfft(oracle.Plan(N, K, B, w, L, pseed), x)
+    return out["idx"], out["val"], time.perf_counter() - t0
 
 
 def oracle_pool(cores: int):
@@ -344,6 +358,137 @@ def measure_served_c5(sfft, torch, dev, args):
                     "submit_lag_max_ms": lag1,
                     "what": "the first requests of the same stream, one at a time (one-slot server)"}
     del idxs, vals, pool
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_split_bf16(sfft, torch, dev, stream, args, W, sigs, xs, idx32, val32, k32):
+    """The headline's signals with the split-BF16 tensor-core DFT (precision
+    1): spectra/s timed by the library, per-stage times, the error figures,
+    and the agreement of its output with the FP32 path's."""
+    from paper_2012_08238_gb300 import metrics as _m
+
+    S = len(xs)
+    plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, W.L, s, precision=1) for s in range(S)]
+    idxs = [torch.zeros(W.K, dtype=torch.int32, device=dev) for _ in range(S)]
+    vals = [torch.zeros(W.K, dtype=torch.complex64, device=dev) for _ in range(S)]
+    kout = torch.zeros(S, dtype=torch.int32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+    torch.cuda.synchronize(dev)
+    total_ms, stage_ms = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, args.steps, stream)
+    k = kout.cpu().numpy()
+    errs, common, d2, n2 = [], 0, 0.0, 0.0
+    for i, sg in enumerate(sigs):
+        ii, vv = idxs[i].cpu().numpy()[: k[i]], vals[i].cpu().numpy()[: k[i]]
+        errs.append(_m.errors(sg.xhat, W.K, ii, vv))
+        c, gi, oi = np.intersect1d(ii, idx32[i][: k32[i]], return_indices=True)
+        common += len(c)
+        d2 += float(np.sum(np.abs(vv[gi].astype(np.complex128) - val32[i][: k32[i]][oi]) ** 2))
+        n2 += float(np.sum(np.abs(val32[i][: k32[i]][oi].astype(np.complex128)) ** 2))
+    st = [sfft.sfft_plan_last_stats(p).device_error for p in plans]
+    del plans
+    return {"value": S * args.steps / (total_ms / 1e3), "unit": UNIT, "ms_per_step": total_ms / args.steps,
+            "stage_ms_per_step": {kk: v / args.steps for kk, v in stage_ms.items()},
+            "l1_error": float(np.mean([e["L1"] for e in errs])),
+            "support_recall": 1.0 - float(np.sum([e["L0"] for e in errs])) / (W.K * S),
+            "support_agreement_with_fp32": common / max(1, int(np.sum(k32))),
+            "value_rel_l2_vs_fp32": float(np.sqrt(d2 / max(n2, 1e-30))), "device_errors": int(np.count_nonzero(st)),
+            "what": "same signals as the headline; the B-point DFT as a tcgen05 GEMM with hi/lo BF16 splits "
+                    "(3 products, FP32 accumulation in tensor memory)"}
+
+
+def measure_precision_sweep(sfft, torch, dev, stream, args, pool):
+    """The precision sweep: N = 2^24, K = 1000, B = 4096, L = 12 at SNR -10,
+    0, 10, 20, 40 dB, args.c4_seeds signals each, through the FP32 and the
+    split-BF16 paths: L1 / L2 error and support recall against the planted
+    spectra, agreement between the two paths; and, on args.c4_oracle_seeds
+    signals per SNR, agreement of both with the FP64 oracle (run on the host
+    cores meanwhile)."""
+    W = configs.SWEEP_N24
+    snrs = (-10.0, 0.0, 10.0, 20.0, 40.0)
+    no = args.c4_oracle_seeds
+    jobs = [(W.N, W.K, W.B, W.window, W.L, j, 30_000 + 100 * i + j, snr) for i, snr in enumerate(snrs)
+            for j in range(no)]
+    pending = pool.map_async(_oracle_signal_job, jobs, chunksize=1) if pool is not None and no > 0 else None
+    S = args.c4_seeds
+    plans = {prec: [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, W.L, s, precision=prec) for s in range(S)]
+             for prec in (0, 1)}
+    idxs = [torch.zeros(W.K, dtype=torch.int32, device=dev) for _ in range(S)]
+    vals = [torch.zeros(W.K, dtype=torch.complex64, device=dev) for _ in range(S)]
+    kout = torch.zeros(S, dtype=torch.int32, device=dev)
+    rows = []
+    for i, snr in enumerate(snrs):
+        row = {"snr_db": snr}
+        gen = [signals.make_signal_device(W.N, W.K, 40_000 + 100 * i + s, snr, dev, with_xhat=True) for s in range(S)]
+        xs = [g[0] for g in gen]
+        outs = {}
+        for prec in (0, 1):
+            sfft.sfft_execute_batch(plans[prec], xs, idxs, vals, kout, stream)
+            torch.cuda.synchronize(dev)
+            k = kout.cpu().numpy()
+            outs[prec] = [(idxs[s][: k[s]].to(torch.int64), vals[s][: k[s]].clone()) for s in range(S)]
+        for prec, name in ((0, "fp32"), (1, "split_bf16")):
+            l1, l2, miss = [], [], 0
+            for s in range(S):
+                x, _, _, xhat = gen[s]
+                supp = torch.sort(torch.topk(xhat.abs(), W.K).indices).values
+                ii, vv = outs[prec][s]
+                from paper_2012_08238_gb300 import metrics as _m
+
+                e = _m.errors_sparse(W.K, supp.cpu().numpy(), xhat[supp].cpu().numpy(), ii.cpu().numpy(),
+                                     vv.cpu().numpy(), xhat[ii].cpu().numpy())
+                l1.append(e["L1"])
+                l2.append(e["L2_rel"])
+                miss += e["L0"]
+            row[name] = {"l1_error": float(np.mean(l1)), "l2_rel_error": float(np.mean(l2)),
+                         "support_recall": 1.0 - miss / (W.K * S)}
+        agree, d2, n2, tot = 0, 0.0, 0.0, 0
+        for s in range(S):
+            a, va = outs[0][s]
+            b, vb = outs[1][s]
+            c, ia, ib = np.intersect1d(a.cpu().numpy(), b.cpu().numpy(), return_indices=True)
+            agree += len(c)
+            tot += len(a)
+            va_, vb_ = va.cpu().numpy()[ia].astype(np.complex128), vb.cpu().numpy()[ib].astype(np.complex128)
+            d2 += float(np.sum(np.abs(vb_ - va_) ** 2))
+            n2 += float(np.sum(np.abs(va_) ** 2))
+        row["support_agreement_bf16_vs_fp32"] = agree / max(tot, 1)
+        row["value_rel_l2_bf16_vs_fp32"] = float(np.sqrt(d2 / max(n2, 1e-30)))
+        rows.append(row)
+        del gen, xs, outs
+        torch.cuda.empty_cache()
+    out = {"workload": f"N=2^24, K={W.K}, B={W.B}, L={W.L}, w={W.window}; {S} signals per SNR", "rows": rows}
+    if pending is not None:
+        res = pending.get()
+        for i, snr in enumerate(snrs):
+            agg = {0: [0, 0, 0.0, 0.0], 1: [0, 0, 0.0, 0.0]}
+            for j in range(no):
+                oidx, oval, _ = res[i * no + j]
+                sig = signals.make_signal(W.N, W.K, 30_000 + 100 * i + j, snr, keep_xhat=False)
+                xd = torch.from_numpy(sig.x).to(dev)
+                for prec in (0, 1):
+                    ii = torch.zeros(W.K, dtype=torch.int32, device=dev)
+                    vv = torch.zeros(W.K, dtype=torch.complex64, device=dev)
+                    ko = torch.zeros(1, dtype=torch.int32, device=dev)
+                    sfft.sfft_execute(plans[prec][j], xd, ii, vv, ko, stream)
+                    torch.cuda.synchronize(dev)
+                    kk = int(ko.item())
+                    gi_, gv_ = ii.cpu().numpy()[:kk], vv.cpu().numpy()[:kk]
+                    c, a, b = np.intersect1d(gi_, oidx, return_indices=True)
+                    g = agg[prec]
+                    g[0] += len(c)
+                    g[1] += len(oidx)
+                    g[2] += float(np.sum(np.abs(gv_[a].astype(np.complex128) - oval[b]) ** 2))
+                    g[3] += float(np.sum(np.abs(oval[b]) ** 2))
+                del xd
+            for prec, name in ((0, "fp32"), (1, "split_bf16")):
+                g = agg[prec]
+                rows[i][name]["support_agreement_vs_oracle"] = g[0] / max(g[1], 1)
+                rows[i][name]["value_rel_l2_vs_oracle"] = float(np.sqrt(g[2] / max(g[3], 1e-30)))
+        out["oracle"] = {"signals_per_snr": no, "seconds_per_signal": float(np.mean([r[2] for r in res])),
+                         "what": "FP64 oracle on the host cores (its own signals of the same recipe)"}
+    del plans
     torch.cuda.empty_cache()
     return out
 
@@ -572,6 +717,11 @@ def run_ours(args):
     cores = host_cores()
     want_cpu = rank == 0 and world == 1 and not args.no_cpu and not args.profile
     pool = oracle_pool(min(cores, args.cpu_signals)) if want_cpu else None
+    # measured plan sizes per size class (the batched and serving legs size their plans by them)
+    tuning = None
+    if args.tuning and os.path.exists(args.tuning):
+        sfft.sfft_tuning_load(args.tuning)
+        tuning = {"file": os.path.relpath(args.tuning, ROOT), "classes": sfft.sfft_tuning_classes()}
 
     W = WORKLOAD
     S = args.signals
@@ -707,8 +857,18 @@ def run_ours(args):
     comb = measure_comb(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
     mean = measure_mean(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
     search = measure_search(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
+    k32 = kout.cpu().numpy()
+    idx32 = [t.cpu().numpy() for t in idxs]
+    val32 = [t.cpu().numpy().astype(np.complex128) for t in vals]
+    split = measure_split_bf16(sfft, torch, dev, stream, args, W, sigs, xs, idx32, val32, k32) if rank == 0 else None
     batched = measure_batched_c3(sfft, torch, dev, stream, args) if rank == 0 and not args.no_c3 else None
+    if batched is not None:
+        batched["plan_sizes"] = tuning or "fixed size-class rule"
     served = measure_served_c5(sfft, torch, dev, args) if rank == 0 and not args.no_c5 else None
+    if served is not None:
+        served["plan_sizes"] = tuning or "fixed size-class rule"
+    sweep = (measure_precision_sweep(sfft, torch, dev, stream, args, pool)
+             if rank == 0 and not args.no_c4 else None)
 
     # ---- CPU baseline: the oracle on a bounded sample, host cores
     cpu = None
@@ -737,6 +897,7 @@ def run_ours(args):
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
         "roofline": roofline, "roofline_scan": roofline_scan, "dense_fft_context": dense,
         "exactly_sparse": exact, "comb_prefilter": comb, "averaging_estimator": mean, "search_location": search,
+        "split_bf16_dft": split, "precision_sweep": sweep,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
@@ -799,6 +960,12 @@ def main():
     ap.add_argument("--c5-budget-gb", type=float, default=96.0, help="serving: device memory budget of the plans")
     ap.add_argument("--c5-plain-requests", type=int, default=4000, help="serving: requests of the one-slot run")
     ap.add_argument("--no-c5", action="store_true", help="skip the serving workload")
+    ap.add_argument("--c4-seeds", type=int, default=64, help="precision sweep: signals per SNR")
+    ap.add_argument("--c4-oracle-seeds", type=int, default=2, help="precision sweep: signals per SNR checked by "
+                                                                       "the oracle")
+    ap.add_argument("--no-c4", action="store_true", help="skip the precision sweep")
+    ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_2012_08238_gb300", "tuning", "gb300.json"),
+                    help="autotuner cache for the batched and serving legs ('' for the fixed rule)")
     ap.add_argument("--variant", default="voting", choices=sorted(PROFILE_VARIANTS),
                     help="plans of this variant (--profile runs only; the bench line is the voting path)")
     ap.add_argument("--profile", action="store_true",

@@ -335,7 +335,7 @@ struct Sizes {
     uint32_t gather = 0, select = 0, vote = 0, jobs = 0;
     uint32_t fb = 0;  // fallback-pass CTAs
     uint32_t max_B = 0, max_flags = 0, L_uniform = 0, max_K = 0;
-    uint32_t est_ctas = kEstimateCtas, est_smem = 0;  // pruned estimate: CTAs per job, staged table bytes
+    uint32_t est_smem = 0;  // pruned estimate: staged table bytes
     bool bits = true;
     bool phase = false;    // every job uses the phase-encoding method
     uint32_t max_L = 0;    // phase encoding: iterations to launch
@@ -495,8 +495,7 @@ cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vecto
             return e;
     if ((e = mark(3)) != cudaSuccess) return e;
     for (const Group &g : gs) {
-        if ((e = launch_estimate(at(5, g), g.z.jobs, g.z.L_uniform, g.z.est_ctas, g.z.est_smem, g.z.max_K, s)) !=
-            cudaSuccess)
+        if ((e = launch_estimate(at(5, g), g.ctas[5], g.z.L_uniform, g.z.est_smem, g.z.max_K, s)) != cudaSuccess)
             return e;
         // jobs whose pruned records could not certify their top K
         if ((e = launch_fallback(at(4, g), g.ctas[4], g.z.L_uniform, g.z.max_K, s)) != cudaSuccess) return e;
@@ -519,6 +518,7 @@ cudaError_t launch_single(const Launch &ln, const Sizes &z, void *dft, cudaStrea
     gs[0].ctas[1] = z.select;
     gs[0].ctas[2] = z.vote;
     gs[0].ctas[4] = z.fb;
+    gs[0].ctas[5] = kEstimateCtas;
     return launch_pipeline(lk, z, gs, dft, s, ev);
 }
 
@@ -532,6 +532,7 @@ Job make_job(const sfft_plan *p, const float *x, int32_t *idx, float *val, int32
     j.rpc = p->h.rpc;
     j.nchunk = p->h.nchunk;
     j.vctas = p->h.vtiles;
+    j.ectas = kEstimateCtas;
     return j;
 }
 
@@ -701,7 +702,7 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     }
     if (o.precision == 1 && (phase || B < 64 || B > (int64_t)kDftMaxB)) {
         set_error("sfft_opts.precision 1 (split-BF16 tensor-core DFT) is for the voting and comb methods with "
-                  "64 <= B <= 1024");
+                  "64 <= B <= 4096");
         return SFFT_EINVAL;
     }
     if (o.residual != 0 && (o.residual != 1 || phase || B < 4 || B > (int32_t)kResidualMaxB)) {
@@ -1112,19 +1113,25 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
     // per group: the pruned scan takes up to 8 vote tiles per CTA while the
     // launch keeps at least kScanWaves waves of resident CTAs (fewer CTAs
     // amortise the per-CTA set-up; too few leave a mostly idle last wave);
-    // the estimate launches kEstimateCtas CTAs per job, of which one per
-    // 2048 survivors takes work
+    // the estimate takes one wave of resident CTAs, shared among the jobs in
+    // proportion to N (their survivors grow with N), 1..kEstimateCtas each
     size_t r0 = 0;
     for (Group &g : b.groups) {
         Sizes &gz = g.z;
         if (gz.L_uniform != 8 && gz.L_uniform != 12 && gz.L_uniform != 16) gz.est_smem = 0;
+        double sumN = 0.0;
+        for (size_t r = r0; r < r0 + gz.jobs; ++r) sumN += (double)plans[order[r]]->N;
+        const double wave = (double)kNumSms * (gz.est_smem ? kEstTabCtasPerSm : kEstSurvCtasPerSm);
         uint64_t vt = 0;
         for (size_t r = r0; r < r0 + gz.jobs; ++r) vt += cnt[r * 6 + 2];
         uint32_t tpc = 8;
         while (tpc > 1 && vt / tpc < (uint64_t)kScanWaves * kNumSms * kScanCtasPerSm) tpc >>= 1;
         gz.vote = 0;
         for (size_t r = r0; r < r0 + gz.jobs; ++r) {
-            cnt[r * 6 + 5] = gz.est_ctas;
+            const double share = std::ceil(wave * (double)plans[order[r]]->N / sumN);
+            const uint32_t ec = (uint32_t)std::max(1.0, std::min((double)kEstimateCtas, share));
+            cnt[r * 6 + 5] = ec;
+            jobs[r].ectas = ec;
             uint32_t &c2 = cnt[r * 6 + 2];
             c2 = (c2 + tpc - 1) / tpc;
             jobs[r].vctas = c2;

@@ -314,7 +314,7 @@ size_t dft_scratch_bytes(uint32_t rows, uint32_t B) {
 
 sfft_status dft_table_prepare(uint32_t B) {
     if (B < 64 || B > kDftMaxB || (B & (B - 1))) {
-        set_error("precision 1 needs B a power of two in [64, 1024]");
+        set_error("precision 1 needs B a power of two in [64, 4096]");
         return SFFT_EINVAL;
     }
     int device = 0;

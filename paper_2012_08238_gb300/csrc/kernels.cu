@@ -983,12 +983,13 @@ __device__ __forceinline__ uint32_t est_active(uint32_t n, uint32_t ctas_per_job
 // bits, im bits}.  The job's last CTA to finish (atomic ticket after a fence)
 // then takes the job's top K (a7).
 template <int LT>
-__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t ctas_per_job, uint32_t cap) {
+__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t cap) {
     extern __shared__ unsigned long long est_topk[];  // top-K buffer of the job's last CTA
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
     enter(ln, P, J, s_local);
+    const uint32_t ctas_per_job = J.ectas;
     const uint32_t n = P.ctr[kNSurv];
     const float theta = __uint_as_float(P.ctr[kTheta]);
     uint32_t *cnt = P.ctr + kNGe;
@@ -1067,12 +1068,13 @@ __device__ void estimate_tab_part(const PlanDev &P, uint32_t s_local, uint32_t a
 // per job, each over a strided share of the survivors, so every lookup is a
 // shared-memory load.
 template <int LT>
-__global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t ctas_per_job, uint32_t cap) {
+__global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t cap) {
     extern __shared__ float4 est_tab[];  // the job's tables, then the last CTA's top-K buffer
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
     enter(ln, P, J, s_local);
+    const uint32_t ctas_per_job = J.ectas;
     const uint32_t n = P.ctr[kNSurv];
     // only the CTAs with a share of at least kEstChunk survivors stage the tables
     const uint32_t active = est_active(n, ctas_per_job);
@@ -1271,10 +1273,10 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
     return scan_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, cand_out, ncand_out, s);
 }
 
-cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
+cudaError_t launch_estimate(const Launch &ln, uint32_t total_ctas, uint32_t L_uniform, uint32_t tab_smem,
                             uint32_t max_K, cudaStream_t s) {
-    if (njobs == 0) return cudaSuccess;
-    const uint32_t ctas = njobs * per;
+    if (total_ctas == 0) return cudaSuccess;
+    const uint32_t ctas = total_ctas;
     uint32_t cap = kRankMax;
     while (cap < max_K) cap <<= 1;  // the top-K buffer holds the K winners (and up to kRankMax records)
     const uint32_t topk_smem = cap * (uint32_t)(sizeof(unsigned long long) + sizeof(uint32_t));
@@ -1283,7 +1285,7 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform
         const uint32_t smem = max(tab_smem, topk_smem);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<ctas, kThreads, smem, s>>>(ln, per, cap);
+        kern<<<ctas, kThreads, smem, s>>>(ln, cap);
         return cudaGetLastError();
     }
     auto kern = L_uniform == 8    ? k_estimate_surv<8>
@@ -1292,7 +1294,7 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform
                                   : k_estimate_surv<0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)topk_smem);
     if (e != cudaSuccess) return e;
-    kern<<<ctas, kThreads, topk_smem, s>>>(ln, per, cap);
+    kern<<<ctas, kThreads, topk_smem, s>>>(ln, cap);
     return cudaGetLastError();
 }
 

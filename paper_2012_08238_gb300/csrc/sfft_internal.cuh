@@ -30,10 +30,12 @@ constexpr uint32_t kEstMedian = 0;      // a6: coordinate-wise median of the per
 constexpr uint32_t kEstMean = 1;        // a6: their mean (every candidate estimated)
 constexpr uint32_t kRefineMaxK = 4096;  // refinement: the found set lives in shared memory
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
-constexpr int kEstimateCtas = 32;       // CTAs per job of the survivor-estimate kernel (tables in L2)
+constexpr int kEstimateCtas = 32;       // most CTAs per job of the survivor-estimate kernels
+constexpr int kEstTabCtasPerSm = 3;     // resident staged-table estimate CTAs per SM (72 KB each)
+constexpr int kEstSurvCtasPerSm = 8;    // resident estimate CTAs per SM with the tables in L2
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
 constexpr uint32_t kResidualMaxB = 8192;  // residual check: a loop's B residuals (FP64) in shared memory
-constexpr uint32_t kDftMaxB = 1024;       // split-BF16 tensor-core DFT: B in [64, 1024]
+constexpr uint32_t kDftMaxB = 4096;       // split-BF16 tensor-core DFT: B in [64, 4096]
 constexpr uint32_t kDftRowTile = 128;     // its GEMM's row tile (rows padded to a multiple)
 
 // Shared-memory bytes of a job's staged estimate tables: zhat (L B complex),
@@ -116,6 +118,7 @@ struct Job {
     int32_t *kout;
     uint32_t rpc, nchunk;  // gather split of this launch: rounds per chunk, chunks (<= plan's nchunk)
     uint32_t vctas;        // pruned-scan CTAs of this job (each takes every vctas-th vote tile)
+    uint32_t ectas;        // survivor-estimate CTAs of this job
 };
 
 // Launch descriptor shared by all stage kernels: either one job passed by
@@ -179,12 +182,12 @@ inline bool scan_uses_bits(uint32_t L_uniform, bool bits) {
 cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_t L_uniform, bool bits,
                         uint32_t max_flags_bytes, uint32_t max_B, int32_t *cand_out, int32_t *ncand_out,
                         cudaStream_t s);
-// Pruned-pass estimates, per CTAs per job (ln's prefix array must match); the
-// job's last CTA to finish then takes the job's top K (running the fallback
-// pass first when fewer than K pruned records reached theta).  tab_smem > 0:
-// every job's tables fit that many bytes of shared memory (estimate_tab_bytes)
-// and L is uniform in {8, 12, 16}; they are then staged there.
-cudaError_t launch_estimate(const Launch &ln, uint32_t njobs, uint32_t L_uniform, uint32_t per, uint32_t tab_smem,
+// Pruned-pass estimates, each job's Job::ectas CTAs (total_ctas in all; ln's
+// prefix array must match); the job's last CTA to finish then takes the
+// job's top K or flags its fallback pass.  tab_smem > 0: every job's tables
+// fit that many bytes of shared memory (estimate_tab_bytes) and L is uniform
+// in {8, 12, 16}; they are then staged there.
+cudaError_t launch_estimate(const Launch &ln, uint32_t total_ctas, uint32_t L_uniform, uint32_t tab_smem,
                             uint32_t max_K, cudaStream_t s);
 // Unpruned fallback pass of the jobs whose pruned records could not certify
 // the top K (the estimate's last CTA flags them): fb_ctas(N) CTAs per job

@@ -127,7 +127,8 @@ def tune(logNs, out_path: str, steps: int = 3, log=print):
             if kb[0] > configs.max_K(N):
                 continue
             for sb in SNR_BANDS:
-                count = int(min(64, max(4, (1 << 25) // N)))
+                # enough signals for a throughput-bound batch (2^27 samples), 4..256
+                count = int(min(256, max(4, (1 << 27) // N)))
                 cs = ClassSet(torch, dev, n, kb, sb, count, seed=7919 * n + 131 * kb[0] + int(sb[0] + 20))
                 results = {}
                 for cand in CANDIDATES:

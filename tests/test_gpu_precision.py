@@ -21,7 +21,8 @@ torch = pytest.importorskip("torch")
 
 @pytest.mark.parametrize("N,K,B,L,snr", [(1 << 14, 10, 64, 8, None), (1 << 16, 20, 128, 12, 20.0),
                                          (1 << 18, 60, 512, 12, 10.0), (1 << 20, 100, 512, 12, 20.0),
-                                         (1 << 18, 200, 1024, 16, 30.0), (1 << 12, 4, 64, 5, 0.0)])
+                                         (1 << 18, 200, 1024, 16, 30.0), (1 << 12, 4, 64, 5, 0.0),
+                                         (1 << 20, 1000, 4096, 12, 20.0)])
 def test_bucket_values_within_split_bf16_tolerance(N, K, B, L, snr):
     w = configs.default_window(N, B)
     seed = 3
@@ -87,4 +88,4 @@ def test_precision_option_checks():
     with pytest.raises(sfft.SfftError):  # B below the tensor-core tile
         sfft.sfft_plan_create_ex(N, K, 32, 32 * 37, 8, 0, precision=1)
     with pytest.raises(sfft.SfftError):  # B above the W tables kept
-        sfft.sfft_plan_create_ex(1 << 20, K, 2048, 2048 * 41, 8, 0, precision=1)
+        sfft.sfft_plan_create_ex(1 << 20, K, 8192, 8192 * 41, 8, 0, precision=1)
