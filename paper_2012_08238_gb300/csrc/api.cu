@@ -153,8 +153,15 @@ void decompose(PlanDev &P) {
                      : 0u;
 }
 
+// Plans whose pruned scan reads the 2-bit table: no register table, and a
+// u16 table beyond the scan's shared memory.
+bool needs_bits2(const PlanDev &P) {
+    return !iterative(P.method) && !P.use_bits && (size_t)P.L * P.B * 2 > (size_t)kFlagsSmemBytes;
+}
+
 struct Layout {
-    size_t plan, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, survf, surv, rscr, resid, dft, ctr, total;
+    size_t plan, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, bits2, survf, surv, rscr, resid, dft, ctr,
+        total;
 };
 
 Layout layout_of(const PlanDev &P, int64_t cap) {
@@ -180,6 +187,7 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.topk = take(sizeof(uint32_t) * L * 32 * (B > 1024 ? B / 1024 : 1));
     o.sel = take(sizeof(int32_t) * L * P.nsel);
     o.flags = take(sizeof(uint16_t) * L * B);
+    o.bits2 = take(needs_bits2(P) ? sizeof(uint32_t) * L * B / 16 : 0);
     // the register-table scan lists survivors of the median bound before their
     // candidacy is checked: each frequency at most once, up to N of them; the
     // other scans list candidates only (at most cap)
@@ -821,6 +829,7 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     P.packed = reinterpret_cast<uint32_t *>(base + lay.topk);
     P.sel = reinterpret_cast<int32_t *>(base + lay.sel);
     P.flags = reinterpret_cast<uint16_t *>(base + lay.flags);
+    P.bits2 = needs_bits2(P) ? reinterpret_cast<uint32_t *>(base + lay.bits2) : nullptr;
     P.survf = reinterpret_cast<uint32_t *>(base + lay.survf);
     P.surv = reinterpret_cast<uint4 *>(base + lay.surv);
     P.ctr = reinterpret_cast<uint32_t *>(base + lay.ctr);

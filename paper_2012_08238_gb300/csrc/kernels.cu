@@ -113,6 +113,22 @@ __device__ __forceinline__ uint32_t packed_word(const PlanDev &P, uint32_t l, ui
     return word;
 }
 
+// Words [w0, w1) of the 2-bit table: word w packs the entries 16 w .. 16 w + 15
+// (flag(e) = kept | strong << 8 of table entry e = l B + h) as kept at bit
+// 2k and strong at bit 2k + 1.
+template <class Flag>
+__device__ __forceinline__ void pack_bits2(const PlanDev &P, uint32_t w0, uint32_t w1, Flag flag) {
+    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        uint32_t word = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < 16; ++k) {
+            const uint32_t f = flag(16 * w + k);
+            word |= ((f & 1u) | (((f >> 8) & 1u) << 1)) << (2 * k);
+        }
+        P.bits2[w] = word;
+    }
+}
+
 // Clustered tail of k_fft_select for loop l (all threads of every CTA of the
 // job's cluster): theta from the loops' ceil(K/L)-th energies read through
 // distributed shared memory, then this loop's flags (kept | strong << 8) and
@@ -149,6 +165,11 @@ __device__ void cluster_tables(const PlanDev &P, uint32_t l, uint32_t kqv, const
     const uint32_t B = P.B;
     for (uint32_t k = threadIdx.x; k < B; k += blockDim.x)
         frow[k] = (uint16_t)(kept_s[k] | (strong_energy(__uint_as_float(en_s[k]), gmul, thr) ? 256u : 0u));
+    if (P.bits2)
+        pack_bits2(P, l * (B >> 4), (l + 1) * (B >> 4), [&](uint32_t e) {
+            const uint32_t k = e - l * B;
+            return kept_s[k] | (strong_energy(__uint_as_float(en_s[k]), gmul, thr) ? 256u : 0u);
+        });
     const bool mean = P.estimator == kEstMean;
     const uint32_t E = table_words(P.logB);
     if (P.use_bits)
@@ -370,6 +391,10 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
             if (strong_energy(en, gmul, thr)) f |= 256;
             P.flags[e] = f;
         }
+    }
+    if (P.bits2) {
+        __syncthreads();  // the flags above are complete
+        pack_bits2(P, 0, P.L * (B >> 4), [&](uint32_t e) { return __ldcg(reinterpret_cast<const unsigned short *>(P.flags) + e); });
     }
     if (P.use_bits) {
         __syncthreads();  // the flags above are complete
@@ -632,7 +657,9 @@ __device__ __forceinline__ void estimate_record(const PlanDev &P, uint32_t f, bo
 //
 // The bucket comes from t = (sigma_l << (32 - log2 N)) f + (half << (32 - log2 N))
 // mod 2^32, whose top log2 B bits are round-half-up(sigma_l f B / N) mod B.
-enum TableKind : int { kTabGlobal = 0, kTabSmem = 1 };
+// kTabBits2: the 2-bit table (kept, strong) of tables too large for the u16
+// one in shared memory, staged there (L B / 4 bytes).
+enum TableKind : int { kTabGlobal = 0, kTabSmem = 1, kTabBits2 = 2 };
 
 // Full adder over 32 bit-lanes: a + b + c = s + 2 cy.
 __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &sum, uint32_t &cy) {
@@ -707,6 +734,22 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
         __syncthreads();
         tab = tab_s;
     }
+    const uint32_t *tab2 = reinterpret_cast<const uint32_t *>(tab_s);
+    const uint32_t wpl = B >> 4;  // 2-bit table: words per loop
+    if constexpr (TAB == kTabBits2) {
+        uint32_t *dst = reinterpret_cast<uint32_t *>(tab_s);
+        for (uint32_t i = threadIdx.x; i < L * wpl; i += blockDim.x) dst[i] = __ldcg(P.bits2 + i);
+        __syncthreads();
+    }
+    // score | strong << 8 of loop l's bucket h
+    auto entry = [&](uint32_t l, uint32_t h) -> uint32_t {
+        if constexpr (TAB == kTabBits2) {
+            const uint32_t v = (tab2[l * wpl + (h >> 4)] >> ((h & 15u) << 1)) & 3u;
+            return (v & 1u) | ((v >> 1) << 8);
+        } else {
+            return tab[l * B + h];
+        }
+    };
     constexpr int LR = LT > 0 ? LT : 1;
     uint32_t av[LR];
     if constexpr (LT > 0) {
@@ -748,10 +791,9 @@ __global__ void __launch_bounds__(kThreads) k_vote_scan(Launch ln, int mode, int
                 uint32_t acc = 0;  // score | strong << 8
                 if constexpr (LT > 0) {
 #pragma unroll
-                    for (int l = 0; l < LT; ++l) acc += tab[l * B + ((av[l] * f + cv) >> top)];
+                    for (int l = 0; l < LT; ++l) acc += entry(l, (av[l] * f + cv) >> top);
                 } else {
-                    for (uint32_t l = 0; l < L; ++l)
-                        acc += tab[l * B + (((P.sigma[l] << (32 - P.logN)) * f + cv) >> top)];
+                    for (uint32_t l = 0; l < L; ++l) acc += entry(l, ((P.sigma[l] << (32 - P.logN)) * f + cv) >> top);
                 }
                 const bool cand = valid && (acc & 0xFFu) >= T;
                 if (mode == kVoteCandidates) {
@@ -1155,11 +1197,11 @@ template <int LT, int TAB>
 cudaError_t scan_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t smem, int32_t *cand_out,
                          int32_t *ncand_out, cudaStream_t s) {
     auto kern = k_vote_scan<LT, TAB>;
-    if (TAB == kTabSmem) {
+    if (TAB != kTabGlobal) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<ctas, kThreads, TAB == kTabSmem ? smem : 0, s>>>(ln, mode, cand_out, ncand_out);
+    kern<<<ctas, kThreads, TAB != kTabGlobal ? smem : 0, s>>>(ln, mode, cand_out, ncand_out);
     return cudaGetLastError();
 }
 
@@ -1270,6 +1312,10 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
     }
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
         return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, cand_out, ncand_out, s);
+    // the pruned pass stages the 2-bit table (L B / 4 bytes, an eighth of the u16 one)
+    if (mode == kVotePrune)
+        return scan_dispatch_l<kTabBits2>(ln, total_ctas, mode, L_uniform, max_flags_bytes / 8, cand_out, ncand_out,
+                                          s);
     return scan_dispatch_l<kTabGlobal>(ln, total_ctas, mode, L_uniform, 0, cand_out, ncand_out, s);
 }
 

@@ -101,6 +101,8 @@ struct PlanDev {
                            // E = B/1024 words per lane for B >= 1024, else 1)
     int32_t *sel;          // [L][nsel]
     uint16_t *flags;       // [L][B]: 1 = kept, +256 = strong
+    uint32_t *bits2;       // [L][B/16]: the same as 2 bits per bucket (kept, strong), when the
+                           // u16 table exceeds the scan's shared memory (else NULL)
     uint32_t *survf;       // [N] with use_bits (survivors of the median bound), else [cap] (candidates)
     uint4 *surv;           // [cap] records {f, key bits, re bits, im bits}
     float2 *rscr;          // refinement: [K][L] per-loop estimates of a pass
@@ -196,9 +198,10 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t total_ctas, uint32_t L_un
 // of jobs without a pending fallback return at once.
 cudaError_t launch_fallback(const Launch &ln, uint32_t total_ctas, uint32_t L_uniform, uint32_t max_K,
                             cudaStream_t s);
-// CTAs per job of the fallback pass: one per 2^16 frequencies, 1..64.
+// CTAs per job of the fallback pass: one per 2^18 frequencies, 1..64 (few:
+// most launches only read the flag).
 __host__ __device__ inline uint32_t fallback_ctas(uint32_t N) {
-    const uint32_t c = (N + 65535u) >> 16;
+    const uint32_t c = (N + 262143u) >> 18;
     return c < 1 ? 1u : (c > 64 ? 64u : c);
 }
 // Spike-train pre-filter of comb plans: one CTA per job (max_Bc: the largest

@@ -52,6 +52,7 @@ SHAPES = [
     (1 << 16, 200, 1024, 1024 * 37, 12, 10, 2, None, "noisy"),    # register-table scan, 1 word per lane
     (1 << 17, 300, 2048, 2048 * 38, 8, 11, 2, None, "noisy"),     # register-table scan, 2 words per lane
     (1 << 18, 500, 4096, 4096 * 39, 16, 12, 2, None, "exact"),    # register-table scan, 4 words per lane
+    (1 << 20, 2000, 8192, 8192 * 41, 12, 13, 2, None, "noisy"),   # 2-bit table scan (u16 table > 96 KB)
 ]
 
 
