@@ -1108,6 +1108,21 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         const Sizes &s = ps[i];
         uint32_t *c = &cnt[(size_t)r * 6];
         c[0] = s.gather;
+        if (count > 1 && !s.phase) {
+            // in a batch the other signals fill the GPU: a job's gather takes
+            // about kNumSms CTAs per 2^20 samples of signal (the plan's split,
+            // one CTA per SM, at N = 2^20), so small signals are not cut into
+            // many CTAs of a few rounds each
+            const PlanDev &P = p->h;
+            const uint32_t per = P.tiles * P.L;
+            const uint64_t want = ((uint64_t)kNumSms * P.N + (1u << 20) - 1) >> 20;
+            uint32_t nc = (uint32_t)std::min<uint64_t>(P.nchunk, std::max<uint64_t>(1, (want + per - 1) / per));
+            const uint32_t rpc = (P.rounds + nc - 1) / nc;
+            nc = (P.rounds + rpc - 1) / rpc;
+            jobs[r].rpc = rpc;
+            jobs[r].nchunk = nc;
+            c[0] = per * nc;
+        }
         c[1] = s.select;
         c[2] = s.vote;
         c[3] = 1;
@@ -1137,7 +1152,8 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         while (tpc > 1 && vt / tpc < (uint64_t)kScanWaves * kNumSms * kScanCtasPerSm) tpc >>= 1;
         gz.vote = 0;
         for (size_t r = r0; r < r0 + gz.jobs; ++r) {
-            const double share = std::ceil(wave * (double)plans[order[r]]->N / sumN);
+            // (rounded down: the group's CTAs stay within one wave)
+            const double share = std::floor(wave * (double)plans[order[r]]->N / sumN);
             const uint32_t ec = (uint32_t)std::max(1.0, std::min((double)kEstimateCtas, share));
             cnt[r * 6 + 5] = ec;
             jobs[r].ectas = ec;

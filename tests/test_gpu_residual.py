@@ -98,8 +98,9 @@ def test_batch_mixes_checking_and_plain_plans():
         for i, p in enumerate(plans):
             st = sfft.sfft_plan_last_stats(p)
             if i % 2:
-                assert st.residual_energy == pytest.approx(refs[i].residual_energy, rel=1e-9)
-                assert st.bucket_energy == pytest.approx(refs[i].bucket_energy, rel=1e-12)
+                # (the batch may split the gather into other chunks: FP32 sums in another order)
+                assert st.residual_energy == pytest.approx(refs[i].residual_energy, rel=1e-5)
+                assert st.bucket_energy == pytest.approx(refs[i].bucket_energy, rel=1e-6)
             else:
                 assert st.residual_energy == -1.0 and st.bucket_energy == -1.0
 
