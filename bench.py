@@ -752,37 +752,39 @@ def run_ours(args):
     l1 = float(np.mean([e["L1"] for e in errs]))
     recall = 1.0 - float(np.sum([e["L0"] for e in errs])) / (W.K * S)
 
-    # ---- timed region: K back-to-back batch steps with stage events
+    # ---- per-stage device times of K steps (CUDA events around each stage on
+    # the launching stream): the stage shares and the gather's roofline
+    total_ms_st, stage_ms = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, args.steps, stream)
+    if args.profile:
+        if pool is not None:
+            pool.close()
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "value": S * args.steps / (total_ms_st / 1e3),
+                              "stage_ms": stage_ms}), flush=True)
+        return
+
+    # ---- timed region: K back-to-back steps through the production call
+    # (sfft_execute_batch: a seen job list replays its cached CUDA graph),
+    # events on the launching stream, barrier + synchronize on both sides
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local).start() if rank == 0 else None
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter()
-    total_ms, stage_ms = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, args.steps, stream)
-    torch.cuda.synchronize(dev)
-    t_wall = time.perf_counter() - t_wall
-    if dist:
-        dist.barrier()
-    clk = clocks.stop() if clocks else None
-    elapsed = replicas.max_over_ranks(total_ms / 1e3, dist, dev)
-    value = replicas.throughput(world * S * args.steps, elapsed)
-    if args.profile:
-        if pool is not None:
-            pool.close()
-        if rank == 0:
-            print(json.dumps({"profile_run": True, "value": value, "stage_ms": stage_ms}), flush=True)
-        return
-
-    # ---- graph replay of the same batch (context)
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    graph_value = S * args.steps / (e0.elapsed_time(e1) / 1e3)
+    t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    total_ms = e0.elapsed_time(e1)
+    elapsed = replicas.max_over_ranks(total_ms / 1e3, dist, dev)
+    value = replicas.throughput(world * S * args.steps, elapsed)
 
     # ---- plain per-signal path (context)
     ks = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -891,8 +893,13 @@ def run_ours(args):
                    "T": W.threshold, "snr_db": W.snr_db, "signals_per_step": S, "parallelism": f"replicas{world}",
                    "l2": f"no flush: inputs {S * W.N * 8 / 2**20:.0f} MiB and touched sectors "
                          f"{sector_bytes / 2**20:.0f} MiB per step exceed the 129 MB L2"},
+        "what": "value: inputs resident in HBM, K steps of sfft_execute_batch (cached CUDA graph) timed with "
+                "CUDA events; stage_timed_value: the same steps with events around every stage (the stage "
+                "shares and the roofline); e2e: the same metric through sfft_execute_batch_host from pinned "
+                "host buffers, bound by the host link (8 MiB copied per spectrum)",
         "l1_error": l1, "support_recall": recall,
-        "plain_value": plain_value, "graph_value": graph_value, "batched_c3": batched, "served_c5": served,
+        "plain_value": plain_value, "stage_timed_value": S * args.steps / (total_ms_st / 1e3),
+        "batched_c3": batched, "served_c5": served,
         "stage_ms_per_step": per_launch, "stage_share": {k: v / sum(per_launch.values()) for k, v in per_launch.items()},
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
         "roofline": roofline, "roofline_scan": roofline_scan, "dense_fft_context": dense,

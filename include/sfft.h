@@ -70,7 +70,7 @@ typedef struct {
     int32_t c;         /* buckets kept per loop = min(c*K, B); 0 -> 2 ("2K large buckets") */
     int32_t T;         /* vote threshold; 0 -> ceil(L/2) */
     int32_t precision; /* B-point transform (a2): 0 -> FP32 radix-2 FFT; 1 -> split-BF16 DFT on the
-                          tensor cores (voting and comb methods, 64 <= B <= 1024; see below) */
+                          tensor cores (voting and comb methods, 64 <= B <= 4096; see below) */
     int32_t method;    /* SFFT_METHOD_VOTING (0, default), SFFT_METHOD_PHASE, SFFT_METHOD_COMB or
                           SFFT_METHOD_SEARCH */
     int32_t comb;      /* SFFT_METHOD_COMB: residue classes Bc (power of two); 0 -> default
