@@ -398,6 +398,79 @@ def measure_split_bf16(sfft, torch, dev, stream, args, W, sigs, xs, idx32, val32
                     "(3 products, FP32 accumulation in tensor memory)"}
 
 
+def _gather_modes_at(sfft, torch, dev, stream, N, K, count, snr, steps):
+    """Permuted vs stream gather on `count` signals of one shape (the fixed
+    size rule's B, w, L): the gather stage's device time, the whole step's
+    spectra/s, and the agreement of the stream plans' supports with the
+    permuted ones'."""
+    B = 64
+    while B < 4 * K:
+        B <<= 1
+    B = min(B, 4096, N // 64)
+    w = min(configs.default_window(N, B), N // B * B)
+    L = 12
+    xs = [signals.make_signal_device(N, K, 900 + i, snr, dev)[0] for i in range(count)]
+    out = {"N": N, "K": K, "B": B, "w": w, "L": L, "signals": count, "snr_db": snr}
+    sup = {}
+    for name, mode in (("permuted", sfft.SFFT_GATHER_PERMUTED), ("stream", sfft.SFFT_GATHER_STREAM)):
+        plans = [sfft.sfft_plan_create_ex(N, K, B, w, L, 900 + i, mode=mode) for i in range(count)]
+        idxs = [torch.zeros(K, dtype=torch.int32, device=dev) for _ in range(count)]
+        vals = [torch.zeros(K, dtype=torch.complex64, device=dev) for _ in range(count)]
+        kout = torch.zeros(count, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+        torch.cuda.synchronize(dev)
+        total_ms, stage_ms = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, steps, stream)
+        k = kout.cpu().numpy()
+        sup[name] = [np.sort(idxs[i].cpu().numpy()[: k[i]]) for i in range(count)]
+        out[name] = {"gather_ms": stage_ms["gather_fold"] / steps, "ms_per_step": total_ms / steps,
+                     "value": count * steps / (total_ms / 1e3),
+                     "gather_read_gbs": count * N * 8 / (stage_ms["gather_fold"] / steps / 1e3) / 1e9}
+        del plans
+    common = sum(len(np.intersect1d(a, b)) for a, b in zip(sup["permuted"], sup["stream"]))
+    out["support_agreement"] = common / max(1, sum(len(a) for a in sup["permuted"]))
+    out["stream_speedup_gather"] = out["permuted"]["gather_ms"] / out["stream"]["gather_ms"]
+    del xs
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_gather_modes(sfft, torch, dev, stream, args, W, xs):
+    """Step a1's two readers (sfft_opts.mode): the headline's signals through
+    stream-gather plans (graph-replay spectra/s and stage times, as the
+    headline), and permuted vs stream at N = 2^14 .. 2^26."""
+    S = len(xs)
+    plans = [sfft.sfft_plan_create_ex(W.N, W.K, W.B, W.window, W.L, s, mode=sfft.SFFT_GATHER_STREAM)
+             for s in range(S)]
+    idxs = [torch.zeros(W.K, dtype=torch.int32, device=dev) for _ in range(S)]
+    vals = [torch.zeros(W.K, dtype=torch.complex64, device=dev) for _ in range(S)]
+    kout = torch.zeros(S, dtype=torch.int32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    replay_ms = e0.elapsed_time(e1)
+    total_ms, stage_ms = sfft.sfft_execute_batch_timed(plans, xs, idxs, vals, kout, args.steps, stream)
+    del plans
+    g_ms = stage_ms["gather_fold"] / args.steps
+    head = {"value": S * args.steps / (replay_ms / 1e3), "unit": UNIT,
+            "stage_timed_value": S * args.steps / (total_ms / 1e3),
+            "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "gather_read_gbs": S * W.N * 8 / (g_ms / 1e3) / 1e9}
+    shapes = [(1 << 14, 100, 256), (1 << 16, 100, 128), (1 << 18, 300, 64), (1 << 20, 100, 64),
+              (1 << 22, 100, 16), (1 << 24, 1000, 4), (1 << 26, 1000, 2)]
+    sweep = [_gather_modes_at(sfft, torch, dev, stream, N, K, n, 20.0, args.steps) for N, K, n in shapes]
+    return {"headline_stream": head, "sweep": sweep,
+            "what": "stream gather: the signal read once in order (8 N bytes, coalesced) and each loop's reads "
+                    "visited by the three-gap return map; permuted: one sector per window tap"}
+
+
 def measure_precision_sweep(sfft, torch, dev, stream, args, pool):
     """The precision sweep: N = 2^24, K = 1000, B = 4096, L = 12 at SNR -10,
     0, 10, 20, 40 dB, args.c4_seeds signals each, through the FP32 and the
@@ -863,6 +936,7 @@ def run_ours(args):
     idx32 = [t.cpu().numpy() for t in idxs]
     val32 = [t.cpu().numpy().astype(np.complex128) for t in vals]
     split = measure_split_bf16(sfft, torch, dev, stream, args, W, sigs, xs, idx32, val32, k32) if rank == 0 else None
+    gmodes = measure_gather_modes(sfft, torch, dev, stream, args, W, xs) if rank == 0 and not args.no_modes else None
     batched = measure_batched_c3(sfft, torch, dev, stream, args) if rank == 0 and not args.no_c3 else None
     if batched is not None:
         batched["plan_sizes"] = tuning or "fixed size-class rule"
@@ -904,7 +978,7 @@ def run_ours(args):
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
         "roofline": roofline, "roofline_scan": roofline_scan, "dense_fft_context": dense,
         "exactly_sparse": exact, "comb_prefilter": comb, "averaging_estimator": mean, "search_location": search,
-        "split_bf16_dft": split, "precision_sweep": sweep,
+        "split_bf16_dft": split, "precision_sweep": sweep, "gather_modes": gmodes,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
@@ -971,6 +1045,7 @@ def main():
     ap.add_argument("--c4-oracle-seeds", type=int, default=2, help="precision sweep: signals per SNR checked by "
                                                                        "the oracle")
     ap.add_argument("--no-c4", action="store_true", help="skip the precision sweep")
+    ap.add_argument("--no-modes", action="store_true", help="skip the permuted-vs-stream gather comparison")
     ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_2012_08238_gb300", "tuning", "gb300.json"),
                     help="autotuner cache for the batched and serving legs ('' for the fixed rule)")
     ap.add_argument("--variant", default="voting", choices=sorted(PROFILE_VARIANTS),

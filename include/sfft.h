@@ -84,6 +84,8 @@ typedef struct {
     int32_t residual;  /* 1: final residual-energy check in FP64 after the output (voting and
                           comb methods; 4 <= B <= 8192), read with sfft_plan_last_stats;
                           0 (default): none */
+    int32_t mode;      /* how step a1 reads the signal: SFFT_GATHER_AUTO (0, default),
+                          SFFT_GATHER_PERMUTED or SFFT_GATHER_STREAM (see below) */
 } sfft_opts;
 
 /* Location methods.
@@ -138,6 +140,26 @@ typedef struct {
    candidates, so every candidate is estimated (slower). */
 #define SFFT_ESTIMATOR_MEDIAN 0
 #define SFFT_ESTIMATOR_MEAN 1
+
+/* sfft_opts.mode: how the bucketization (step a1, "The analysis of
+   bucketization through the flat filter") reads the signal; both give the
+   same bucket sums up to FP32 rounding order.
+   PERMUTED: each window tap reads its sample at the permuted position
+     (sigma m + tau) mod N, one 8-byte read (a 32-byte sector) per tap: L w
+     reads per signal, the whole signal from DRAM when L w >~ N/4.
+   STREAM: the signal is read once, in order (8 N bytes, coalesced); per
+     loop, one thread per segment visits the samples the window reads in
+     sample order through the three-gap return map of the permutation
+     (sfft_window_walk), and the taps are added into shared-memory bins
+     (FP32 atomics: the order of the additions, hence the last bits, may
+     differ from run to run).  Voting and comb methods, N >= 2^12,
+     B <= 4096; plans with L B > 6144 take their loops in groups, each
+     reading the signal again (mostly from L2).  Keeps a table of 4 L
+     N / seglen bytes (segment starts, seglen = N / (8 V nclu)).
+   AUTO: the permuted gather. */
+#define SFFT_GATHER_AUTO 0
+#define SFFT_GATHER_PERMUTED 1
+#define SFFT_GATHER_STREAM 2
 
 /* sfft_opts.refine > 0: after the top K, the iterative framework's
    subtraction ("Four algorithmic frameworks") refines the K output values.
@@ -265,6 +287,17 @@ sfft_status sfft_loop_params(int64_t N, int32_t L, uint64_t seed, uint32_t *sigm
    K = 1000: 4096).  Errors: SFFT_EINVAL (N not a power of two in
    [2, 2^30], K not in [1, N], K beyond the rule's range, NULL outputs). */
 sfft_status sfft_suggest_params(int64_t N, int32_t K, double snr_db, int32_t *B, int64_t *w, int32_t *L);
+
+/* Sampling geometry of one loop of the stream gather (host only; for tests
+   and tools).  The loop with permutation (sigma odd, tau) reads sample p with
+   window tap q(p) = (sigma^-1 (p - tau) + floor(w/2)) mod N whenever
+   q(p) < w (2 <= w <= N, N a power of two in [2, 2^30], p0 < N).  out[0]:
+   the first sample p >= p0 the loop reads (cyclically, mod N); out[1]: its
+   tap; out[2..5]: the return map {k+, alpha, k-, beta} (three-distance
+   theorem): after the read with tap q the next read is p + k+ (tap
+   q + alpha) if q + alpha < w, else p + k- (tap q - beta) if q >= beta,
+   else p + k+ + k- (tap q + alpha - beta).  SFFT_EINVAL on bad arguments. */
+sfft_status sfft_window_walk(int64_t N, int64_t w, uint64_t sigma, uint64_t tau, int64_t p0, int64_t out[6]);
 
 /* Load the autotuner's cache (JSON written by paper_2012_08238_gb300/tune.py,
    which measures per size class the fastest B/K ratio, window width and L

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "sfft_internal.cuh"
+#include "walk.cuh"
 
 struct sfft_plan {
     uint64_t id;  // unique per plan, keys the batch-graph cache
@@ -151,6 +152,24 @@ void decompose(PlanDev &P) {
                   (P.estimator == kEstMedian || P.T == P.M))
                      ? 1u
                      : 0u;
+    if (P.gmode == kGatherStream) {
+        // stream gather: loop groups whose L B bins fit kStreamBins; walkers
+        // per loop and CTA a power of two (V lg <= 256, V <= 64); CTAs of
+        // min(N/8, 2^15) samples, eight per cluster, one cluster per 2^18
+        // samples and loop group (a partial chunk each); V segments per CTA,
+        // streamed in pieces of kStreamStageSamples / V samples
+        const uint32_t lmax = std::max<uint32_t>(1, kStreamBins / P.B);
+        P.sgrp = (P.L + lmax - 1) / lmax;
+        P.slg = (P.L + P.sgrp - 1) / P.sgrp;
+        uint32_t V = 1;
+        while (V < 64 && 2 * V * P.slg <= 256) V *= 2;
+        P.sV = V;
+        P.snclu = std::max<uint32_t>(1, P.N >> 18);
+        const uint32_t seglen = P.N / (kStreamCluster * P.snclu) / V;
+        P.sseg = ilog2(seglen);
+        P.spiece = std::min<uint32_t>(kStreamStageSamples / V, seglen);
+        P.nchunk = P.snclu;
+    }
 }
 
 // Plans whose pruned scan reads the 2-bit table: no register table, and a
@@ -160,8 +179,8 @@ bool needs_bits2(const PlanDev &P) {
 }
 
 struct Layout {
-    size_t plan, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, bits2, survf, surv, rscr, resid, dft, ctr,
-        total;
+    size_t plan, ctw, cls, keptc, part, zhat, en, lkth, topk, sel, flags, bits2, survf, surv, rscr, resid, dft, walk,
+        wq, ctr, total;
 };
 
 Layout layout_of(const PlanDev &P, int64_t cap) {
@@ -196,6 +215,9 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
     o.rscr = take(P.refine ? sizeof(float2) * P.K * P.L : 0);
     o.resid = take(P.residual ? sizeof(double) * 2 * P.L : 0);
     o.dft = take(P.precision ? dft_scratch_bytes(P.L, P.B) + 256 : 0);  // (+ its error word)
+    const bool stream = P.gmode == kGatherStream;
+    o.walk = take(stream ? sizeof(uint4) * P.L : 0);
+    o.wq = take(stream ? sizeof(uint32_t) * P.L * (size_t)(P.N >> P.sseg) : 0);
     o.ctr = take(sizeof(uint32_t) * kNumCounters);
     o.total = off;
     return o;
@@ -204,7 +226,8 @@ Layout layout_of(const PlanDev &P, int64_t cap) {
 // Sizes and work split of a plan, without touching the device.
 void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, int32_t c, int32_t T,
                    int64_t *cap, uint32_t method, uint32_t Bc, uint32_t estimator = kEstMedian,
-                   uint32_t refine = 0, uint32_t srch_b = 1, uint32_t residual = 0, uint32_t precision = 0) {
+                   uint32_t refine = 0, uint32_t srch_b = 1, uint32_t residual = 0, uint32_t precision = 0,
+                   uint32_t gmode = kGatherPermuted) {
     memset(&P, 0, sizeof(P));
     const int32_t nsel = (int32_t)std::min<int64_t>((int64_t)c * K, B);
     P.N = (uint32_t)N;
@@ -228,6 +251,7 @@ void fill_plan_dev(PlanDev &P, int64_t N, int32_t K, int32_t B, int64_t w, int32
     P.srch_b = srch_b;
     P.residual = residual;
     P.precision = precision;
+    P.gmode = gmode;
     if (method == kMethodComb) {
         P.Bc = Bc;
         P.logBc = ilog2(Bc);
@@ -324,7 +348,8 @@ size_t plan_device_bytes(int64_t N, int32_t K, int32_t B, int64_t w, int32_t L, 
                   (uint32_t)std::min<int64_t>(N, kMaxComb),
                   o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian,
                   (uint32_t)std::max<int32_t>(o.refine, 0), (uint32_t)std::max<int32_t>(o.search_bits, 1),
-                  o.residual ? 1u : 0u, o.precision ? 1u : 0u);
+                  o.residual ? 1u : 0u, o.precision ? 1u : 0u,
+                  o.mode == SFFT_GATHER_STREAM ? kGatherStream : kGatherPermuted);
     return layout_of(P, cap).total;
 }
 
@@ -356,6 +381,8 @@ struct Sizes {
     uint32_t max_rK = 0;   // refinement: largest K of the refining jobs
     uint32_t max_resB = 0; // residual check: largest B of the checking jobs (0: none checks)
     uint32_t dft_B = 0;    // split-BF16 tensor-core DFT of B buckets (0: the FP32 FFT)
+    bool stream = false;   // the job's a1 is the stream gather (groups: every job's)
+    uint32_t stream_smem = 0;  // stream gather: largest dynamic shared memory of the jobs
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -380,6 +407,11 @@ Sizes plan_sizes(const sfft_plan *p) {
     z.comb = p->h.method == kMethodComb;
     z.max_Bc = p->h.Bc;
     z.gather = p->h.tiles * p->h.L * p->h.nchunk;
+    if (p->h.gmode == kGatherStream) {
+        z.stream = true;
+        z.gather = kStreamCluster * p->h.sgrp * p->h.snclu;
+        z.stream_smem = stream_smem_bytes(p->h.slg, p->h.B, p->h.sV, p->h.spiece);
+    }
     z.select = p->h.L;
     z.fb = fallback_ctas(p->h.N);
     z.vote = p->h.vtiles;
@@ -477,7 +509,25 @@ cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vecto
         if ((e = launch_comb(lk[3], all.jobs, all.max_Bc, sr->s)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(sr->join, sr->s)) != cudaSuccess) return e;
     }
-    if ((e = launch_gather(lk[0], all.gather, s)) != cudaSuccess) return e;
+    {
+        // a1: the permuted gather over its jobs (a prefix of the slot's map:
+        // stream-gather groups sort last), then the stream gather
+        uint32_t perm = 0, str = 0, smem = 0;
+        for (const Group &g : gs) {
+            if (g.z.stream) {
+                str += g.ctas[0];
+                smem = std::max(smem, g.z.stream_smem);
+            } else {
+                perm += g.ctas[0];
+            }
+        }
+        if ((e = launch_gather(lk[0], perm, s)) != cudaSuccess) return e;
+        if (str) {
+            Launch l = lk[0];
+            l.cta0 = perm;
+            if ((e = launch_gather_stream(l, str, smem, s)) != cudaSuccess) return e;
+        }
+    }
     if ((e = mark(1)) != cudaSuccess) return e;
     for (const Group &g : gs) {
         const uint32_t cl = fft_select_cluster_ok(g.z.L_uniform, g.z.max_B) ? g.z.L_uniform : 0u;
@@ -523,6 +573,7 @@ cudaError_t launch_single(const Launch &ln, const Sizes &z, void *dft, cudaStrea
     Launch lk[6] = {ln, ln, ln, ln, ln, ln};
     std::vector<Group> gs(1);
     gs[0].z = z;
+    gs[0].ctas[0] = z.gather;
     gs[0].ctas[1] = z.select;
     gs[0].ctas[2] = z.vote;
     gs[0].ctas[4] = z.fb;
@@ -616,6 +667,26 @@ extern "C" sfft_status sfft_loop_params(int64_t N, int32_t L, uint64_t seed, uin
         return SFFT_EINVAL;
     }
     loop_params_host(N, L, seed, sigma, tau, sigma_inv);
+    return SFFT_OK;
+}
+
+extern "C" sfft_status sfft_window_walk(int64_t N, int64_t w, uint64_t sigma, uint64_t tau, int64_t p0,
+                                        int64_t out[6]) {
+    if (!out || !is_pow2(N) || N < 2 || N > (1ll << kMaxLogN) || w < 2 || w > N || !(sigma & 1) ||
+        sigma >= (uint64_t)N || tau >= (uint64_t)N || p0 < 0 || p0 >= N) {
+        set_error("sfft_window_walk: N a power of two in [2, 2^30], 2 <= w <= N, sigma odd < N, tau, p0 < N");
+        return SFFT_EINVAL;
+    }
+    const uint32_t n = (uint32_t)N, s = inv_odd_u32((uint32_t)sigma) & (n - 1);
+    const WindowWalk wk = window_walk(n, s, (uint32_t)w);
+    uint32_t k = 0, q = 0;
+    window_first_read(n, s, (uint32_t)tau, (uint32_t)w, (uint32_t)(w / 2), (uint32_t)p0, &k, &q);
+    out[0] = (int64_t)(((uint64_t)p0 + k) % (uint64_t)N);
+    out[1] = q;
+    out[2] = wk.kp;
+    out[3] = wk.alpha;
+    out[4] = wk.km;
+    out[5] = wk.beta;
     return SFFT_OK;
 }
 
@@ -717,6 +788,16 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
         set_error("sfft_opts.residual must be 0 or 1, for the voting and comb methods with 4 <= B <= 8192");
         return SFFT_EINVAL;
     }
+    if (o.mode != SFFT_GATHER_AUTO && o.mode != SFFT_GATHER_PERMUTED && o.mode != SFFT_GATHER_STREAM) {
+        set_error("sfft_opts.mode must be SFFT_GATHER_AUTO, SFFT_GATHER_PERMUTED or SFFT_GATHER_STREAM");
+        return SFFT_EINVAL;
+    }
+    const bool stream = o.mode == SFFT_GATHER_STREAM;
+    if (stream && (phase || N < (1ll << kStreamMinLogN) || B > 4096)) {
+        set_error("sfft_opts.mode SFFT_GATHER_STREAM is for the voting and comb methods with N >= 2^12 and "
+                  "B <= 4096");
+        return SFFT_EINVAL;
+    }
     // (phase encoding reads no c or T)
     const int32_t c = phase ? 1 : (o.c > 0 ? o.c : 2);
     const int32_t T = phase ? 1 : (o.T > 0 ? o.T : (L + 1) / 2);
@@ -784,7 +865,7 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     PlanDev &P = p->h;
     fill_plan_dev(P, N, K_cap, (int32_t)B, w, L, c, T, &p->cap, (uint32_t)o.method, Bc,
                   o.estimator == SFFT_ESTIMATOR_MEAN ? kEstMean : kEstMedian, (uint32_t)o.refine, (uint32_t)sb,
-                  (uint32_t)o.residual, (uint32_t)o.precision);
+                  (uint32_t)o.residual, (uint32_t)o.precision, stream ? kGatherStream : kGatherPermuted);
     const Layout lay = layout_of(P, p->cap);
     if (K != K_cap) set_K(P, K, &p->cap, c);
     p->nsel = (int32_t)P.nsel;
@@ -832,9 +913,12 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     P.bits2 = needs_bits2(P) ? reinterpret_cast<uint32_t *>(base + lay.bits2) : nullptr;
     P.survf = reinterpret_cast<uint32_t *>(base + lay.survf);
     P.surv = reinterpret_cast<uint4 *>(base + lay.surv);
+    P.walk = stream ? reinterpret_cast<const uint4 *>(base + lay.walk) : nullptr;
+    P.wq = stream ? reinterpret_cast<uint32_t *>(base + lay.wq) : nullptr;
     P.ctr = reinterpret_cast<uint32_t *>(base + lay.ctr);
 
-    // descriptor, counters and the comb twiddles on the thread's set-up stream
+    // descriptor, counters, the comb twiddles and the stream gather's walk
+    // tables on the thread's set-up stream
     auto fail = [&](cudaError_t err, const char *what) {
         cudaFree(p->dmem);
         tables_release(p->tables);
@@ -849,6 +933,7 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
         return fail(e, "clear counters");
     if (comb && (e = plan_twiddles(P.Bc, const_cast<float2 *>(P.ctw), s)) != cudaSuccess)
         return fail(e, "comb twiddles");
+    if ((e = launch_walk_start(P, p->sigma_inv, s)) != cudaSuccess) return fail(e, "stream gather walk tables");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "plan set-up");
     *plan = p;
     return SFFT_OK;
@@ -877,6 +962,7 @@ sfft_status plan_rebind(sfft_plan *p, int32_t K, uint64_t seed, cudaStream_t s) 
     p->samples_touched = -1;
     // (from pageable memory: the descriptor is staged before the call returns)
     SFFT_CUDA_TRY(cudaMemcpyAsync(p->d, &P, sizeof(PlanDev), cudaMemcpyHostToDevice, s));
+    SFFT_CUDA_TRY(launch_walk_start(P, p->sigma_inv, s));
     return SFFT_OK;
 }
 
@@ -1065,6 +1151,8 @@ void merge_sizes(Sizes &z, const Sizes &s, bool first) {
     z.max_rK = std::max(z.max_rK, s.max_rK);
     z.max_resB = std::max(z.max_resB, s.max_resB);
     z.dft_B = std::max(z.dft_B, s.dft_B);
+    z.stream = first ? s.stream : (z.stream && s.stream);
+    z.stream_smem = std::max(z.stream_smem, s.stream_smem);
     z.gather += s.gather;
     z.select += s.select;
     z.vote += s.vote;
@@ -1082,7 +1170,8 @@ uint32_t variant_key(const Sizes &s) {
     const uint32_t est = (s.est_smem && (L == 8 || L == 12 || L == 16)) ? 0u : 1u;
     const uint32_t cl = s.max_B <= (uint32_t)kClusterMaxB ? 0u : 1u;
     const uint32_t dft = s.dft_B ? ilog2(s.dft_B) : 0u;  // tensor-core DFT groups share B
-    return (dft << 16) | (L << 8) | (scan << 4) | (est << 2) | cl;
+    // (stream-gather jobs sort last: their gather CTAs end the slot's map)
+    return ((s.stream ? 1u : 0u) << 24) | (dft << 16) | (L << 8) | (scan << 4) | (est << 2) | cl;
 }
 
 BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t *const *idx,
@@ -1108,7 +1197,7 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         const Sizes &s = ps[i];
         uint32_t *c = &cnt[(size_t)r * 6];
         c[0] = s.gather;
-        if (count > 1 && !s.phase) {
+        if (count > 1 && !s.phase && !s.stream) {
             // in a batch the other signals fill the GPU: a job's gather takes
             // about kNumSms CTAs per 2^20 samples of signal (the plan's split,
             // one CTA per SM, at N = 2^20), so small signals are not cut into
@@ -1494,7 +1583,7 @@ extern "C" sfft_status sfft_bucketize(sfft_plan *p, const float *x_dev, float *z
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Launch ln = single(make_job(p, x_dev, nullptr, nullptr, nullptr));
     const Sizes z = plan_sizes(p);
-    SFFT_CUDA_TRY(launch_gather(ln, z.gather, s));
+    SFFT_CUDA_TRY(z.stream ? launch_gather_stream(ln, z.gather, z.stream_smem, s) : launch_gather(ln, z.gather, s));
     if (z.dft_B) {
         // the plan's tensor-core DFT, as in the pipeline
         uint32_t *err = reinterpret_cast<uint32_t *>(static_cast<char *>(p->dft) + dft_scratch_bytes(z.select, z.dft_B));

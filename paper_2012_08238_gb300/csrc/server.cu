@@ -41,10 +41,11 @@ int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
 }
 
-// shape of a cached plan: N, w, K capacity, B, L, c, T, method, comb, estimator, refine, search bits, residual
+// shape of a cached plan: N, w, K capacity, B, L, c, T, method, comb, estimator, refine, search bits, residual,
+// precision, gather mode
 using PlanKey =
     std::tuple<int64_t, int64_t, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t,
-               int32_t, int32_t>;
+               int32_t, int32_t, int32_t, int32_t>;
 
 struct Request {
     uint64_t ticket = 0;
@@ -402,7 +403,7 @@ extern "C" sfft_status sfft_submit(sfft_server *s, const sfft_request *q, uint64
     r->req = *q;
     r->K_cap = K_cap;
     r->key = PlanKey(q->N, q->w, K_cap, q->B, q->L, c, T, q->opts.method, q->opts.comb, q->opts.estimator,
-                     q->opts.refine, q->opts.search_bits, q->opts.residual);
+                     q->opts.refine, q->opts.search_bits, q->opts.residual, q->opts.precision, q->opts.mode);
     r->t_submit = now_ns();
     {
         std::lock_guard<std::mutex> lk(s->mu);

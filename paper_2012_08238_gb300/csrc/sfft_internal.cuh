@@ -37,6 +37,13 @@ constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up t
 constexpr uint32_t kResidualMaxB = 8192;  // residual check: a loop's B residuals (FP64) in shared memory
 constexpr uint32_t kDftMaxB = 4096;       // split-BF16 tensor-core DFT: B in [64, 4096]
 constexpr uint32_t kDftRowTile = 128;     // its GEMM's row tile (rows padded to a multiple)
+constexpr uint32_t kGatherPermuted = 0;   // a1 read at the permuted positions, sample by sample
+constexpr uint32_t kGatherStream = 1;     // a1 read once in sample order (stream gather)
+constexpr uint32_t kStreamCluster = 8;    // stream gather: CTAs per cluster (bins summed through DSMEM)
+constexpr uint32_t kStreamStages = 4;     // stream gather: cp.async ring depth
+constexpr uint32_t kStreamStageSamples = 2048;  // stream gather: samples per stage (V pieces)
+constexpr uint32_t kStreamBins = 6144;    // stream gather: L B bins of one loop group (48 KB)
+constexpr uint32_t kStreamMinLogN = 12;   // stream gather: N >= 2^12
 
 // Shared-memory bytes of a job's staged estimate tables: zhat (L B complex),
 // 1/G~ (N/B complex), kept bits (L B / 8 bytes); 0 when B < 32 (whole bit words).
@@ -84,7 +91,11 @@ struct PlanDev {
     uint32_t refine;                          // refinement passes (0: none)
     uint32_t residual;                        // final residual-energy check (0: none)
     uint32_t precision;                       // 0: FP32 radix-2 FFT; 1: split-BF16 tensor-core DFT
-    uint32_t pad0;
+    uint32_t gmode;                           // a1: kGatherPermuted or kGatherStream
+    // stream gather: loops per CTA group, loop groups, walkers (segments) per
+    // loop and CTA, samples per stage piece, log2 segment length, clusters
+    // per loop group (= nchunk)
+    uint32_t slg, sgrp, sV, spiece, sseg, snclu;
     uint32_t sigma[kMaxL], tau[kMaxL];
     const float *taps;     // [w]
     const float2 *tw;      // [B/2] exp(-2 pi i k / B)
@@ -108,6 +119,8 @@ struct PlanDev {
     float2 *rscr;          // refinement: [K][L] per-loop estimates of a pass
     const double2 *gext64; // residual check: [3N/B] G~(nu) in FP64, as gext
     double *resid;         // residual check: [L][2] energy left, bucket energy per loop
+    const uint4 *walk;     // stream gather: [L] return map {k+, alpha, k-, beta} (walk.cuh)
+    uint32_t *wq;          // stream gather: [L][N >> sseg] tap of each segment's first read
     uint32_t *ctr;         // [kNumCounters]
 };
 
@@ -154,6 +167,14 @@ int64_t samples_touched_of(int64_t N, int32_t B, int64_t w, int32_t L, uint64_t 
 
 // Kernel launchers (stream-ordered, no synchronisation).
 cudaError_t launch_gather(const Launch &ln, uint32_t total_ctas, cudaStream_t s);
+// Stream gather (gather_stream.cu): every job has gmode = kGatherStream and
+// kStreamCluster * sgrp * snclu CTAs, starting at a multiple of
+// kStreamCluster; smem: the largest stream_smem_bytes of the jobs.  The
+// per-plan table of segment starts is written by launch_walk_start (sinv:
+// sigma_l^-1 mod N) whenever sigma, tau change.
+cudaError_t launch_gather_stream(const Launch &ln, uint32_t total_ctas, uint32_t smem, cudaStream_t s);
+cudaError_t launch_walk_start(const PlanDev &P, const uint32_t *sinv, cudaStream_t s);
+uint32_t stream_smem_bytes(uint32_t lg, uint32_t B, uint32_t V, uint32_t piece);
 // cluster_L > 0: every job has L = cluster_L and the job's CTAs form one
 // thread-block cluster (fft_select_cluster_ok(cluster_L, max_B) must hold).
 // dftC != NULL: the bucket values are the tensor-core DFT's partial planes

@@ -28,7 +28,8 @@ SFFT_OK, SFFT_EINVAL, SFFT_ENOMEM, SFFT_ECUDA, SFFT_EBUSY, SFFT_ETIMEDOUT, SFFT_
 
 class sfft_opts(ctypes.Structure):
     _fields_ = [("c", _i32), ("T", _i32), ("precision", _i32), ("method", _i32), ("comb", _i32),
-                ("estimator", _i32), ("refine", _i32), ("search_bits", _i32), ("residual", _i32)]
+                ("estimator", _i32), ("refine", _i32), ("search_bits", _i32), ("residual", _i32),
+                ("mode", _i32)]
 
 
 class sfft_plan_info(ctypes.Structure):
@@ -62,6 +63,7 @@ _SIGS = {
     "sfft_plan_get_loops": (_i32, [_p, _p, _p, _p]),
     "sfft_loop_params": (_i32, [_i64, _i32, _u64, _p, _p, _p]),
     "sfft_suggest_params": (_i32, [_i64, _i32, ctypes.c_double, _p, _p, _p]),
+    "sfft_window_walk": (_i32, [_i64, _i64, _u64, _u64, _i64, _p]),
     "sfft_tuning_load": (_i32, [ctypes.c_char_p]),
     "sfft_tuning_clear": (None, []),
     "sfft_tuning_classes": (_i32, []),
@@ -191,12 +193,24 @@ SFFT_METHOD_SEARCH = 3
 SFFT_ESTIMATOR_MEDIAN = 0
 SFFT_ESTIMATOR_MEAN = 1
 SFFT_MAX_REFINE = 8
+SFFT_GATHER_AUTO = 0
+SFFT_GATHER_PERMUTED = 1
+SFFT_GATHER_STREAM = 2
 
 
 def sfft_plan_create_ex(N, K, B, w, L, seed, c=0, T=0, precision=0, method=SFFT_METHOD_VOTING, comb=0,
-                        estimator=SFFT_ESTIMATOR_MEDIAN, refine=0, search_bits=0, residual=0) -> Plan:
+                        estimator=SFFT_ESTIMATOR_MEDIAN, refine=0, search_bits=0, residual=0,
+                        mode=SFFT_GATHER_AUTO) -> Plan:
     return sfft_plan_create(N, K, B, w, L, seed,
-                            sfft_opts(c, T, precision, method, comb, estimator, refine, search_bits, residual))
+                            sfft_opts(c, T, precision, method, comb, estimator, refine, search_bits, residual,
+                                      mode))
+
+
+def sfft_window_walk(N, w, sigma, tau, p0):
+    """(first read p >= p0, its tap, k+, alpha, k-, beta) of one loop's window (host only)."""
+    out = (ctypes.c_int64 * 6)()
+    _check(lib().sfft_window_walk(N, w, sigma, tau, p0, out))
+    return tuple(out)
 
 
 def sfft_plan_destroy(plan: Plan):
@@ -361,9 +375,9 @@ def sfft_server_destroy(srv: Server):
 
 
 def sfft_submit(srv: Server, N, K, B, w, L, seed, x, idx, val, c=0, T=0, method=0, comb=0, estimator=0,
-                refine=0, search_bits=0, residual=0, count_samples=1) -> int:
+                refine=0, search_bits=0, residual=0, count_samples=1, precision=0, mode=0) -> int:
     req = sfft_request(N, w, K, B, L, seed,
-                       sfft_opts(c, T, 0, method, comb, estimator, refine, search_bits, residual),
+                       sfft_opts(c, T, precision, method, comb, estimator, refine, search_bits, residual, mode),
                        _addr(x), _addr(idx), _addr(val), int(count_samples))
     ticket = _u64()
     _check(lib().sfft_submit(srv.handle, ctypes.byref(req), ctypes.byref(ticket)))
