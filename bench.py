@@ -54,6 +54,7 @@ PROFILE_VARIANTS = {
     "mean_refine": {"estimator": "SFFT_ESTIMATOR_MEAN", "refine": 2},
     "search": {"method": "SFFT_METHOD_SEARCH", "L": 8},
     "split_bf16": {"precision": 1},
+    "stream": {"mode": "SFFT_GATHER_STREAM"},
 }
 WORKLOAD = configs.GENERAL_N20
 

@@ -106,31 +106,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather_stream(Launch ln) {
         const uint32_t p = (P.sigma[wl] * (q - P.halfw) + P.tau[wl]) & P.mask;
         rel = (p - ((seg0 + wv) << seglog)) & P.mask;
     }
+    const uint32_t kpm = wk.kp + wk.km, amb = wk.alpha - wk.beta;  // (unsigned wrap: q + amb >= 0)
     float2 *mybins = bins + (size_t)(wl - l0) * B;
     const float *__restrict__ taps = P.taps;
     const uint32_t w = P.w, halfw = P.halfw, bmask = B - 1;
 
-    // stage st: samples [st piece, (st + 1) piece) of each of the V segments
+    // stage st: samples [st piece, (st + 1) piece) of each of the V segments,
+    // copied in units of 16 bytes (8 when the signal is only 8-byte aligned);
+    // this thread's units u = t + 256 i keep their offsets from stage to stage
     const float2 *x = J.x;
     const bool a16 = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stg);
+    const uint32_t ub = a16 ? 2u : 1u, per = piece / ub, nunit = V * per;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stg), bufbytes = 8u * V * piece;
+    constexpr int kMaxUnits = kStreamStageSamples / kThreads;  // (8-byte units)
+    size_t soff[kMaxUnits];
+    uint32_t doff[kMaxUnits];
+#pragma unroll
+    for (int i = 0; i < kMaxUnits; ++i) {
+        const uint32_t u = threadIdx.x + kThreads * i, v = u / per, o = (u % per) * ub;
+        soff[i] = ((size_t)(seg0 + v) << seglog) + o;
+        doff[i] = 8u * (v * piece + o);
+    }
     auto issue = [&](uint32_t st) {
         if (st < nstage) {
-            const uint32_t buf = st % kStreamStages;
-            if (a16) {
-                const uint32_t per = piece / 2, n = V * per;  // 16-byte units
-                for (uint32_t u = threadIdx.x; u < n; u += kThreads) {
-                    const uint32_t v = u / per, o = 2 * (u % per);
-                    const float2 *src = x + ((size_t)(seg0 + v) << seglog) + (size_t)st * piece + o;
-                    cp_async16_s(sbase + 8u * ((buf * V + v) * piece + o), src);
-                }
-            } else {
-                const uint32_t n = V * piece;
-                for (uint32_t u = threadIdx.x; u < n; u += kThreads) {
-                    const uint32_t v = u / piece, o = u % piece;
-                    const float2 *src = x + ((size_t)(seg0 + v) << seglog) + (size_t)st * piece + o;
-                    cp_async8_s(sbase + 8u * ((buf * V + v) * piece + o), src);
-                }
+            const float2 *xs = x + (size_t)st * piece;
+            const uint32_t d0 = sbase + (st % kStreamStages) * bufbytes;
+#pragma unroll
+            for (int i = 0; i < kMaxUnits; ++i) {
+                if (threadIdx.x + kThreads * i >= nunit) break;
+                if (a16) cp_async16_s(d0 + doff[i], xs + soff[i]);
+                else cp_async8_s(d0 + doff[i], xs + soff[i]);
             }
         }
         cp_async_commit();  // (an empty group past the last stage keeps the counting uniform)
@@ -151,7 +156,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather_stream(Launch ln) {
             for (int k = 0; k < kWalkBatch; ++k) {
                 qk[k] = q;
                 rk[k] = rel;
-                if (rel < end) rel += window_step(wk, w, q);
+                if (rel < end) {
+                    // the return map (walk.cuh), with k+ + k- and alpha - beta precomputed
+                    const bool up = q + wk.alpha < w, down = q >= wk.beta;
+                    rel += up ? wk.kp : (down ? wk.km : kpm);
+                    q = up ? q + wk.alpha : (down ? q - wk.beta : q + amb);
+                }
             }
             float gk[kWalkBatch];
             float2 vk[kWalkBatch];
@@ -173,8 +183,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather_stream(Launch ln) {
     cp_async_wait_group<0>();
     // the cluster's bins, summed in rank order: CTA r writes the r-th eighth
     cl.sync();
-    const uint32_t per = (nb + kStreamCluster - 1) / kStreamCluster;
-    const uint32_t i0 = rank * per, i1 = min(nb, i0 + per);
+    const uint32_t share = (nb + kStreamCluster - 1) / kStreamCluster;
+    const uint32_t i0 = rank * share, i1 = min(nb, i0 + share);
     float2 *dst = P.partial + ((size_t)clu * P.L + l0) * B;
     for (uint32_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
         float2 acc = make_float2(0.f, 0.f);
