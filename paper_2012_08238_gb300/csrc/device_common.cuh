@@ -17,6 +17,36 @@ constexpr int kThreads = 256;  // every kernel but the comb
 constexpr int kCombThreads = 1024;
 constexpr uint32_t kTwSmemMaxB = 8192;  // FFT twiddles staged in shared memory up to this B
 
+// Launch of a pipeline kernel after the stream's previous kernel with
+// programmatic dependent launch (the kernel's CTAs may start while that
+// kernel finishes and wait in enter()), in clusters of `cluster` CTAs when
+// nonzero.  The kernel must wait (enter() or grid_dep_wait()) before it
+// reads anything an earlier kernel of the stream wrote.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), uint32_t grid, uint32_t block, size_t smem, cudaStream_t s,
+                       uint32_t cluster, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    unsigned n = 0;
+    at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+    if (cluster) {
+        at[n].id = cudaLaunchAttributeClusterDimension;
+        at[n].val.clusterDim.x = cluster;
+        at[n].val.clusterDim.y = 1;
+        at[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 __device__ __forceinline__ void locate(const Launch &ln, uint32_t bid, Job &job, uint32_t &local) {
     if (ln.jobs == nullptr) {
         job = ln.one;
@@ -37,7 +67,16 @@ __device__ __forceinline__ void load_plan(PlanDev &dst, const PlanDev *src) {
     for (uint32_t i = threadIdx.x; i < sizeof(PlanDev) / 8; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-// Locate + load in one call; every kernel starts with it.
+// Programmatic dependent launch: wait for the stream's previous kernel to
+// complete (its writes visible; a no-op when this launch does not overlap
+// it), and allow the stream's next kernel to start its prologue.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Locate + load in one call; every kernel starts with it.  The job list and
+// the plan descriptor are written before a pipeline's first kernel, so they
+// are read before the wait for the previous kernel (launch_pdl overlaps this
+// prologue with that kernel's tail).
 __device__ __forceinline__ void enter(const Launch &ln, PlanDev &P, Job &J, uint32_t &s_local) {
     if (threadIdx.x == 0) {
         Job j;
@@ -49,6 +88,7 @@ __device__ __forceinline__ void enter(const Launch &ln, PlanDev &P, Job &J, uint
     __syncthreads();
     load_plan(P, J.p);
     __syncthreads();
+    grid_dep_wait();
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {

@@ -1136,6 +1136,7 @@ __global__ void __launch_bounds__(kThreads) k_fallback(Launch ln, uint32_t cap) 
     __shared__ Job J;
     __shared__ uint32_t s_local, s_cnt;
     __shared__ int s_go, s_last;
+    grid_dep_wait();  // (the flag and records come from the estimate kernel)
     if (threadIdx.x == 0) {
         Job j;
         uint32_t loc;
@@ -1201,8 +1202,7 @@ cudaError_t scan_variant(const Launch &ln, uint32_t ctas, int mode, uint32_t sme
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<ctas, kThreads, TAB != kTabGlobal ? smem : 0, s>>>(ln, mode, cand_out, ncand_out);
-    return cudaGetLastError();
+    return launch_pdl(kern, ctas, kThreads, TAB != kTabGlobal ? smem : 0, s, 0, ln, mode, cand_out, ncand_out);
 }
 
 template <int TAB>
@@ -1232,29 +1232,15 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
                            (max_B <= kTwSmemMaxB ? max_B / 2 * sizeof(float2) : 0) + (cluster_L ? max_B : 0));
     cudaError_t e = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    if (!cluster_L) {
-        k_fft_select<<<total_ctas, kThreads, smem, s>>>(ln, select_only, 0, reinterpret_cast<const float2 *>(dftC),
-                                                        dft_mpad, dft_err);
-        return cudaGetLastError();
-    }
+    if (!cluster_L)
+        return launch_pdl(k_fft_select, total_ctas, kThreads, smem, s, 0, ln, select_only, 0,
+                          reinterpret_cast<const float2 *>(dftC), dft_mpad, dft_err);
     if (cluster_L > 8) {
         e = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(total_ctas);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = (size_t)smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cluster_L;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_fft_select, ln, select_only, 1, reinterpret_cast<const float2 *>(dftC),
-                              dft_mpad, dft_err);
+    return launch_pdl(k_fft_select, total_ctas, kThreads, (size_t)smem, s, cluster_L, ln, select_only, 1,
+                      reinterpret_cast<const float2 *>(dftC), dft_mpad, dft_err);
 }
 
 bool fft_select_cluster_ok(uint32_t L, uint32_t max_B) {
@@ -1297,18 +1283,19 @@ cudaError_t launch_vote(const Launch &ln, uint32_t total_ctas, int mode, uint32_
     if (mode == kVotePrune && scan_uses_bits(L_uniform, bits)) {
         // words per lane and loop of the largest B (every job's B in the group is the same class)
         const uint32_t E = table_words(31 - __builtin_clz(max_B));
+        cudaError_t e = cudaSuccess;
         switch (L_uniform * 8 + E) {
-            case 8 * 8 + 1: k_scan_bits<8, 1><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            case 8 * 8 + 2: k_scan_bits<8, 2><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            case 8 * 8 + 4: k_scan_bits<8, 4><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            case 12 * 8 + 1: k_scan_bits<12, 1><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            case 12 * 8 + 2: k_scan_bits<12, 2><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            case 12 * 8 + 4: k_scan_bits<12, 4><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            case 16 * 8 + 1: k_scan_bits<16, 1><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            case 16 * 8 + 2: k_scan_bits<16, 2><<<total_ctas, kThreads, 0, s>>>(ln); break;
-            default: k_scan_bits<16, 4><<<total_ctas, kThreads, 0, s>>>(ln); break;
+            case 8 * 8 + 1: e = launch_pdl(k_scan_bits<8, 1>, total_ctas, kThreads, 0, s, 0, ln); break;
+            case 8 * 8 + 2: e = launch_pdl(k_scan_bits<8, 2>, total_ctas, kThreads, 0, s, 0, ln); break;
+            case 8 * 8 + 4: e = launch_pdl(k_scan_bits<8, 4>, total_ctas, kThreads, 0, s, 0, ln); break;
+            case 12 * 8 + 1: e = launch_pdl(k_scan_bits<12, 1>, total_ctas, kThreads, 0, s, 0, ln); break;
+            case 12 * 8 + 2: e = launch_pdl(k_scan_bits<12, 2>, total_ctas, kThreads, 0, s, 0, ln); break;
+            case 12 * 8 + 4: e = launch_pdl(k_scan_bits<12, 4>, total_ctas, kThreads, 0, s, 0, ln); break;
+            case 16 * 8 + 1: e = launch_pdl(k_scan_bits<16, 1>, total_ctas, kThreads, 0, s, 0, ln); break;
+            case 16 * 8 + 2: e = launch_pdl(k_scan_bits<16, 2>, total_ctas, kThreads, 0, s, 0, ln); break;
+            default: e = launch_pdl(k_scan_bits<16, 4>, total_ctas, kThreads, 0, s, 0, ln); break;
         }
-        return cudaGetLastError();
+        return e;
     }
     if (max_flags_bytes <= (uint32_t)kFlagsSmemBytes)
         return scan_dispatch_l<kTabSmem>(ln, total_ctas, mode, L_uniform, max_flags_bytes, cand_out, ncand_out, s);
@@ -1331,8 +1318,7 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t total_ctas, uint32_t L_un
         const uint32_t smem = max(tab_smem, topk_smem);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<ctas, kThreads, smem, s>>>(ln, cap);
-        return cudaGetLastError();
+        return launch_pdl(kern, ctas, kThreads, smem, s, 0, ln, cap);
     }
     auto kern = L_uniform == 8    ? k_estimate_surv<8>
                 : L_uniform == 12 ? k_estimate_surv<12>
@@ -1340,8 +1326,7 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t total_ctas, uint32_t L_un
                                   : k_estimate_surv<0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)topk_smem);
     if (e != cudaSuccess) return e;
-    kern<<<ctas, kThreads, topk_smem, s>>>(ln, cap);
-    return cudaGetLastError();
+    return launch_pdl(kern, ctas, kThreads, topk_smem, s, 0, ln, cap);
 }
 
 
@@ -1357,8 +1342,7 @@ cudaError_t launch_fallback(const Launch &ln, uint32_t total_ctas, uint32_t L_un
                                   : k_fallback<0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<total_ctas, kThreads, smem, s>>>(ln, cap);
-    return cudaGetLastError();
+    return launch_pdl(kern, total_ctas, kThreads, smem, s, 0, ln, cap);
 }
 
 cudaError_t launch_estimate_list(const PlanDev *p, uint32_t L, const float2 *zhat, const int32_t *cand,

@@ -781,8 +781,7 @@ cudaError_t launch_refine(const Launch &ln, uint32_t njobs, uint32_t max_K, uint
                                                                                                     : k_refine<0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<njobs, kRefineThreads, smem, s>>>(ln);
-    return cudaGetLastError();
+    return launch_pdl(kern, njobs, kRefineThreads, smem, s, 0, ln);
 }
 
 cudaError_t launch_bs(const Launch &ln, uint32_t njobs, uint32_t max_B, uint32_t max_K, uint32_t max_cap,

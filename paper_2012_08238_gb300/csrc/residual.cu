@@ -100,8 +100,7 @@ cudaError_t launch_residual(const Launch &ln, uint32_t total_ctas, uint32_t max_
     const int smem = (int)(sizeof(double2) * max_B);
     cudaError_t e = cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_residual<<<total_ctas, kThreads, smem, s>>>(ln);
-    return cudaGetLastError();
+    return launch_pdl(k_residual, total_ctas, kThreads, smem, s, 0, ln);
 }
 
 }  // namespace sfft
