@@ -42,7 +42,7 @@ LAUNCHES_PER_STEP = 5
 # dram__bytes_write.sum of one ncu capture of the 64-signal launch, divided by
 # 64); the capture's summary is under profiles/.  None when the kernel changed
 # after the capture.
-NCU_GATHER_TRAFFIC_PER_SPECTRUM = (537_337_856 + 22_532_352) / 64
+NCU_GATHER_TRAFFIC_PER_SPECTRUM = (531_569_408 + 22_112_512) / 64
 UNIT = "spectra/s"
 
 # plan options of the variants a --profile run may take (the headline is
