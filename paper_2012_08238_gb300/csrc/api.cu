@@ -1174,6 +1174,29 @@ uint32_t variant_key(const Sizes &s) {
     return ((s.stream ? 1u : 0u) << 24) | (dft << 16) | (L << 8) | (scan << 4) | (est << 2) | cl;
 }
 
+// Expected estimate work of a job, for sharing the estimate's CTAs: N times
+// the fraction of frequencies the pruned pass estimates.  A frequency
+// survives the median bound with >= M strong loops, and a loop's bucket is
+// strong about as often as it holds one of the K coefficients, so the
+// fraction is about P[Bin(L, min(1, K/B)) >= M] (measured on the batched
+// workload: 0.52 of N at N = 2^14, K/B ~ 1/2, against 0.015 at K/B ~ 1/5);
+// the mean estimator estimates every candidate (kept in >= T loops,
+// p = nsel/B); comb plans only the kept classes' share.  A floor of 0.5%
+// stands for buckets made strong by noise.
+double estimate_weight(const PlanDev &P) {
+    const bool mean = P.estimator == kEstMean;
+    const double p = std::min(1.0, (double)(mean ? P.nsel : P.K) / (double)P.B);
+    const uint32_t need = mean ? P.T : P.M;
+    double tail = 0.0, c = 1.0;  // c = C(L, k)
+    for (uint32_t k = 0; k <= P.L; ++k) {
+        if (k >= need) tail += c * std::pow(p, (double)k) * std::pow(1.0 - p, (double)(P.L - k));
+        c = c * (double)(P.L - k) / (double)(k + 1);
+    }
+    double f = std::max(tail, 0.005);
+    if (P.method == kMethodComb && P.Bc) f *= (double)P.ncls / (double)P.Bc;
+    return (double)P.N * f;
+}
+
 BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t *const *idx,
                         float *const *val, int32_t *kout, int32_t count) {
     BatchLayout b;
@@ -1227,13 +1250,14 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
     // its CTAs within kScanWaves waves of resident CTAs (fewer CTAs amortise
     // the per-CTA set-up; a partial last wave costs a whole CTA lifetime);
     // the estimate takes one wave of resident CTAs, shared among the jobs in
-    // proportion to N (their survivors grow with N), 1..kEstimateCtas each
+    // proportion to their expected survivors (estimate_weight),
+    // 1..kEstimateCtas each
     size_t r0 = 0;
     for (Group &g : b.groups) {
         Sizes &gz = g.z;
         if (gz.L_uniform != 8 && gz.L_uniform != 12 && gz.L_uniform != 16) gz.est_smem = 0;
-        double sumN = 0.0;
-        for (size_t r = r0; r < r0 + gz.jobs; ++r) sumN += (double)plans[order[r]]->N;
+        double sumW = 0.0;
+        for (size_t r = r0; r < r0 + gz.jobs; ++r) sumW += estimate_weight(plans[order[r]]->h);
         const double wave = (double)kNumSms * (gz.est_smem ? kEstTabCtasPerSm : kEstSurvCtasPerSm);
         uint64_t vt = 0;
         for (size_t r = r0; r < r0 + gz.jobs; ++r) vt += cnt[r * 6 + 2];
@@ -1244,7 +1268,7 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         gz.vote = 0;
         for (size_t r = r0; r < r0 + gz.jobs; ++r) {
             // (rounded down: the group's CTAs stay within one wave)
-            const double share = std::floor(wave * (double)plans[order[r]]->N / sumN);
+            const double share = std::floor(wave * estimate_weight(plans[order[r]]->h) / sumW);
             const uint32_t ec = (uint32_t)std::max(1.0, std::min((double)kEstimateCtas, share));
             cnt[r * 6 + 5] = ec;
             jobs[r].ectas = ec;

@@ -30,7 +30,7 @@ constexpr uint32_t kEstMedian = 0;      // a6: coordinate-wise median of the per
 constexpr uint32_t kEstMean = 1;        // a6: their mean (every candidate estimated)
 constexpr uint32_t kRefineMaxK = 4096;  // refinement: the found set lives in shared memory
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
-constexpr int kEstimateCtas = 32;       // most CTAs per job of the survivor-estimate kernels
+constexpr int kEstimateCtas = 64;       // most CTAs per job of the survivor-estimate kernels
 constexpr int kEstTabCtasPerSm = 3;     // resident staged-table estimate CTAs per SM (72 KB each)
 constexpr int kEstSurvCtasPerSm = 8;    // resident estimate CTAs per SM with the tables in L2
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
