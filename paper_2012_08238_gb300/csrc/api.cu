@@ -489,7 +489,7 @@ struct Group {
 // of comb plans), scan, estimate + top-K, refinement (empty unless a plan
 // refines), residual check (empty unless a plan checks).
 cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vector<Group> &gs, void *dft_scratch,
-                            cudaStream_t s, cudaEvent_t *ev = nullptr) {
+                            cudaStream_t s, cudaEvent_t *ev = nullptr, uint32_t *gctr = nullptr) {
     cudaError_t e;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     auto at = [&](int k, const Group &g) {
@@ -552,8 +552,12 @@ cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vecto
                              nullptr, nullptr, s)) != cudaSuccess)
             return e;
     if ((e = mark(3)) != cudaSuccess) return e;
-    for (const Group &g : gs) {
-        if ((e = launch_estimate(at(5, g), g.ctas[5], g.z.L_uniform, g.z.est_smem, g.z.max_K, s)) != cudaSuccess)
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+        const Group &g = gs[gi];
+        // (batch groups of up to kDynMaxJobs jobs share their survivors' chunks dynamically)
+        Launch le = at(5, g);
+        le.gctr = gctr && g.z.jobs <= kDynMaxJobs ? gctr + 2 * gi : nullptr;
+        if ((e = launch_estimate(le, g.ctas[5], g.z.L_uniform, g.z.est_smem, g.z.max_K, s)) != cudaSuccess)
             return e;
         // jobs whose pruned records could not certify their top K
         if ((e = launch_fallback(at(4, g), g.ctas[4], g.z.L_uniform, g.z.max_K, s)) != cudaSuccess) return e;
@@ -603,6 +607,7 @@ Launch single(const Job &j) {
     ln.map = nullptr;
     ln.njobs = 1;
     ln.cta0 = 0;
+    ln.gctr = nullptr;
     ln.one = j;
     return ln;
 }
@@ -1122,8 +1127,9 @@ extern "C" sfft_status sfft_execute_host(sfft_plan *p, const float *x_host, int3
 namespace {
 
 struct BatchLayout {
-    std::vector<unsigned char> bytes;  // jobs, then per kernel a CTA prefix and a CTA -> job map
-    size_t off_offs[6], off_map[6];
+    std::vector<unsigned char> bytes;  // jobs, then per kernel a CTA prefix and a CTA -> job map,
+                                       // then two zero words per group (the estimate's chunk counters)
+    size_t off_offs[6], off_map[6], off_gctr = 0;
     Sizes z;                  // the whole batch
     std::vector<Group> groups;  // runs of jobs with common kernel variants
     size_t dft_bytes = 0;     // tensor-core DFT scratch after the bytes (largest group; groups run in turn)
@@ -1290,6 +1296,8 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         b.off_map[k] = off;
         off += align256(sizeof(uint32_t) * tot[k]);
     }
+    b.off_gctr = off;
+    off += align256(2 * sizeof(uint32_t) * std::max<size_t>(1, b.groups.size()));
     b.bytes.assign(off, 0);
     memcpy(b.bytes.data(), jobs.data(), sizeof(Job) * count);
     for (int k = 0; k < 6; ++k) {
@@ -1334,11 +1342,13 @@ cudaError_t launch_batch(const BatchLayout &b, const void *dev, int32_t count, c
         ln[k].map = reinterpret_cast<const uint32_t *>(base + b.off_map[k]);
         ln[k].njobs = count;
         ln[k].cta0 = 0;
+        ln[k].gctr = nullptr;
         memset(&ln[k].one, 0, sizeof(Job));
     }
     if (b.z.phase) return launch_phase(ln[1], b.z, s, ev);
     void *dft = b.dft_bytes ? static_cast<void *>(const_cast<char *>(base) + align256(b.bytes.size())) : nullptr;
-    return launch_pipeline(ln, b.z, b.groups, dft, s, ev);
+    uint32_t *gctr = reinterpret_cast<uint32_t *>(const_cast<char *>(base) + b.off_gctr);
+    return launch_pipeline(ln, b.z, b.groups, dft, s, ev, gctr);
 }
 
 sfft_status check_batch_args(sfft_plan *const *plans, const void *const *x, const void *const *idx,

@@ -526,9 +526,10 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
     return v;
 }
 
-// Tables: the plan's in global memory (SM false), or copies in shared memory
-// (zt: zhat [L][B], gt: 1/G~ [N/B], kt: kept bits [L][B/32]).
-template <int LT, bool SM>
+// Tables: the plan's in global memory (SM 0), the gains' copy in shared
+// memory (SM 1: gt, 1/G~ [N/B]) or copies of all three (SM 2: zt, zhat
+// [L][B]; gt; kt, kept bits [L][B/32]).
+template <int LT, int SM>
 __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, float theta, float a,
                                                 uint32_t *cnt, const float2 *zt, const float2 *gt,
                                                 const uint32_t *kt) {
@@ -536,38 +537,62 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
     const uint32_t cv = P.half << sN;
     const uint32_t osh = P.logB + sN;  // offset in the bucket: the word's bits below the bucket bits
     const uint32_t B = P.B;
-    float2 z[LT], g[LT];
-    uint32_t ph[LT];
-#pragma unroll
-    for (int l = 0; l < LT; ++l) {
+    // loop l's bucket value and gain (one hash word feeds both loads) and its turn
+    auto fetch = [&](int l, float2 &z, float2 &g, uint32_t &ph) {
         const uint32_t t = (P.sigma[l] << sN) * f + cv;
         const uint32_t h = t >> top;
         const uint32_t opos = osh < 32 ? (t << P.logB) >> osh : 0u;
-        if constexpr (SM) {
+        if constexpr (SM == 2) {
             const uint32_t zb = (uint32_t)__cvta_generic_to_shared(zt);
             const uint32_t gb = (uint32_t)__cvta_generic_to_shared(gt);
-            z[l] = lds_f2(zb + 8 * (l * B + h));
-            g[l] = lds_f2(gb + 8 * opos);
+            z = lds_f2(zb + 8 * (l * B + h));
+            g = lds_f2(gb + 8 * opos);
+        } else if constexpr (SM == 1) {
+            z = __ldg(P.zhat + l * B + h);
+            g = lds_f2((uint32_t)__cvta_generic_to_shared(gt) + 8 * opos);
         } else {
-            z[l] = __ldg(P.zhat + l * B + h);
-            g[l] = __ldg(P.ginv + opos);
+            z = __ldg(P.zhat + l * B + h);
+            g = __ldg(P.ginv + opos);
         }
-        ph[l] = (P.tau[l] << sN) * f;
-    }
+        ph = (P.tau[l] << sN) * f;
+    };
+    // pass 1, in batches of GB loops (a batch's loads issued together): the
+    // reject's counts and, for the mean, the sums in loop order.  Tables in
+    // shared memory: one batch of all L (their CTAs are limited by shared
+    // memory, not registers); tables in L2: batches of four, so that four
+    // CTAs per SM fit 64 registers and hide the L2 latency
+    constexpr int GB = SM == 2 ? LT : (LT % 4 == 0 ? 4 : 1);
+    // (shared-memory tables also keep the L values for the medians; tables in
+    // L2 fetch them again in pass 2, for the few that pass)
+    constexpr bool KEEP = SM == 2;
     bool keep = true;
     const bool mean = P.estimator == kEstMean;
+    float sr = 0.f, si = 0.f;
     float re[LT], im[LT];
     {
         uint32_t rp = 0, rn = 0, ip = 0, in = 0;
 #pragma unroll
-        for (int l = 0; l < LT; ++l) {
-            const float2 v = turn_scale(z[l], g[l], ph[l]);
-            re[l] = v.x;
-            im[l] = v.y;
-            rp += v.x >= a;
-            rn += v.x <= -a;
-            ip += v.y >= a;
-            in += v.y <= -a;
+        for (int l0 = 0; l0 < LT; l0 += GB) {
+            float2 z[GB], g[GB];
+            uint32_t ph[GB];
+#pragma unroll
+            for (int k = 0; k < GB; ++k) fetch(l0 + k, z[k], g[k], ph[k]);
+#pragma unroll
+            for (int k = 0; k < GB; ++k) {
+                const float2 v = turn_scale(z[k], g[k], ph[k]);
+                if constexpr (KEEP) {
+                    re[l0 + k] = v.x;
+                    im[l0 + k] = v.y;
+                }
+                rp += v.x >= a;
+                rn += v.x <= -a;
+                ip += v.y >= a;
+                in += v.y <= -a;
+                if (mean) {
+                    sr += v.x;
+                    si += v.y;
+                }
+            }
         }
         constexpr uint32_t M = (LT + 1) / 2;
         keep = mean || rp >= M || rn >= M || ip >= M || in >= M;
@@ -579,7 +604,7 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
 #pragma unroll
         for (int l = 0; l < LT; ++l) {
             const uint32_t h = ((P.sigma[l] << sN) * f + cv) >> top;
-            if constexpr (SM)
+            if constexpr (SM == 2)
                 kept += (lds_u32((uint32_t)__cvta_generic_to_shared(kt) + 4 * ((l * B + h) >> 5)) >> (h & 31u)) & 1u;
             else
                 kept += __ldg(P.flags + l * B + h) & 1u;
@@ -590,14 +615,20 @@ __device__ __forceinline__ void estimate_pruned(const PlanDev &P, uint32_t f, fl
     float key = 0.f;
     if (keep) {
         if (mean) {
-            float sr = 0.f, si = 0.f;
-#pragma unroll
-            for (int l = 0; l < LT; ++l) {
-                sr += re[l];
-                si += im[l];
-            }
             v = make_float2(sr / (float)LT, si / (float)LT);
         } else {
+            if constexpr (!KEEP) {
+                // pass 2 (the few that passed): the L values again, for the medians
+#pragma unroll
+                for (int l = 0; l < LT; ++l) {
+                    float2 z, g;
+                    uint32_t ph;
+                    fetch(l, z, g, ph);
+                    const float2 w = turn_scale(z, g, ph);
+                    re[l] = w.x;
+                    im[l] = w.y;
+                }
+            }
             sort_net<LT>(re);
             sort_net<LT>(im);
             v = make_float2(median_sorted(re, LT), median_sorted(im, LT));
@@ -1018,22 +1049,162 @@ __device__ bool last_of_job(const PlanDev &P, uint32_t ctas_per_job) {
 // estimate from 31.0 to 21.5 us and left 64 and 128 unchanged; 256 was no
 // faster.)
 constexpr uint32_t kEstChunk = 512;
+// Shared memory of the survivor-estimate kernel with its tables in L2: at
+// least this much, where the gains (N/B complex) are staged when they fit.
+constexpr uint32_t kSurvGainSmem = 16384;
 __device__ __forceinline__ uint32_t est_active(uint32_t n, uint32_t ctas_per_job) {
     const uint32_t a = (n + kEstChunk - 1) / kEstChunk;
     return a < 1 ? 1u : (a > ctas_per_job ? ctas_per_job : a);
 }
 
+// Stages the job's gains (N/B complex) in shared memory (all threads).
+__device__ __forceinline__ void stage_gains(const PlanDev &P, float2 *gsm) {
+    const uint32_t NB = P.N >> P.logB;
+    const uint32_t gb = (uint32_t)__cvta_generic_to_shared(gsm);
+    for (uint32_t k = threadIdx.x; k < NB / 2; k += kThreads) cp_async16(gb + 16 * k, P.ginv + 2 * k);
+    if ((NB & 1u) && threadIdx.x == 0) gsm[NB - 1] = __ldg(P.ginv + NB - 1);
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+// Survivor estimates of a batch group with the survivors of all its jobs
+// shared out dynamically: every CTA reads the jobs' survivor counts (the
+// scan's), cuts each job's list into chunks of C survivors (C sized so the
+// group has about two chunks per CTA, 256..2048) and takes chunks in job
+// order from the group's counter gctr[0], loading a job's descriptor (and
+// staging its gains) when its chunk is another job's; the CTA that finishes
+// a job's last chunk (per-job ticket after a fence) takes that job's top K.
+// The group's last CTA to finish resets the counters for the next launch.
+// Balances jobs whose survivors differ by orders of magnitude (low SNR,
+// dense windows), which fixed per-job shares cannot.
+template <int LT>
+__device__ void estimate_dynamic(const Launch &ln, PlanDev &P, Job &J, uint32_t cap, uint32_t gain_max,
+                                 unsigned long long *smem) {
+    __shared__ uint32_t s_pre[kDynMaxJobs + 1];  // chunk prefix over the group's jobs
+    __shared__ uint32_t s_wsum[kThreads / 32], s_tot, s_c;
+    __shared__ int s_last;
+    const uint32_t j0 = __ldg(ln.map + ln.cta0), j1 = __ldg(ln.map + ln.cta0 + gridDim.x - 1) + 1;
+    const uint32_t nj = j1 - j0;
+    // each thread's jobs: survivor counts (three dependent loads per job, a thread's jobs in flight together)
+    constexpr uint32_t kPer = kDynMaxJobs / kThreads;
+    uint32_t cnt[kPer];
+    uint32_t mysum = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; ++q) {
+        const uint32_t k = threadIdx.x * kPer + q;
+        cnt[q] = 0;
+        if (k < nj) {
+            const PlanDev *pd = ln.jobs[j0 + k].p;
+            const uint32_t *ctr = *reinterpret_cast<uint32_t *const *>(reinterpret_cast<const char *>(pd) +
+                                                                       offsetof(PlanDev, ctr));
+            cnt[q] = __ldcg(ctr + kNSurv);
+        }
+        mysum += cnt[q];
+    }
+    const uint32_t allsurv = block_incl_scan(mysum, s_wsum);
+    if (threadIdx.x == kThreads - 1) s_tot = allsurv;
+    __syncthreads();
+    uint32_t C = s_tot / (2 * gridDim.x);
+    C = C < 256 ? 256u : (C > 2048 ? 2048u : C);
+    uint32_t mych = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; ++q)
+        if (threadIdx.x * kPer + q < nj) mych += cnt[q] > 0 ? (cnt[q] + C - 1) / C : 1u;
+    const uint32_t incl = block_incl_scan(mych, s_wsum);
+    uint32_t run = incl - mych;
+    if (threadIdx.x == 0) s_pre[0] = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; ++q) {
+        const uint32_t k = threadIdx.x * kPer + q;
+        if (k < nj) {
+            run += cnt[q] > 0 ? (cnt[q] + C - 1) / C : 1u;
+            s_pre[k + 1] = run;
+        }
+    }
+    if (threadIdx.x == kThreads - 1) s_tot = incl;
+    uint32_t nxt = 0;  // thread 0: the next chunk's ticket
+    if (threadIdx.x == 0) nxt = atomicAdd(ln.gctr, 1u);
+    __syncthreads();
+    const uint32_t total = s_tot;
+    float2 *gsm = reinterpret_cast<float2 *>(smem);
+    uint32_t cur = 0xFFFFFFFFu;
+    bool staged = false;
+    for (;;) {
+        if (threadIdx.x == 0) s_c = nxt;
+        __syncthreads();
+        const uint32_t c = s_c;
+        if (c >= total) break;
+        if (threadIdx.x == 0) nxt = atomicAdd(ln.gctr, 1u);  // (in flight while this chunk is estimated)
+        // the chunk's job: s_pre[jr] <= c < s_pre[jr + 1]
+        uint32_t lo = 0, hi = nj;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_pre[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t jr = lo, nch = s_pre[jr + 1] - s_pre[jr], cj = c - s_pre[jr];
+        if (jr != cur) {
+            __syncthreads();  // (everyone is done with the previous descriptor)
+            if (threadIdx.x == 0) J = ln.jobs[j0 + jr];
+            __syncthreads();
+            load_plan(P, J.p);
+            __syncthreads();
+            staged = (P.N >> P.logB) <= gain_max;
+            if (staged) stage_gains(P, gsm);
+            cur = jr;
+        }
+        const uint32_t n = __ldcg(P.ctr + kNSurv);
+        const float theta = __uint_as_float(__ldcg(P.ctr + kTheta));
+        const float a = sqrtf(0.5f * theta) * (1.0f - 1.0f / 1024.0f);
+        const uint32_t e1 = min(n, (cj + 1) * C);
+        for (uint32_t i = cj * C + threadIdx.x; i < e1; i += kThreads) {
+            const uint32_t f = __ldg(P.survf + i);
+            if (staged)
+                estimate_pruned<LT, 1>(P, f, theta, a, P.ctr + kNGe, nullptr, gsm, nullptr);
+            else
+                estimate_pruned<LT, 0>(P, f, theta, a, P.ctr + kNGe, nullptr, nullptr, nullptr);
+        }
+        // the job's chunk ticket; the last chunk's CTA takes the top K
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(P.ctr + kEstDone, 1u) == nch - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            topk_job(P, J, smem, cap);  // (overwrites the staged gains)
+            __syncthreads();
+            if (threadIdx.x == 0) P.ctr[kEstDone] = 0;
+            cur = 0xFFFFFFFFu;
+        }
+    }
+    if (threadIdx.x == 0 && atomicAdd(ln.gctr + 1, 1u) == gridDim.x - 1) {
+        // every CTA has taken its last ticket: re-arm the group for the next launch
+        ln.gctr[0] = 0;
+        ln.gctr[1] = 0;
+        __threadfence();
+    }
+}
+
 // Pruned-pass median estimates of the job's survivors, ctas_per_job CTAs per
 // job: candidates whose key reaches theta are recorded as {f, key bits, re
 // bits, im bits}.  The job's last CTA to finish (atomic ticket after a fence)
-// then takes the job's top K (a7).
+// then takes the job's top K (a7).  Batch groups with ln.gctr share their
+// survivors out dynamically instead (estimate_dynamic).
 template <int LT>
-__global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t cap) {
-    extern __shared__ unsigned long long est_topk[];  // top-K buffer of the job's last CTA
+__global__ void __launch_bounds__(kThreads, 4) k_estimate_surv(Launch ln, uint32_t cap, uint32_t gain_max) {
+    // the job's 1/G~ when N/B <= gain_max (survivor CTAs), then the top-K
+    // buffer of the job's last CTA
+    extern __shared__ unsigned long long est_topk[];
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
     enter(ln, P, J, s_local);
+    if constexpr (LT > 0) {
+        if (ln.gctr) {
+            estimate_dynamic<LT>(ln, P, J, cap, gain_max, est_topk);
+            return;
+        }
+    }
     const uint32_t ctas_per_job = J.ectas;
     const uint32_t n = P.ctr[kNSurv];
     const float theta = __uint_as_float(P.ctr[kTheta]);
@@ -1044,13 +1215,21 @@ __global__ void __launch_bounds__(kThreads) k_estimate_surv(Launch ln, uint32_t 
     const uint32_t i0 = s_local < active ? s_local * kThreads + threadIdx.x : n;
     if constexpr (LT > 0) {
         const float a = sqrtf(0.5f * theta) * (1.0f - 1.0f / 1024.0f);
+        // gains staged in shared memory when they fit (uniform over the CTA)
+        const uint32_t NB = P.N >> P.logB;
+        float2 *gsm = reinterpret_cast<float2 *>(est_topk);
+        const bool staged = NB <= gain_max && s_local < active;
+        if (staged) stage_gains(P, gsm);
         // the next survivor's frequency is fetched while this one is estimated
         uint32_t i = i0;
         uint32_t fn = i < n ? __ldg(P.survf + i) : 0u;
         for (; i < n; i += stride) {
             const uint32_t f = fn;
             if (i + stride < n) fn = __ldg(P.survf + i + stride);
-            estimate_pruned<LT, false>(P, f, theta, a, cnt, nullptr, nullptr, nullptr);
+            if (staged)
+                estimate_pruned<LT, 1>(P, f, theta, a, cnt, nullptr, gsm, nullptr);
+            else
+                estimate_pruned<LT, 0>(P, f, theta, a, cnt, nullptr, nullptr, nullptr);
         }
     } else {
         for (uint32_t i = i0; i < n; i += stride) estimate_record<LT>(P, P.survf[i], true, theta, cnt);
@@ -1104,7 +1283,7 @@ __device__ void estimate_tab_part(const PlanDev &P, uint32_t s_local, uint32_t a
     for (; i < n; i += stride) {
         const uint32_t f = fn;
         if (i + stride < n) fn = __ldg(P.survf + i + stride);
-        estimate_pruned<LT, true>(P, f, theta, a, P.ctr + kNGe, zs, gs, ks);
+        estimate_pruned<LT, 2>(P, f, theta, a, P.ctr + kNGe, zs, gs, ks);
     }
 }
 
@@ -1327,9 +1506,14 @@ cudaError_t launch_estimate(const Launch &ln, uint32_t total_ctas, uint32_t L_un
                 : L_uniform == 12 ? k_estimate_surv<12>
                 : L_uniform == 16 ? k_estimate_surv<16>
                                   : k_estimate_surv<0>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)topk_smem);
+    // at least kSurvGainSmem, so the gains of N/B <= 2048 are staged (eight
+    // CTAs per SM stay resident)
+    const uint32_t smem = max(topk_smem, kSurvGainSmem);
+    uint32_t gain_max = 1;
+    while (2 * gain_max * (uint32_t)sizeof(float2) <= smem) gain_max <<= 1;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(kern, ctas, kThreads, topk_smem, s, 0, ln, cap);
+    return launch_pdl(kern, ctas, kThreads, smem, s, 0, ln, cap, gain_max);
 }
 
 

@@ -31,8 +31,9 @@ constexpr uint32_t kEstMean = 1;        // a6: their mean (every candidate estim
 constexpr uint32_t kRefineMaxK = 4096;  // refinement: the found set lives in shared memory
 constexpr int kVoteTileF = 4096;        // frequencies per vote tile (= survivor queue capacity)
 constexpr int kEstimateCtas = 64;       // most CTAs per job of the survivor-estimate kernels
+constexpr uint32_t kDynMaxJobs = 2048;  // groups of at most this many jobs share survivor chunks dynamically
 constexpr int kEstTabCtasPerSm = 3;     // resident staged-table estimate CTAs per SM (72 KB each)
-constexpr int kEstSurvCtasPerSm = 8;    // resident estimate CTAs per SM with the tables in L2
+constexpr int kEstSurvCtasPerSm = 4;    // resident estimate CTAs per SM with the tables in L2 (64 registers)
 constexpr uint32_t kEstTabMaxBytes = 72 * 1024;  // staged estimate tables: up to 3 CTAs per SM
 constexpr uint32_t kResidualMaxB = 8192;  // residual check: a loop's B residuals (FP64) in shared memory
 constexpr uint32_t kDftMaxB = 4096;       // split-BF16 tensor-core DFT: B in [64, 4096]
@@ -145,6 +146,8 @@ struct Launch {
     const uint32_t *map;    // [total CTAs] job of each CTA (batch only)
     int njobs;
     uint32_t cta0;          // batch: CTA of the map that this launch's block 0 is (a group's first)
+    uint32_t *gctr;         // batch estimate of a group: {next chunk, finished CTAs}, zero between
+                            // launches (dynamic survivor chunks; nullptr: static shares)
     Job one;
 };
 
