@@ -556,11 +556,13 @@ cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vecto
         const Group &g = gs[gi];
         // (batch groups of up to kDynMaxJobs jobs share their survivors' chunks dynamically)
         Launch le = at(5, g);
-        le.gctr = gctr && g.z.jobs <= kDynMaxJobs ? gctr + 2 * gi : nullptr;
+        le.gctr = gctr && g.z.jobs <= kDynMaxJobs ? gctr + 8 * gi : nullptr;
         if ((e = launch_estimate(le, g.ctas[5], g.z.L_uniform, g.z.est_smem, g.z.max_K, s)) != cudaSuccess)
             return e;
         // jobs whose pruned records could not certify their top K
-        if ((e = launch_fallback(at(4, g), g.ctas[4], g.z.L_uniform, g.z.max_K, s)) != cudaSuccess) return e;
+        Launch lf = at(4, g);
+        lf.gctr = le.gctr;  // (words 2, 3: the fallback's chunk counters; 4: jobs flagged for it)
+        if ((e = launch_fallback(lf, g.ctas[4], g.z.L_uniform, g.z.max_K, s)) != cudaSuccess) return e;
     }
     if ((e = mark(4)) != cudaSuccess) return e;
     // refining jobs: the iterative framework's subtraction over the found set
@@ -1128,7 +1130,7 @@ namespace {
 
 struct BatchLayout {
     std::vector<unsigned char> bytes;  // jobs, then per kernel a CTA prefix and a CTA -> job map,
-                                       // then two zero words per group (the estimate's chunk counters)
+                                       // then eight zero words per group (Launch::gctr)
     size_t off_offs[6], off_map[6], off_gctr = 0;
     Sizes z;                  // the whole batch
     std::vector<Group> groups;  // runs of jobs with common kernel variants
@@ -1297,7 +1299,7 @@ BatchLayout build_batch(sfft_plan *const *plans, const float *const *x, int32_t 
         off += align256(sizeof(uint32_t) * tot[k]);
     }
     b.off_gctr = off;
-    off += align256(2 * sizeof(uint32_t) * std::max<size_t>(1, b.groups.size()));
+    off += align256(8 * sizeof(uint32_t) * std::max<size_t>(1, b.groups.size()));
     b.bytes.assign(off, 0);
     memcpy(b.bytes.data(), jobs.data(), sizeof(Job) * count);
     for (int k = 0; k < 6; ++k) {

@@ -1017,11 +1017,15 @@ __device__ void rank_records(const PlanDev &P, const Job &J, unsigned long long 
 
 // The estimate's last CTA of a job: the top K of the pruned records, or, when
 // they cannot certify it, the flag that hands the job to the fallback pass.
-__device__ void topk_job(const PlanDev &P, const Job &J, unsigned long long *tk, uint32_t cap) {
+// gctr (batch groups): a flagged job also counts itself in gctr[4], which the
+// group's fallback CTAs read first.
+__device__ void topk_job(const PlanDev &P, const Job &J, unsigned long long *tk, uint32_t cap,
+                         uint32_t *gctr = nullptr) {
     __shared__ int s_fb;
     if (threadIdx.x == 0) {
         s_fb = needs_fallback(P);
         P.ctr[kFbPend] = s_fb ? 1u : 0u;
+        if (s_fb && gctr) atomicAdd(gctr + 4, 1u);
     }
     __syncthreads();
     if (!s_fb) rank_records(P, J, tk, cap, __ldcg(P.ctr + kNGe), P.K);  // >= K candidates exist
@@ -1171,7 +1175,7 @@ __device__ void estimate_dynamic(const Launch &ln, PlanDev &P, Job &J, uint32_t 
         __syncthreads();
         if (s_last) {
             __threadfence();
-            topk_job(P, J, smem, cap);  // (overwrites the staged gains)
+            topk_job(P, J, smem, cap, ln.gctr);  // (overwrites the staged gains)
             __syncthreads();
             if (threadIdx.x == 0) P.ctr[kEstDone] = 0;
             cur = 0xFFFFFFFFu;
@@ -1234,7 +1238,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_estimate_surv(Launch ln, uint32
     } else {
         for (uint32_t i = i0; i < n; i += stride) estimate_record<LT>(P, P.survf[i], true, theta, cnt);
     }
-    if (last_of_job(P, ctas_per_job)) topk_job(P, J, est_topk, cap);
+    if (last_of_job(P, ctas_per_job)) topk_job(P, J, est_topk, cap, ln.gctr);
 }
 
 template <int LT>
@@ -1303,14 +1307,116 @@ __global__ void __launch_bounds__(kThreads) k_estimate_tab(Launch ln, uint32_t c
     // only the CTAs with a share of at least kEstChunk survivors stage the tables
     const uint32_t active = est_active(n, ctas_per_job);
     if (s_local < active) estimate_tab_part<LT>(P, s_local, active, n, est_tab);
-    if (last_of_job(P, ctas_per_job)) topk_job(P, J, reinterpret_cast<unsigned long long *>(est_tab), cap);
+    if (last_of_job(P, ctas_per_job))
+        topk_job(P, J, reinterpret_cast<unsigned long long *>(est_tab), cap, ln.gctr);
 }
 
+
+// Frequencies per chunk of the dynamic fallback pass.
+constexpr uint32_t kFbChunk = 16384;
+
+// The fallback pass of a batch group with the pending jobs' frequencies
+// shared out dynamically over every CTA of the group (most jobs have no
+// pending fallback; one that has, at low SNR, may hold most of its N as
+// candidates): each CTA reads the jobs' flags and sizes, cuts each pending
+// job's frequencies into chunks of kFbChunk and takes chunks in job order
+// from the group's counter gctr[2]; the CTA that finishes a job's last chunk
+// ranks its records.  Nothing pending: every CTA returns after the flags.
+template <int LT>
+__device__ void fallback_dynamic(const Launch &ln, PlanDev &P, Job &J, uint32_t cap, unsigned long long *smem) {
+    __shared__ uint32_t s_pre[kDynMaxJobs + 1];  // chunk prefix over the group's jobs
+    __shared__ uint32_t s_wsum[kThreads / 32], s_tot, s_c, s_cnt;
+    __shared__ int s_last, s_any;
+    uint32_t *gc = ln.gctr + 2;
+    // jobs the estimate flagged (gctr[4]): none, the common case, ends every CTA here
+    if (threadIdx.x == 0) s_any = __ldcg(ln.gctr + 4) != 0;
+    __syncthreads();
+    if (!s_any) return;
+    const uint32_t j0 = __ldg(ln.map + ln.cta0), j1 = __ldg(ln.map + ln.cta0 + gridDim.x - 1) + 1;
+    const uint32_t nj = j1 - j0;
+    constexpr uint32_t kPer = kDynMaxJobs / kThreads;
+    uint32_t nch[kPer];
+    uint32_t mych = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; ++q) {
+        const uint32_t k = threadIdx.x * kPer + q;
+        nch[q] = 0;
+        if (k < nj) {
+            const char *pd = reinterpret_cast<const char *>(ln.jobs[j0 + k].p);
+            const uint32_t *ctr = *reinterpret_cast<uint32_t *const *>(pd + offsetof(PlanDev, ctr));
+            const uint32_t N = *reinterpret_cast<const uint32_t *>(pd + offsetof(PlanDev, N));
+            if (__ldcg(ctr + kFbPend)) nch[q] = (N + kFbChunk - 1) / kFbChunk;
+        }
+        mych += nch[q];
+    }
+    const uint32_t incl = block_incl_scan(mych, s_wsum);
+    uint32_t run = incl - mych;
+    if (threadIdx.x == 0) s_pre[0] = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; ++q) {
+        const uint32_t k = threadIdx.x * kPer + q;
+        if (k < nj) {
+            run += nch[q];
+            s_pre[k + 1] = run;
+        }
+    }
+    if (threadIdx.x == kThreads - 1) s_tot = incl;
+    __syncthreads();
+    const uint32_t total = s_tot;
+    if (total == 0) return;  // (uniform: no job of the group is pending)
+    uint32_t nxt = 0;  // thread 0: the next chunk's ticket
+    if (threadIdx.x == 0) nxt = atomicAdd(gc, 1u);
+    uint32_t cur = 0xFFFFFFFFu;
+    for (;;) {
+        if (threadIdx.x == 0) s_c = nxt;
+        __syncthreads();
+        const uint32_t c = s_c;
+        if (c >= total) break;
+        if (threadIdx.x == 0) nxt = atomicAdd(gc, 1u);  // (in flight while this chunk runs)
+        // the chunk's job: the last jr with s_pre[jr] <= c (jobs without chunks have s_pre[jr] == s_pre[jr + 1])
+        uint32_t lo = 0, hi = nj;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_pre[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t jr = lo, cj = c - s_pre[jr], jn = s_pre[jr + 1] - s_pre[jr];
+        if (jr != cur) {
+            __syncthreads();
+            if (threadIdx.x == 0) J = ln.jobs[j0 + jr];
+            __syncthreads();
+            load_plan(P, J.p);
+            __syncthreads();
+            cur = jr;
+        }
+        const uint32_t f0 = cj * kFbChunk, f1 = min(P.N, f0 + kFbChunk);
+        fallback_share<LT>(P, f0, f1, &s_cnt);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(P.ctr + kFbDone, 1u) == jn - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const uint32_t S = __ldcg(P.ctr + kNRec2), kout = min(P.K, __ldcg(P.ctr + kNCand));
+            rank_records(P, J, smem, cap, S, kout);
+            __syncthreads();
+            if (threadIdx.x == 0) P.ctr[kFbDone] = 0;
+        }
+    }
+    if (threadIdx.x == 0 && atomicAdd(gc + 1, 1u) == gridDim.x - 1) {
+        gc[0] = 0;  // every CTA has taken its last ticket: re-arm for the next launch
+        gc[1] = 0;
+        ln.gctr[4] = 0;
+        __threadfence();
+    }
+}
 
 // Unpruned fallback pass, fallback_ctas(N) CTAs per job: a CTA of a job with
 // no pending fallback returns after reading one flag; otherwise it records
 // the candidates of its share of the frequencies, and the job's last CTA to
 // finish (atomic ticket after a fence) ranks them (top K of every candidate).
+// Batch groups with ln.gctr share the pending jobs' chunks dynamically
+// instead (fallback_dynamic).
 template <int LT>
 __global__ void __launch_bounds__(kThreads) k_fallback(Launch ln, uint32_t cap) {
     extern __shared__ unsigned long long fb_topk[];
@@ -1319,6 +1425,10 @@ __global__ void __launch_bounds__(kThreads) k_fallback(Launch ln, uint32_t cap) 
     __shared__ uint32_t s_local, s_cnt;
     __shared__ int s_go, s_last;
     grid_dep_wait();  // (the flag and records come from the estimate kernel)
+    if (ln.gctr) {
+        fallback_dynamic<LT>(ln, P, J, cap, fb_topk);
+        return;
+    }
     if (threadIdx.x == 0) {
         Job j;
         uint32_t loc;

@@ -146,8 +146,9 @@ struct Launch {
     const uint32_t *map;    // [total CTAs] job of each CTA (batch only)
     int njobs;
     uint32_t cta0;          // batch: CTA of the map that this launch's block 0 is (a group's first)
-    uint32_t *gctr;         // batch estimate of a group: {next chunk, finished CTAs}, zero between
-                            // launches (dynamic survivor chunks; nullptr: static shares)
+    uint32_t *gctr;         // batch group (estimate, fallback): 8 words, zero between launches:
+                            // the estimate's {next chunk, finished CTAs}, the fallback's, and
+                            // the count of jobs flagged for the fallback (nullptr: static shares)
     Job one;
 };
 
