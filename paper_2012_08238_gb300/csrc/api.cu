@@ -900,6 +900,7 @@ sfft_status plan_create(sfft_plan **plan, int64_t N, int32_t K, int32_t K_cap, i
     p->d = reinterpret_cast<PlanDev *>(base + lay.plan);
     P.taps = tab.taps;
     P.tw = tab.tw;
+    P.twst = tab.twst;
     P.ginv = tab.ginv;
     P.gext = tab.gext;
     P.gext64 = tab.gext64;

@@ -197,11 +197,10 @@ __device__ void cluster_tables(const PlanDev &P, uint32_t l, uint32_t kqv, const
 __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int select_only, int clustered,
                                                             const float2 *dftC, uint32_t dft_mpad,
                                                             const uint32_t *dft_err) {
-    // B values, B energies, B/2 twiddles (B <= kTwSmemMaxB), B kept bytes (clustered)
+    // B values, B energies, B kept bytes (clustered)
     extern __shared__ unsigned long long sm[];
     float2 *buf = reinterpret_cast<float2 *>(sm);
     uint32_t *en_s;
-    const float2 *tw;
     __shared__ PlanDev P;
     __shared__ Job J;
     __shared__ uint32_t s_local;
@@ -212,8 +211,11 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
 
     const uint32_t l = s_local, B = P.B, logB = P.logB;
     en_s = reinterpret_cast<uint32_t *>(buf + B);
-    float2 *tw_s = B <= kTwSmemMaxB ? reinterpret_cast<float2 *>(en_s + B) : nullptr;
-    tw = tw_s ? tw_s : P.tw;
+    // the FFT's values sit at sw(i): the low four bits XOR the top four, so the
+    // bit-reversed stores of a half-warp (top bits differing) and the
+    // butterflies' runs of consecutive indices both fall in distinct banks
+    const uint32_t swsh = logB >= 8 ? logB - 4 : 31u;
+    auto sw = [&](uint32_t i) { return swsh < 31u ? i ^ ((i >> swsh) & 15u) : i; };
     float2 *zrow = P.zhat + (size_t)l * B;
     float *erow = P.energy + (size_t)l * B;
     uint16_t *frow = P.flags + (size_t)l * B;
@@ -231,8 +233,6 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
         if (threadIdx.x == 0 && *dft_err) P.ctr[kErr] = *dft_err;  // a tensor-core wait gave up
     } else if (!select_only) {
         const uint32_t nchunk = J.nchunk;
-        if (tw_s)
-            for (uint32_t k = threadIdx.x; k < B / 2; k += blockDim.x) tw_s[k] = __ldg(P.tw + k);
         const size_t cstride = (size_t)P.L * B;
         for (uint32_t j = threadIdx.x; j < B; j += blockDim.x) {
             // chunk order, up to 8 chunk loads in flight at once
@@ -251,26 +251,29 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
                     }
                 }
             }
-            buf[__brev(j) >> (32 - logB)] = acc;
+            buf[sw(__brev(j) >> (32 - logB))] = acc;
         }
         __syncthreads();
         // iterative radix-2 decimation in time, twiddles exp(-2 pi i k / (2h))
+        // read by stage from the table whose stage h holds them at h - 1 + k
+        // (consecutive butterflies, consecutive entries)
+        const float2 *__restrict__ twst = P.twst;
         for (uint32_t hs = 0; hs < logB; ++hs) {
             const uint32_t h = 1u << hs;
             for (uint32_t bf = threadIdx.x; bf < B / 2; bf += blockDim.x) {
                 const uint32_t k = bf & (h - 1);
                 const uint32_t i0 = ((bf >> hs) << (hs + 1)) + k;
                 const uint32_t i1 = i0 + h;
-                const float2 w = tw[k << (logB - 1 - hs)];
-                const float2 a = buf[i0];
-                const float2 t = cmul(w, buf[i1]);
-                buf[i0] = make_float2(a.x + t.x, a.y + t.y);
-                buf[i1] = make_float2(a.x - t.x, a.y - t.y);
+                const float2 w = __ldg(twst + (h - 1) + k);
+                const float2 a = buf[sw(i0)];
+                const float2 t = cmul(w, buf[sw(i1)]);
+                buf[sw(i0)] = make_float2(a.x + t.x, a.y + t.y);
+                buf[sw(i1)] = make_float2(a.x - t.x, a.y - t.y);
             }
             __syncthreads();
         }
         for (uint32_t k = threadIdx.x; k < B; k += blockDim.x) {
-            const float2 z = buf[k];
+            const float2 z = buf[sw(k)];
             const float e = z.x * z.x + z.y * z.y;
             zrow[k] = z;
             erow[k] = e;
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_fft_select(Launch ln, int selec
         uint32_t eq = 0;
         for (uint32_t k = k0; k < k1; ++k) eq += en_s[k] == kth;
         uint32_t r = block_incl_scan(eq, s_wsum) - eq;  // equal keys before k0
-        uint8_t *kept_s = reinterpret_cast<uint8_t *>(tw_s + B / 2);  // clustered only
+        uint8_t *kept_s = reinterpret_cast<uint8_t *>(en_s + B);  // clustered only
         for (uint32_t k = k0; k < k1; ++k) {
             const uint32_t e = en_s[k];
             bool keep = e > kth;
@@ -1520,8 +1523,7 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
                               uint32_t cluster_L, cudaStream_t s, const float *dftC, uint32_t dft_mpad,
                               const uint32_t *dft_err) {
     if (total_ctas == 0) return cudaSuccess;
-    const int smem = (int)(max_B * (sizeof(float2) + sizeof(uint32_t)) +
-                           (max_B <= kTwSmemMaxB ? max_B / 2 * sizeof(float2) : 0) + (cluster_L ? max_B : 0));
+    const int smem = (int)(max_B * (sizeof(float2) + sizeof(uint32_t)) + (cluster_L ? max_B : 0));
     cudaError_t e = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (!cluster_L)
@@ -1543,7 +1545,7 @@ bool fft_select_cluster_ok(uint32_t L, uint32_t max_B) {
     std::lock_guard<std::mutex> lk(mu);
     if (!known[L][bb]) {
         const uint32_t qB = bb ? (uint32_t)kClusterMaxB : 1024u;
-        const int smem = (int)(qB * (sizeof(float2) + sizeof(uint32_t)) + qB / 2 * sizeof(float2) + qB);
+        const int smem = (int)(qB * (sizeof(float2) + sizeof(uint32_t)) + qB);
         bool ok = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
         if (ok && L > 8)
             ok = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;

@@ -101,6 +101,19 @@ __global__ void k_twiddle(uint32_t B, float2 *tw) {
     }
 }
 
+// The same twiddles by FFT stage: entry h - 1 + k (h = 1, 2, ..., B/2, k < h)
+// is exp(-2 pi i k / (2h)) = exp(-2 pi i (k B / 2h) / B), bit-identical to
+// k_twiddle's entry k B / 2h (the FP64 arguments are equal); a stage's
+// butterflies read consecutive entries.
+__global__ void k_twiddle_stages(uint32_t B, float2 *twst) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i + 1 < B; i += gridDim.x * blockDim.x) {
+        const uint32_t h = 1u << (31 - __clz(i + 1)), k = i + 1 - h;
+        double sn, cs;
+        sincospi(-2.0 * (double)k / (double)(2 * h), &sn, &cs);
+        twst[i] = make_float2((float)cs, (float)sn);
+    }
+}
+
 // max of non-negative doubles through their (monotone) bit patterns
 __global__ void k_max_bits(const double *v, uint32_t n, unsigned long long *out) {
     unsigned long long m = 0;
@@ -125,7 +138,7 @@ cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, 
     return cudaGetLastError();
 }
 
-cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
+cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *twst, float2 *ginv,
                         double *ginv2, float2 *gext, double2 *gext64, cudaStream_t s) {
     double *g64 = nullptr;
     cudaError_t e = cudaMallocAsync(&g64, sizeof(double) * w, s);
@@ -136,6 +149,7 @@ cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 
     k_gain<<<N / B, 256, 0, s>>>(N, B, w, g64, ginv, ginv2);
     if (gext || gext64) k_gain_ext<<<3 * (N / B), 256, 0, s>>>(N, B, w, g64, gext, gext64);
     k_twiddle<<<(B / 2 + 255) / 256, 256, 0, s>>>(B, tw);
+    if (B > 1) k_twiddle_stages<<<(B + 255) / 256, 256, 0, s>>>(B, twst);
     e = cudaGetLastError();
     cudaError_t e2 = cudaFreeAsync(g64, s);
     return e != cudaSuccess ? e : e2;

@@ -100,6 +100,7 @@ struct PlanDev {
     uint32_t sigma[kMaxL], tau[kMaxL];
     const float *taps;     // [w]
     const float2 *tw;      // [B/2] exp(-2 pi i k / B)
+    const float2 *twst;    // [B - 1] by FFT stage: exp(-2 pi i k / (2h)) at h - 1 + k, k < h
     const float2 *ginv;    // [N/B] 1 / G~(o), o + half
     const float2 *gext;    // phase encoding, refinement: [3N/B] G~(nu) for nu + 3N/2B in [0, 3N/B)
     const float2 *ctw;     // comb: [Bc/2] exp(-2 pi i k / Bc)
@@ -266,6 +267,7 @@ cudaError_t launch_flags_from_sel(const PlanDev *p, uint32_t L, const int32_t *s
 struct TableSet {
     const float *taps;      // [w]
     const float2 *tw;       // [B/2]
+    const float2 *twst;     // [B - 1] the twiddles by FFT stage (PlanDev::twst)
     const float2 *ginv;     // [N/B]
     const float2 *gext;     // [3N/B] or NULL
     const double2 *gext64;  // [3N/B] or NULL
@@ -282,7 +284,7 @@ void tables_release(const void *handle);
 // Plan-time FP64 kernels (plan.cu).
 // gext (phase-encoding plans, else NULL): G~ over three buckets around 0.
 // gext64 (residual-checking plans, else NULL): the same three buckets in FP64.
-cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *ginv,
+cudaError_t plan_tables(uint32_t N, uint32_t B, uint32_t w, float *taps, float2 *tw, float2 *twst, float2 *ginv,
                         double *ginv2, float2 *gext, double2 *gext64, cudaStream_t s);
 cudaError_t plan_max_bits(const double *v, uint32_t n, unsigned long long *out, cudaStream_t s);
 // exp(-2 pi i k / n), k < n/2 (FP64 -> FP32)

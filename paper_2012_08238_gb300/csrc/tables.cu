@@ -58,25 +58,27 @@ void drop_idle_beyond(size_t keep) {
 cudaError_t build(Entry &en) {
     const uint32_t N = en.N, B = en.B, w = en.w, NB = N / B;
     const size_t b_taps = a256(sizeof(float) * w), b_tw = a256(sizeof(float2) * (B / 2 > 0 ? B / 2 : 1)),
-                 b_ginv = a256(sizeof(float2) * NB), b_gext = en.ext ? a256(sizeof(float2) * 3 * NB) : 0,
+                 b_twst = a256(sizeof(float2) * (B > 1 ? B - 1 : 1)), b_ginv = a256(sizeof(float2) * NB), b_gext = en.ext ? a256(sizeof(float2) * 3 * NB) : 0,
                  b_gx64 = en.ext64 ? a256(sizeof(double2) * 3 * NB) : 0;
     // scratch for the build: FP64 |1/G~|^2 and its maximum
     const size_t b_g2 = a256(sizeof(double) * NB), b_max = 256;
-    const size_t keep = b_taps + b_tw + b_ginv + b_gext + b_gx64;
+    const size_t keep = b_taps + b_tw + b_twst + b_ginv + b_gext + b_gx64;
     cudaError_t e = cudaMalloc(&en.mem, keep + b_g2 + b_max);
     if (e != cudaSuccess) return e;
     char *base = static_cast<char *>(en.mem);
     float *taps = reinterpret_cast<float *>(base);
     float2 *tw = reinterpret_cast<float2 *>(base + b_taps);
-    float2 *ginv = reinterpret_cast<float2 *>(base + b_taps + b_tw);
-    float2 *gext = en.ext ? reinterpret_cast<float2 *>(base + b_taps + b_tw + b_ginv) : nullptr;
-    double2 *gx64 = en.ext64 ? reinterpret_cast<double2 *>(base + b_taps + b_tw + b_ginv + b_gext) : nullptr;
+    float2 *twst = reinterpret_cast<float2 *>(base + b_taps + b_tw);
+    float2 *ginv = reinterpret_cast<float2 *>(base + b_taps + b_tw + b_twst);
+    float2 *gext = en.ext ? reinterpret_cast<float2 *>(base + b_taps + b_tw + b_twst + b_ginv) : nullptr;
+    double2 *gx64 =
+        en.ext64 ? reinterpret_cast<double2 *>(base + b_taps + b_tw + b_twst + b_ginv + b_gext) : nullptr;
     double *g2 = reinterpret_cast<double *>(base + keep);
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(base + keep + b_g2);
     cudaStream_t s = nullptr;
     if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return e;
     unsigned long long hmax = 0;
-    e = plan_tables(N, B, w, taps, tw, ginv, g2, gext, gx64, s);
+    e = plan_tables(N, B, w, taps, tw, twst, ginv, g2, gext, gx64, s);
     if (e == cudaSuccess) e = plan_max_bits(g2, NB, mx, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hmax, mx, sizeof(hmax), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -92,6 +94,7 @@ cudaError_t build(Entry &en) {
     if ((double)gf < gmax) gf = nextafterf(gf, INFINITY);
     en.t.taps = taps;
     en.t.tw = tw;
+    en.t.twst = twst;
     en.t.ginv = ginv;
     en.t.gext = gext;
     en.t.gext64 = gx64;
