@@ -1177,7 +1177,8 @@ uint32_t variant_key(const Sizes &s) {
     const uint32_t scan = scan_uses_bits(L, s.bits) ? (s.max_B > 1024 ? s.max_B / 1024 : 0u)
                                                     : (s.max_flags <= (uint32_t)kFlagsSmemBytes ? 8u : 9u);
     const uint32_t est = (s.est_smem && (L == 8 || L == 12 || L == 16)) ? 0u : 1u;
-    const uint32_t cl = s.max_B <= (uint32_t)kClusterMaxB ? 0u : 1u;
+    // (the FFT/select's shared memory and cluster check go by the group's largest B)
+    const uint32_t cl = s.max_B <= 1024 ? 0u : s.max_B <= 4096 ? 1u : s.max_B <= 8192 ? 2u : 3u;
     const uint32_t dft = s.dft_B ? ilog2(s.dft_B) : 0u;  // tensor-core DFT groups share B
     // (stream-gather jobs sort last: their gather CTAs end the slot's map)
     return ((s.stream ? 1u : 0u) << 24) | (dft << 16) | (L << 8) | (scan << 4) | (est << 2) | cl;

@@ -1540,11 +1540,11 @@ cudaError_t launch_fft_select(const Launch &ln, uint32_t total_ctas, uint32_t ma
 bool fft_select_cluster_ok(uint32_t L, uint32_t max_B) {
     if (L < 2 || L > 16 || max_B > (uint32_t)kClusterMaxB) return false;
     static std::mutex mu;
-    static int known[17][2] = {};  // [L][B > 1024]: 0 unknown, 1 yes, 2 no
-    const int bb = max_B > 1024 ? 1 : 0;
+    static int known[17][4] = {};  // [L][B class: <= 1024, 4096, 8192, 16384]: 0 unknown, 1 yes, 2 no
+    const int bb = max_B <= 1024 ? 0 : max_B <= 4096 ? 1 : max_B <= 8192 ? 2 : 3;
     std::lock_guard<std::mutex> lk(mu);
     if (!known[L][bb]) {
-        const uint32_t qB = bb ? (uint32_t)kClusterMaxB : 1024u;
+        const uint32_t qB = bb == 0 ? 1024u : bb == 1 ? 4096u : bb == 2 ? 8192u : 16384u;
         const int smem = (int)(qB * (sizeof(float2) + sizeof(uint32_t)) + qB);
         bool ok = cudaFuncSetAttribute(k_fft_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
         if (ok && L > 8)

@@ -15,7 +15,7 @@ constexpr int kMaxB = 16384;
 constexpr int kMaxK = 16384;
 constexpr int kMaxLogN = 30;
 constexpr int kFlagsSmemBytes = 96 * 1024;
-constexpr int kClusterMaxB = 4096;     // clustered FFT/select up to this B
+constexpr int kClusterMaxB = 16384;    // clustered FFT/select up to this B (when a cluster of L fits)
 constexpr uint32_t kMethodVoting = 0;  // sFFT1.0-style voting (the default)
 constexpr uint32_t kMethodPhase = 1;   // sFFT3.0-style phase encoding, iterative framework
 constexpr uint32_t kPeSmemFound = 2048;  // phase encoding: found lists up to this size live in shared memory
