@@ -702,6 +702,34 @@ def measure_search(sfft, torch, dev, stream, args, W, sigs, xs, R=8):
     return out
 
 
+def measure_batch_sizes(sfft, torch, dev, stream, args, W, sizes=(8, 16, 32, 128, 256)):
+    """The headline's signal shape at other batch sizes (context for the
+    headline's 64): spectra/s through sfft_execute_batch (graph replay),
+    device-generated signals of the same recipe."""
+    out = []
+    for S in sizes:
+        plans = [sfft.sfft_plan_create(W.N, W.K, W.B, W.window, W.L, 7000 + s) for s in range(S)]
+        xs = [signals.make_signal_device(W.N, W.K, 7000 + s, W.snr_db, dev)[0] for s in range(S)]
+        idxs = [torch.zeros(W.K, dtype=torch.int32, device=dev) for _ in range(S)]
+        vals = [torch.zeros(W.K, dtype=torch.complex64, device=dev) for _ in range(S)]
+        kout = torch.zeros(S, dtype=torch.int32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sfft.sfft_execute_batch(plans, xs, idxs, vals, kout, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        out.append({"signals_per_step": S, "value": S / (ms / 1e3), "unit": UNIT, "ms_per_step": ms})
+        del plans, xs
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_exact(sfft, torch, dev, stream, args, S=256, R=8):
     """The exactly sparse workload (N = 2^16, K = 10, noiseless, B = 64) through
     sfft_execute_batch with the phase-encoding method and the binary and
@@ -929,6 +957,7 @@ def run_ours(args):
     del xb
 
     # ---- exactly sparse workload: phase encoding (iterative) vs voting (context)
+    batch_sizes = measure_batch_sizes(sfft, torch, dev, stream, args, W) if rank == 0 else None
     exact = measure_exact(sfft, torch, dev, stream, args) if rank == 0 else None
     comb = measure_comb(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
     mean = measure_mean(sfft, torch, dev, stream, args, W, sigs, xs) if rank == 0 else None
@@ -979,7 +1008,7 @@ def run_ours(args):
         "samples_touched": info.samples_touched, "sampling_ratio": info.samples_touched / W.N,
         "roofline": roofline, "roofline_scan": roofline_scan, "dense_fft_context": dense,
         "exactly_sparse": exact, "comb_prefilter": comb, "averaging_estimator": mean, "search_location": search,
-        "split_bf16_dft": split, "precision_sweep": sweep, "gather_modes": gmodes,
+        "split_bf16_dft": split, "precision_sweep": sweep, "gather_modes": gmodes, "batch_sizes": batch_sizes,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
