@@ -33,6 +33,9 @@ __global__ void __launch_bounds__(kThreads) k_gather(Launch ln) {
     __shared__ uint32_t s_local;
     __shared__ float2 red[kThreads];
     enter(ln, P, J, s_local);
+    // the FFT/select may be placed once every gather CTA has started (its CTAs
+    // take the slots the gather's last, partial wave leaves and wait there)
+    grid_dep_launch();
 
     const uint32_t local = s_local;
     const uint32_t tile = local % P.tiles;
