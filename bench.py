@@ -173,14 +173,16 @@ def oracle_pool(cores: int):
     return ctx.Pool(cores, initializer=_oracle_init, initargs=(WORKLOAD,))
 
 
-def time_oracle(pool, seeds) -> float:
+def time_oracle(pool, seeds):
     """Seconds the oracle needs for `seeds` on the pool's workers running in
     parallel: the largest per-worker sum of compute time (signal synthesis
-    and inter-process transfer excluded)."""
-    per = {}
+    and inter-process transfer excluded); and the median seconds of one
+    signal on one core."""
+    per, each = {}, []
     for pid, dt, _ in pool.map(_oracle_run, seeds, chunksize=1):
         per[pid] = per.get(pid, 0.0) + dt
-    return max(per.values())
+        each.append(dt)
+    return max(per.values()), float(np.median(each))
 
 
 def _slices(torch, dev, Ks):
@@ -981,9 +983,10 @@ def run_ours(args):
     if pool is not None:
         n = args.cpu_signals
         cs = seeds[:n]
-        wall = time_oracle(pool, cs)
+        wall, one = time_oracle(pool, cs)
         pool.close()
         cpu = {"value": n / wall, "unit": UNIT, "cores": min(cores, n), "kind": "oracle",
+               "single_thread_s_per_signal": one, "host_nproc": os.cpu_count(),
                "sample": f"{n} signals of the same workload (seeds {cs[0]}..{cs[-1]}), one per worker process, "
                          f"plan tables precomputed per worker"}
     elif pool is not None:
@@ -1037,7 +1040,7 @@ def run_reference(args):
         seed += per_step
     t = 0.0
     for _ in range(args.steps):
-        t += time_oracle(pool, list(range(seed, seed + per_step)))
+        t += time_oracle(pool, list(range(seed, seed + per_step)))[0]
         seed += per_step
     pool.close()
     value = per_step * args.steps / t
