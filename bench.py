@@ -268,7 +268,30 @@ def measure_batched_c3(sfft, torch, dev, stream, args):
                    "uniform on [0, 40] dB, one batch (one launch per stage); B, w, L per signal by "
                    "sfft_suggest_params; errors over every "
                    f"{args.c3_error_stride}th signal"}
-    del plans, xs
+    # the same batch with the split-BF16 tensor-core DFT where B allows it (64 <= B <= 4096)
+    k32 = kout.cpu().numpy().copy()
+    ref = [idxs[i][: k32[i]].cpu().numpy() for i in range(len(specs))]
+    sizes = [(p.info.B, p.info.w, p.info.L) for p in plans]
+    del plans
+    torch.cuda.empty_cache()
+    plans16, n16 = [], 0
+    for (N, K, snr, seed), (B, w, L) in zip(specs, sizes):
+        prec = 1 if 64 <= B <= 4096 else 0
+        n16 += prec
+        plans16.append(sfft.sfft_plan_create_ex(N, K, B, w, L, 50_000 + seed, precision=prec))
+    for _ in range(max(3, args.warmup)):
+        sfft.sfft_execute_batch(plans16, xs, idxs, vals, kout, stream)
+    torch.cuda.synchronize(dev)
+    t16, st16 = sfft.sfft_execute_batch_timed(plans16, xs, idxs, vals, kout, steps, stream)
+    k16 = kout.cpu().numpy()
+    common = sum(len(np.intersect1d(idxs[i][: k16[i]].cpu().numpy(), ref[i])) for i in range(len(specs)))
+    out["split_bf16"] = {"value": S * steps / (t16 / 1e3), "unit": UNIT, "ms_per_step": t16 / steps,
+                         "signals_on_tensor_cores": n16,
+                         "support_agreement_with_fp32": common / max(1, int(np.sum(k32))),
+                         "stage_ms_per_step": {kk: v / steps for kk, v in st16.items()},
+                         "what": "the same batch with precision 1 (split-BF16 B-point DFT) for every plan with "
+                                 "64 <= B <= 4096, the rest FP32"}
+    del plans16, xs
     torch.cuda.empty_cache()
     return out
 
