@@ -123,6 +123,33 @@ def test_host_buffer_paths_equal_device_paths():
         assert _same(r, (ihs[i].numpy()[:k], vhs[i].numpy()[:k]))
 
 
+def test_host_buffer_batches_across_signals_and_reseeds():
+    # host-buffer batches of voting plans (one with the stream gather) and of
+    # comb plans (a batch of their own method): every result equals its
+    # device-path call, across signals and a reseed.
+    voting = [(1 << 16, 10, 64, 2368, 8, 0, sfft.SFFT_METHOD_VOTING, 0),
+              (1 << 18, 40, 256, 256 * 39, 12, 1, sfft.SFFT_METHOD_VOTING, 0),
+              (1 << 17, 20, 128, 128 * 38, 12, 2, sfft.SFFT_METHOD_VOTING, sfft.SFFT_GATHER_STREAM)]
+    comb = [(1 << 16, 10, 64, 2368, 8, 3, sfft.SFFT_METHOD_COMB, 0),
+            (1 << 16, 12, 64, 2368, 8, 4, sfft.SFFT_METHOD_COMB, 0)]
+    for specs in (voting, comb):
+        plans = [sfft.sfft_plan_create_ex(N, K, B, w, L, seed, method=m, mode=mode)
+                 for N, K, B, w, L, seed, m, mode in specs]
+        for round_ in range(3):
+            if round_ == 2:
+                sfft.sfft_plan_reseed(plans[1], 77)
+                torch.cuda.synchronize()
+            sigs = [signals.make_signal(sp[0], sp[1], 40 + 10 * round_ + i, 20.0).x for i, sp in enumerate(specs)]
+            xh = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in sigs]
+            ihs = [torch.zeros(sp[1], dtype=torch.int32).pin_memory() for sp in specs]
+            vhs = [torch.zeros(sp[1], dtype=torch.complex64).pin_memory() for sp in specs]
+            khs = torch.zeros(len(specs), dtype=torch.int32).pin_memory()
+            sfft.sfft_execute_batch_host(plans, xh, ihs, vhs, khs)
+            for i, (p, x) in enumerate(zip(plans, sigs)):
+                k = int(khs[i])
+                assert _same(run_execute(p, x)[:2], (ihs[i].numpy()[:k], vhs[i].numpy()[:k])), (round_, i)
+
+
 def test_timed_batch_reports_stage_times():
     plans, xs, idxs, vals, kout, sigs = _setup(MIX)
     ref = [run_execute(p, s.x)[:2] for p, s in zip(plans, sigs)]
