@@ -110,7 +110,7 @@ def choose(results: dict):
     return best
 
 
-def tune(logNs, out_path: str, steps: int = 3, log=print):
+def tune(logNs, out_path: str, steps: int = 3, log=print, signals_max: int = 256):
     import torch
 
     dev = torch.device("cuda", 0)
@@ -127,8 +127,8 @@ def tune(logNs, out_path: str, steps: int = 3, log=print):
             if kb[0] > configs.max_K(N):
                 continue
             for sb in SNR_BANDS:
-                # enough signals for a throughput-bound batch (2^27 samples), 4..256
-                count = int(min(256, max(4, (1 << 27) // N)))
+                # enough signals for a throughput-bound batch (2^27 samples), 4..signals_max
+                count = int(min(signals_max, max(4, (1 << 27) // N)))
                 cs = ClassSet(torch, dev, n, kb, sb, count, seed=7919 * n + 131 * kb[0] + int(sb[0] + 20))
                 results = {}
                 for cand in CANDIDATES:
@@ -165,9 +165,11 @@ def main(argv=None):
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "gb300.json"))
     ap.add_argument("--logN", default="12-26", help="range of log2 N to tune, e.g. 14-22")
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--signals-max", type=int, default=256,
+                    help="most signals per class (fewer: a class measured nearer its share of a mixed batch)")
     a = ap.parse_args(argv)
     lo, hi = (int(v) for v in a.logN.split("-"))
-    tune(list(range(lo, hi + 1)), a.out, a.steps, log=lambda m: print(m, flush=True))
+    tune(list(range(lo, hi + 1)), a.out, a.steps, log=lambda m: print(m, flush=True), signals_max=a.signals_max)
 
 
 if __name__ == "__main__":
