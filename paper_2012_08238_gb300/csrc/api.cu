@@ -383,6 +383,7 @@ struct Sizes {
     uint32_t dft_B = 0;    // split-BF16 tensor-core DFT of B buckets (0: the FP32 FFT)
     bool stream = false;   // the job's a1 is the stream gather (groups: every job's)
     uint32_t stream_smem = 0;  // stream gather: largest dynamic shared memory of the jobs
+    uint64_t sum_N = 0;    // the jobs' N summed
 };
 
 Sizes plan_sizes(const sfft_plan *p) {
@@ -406,6 +407,7 @@ Sizes plan_sizes(const sfft_plan *p) {
     }
     z.comb = p->h.method == kMethodComb;
     z.max_Bc = p->h.Bc;
+    z.sum_N = p->h.N;
     z.gather = p->h.tiles * p->h.L * p->h.nchunk;
     if (p->h.gmode == kGatherStream) {
         z.stream = true;
@@ -554,9 +556,10 @@ cudaError_t launch_pipeline(const Launch *lk, const Sizes &all, const std::vecto
     if ((e = mark(3)) != cudaSuccess) return e;
     for (size_t gi = 0; gi < gs.size(); ++gi) {
         const Group &g = gs[gi];
-        // (batch groups of up to kDynMaxJobs jobs share their survivors' chunks dynamically)
+        // (batch groups of up to kDynMaxJobs jobs share their survivors' chunks
+        // dynamically; their counts and chunk sums are 32-bit: N summed < 2^31)
         Launch le = at(5, g);
-        le.gctr = gctr && g.z.jobs <= kDynMaxJobs ? gctr + 8 * gi : nullptr;
+        le.gctr = gctr && g.z.jobs <= kDynMaxJobs && g.z.sum_N < (1ull << 31) ? gctr + 8 * gi : nullptr;
         if ((e = launch_estimate(le, g.ctas[5], g.z.L_uniform, g.z.est_smem, g.z.max_K, s)) != cudaSuccess)
             return e;
         // jobs whose pruned records could not certify their top K
@@ -1162,6 +1165,7 @@ void merge_sizes(Sizes &z, const Sizes &s, bool first) {
     z.dft_B = std::max(z.dft_B, s.dft_B);
     z.stream = first ? s.stream : (z.stream && s.stream);
     z.stream_smem = std::max(z.stream_smem, s.stream_smem);
+    z.sum_N = (first ? 0 : z.sum_N) + s.sum_N;
     z.gather += s.gather;
     z.select += s.select;
     z.vote += s.vote;
